@@ -1,0 +1,243 @@
+"""ctypes binding of the plain FP64 CPU oracle (``crp_oracle.c``).
+
+TEST INFRASTRUCTURE: imported only by the tests, the smoke check and the benchmark's
+CPU-baseline leg. The product package never imports this module.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "crp_oracle.c")
+LIB = os.path.join(HERE, "liborc.so")
+
+ACTIVE, DONE, NAN, RANGE = 0, 1, 2, 3
+OK, ERR_INVALID_ARG, ERR_QUEUE_FULL = 0, -1, -4
+F64, F32, BF16, F16 = 0, 1, 2, 3
+
+CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+          "-pthread"]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with the host C compiler (no FMA contraction)."""
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
+        tmp = LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, SRC, "-lm"])
+        os.replace(tmp, LIB)
+    return LIB
+
+
+class Field(C.Structure):
+    _fields_ = [("data", C.c_void_p), ("dtype", C.c_int32), ("nx", C.c_int32),
+                ("ny", C.c_int32), ("nz", C.c_int32), ("pad_", C.c_int32),
+                ("spacing", C.c_double), ("origin", C.c_double * 3), ("scale", C.c_double)]
+
+
+class Tables(C.Structure):
+    _fields_ = [("z_max", C.c_int32), ("n_max", C.c_int32), ("n_nodes", C.c_int32),
+                ("pad_", C.c_int32), ("x0", C.c_double), ("inv_dx", C.c_double),
+                ("log10_loss", C.c_void_p), ("log10_pd", C.c_void_p),
+                ("has_loss", C.c_void_p), ("has_pd", C.c_void_p)]
+
+
+class Params(C.Structure):
+    _fields_ = [("tol", C.c_double), ("hmin", C.c_double), ("hmax", C.c_double),
+                ("dmax", C.c_double), ("seed", C.c_uint64), ("max_steps", C.c_int64),
+                ("n_threads", C.c_int32), ("pad_", C.c_int32)]
+
+
+_DBL = ["x", "y", "z", "ux", "uy", "uz", "E", "s", "hprop", "tau", "u0x", "u0y", "u0z"]
+_I32 = ["A", "Z", "n_int", "status", "grid_id"]
+_I64 = ["uid", "n_steps", "n_att"]
+
+
+class _StateC(C.Structure):
+    _fields_ = ([(n, C.c_void_p) for n in _DBL + _I32 + _I64]
+                + [("capacity", C.c_int64), ("n", C.c_int64)])
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(LIB)
+        d, p, i32, i64, u32, u64 = C.c_double, C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_uint64
+        L.orc_philox4x32_10.argtypes = [p, p, p]
+        L.orc_uniform.argtypes = [u64, u64, u32, u32]
+        L.orc_uniform.restype = d
+        L.orc_exp.argtypes = [d]
+        L.orc_exp.restype = d
+        L.orc_log.argtypes = [d]
+        L.orc_log.restype = d
+        L.orc_field_value.argtypes = [p, p, p]
+        L.orc_deriv.argtypes = [p, d, p, p]
+        L.orc_ck_attempt.argtypes = [p, d, p, p, d, p, p]
+        L.orc_error_ratio.argtypes = [p, d, d]
+        L.orc_error_ratio.restype = d
+        L.orc_rates.argtypes = [p, i32, i32, d, p, p]
+        L.orc_rates.restype = C.c_int
+        L.orc_inject.argtypes = [p, i64, i64, u64, p]
+        L.orc_inject.restype = C.c_int
+        L.orc_propagate.argtypes = [p, p, i32, p, p, p]
+        L.orc_propagate.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+class OracleField:
+    """Keeps the grid array alive next to its C descriptor."""
+
+    def __init__(self, grid: np.ndarray, spacing: float, origin=(0.0, 0.0, 0.0), scale: float = 1.0,
+                 dtype: int | None = None):
+        if dtype is None:
+            dtype = {np.dtype(np.float64): F64, np.dtype(np.float32): F32}[grid.dtype]
+        self.grid = np.ascontiguousarray(grid)
+        nx, ny, nz = self.grid.shape[:3]
+        self.c = Field(_ptr(self.grid), dtype, nx, ny, nz, 0, float(spacing),
+                       (C.c_double * 3)(*origin), float(scale))
+
+
+class OracleTables:
+    def __init__(self, t):
+        self.t = t
+        self.ll = np.ascontiguousarray(t.log10_loss, dtype=np.float64)
+        self.lp = np.ascontiguousarray(t.log10_pd, dtype=np.float64)
+        self.hl = np.ascontiguousarray(t.has_loss, dtype=np.uint8)
+        self.hp = np.ascontiguousarray(t.has_pd, dtype=np.uint8)
+        self.c = Tables(t.z_max, t.n_max, t.n_nodes, 0, t.x0, t.inv_dx, _ptr(self.ll),
+                        _ptr(self.lp), _ptr(self.hl), _ptr(self.hp))
+
+
+class OracleState:
+    """Structure-of-arrays particle state with `capacity` slots."""
+
+    def __init__(self, capacity: int):
+        self.capacity = int(capacity)
+        for n in _DBL:
+            setattr(self, n, np.zeros(self.capacity, dtype=np.float64))
+        for n in _I32:
+            setattr(self, n, np.zeros(self.capacity, dtype=np.int32))
+        for n in _I64:
+            setattr(self, n, np.zeros(self.capacity, dtype=np.int64))
+        self.c = _StateC(*[_ptr(getattr(self, n)) for n in _DBL + _I32 + _I64], self.capacity, 0)
+
+    @property
+    def n(self) -> int:
+        return int(self.c.n)
+
+    def grow(self, capacity: int) -> None:
+        """Copy into larger arrays (used to resume after a full secondary queue)."""
+        old = self.n
+        for n in _DBL + _I32 + _I64:
+            a = getattr(self, n)
+            b = np.zeros(capacity, dtype=a.dtype)
+            b[:old] = a[:old]
+            setattr(self, n, b)
+        self.capacity = int(capacity)
+        self.c = _StateC(*[_ptr(getattr(self, n)) for n in _DBL + _I32 + _I64], self.capacity, old)
+
+    def load(self, p, first: int = 0) -> None:
+        n = len(p)
+        sl = slice(first, first + n)
+        self.x[sl], self.y[sl], self.z[sl] = p.x[:, 0], p.x[:, 1], p.x[:, 2]
+        self.ux[sl], self.uy[sl], self.uz[sl] = p.u[:, 0], p.u[:, 1], p.u[:, 2]
+        self.E[sl] = p.E
+        self.A[sl] = p.A
+        self.Z[sl] = p.Z
+        self.uid[sl] = p.uid
+        self.grid_id[sl] = p.grid_id
+
+    def snapshot(self) -> dict:
+        n = self.n
+        return {k: getattr(self, k)[:n].copy() for k in _DBL + _I32 + _I64}
+
+
+def inject(state: OracleState, particles, seed: int, tables: OracleTables | None = None,
+           first: int = 0) -> None:
+    state.load(particles, first)
+    rc = lib().orc_inject(C.byref(state.c), first, len(particles), seed,
+                          C.byref(tables.c) if tables else None)
+    if rc != OK:
+        raise ValueError(f"orc_inject failed: {rc}")
+
+
+def propagate(state: OracleState, fields, tables: OracleTables | None, tol: float, hmin: float,
+              hmax: float, dmax: float, seed: int = 1, max_steps: int = 0, n_threads: int = 0):
+    """Returns (rc, stats dict)."""
+    if n_threads <= 0:
+        n_threads = os.cpu_count() or 1
+    arr = (Field * len(fields))(*[f.c for f in fields])
+    prm = Params(tol, hmin, hmax, dmax, seed, max_steps, n_threads, 0)
+    stats = np.zeros(4, dtype=np.int64)
+    rc = lib().orc_propagate(C.byref(state.c), arr, len(fields),
+                             C.byref(tables.c) if tables else None, C.byref(prm), _ptr(stats))
+    return rc, dict(accepted=int(stats[0]), attempted=int(stats[1]), finished=int(stats[2]),
+                    secondaries=int(stats[3]))
+
+
+# ---- small helpers used by the pins -----------------------------------------------------
+def field_value(field: OracleField, x) -> np.ndarray:
+    xa = np.ascontiguousarray(x, dtype=np.float64)
+    B = np.zeros(3)
+    lib().orc_field_value(C.byref(field.c), _ptr(xa), _ptr(B))
+    return B
+
+
+def deriv(field: OracleField, kappa: float, y) -> np.ndarray:
+    ya = np.ascontiguousarray(y, dtype=np.float64)
+    k = np.zeros(6)
+    lib().orc_deriv(C.byref(field.c), kappa, _ptr(ya), _ptr(k))
+    return k
+
+
+def ck_attempt(field: OracleField, kappa: float, y, h: float):
+    ya = np.ascontiguousarray(y, dtype=np.float64)
+    k1 = deriv(field, kappa, ya)
+    y5 = np.zeros(6)
+    err = np.zeros(6)
+    lib().orc_ck_attempt(C.byref(field.c), kappa, _ptr(ya), _ptr(k1), h, _ptr(y5), _ptr(err))
+    return y5, err
+
+
+def error_ratio(err, h: float, tol: float) -> float:
+    e = np.ascontiguousarray(err, dtype=np.float64)
+    return lib().orc_error_ratio(_ptr(e), h, tol)
+
+
+def rates(tables: OracleTables, A: int, Z: int, E: float):
+    rl = C.c_double()
+    rp = C.c_double()
+    rc = lib().orc_rates(C.byref(tables.c), A, Z, E, C.byref(rl), C.byref(rp))
+    return rc, rl.value, rp.value
+
+
+def philox(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    o = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox4x32_10(_ptr(c), _ptr(k), _ptr(o))
+    return o
+
+
+def uniform(seed: int, uid: int, k: int, tag: int) -> float:
+    return lib().orc_uniform(seed, uid, k, tag)
+
+
+def exp(x: float) -> float:
+    return lib().orc_exp(x)
+
+
+def log(x: float) -> float:
+    return lib().orc_log(x)

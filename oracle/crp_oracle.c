@@ -1,0 +1,557 @@
+/*
+ * crp_oracle.c -- plain FP64 CPU oracle for the 3D-mode propagation hot path of
+ * "Cosmic ray propagation with CRPropa 3" (arXiv:1410.5323).
+ *
+ * TEST INFRASTRUCTURE: the slow, obviously correct reference the GPU path is checked
+ * against. Only the tests, the smoke check and the benchmark's CPU-baseline leg use it.
+ * It shares no code, header or constant generator with the product library.
+ *
+ * Build: cc -O2 -ffp-contract=off -fPIC -shared -pthread (no fused multiply-add, no
+ * reassociation, so every FP64 operation is one IEEE-rounded operation in the order
+ * written here).
+ *
+ * What each part follows (the paper gives the method qualitatively; the numerical
+ * readings below are the ones stated in the design notes of this project):
+ *   - per-step module sequence: propagation -> continuous loss -> interaction -> observer
+ *     (Sec. 3.1, modular layout; modules called in turn until the particle is done);
+ *   - step-size bidding, smallest bid wins (Sec. 3.1);
+ *   - 3D deflection of charged nuclei in a gridded field (Sec. 2, Sec. 3.2 regular grids);
+ *     equation of motion: ultra-relativistic Lorentz force in path length s,
+ *     dx/ds = u, du/ds = (Z c / E) u x B;
+ *   - integrator: Cash & Karp (1990) embedded RK4(5), 5th-order solution propagated;
+ *   - continuous energy loss and photo-disintegration with nucleon secondaries (Sec. 2),
+ *     from tabulated rates, sampled with Philox4x32-10 (Salmon et al. 2011).
+ * parity unpinned: full turbulent-field trajectories (the paper prints none); they are
+ * held by closed-form sub-cases and invariants in the tests.
+ */
+#include "crp_oracle.h"
+
+#include <math.h>
+#include <pthread.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---- physical constants (readings; the paper states none) ---------------------- */
+static const double C_LIGHT = 299792458.0;       /* m/s */
+static const double MP_C2_EV = 938272088.16;     /* proton rest energy, eV (CODATA 2018) */
+
+/* ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11, Sec. 5) ---------------- */
+/* One round: two 32x32->64 multiplications, the high halves xored with the other
+ * counter words and the round key, the words permuted. The key is bumped by the
+ * Weyl constants (golden ratio, sqrt(3)-1) between rounds. */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)p1;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)p0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Uniform in the open interval (0,1) from counter (uid_lo, uid_hi, k, tag), key = seed:
+ * 52 random bits m = (w0 << 20) | (w1 >> 12), U = (m + 1/2) * 2^-52 (exact in FP64). */
+double orc_uniform(uint64_t seed, uint64_t uid, uint32_t k, uint32_t tag)
+{
+    uint32_t ctr[4] = {(uint32_t)uid, (uint32_t)(uid >> 32), k, tag};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t w[4];
+    orc_philox4x32_10(ctr, key, w);
+    uint64_t m = ((uint64_t)w[0] << 20) | (uint64_t)(w[1] >> 12);
+    return ((double)m + 0.5) * 0x1p-52;
+}
+
+/* Photo-disintegration nucleon choice: the removed nucleon is a proton iff
+ * (w0 mod A) < Z for the Philox word w0 of counter (uid, k, tag 1). */
+static int nucleon_is_proton(uint64_t seed, uint64_t uid, uint32_t k, int32_t A, int32_t Z)
+{
+    uint32_t ctr[4] = {(uint32_t)uid, (uint32_t)(uid >> 32), k, 1u};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t w[4];
+    orc_philox4x32_10(ctr, key, w);
+    return (int32_t)(w[0] % (uint32_t)A) < Z;
+}
+
+/* ---- exp and log, evaluated by one stated algorithm ------------------------------
+ * Cody & Waite (1980) argument reduction with ln 2 split into a 32-bit head (so that
+ * n*head is exact) and a tail; the reduced argument goes through a truncated series.
+ * Accuracy is pinned against the C library in the tests (<= 2 ulp). */
+static const double LN2_HI = 0x1.62e42feep-1;           /* ln 2 truncated to 32 bits */
+static const double LN2_LO = 0x1.a39ef35793c76p-33;     /* ln 2 - LN2_HI */
+static const double INV_LN2 = 0x1.71547652b82fep+0;     /* 1/ln 2 */
+static const double SQRT_HALF = 0x1.6a09e667f3bcdp-1;   /* sqrt(1/2) */
+static const double LN10 = 0x1.26bb1bbb55516p+1;        /* ln 10 */
+static const double INV_LN10 = 0.4342944819032518;      /* 1/ln 10 */
+
+/* exp(x) = 2^n exp(r), x = n ln2 + r, |r| <= ln2/2; exp(r) by its Taylor series through
+ * r^14/14! (truncation below 2^-60 on that interval), Horner order. */
+double orc_exp(double x)
+{
+    if (x != x) return x;
+    if (x > 709.782712893384) return INFINITY;
+    if (x < -745.1332191019412) return 0.0;
+    double n = floor(x * INV_LN2 + 0.5);
+    double r = (x - n * LN2_HI) - n * LN2_LO;
+    double p = 1.0 / 87178291200.0;         /* 1/14! */
+    p = p * r + 1.0 / 6227020800.0;          /* 1/13! */
+    p = p * r + 1.0 / 479001600.0;           /* 1/12! */
+    p = p * r + 1.0 / 39916800.0;            /* 1/11! */
+    p = p * r + 1.0 / 3628800.0;             /* 1/10! */
+    p = p * r + 1.0 / 362880.0;              /* 1/9!  */
+    p = p * r + 1.0 / 40320.0;               /* 1/8!  */
+    p = p * r + 1.0 / 5040.0;                /* 1/7!  */
+    p = p * r + 1.0 / 720.0;                 /* 1/6!  */
+    p = p * r + 1.0 / 120.0;                 /* 1/5!  */
+    p = p * r + 1.0 / 24.0;                  /* 1/4!  */
+    p = p * r + 1.0 / 6.0;                   /* 1/3!  */
+    p = p * r + 0.5;                         /* 1/2!  */
+    p = p * r + 1.0;                         /* 1/1!  */
+    p = p * r + 1.0;                         /* 1/0!  */
+    return ldexp(p, (int)n);
+}
+
+/* log(x) = e ln2 + log(m), x = m 2^e with m in [sqrt(1/2), sqrt(2));
+ * log(m) = 2 atanh(s), s = (m-1)/(m+1), |s| <= 0.1716, series through s^23/23. */
+double orc_log(double x)
+{
+    if (x != x) return x;
+    if (x < 0.0) return NAN;
+    if (x == 0.0) return -INFINITY;
+    if (isinf(x)) return INFINITY;
+    int e;
+    double m = frexp(x, &e);
+    if (m < SQRT_HALF) {
+        m = m * 2.0;
+        e = e - 1;
+    }
+    double s = (m - 1.0) / (m + 1.0);
+    double s2 = s * s;
+    double p = 1.0 / 23.0;
+    p = p * s2 + 1.0 / 21.0;
+    p = p * s2 + 1.0 / 19.0;
+    p = p * s2 + 1.0 / 17.0;
+    p = p * s2 + 1.0 / 15.0;
+    p = p * s2 + 1.0 / 13.0;
+    p = p * s2 + 1.0 / 11.0;
+    p = p * s2 + 1.0 / 9.0;
+    p = p * s2 + 1.0 / 7.0;
+    p = p * s2 + 1.0 / 5.0;
+    p = p * s2 + 1.0 / 3.0;
+    double t = s2 * p;                       /* s^2/3 + s^4/5 + ... */
+    double log_m = 2.0 * s + 2.0 * s * t;
+    double de = (double)e;
+    return de * LN2_HI + (de * LN2_LO + log_m);
+}
+
+/* ---- field lookup: trilinear interpolation on a periodic regular grid (Sec. 3.2) --- */
+static double bf16_to_double(uint16_t b)
+{
+    uint32_t u = (uint32_t)b << 16;
+    float f;
+    memcpy(&f, &u, 4);
+    return (double)f;
+}
+
+static double f16_to_double(uint16_t h)
+{
+    int sign = (h >> 15) & 1;
+    int ex = (h >> 10) & 0x1f;
+    int man = h & 0x3ff;
+    double v;
+    if (ex == 0) v = ldexp((double)man, -24);                       /* subnormal / zero */
+    else if (ex == 31) v = man ? NAN : INFINITY;
+    else v = ldexp((double)(man + 1024), ex - 25);
+    return sign ? -v : v;
+}
+
+static double grid_at(const orc_field* f, int64_t i, int64_t j, int64_t k, int c)
+{
+    int64_t idx = ((i * f->ny + j) * f->nz + k) * 3 + c;
+    switch (f->dtype) {
+    case ORC_F64: return ((const double*)f->data)[idx];
+    case ORC_F32: return (double)((const float*)f->data)[idx];
+    case ORC_BF16: return bf16_to_double(((const uint16_t*)f->data)[idx]) * f->scale;
+    default: return f16_to_double(((const uint16_t*)f->data)[idx]) * f->scale;
+    }
+}
+
+/* Fractional index r = (x - origin) * (1/spacing); cell i0 = floor(r) wrapped modulo n;
+ * weights (1 - f, f) with f = r - floor(r). B is the sum over the 8 cell corners, taken
+ * in the order (a,b,c) = 000, 001, 010, ..., 111, of ((w_x,a * w_y,b) * w_z,c) * B_corner. */
+void orc_field_value(const orc_field* f, const double x[3], double B[3])
+{
+    double inv = 1.0 / f->spacing;
+    int64_t dims[3] = {f->nx, f->ny, f->nz};
+    int64_t idx[3][2];
+    double w[3][2];
+    for (int a = 0; a < 3; ++a) {
+        double r = (x[a] - f->origin[a]) * inv;
+        double fl = floor(r);
+        double fr = r - fl;
+        int64_t i = (int64_t)fl;
+        int64_t n = dims[a];
+        int64_t i0 = ((i % n) + n) % n;
+        idx[a][0] = i0;
+        idx[a][1] = (i0 + 1) % n;
+        w[a][0] = 1.0 - fr;
+        w[a][1] = fr;
+    }
+    B[0] = 0.0; B[1] = 0.0; B[2] = 0.0;
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            for (int c = 0; c < 2; ++c) {
+                double wt = (w[0][a] * w[1][b]) * w[2][c];
+                for (int q = 0; q < 3; ++q)
+                    B[q] = B[q] + wt * grid_at(f, idx[0][a], idx[1][b], idx[2][c], q);
+            }
+}
+
+/* ---- equation of motion (Sec. 2, 3D deflections) -------------------------------- */
+/* y = (x, u); f(y) = (u, kappa u x B(x)), kappa = Z c / E (1/(T m)). */
+void orc_deriv(const orc_field* f, double kappa, const double y[6], double k[6])
+{
+    double B[3];
+    orc_field_value(f, y, B);
+    k[0] = y[3];
+    k[1] = y[4];
+    k[2] = y[5];
+    k[3] = kappa * (y[4] * B[2] - y[5] * B[1]);
+    k[4] = kappa * (y[5] * B[0] - y[3] * B[2]);
+    k[5] = kappa * (y[3] * B[1] - y[4] * B[0]);
+}
+
+/* ---- Cash & Karp (1990) embedded Runge-Kutta 4(5) tableau --------------------------- */
+static const double CK_A[6][5] = {
+    {0.0, 0.0, 0.0, 0.0, 0.0},
+    {1.0 / 5.0, 0.0, 0.0, 0.0, 0.0},
+    {3.0 / 40.0, 9.0 / 40.0, 0.0, 0.0, 0.0},
+    {3.0 / 10.0, -9.0 / 10.0, 6.0 / 5.0, 0.0, 0.0},
+    {-11.0 / 54.0, 5.0 / 2.0, -70.0 / 27.0, 35.0 / 27.0, 0.0},
+    {1631.0 / 55296.0, 175.0 / 512.0, 575.0 / 13824.0, 44275.0 / 110592.0, 253.0 / 4096.0},
+};
+/* fifth-order weights b_i */
+static const double CK_B5[6] = {37.0 / 378.0, 0.0, 250.0 / 621.0, 125.0 / 594.0, 0.0, 512.0 / 1771.0};
+/* b_i - b*_i (fifth minus embedded fourth order), each reduced to one exact rational */
+static const double CK_E[6] = {-277.0 / 64512.0, 0.0, 6925.0 / 370944.0, -6925.0 / 202752.0,
+                               -277.0 / 14336.0, 277.0 / 7084.0};
+
+/* One attempt of step h from y (k1 = f(y) given): stages y_i = y + h * sum_j a_ij k_j,
+ * sums taken left to right; y5 = y + h * sum_i b_i k_i; err = h * sum_i (b_i - b*_i) k_i. */
+void orc_ck_attempt(const orc_field* f, double kappa, const double y[6], const double k1[6],
+                    double h, double y5[6], double err[6])
+{
+    double k[6][6];
+    for (int c = 0; c < 6; ++c) k[0][c] = k1[c];
+    for (int i = 1; i < 6; ++i) {
+        double yt[6];
+        for (int c = 0; c < 6; ++c) {
+            double acc = CK_A[i][0] * k[0][c];
+            for (int j = 1; j < i; ++j) acc = acc + CK_A[i][j] * k[j][c];
+            yt[c] = y[c] + h * acc;
+        }
+        orc_deriv(f, kappa, yt, k[i]);
+    }
+    for (int c = 0; c < 6; ++c) {
+        double acc = CK_B5[0] * k[0][c];
+        for (int j = 1; j < 6; ++j) acc = acc + CK_B5[j] * k[j][c];
+        y5[c] = y[c] + h * acc;
+    }
+    for (int c = 0; c < 6; ++c) {
+        double acc = CK_E[0] * k[0][c];
+        for (int j = 1; j < 6; ++j) acc = acc + CK_E[j] * k[j][c];
+        err[c] = h * acc;
+    }
+}
+
+/* Error ratio r = max(|dx|/h, |du|) / tol with Euclidean norms ((a0^2 + a1^2) + a2^2);
+ * r = 0 for a zero-length step. Accept iff r <= 1. */
+double orc_error_ratio(const double err[6], double h, double tol)
+{
+    if (h == 0.0) return 0.0;
+    double ex = sqrt((err[0] * err[0] + err[1] * err[1]) + err[2] * err[2]) / h;
+    double eu = sqrt((err[3] * err[3] + err[4] * err[4]) + err[5] * err[5]);
+    return fmax(ex, eu) / tol;
+}
+
+/* ---- tabulated rates (Sec. 2 interactions; synthetic tables) -----------------------
+ * gamma0 = E / (A m_p c^2); x = log(gamma0) * (1/ln 10); t = (x - x0) * inv_dx clamped to
+ * [0, n_nodes-1]; j = floor(t) (at most n_nodes-2); v = T_j + (t - j)(T_{j+1} - T_j);
+ * rate = exp(v ln 10). Returns 0 or ORC_RANGE if the species is outside the table. */
+int orc_rates(const orc_tables* t, int32_t A, int32_t Z, double E, double* r_loss, double* r_pd)
+{
+    *r_loss = 0.0;
+    *r_pd = 0.0;
+    if (!t) return 0;
+    int32_t N = A - Z;
+    if (Z < 0 || N < 0 || Z > t->z_max || N > t->n_max) return ORC_RANGE;
+    int64_t sp = (int64_t)Z * (t->n_max + 1) + N;
+    double gamma0 = E / ((double)A * MP_C2_EV);
+    double x = orc_log(gamma0) * INV_LN10;
+    double tt = (x - t->x0) * t->inv_dx;
+    double tmax = (double)(t->n_nodes - 1);
+    tt = fmin(fmax(tt, 0.0), tmax);
+    int64_t j = (int64_t)floor(tt);
+    if (j > t->n_nodes - 2) j = t->n_nodes - 2;
+    double fr = tt - (double)j;
+    if (t->has_loss[sp]) {
+        const double* T = t->log10_loss + sp * t->n_nodes;
+        double v = T[j] + fr * (T[j + 1] - T[j]);
+        *r_loss = orc_exp(v * LN10);
+    }
+    if (t->has_pd[sp]) {
+        const double* T = t->log10_pd + sp * t->n_nodes;
+        double v = T[j] + fr * (T[j + 1] - T[j]);
+        *r_pd = orc_exp(v * LN10);
+    }
+    return 0;
+}
+
+/* ---- source injection (Sec. 4: isotropic emission; sampled positions/directions are
+ * inputs). Sets the per-particle bookkeeping: s = 0, no step proposal yet (+inf), first
+ * optical depth tau = -ln U(uid, k = 0, tag 0), counters 0, u0 = u. ------------------- */
+int orc_inject(orc_state* st, int64_t first, int64_t count, uint64_t seed, const orc_tables* t)
+{
+    if (!st || first < 0 || count < 0 || first + count > st->capacity) return ORC_ERR_INVALID_ARG;
+    for (int64_t i = first; i < first + count; ++i) {
+        if (st->uid[i] < 0 || st->uid[i] >= ((int64_t)1 << 32)) return ORC_ERR_INVALID_ARG;
+        if (st->A[i] < 1 || st->Z[i] < 0 || st->Z[i] > st->A[i]) return ORC_ERR_INVALID_ARG;
+        if (t && (st->Z[i] > t->z_max || st->A[i] - st->Z[i] > t->n_max)) return ORC_ERR_INVALID_ARG;
+        st->s[i] = 0.0;
+        st->hprop[i] = INFINITY;
+        st->tau[i] = -orc_log(orc_uniform(seed, (uint64_t)st->uid[i], 0u, 0u));
+        st->u0x[i] = st->ux[i];
+        st->u0y[i] = st->uy[i];
+        st->u0z[i] = st->uz[i];
+        st->n_int[i] = 0;
+        st->status[i] = ORC_ACTIVE;
+        st->n_steps[i] = 0;
+        st->n_att[i] = 0;
+    }
+    if (first + count > st->n) st->n = first + count;
+    return ORC_OK;
+}
+
+/* ---- one particle, module sequence per step (Sec. 3.1) ----------------------------- */
+typedef struct {
+    orc_state* st;
+    const orc_field* fields;
+    int32_t n_fields;
+    const orc_tables* tab;
+    const orc_params* p;
+    int64_t next;             /* next slot to process (atomic) */
+    int64_t end;
+    int64_t reserved;         /* slot counter for secondaries (atomic) */
+    int64_t accepted, attempted, finished, secondaries;   /* totals (atomic) */
+    int32_t queue_full;
+} orc_job;
+
+static double clamp(double v, double lo, double hi) { return fmin(fmax(v, lo), hi); }
+
+static void propagate_one(orc_job* job, int64_t i)
+{
+    orc_state* st = job->st;
+    const orc_params* p = job->p;
+    const orc_tables* tab = job->tab;
+    if (st->status[i] != ORC_ACTIVE) return;
+    const orc_field* fld = &job->fields[st->grid_id[i]];
+
+    double y[6] = {st->x[i], st->y[i], st->z[i], st->ux[i], st->uy[i], st->uz[i]};
+    double E = st->E[i], s = st->s[i], hprop = st->hprop[i], tau = st->tau[i];
+    int32_t A = st->A[i], Z = st->Z[i], n_int = st->n_int[i], status = ORC_ACTIVE;
+    int64_t uid = st->uid[i], n_steps = st->n_steps[i], n_att = st->n_att[i];
+    int64_t acc_total = 0, att_total = 0, taken = 0;
+
+    while (status == ORC_ACTIVE && (p->max_steps <= 0 || taken < p->max_steps)) {
+        /* rates at the start of the step (gamma0) */
+        double rl = 0.0, rpd = 0.0;
+        if (orc_rates(tab, A, Z, E, &rl, &rpd) != 0) {
+            status = ORC_RANGE;
+            break;
+        }
+        /* bids (Sec. 3.1): propagation, continuous loss, interaction, distance; lowest wins */
+        double h_prop = fmin(fmax(hprop, p->hmin), p->hmax);
+        double h_loss = rl > 0.0 ? 0.1 / rl : INFINITY;
+        double h_int = rpd > 0.0 ? fmax(tau, 0.0) / rpd : INFINITY;
+        double h_dist = p->dmax - s;
+        double h = h_prop;
+        if (h_loss < h) h = h_loss;
+        if (h_int < h) h = h_int;
+        if (h_dist < h) h = h_dist;
+        double h_first = h;
+
+        /* propagation: Cash-Karp attempts until the FP64 error ratio is <= 1 */
+        double kappa = (double)Z * C_LIGHT / E;
+        double k1[6], y5[6], err[6], r;
+        orc_deriv(fld, kappa, y, k1);
+        int rejected = 0;
+        int64_t att_step = 0;
+        for (;;) {
+            orc_ck_attempt(fld, kappa, y, k1, h, y5, err);
+            att_step += 1;
+            r = orc_error_ratio(err, h, p->tol);
+            if (r <= 1.0 || h <= p->hmin) break;
+            double shrink = clamp(0.95 * orc_exp(-0.25 * orc_log(r)), 0.1, 1.0);
+            h = fmax(h * shrink, p->hmin);
+            rejected = 1;
+        }
+        int finite = 1;
+        for (int c = 0; c < 6; ++c) finite &= isfinite(y5[c]) ? 1 : 0;
+        if (!finite) {
+            n_att += att_step;
+            att_total += att_step;
+            status = ORC_NAN;
+            break;
+        }
+
+        /* split needs a free slot: reserve it before committing the step */
+        int fires = (rpd > 0.0 && h == h_int);
+        int64_t slot = -1;
+        if (fires) {
+            slot = __atomic_fetch_add(&job->reserved, 1, __ATOMIC_RELAXED);
+            if (slot >= st->capacity) {
+                __atomic_store_n(&job->queue_full, 1, __ATOMIC_RELAXED);
+                break;      /* parked at the start of this step; resumable */
+            }
+        }
+
+        /* accept */
+        n_att += att_step;
+        att_total += att_step;
+        for (int c = 0; c < 6; ++c) y[c] = y5[c];
+        int done = (h == h_dist);
+        s = done ? p->dmax : s + h;
+        n_steps += 1;
+        acc_total += 1;
+        taken += 1;
+        double grow = (r == 0.0) ? 5.0 : clamp(0.95 * orc_exp(-0.2 * orc_log(r)), 0.2, 5.0);
+        double hnext = h * grow;
+        if (!rejected && h_first < h_prop) hnext = fmax(hnext, h_prop);
+        hprop = clamp(hnext, p->hmin, p->hmax);
+
+        /* continuous energy loss, rate at gamma0 */
+        if (rl > 0.0) E = E * orc_exp(-h * rl);
+
+        /* photo-disintegration: fires when the interaction bid was the step taken */
+        if (rpd > 0.0) {
+            if (fires) {
+                uint32_t kk = (uint32_t)(n_int + 1);
+                int proton = nucleon_is_proton(p->seed, (uint64_t)uid, kk, A, Z);
+                int32_t dz = proton ? 1 : 0;
+                double E_sec = E / (double)A;
+                double E_par = E * (double)(A - 1) / (double)A;
+                /* secondary nucleon: inherits x, u, s, u0; new uid */
+                int64_t q = slot;
+                st->x[q] = y[0]; st->y[q] = y[1]; st->z[q] = y[2];
+                st->ux[q] = y[3]; st->uy[q] = y[4]; st->uz[q] = y[5];
+                st->E[q] = E_sec;
+                st->s[q] = s;
+                st->hprop[q] = INFINITY;
+                st->u0x[q] = st->u0x[i]; st->u0y[q] = st->u0y[i]; st->u0z[q] = st->u0z[i];
+                st->A[q] = 1;
+                st->Z[q] = dz;
+                st->n_int[q] = 0;
+                st->grid_id[q] = st->grid_id[i];
+                st->uid[q] = ((int64_t)1 << 32) + uid * 64 + (int64_t)kk;
+                st->tau[q] = -orc_log(orc_uniform(p->seed, (uint64_t)st->uid[q], 0u, 0u));
+                st->n_steps[q] = 0;
+                st->n_att[q] = 0;
+                st->status[q] = done ? ORC_DONE : ORC_ACTIVE;
+                __atomic_fetch_add(&job->secondaries, 1, __ATOMIC_RELAXED);
+                if (done) __atomic_fetch_add(&job->finished, 1, __ATOMIC_RELAXED);
+                /* parent */
+                A = A - 1;
+                Z = Z - dz;
+                E = E_par;
+                n_int = (int32_t)kk;
+                tau = -orc_log(orc_uniform(p->seed, (uint64_t)uid, kk, 0u));
+            } else {
+                tau = tau - h * rpd;
+            }
+        }
+
+        /* observer: trajectory-length limit */
+        if (done) status = ORC_DONE;
+    }
+
+    st->x[i] = y[0]; st->y[i] = y[1]; st->z[i] = y[2];
+    st->ux[i] = y[3]; st->uy[i] = y[4]; st->uz[i] = y[5];
+    st->E[i] = E; st->s[i] = s; st->hprop[i] = hprop; st->tau[i] = tau;
+    st->A[i] = A; st->Z[i] = Z; st->n_int[i] = n_int; st->status[i] = status;
+    st->n_steps[i] = n_steps; st->n_att[i] = n_att;
+    __atomic_fetch_add(&job->accepted, acc_total, __ATOMIC_RELAXED);
+    __atomic_fetch_add(&job->attempted, att_total, __ATOMIC_RELAXED);
+    if (status != ORC_ACTIVE) __atomic_fetch_add(&job->finished, 1, __ATOMIC_RELAXED);
+}
+
+static void* worker(void* arg)
+{
+    orc_job* job = (orc_job*)arg;
+    for (;;) {
+        int64_t i = __atomic_fetch_add(&job->next, 1, __ATOMIC_RELAXED);
+        if (i >= job->end) break;
+        propagate_one(job, i);
+    }
+    return NULL;
+}
+
+/* Propagate every active particle until it finishes or has taken max_steps accepted
+ * steps in this call; secondaries created in the call are appended at slot n.. and
+ * propagated in the same call. Particles are independent (Sec. 3.1), so threads take
+ * them one at a time from a shared counter. stats = {accepted, attempted, finished,
+ * secondaries}. Returns ORC_ERR_QUEUE_FULL if some split found no free slot (that
+ * particle is parked at the start of the step and the call can be repeated). */
+int orc_propagate(orc_state* st, const orc_field* fields, int32_t n_fields, const orc_tables* t,
+                  const orc_params* p, int64_t stats[4])
+{
+    if (!st || !fields || n_fields < 1 || !p) return ORC_ERR_INVALID_ARG;
+    if (!(p->tol > 0.0) || !(p->hmin > 0.0) || !(p->hmax >= p->hmin) || !(p->dmax > 0.0))
+        return ORC_ERR_INVALID_ARG;
+    for (int64_t i = 0; i < st->n; ++i)
+        if (st->grid_id[i] < 0 || st->grid_id[i] >= n_fields) return ORC_ERR_INVALID_ARG;
+    orc_job job;
+    memset(&job, 0, sizeof job);
+    job.st = st;
+    job.fields = fields;
+    job.n_fields = n_fields;
+    job.tab = t;
+    job.p = p;
+    job.reserved = st->n;
+    int nt = p->n_threads > 0 ? p->n_threads : 1;
+    int64_t begin = 0;
+    while (begin < st->n) {
+        job.next = begin;
+        job.end = st->n;
+        if (nt == 1) {
+            worker(&job);
+        } else {
+            pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)nt);
+            int started = 0;
+            for (int w = 0; w < nt; ++w)
+                if (pthread_create(&th[w], NULL, worker, &job) == 0) started++;
+                else break;
+            if (started == 0) worker(&job);
+            for (int w = 0; w < started; ++w) pthread_join(th[w], NULL);
+            free(th);
+        }
+        begin = job.end;
+        st->n = job.reserved < st->capacity ? job.reserved : st->capacity;
+        job.reserved = st->n;
+    }
+    if (stats) {
+        stats[0] = job.accepted;
+        stats[1] = job.attempted;
+        stats[2] = job.finished;
+        stats[3] = job.secondaries;
+    }
+    return job.queue_full ? ORC_ERR_QUEUE_FULL : ORC_OK;
+}

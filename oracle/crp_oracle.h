@@ -1,0 +1,100 @@
+/*
+ * crp_oracle.h -- plain FP64 CPU oracle for the 3D-mode propagation hot path of
+ * "Cosmic ray propagation with CRPropa 3" (arXiv:1410.5323).
+ *
+ * TEST INFRASTRUCTURE. This library is the checker the GPU path is compared against.
+ * Only the test suite, the smoke check and the benchmark's CPU-baseline leg load it;
+ * the product library never links, loads or calls it, and it shares no code with it.
+ *
+ * Units: lengths in metres, energies in eV, magnetic field in tesla.
+ * Every function names the passage of the paper (section / equation) it follows;
+ * the paper states the method only qualitatively, so every constant not in the
+ * paper is a stated reading (Cash & Karp 1990 for the integrator, Salmon et al. 2011
+ * for Philox4x32-10, Cody & Waite 1980 for the exp/log argument reduction).
+ */
+#ifndef CRP_ORACLE_H
+#define CRP_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Particle status values (shared meaning with the product library, separate code). */
+#define ORC_ACTIVE 0
+#define ORC_DONE 1        /* reached the trajectory-length limit (observer, paper Sec. 3.1) */
+#define ORC_NAN 2         /* state became non-finite; particle stopped */
+#define ORC_RANGE 3       /* species outside the interaction tables; particle stopped */
+
+/* Return codes of orc_propagate / orc_inject. */
+#define ORC_OK 0
+#define ORC_ERR_INVALID_ARG (-1)
+#define ORC_ERR_QUEUE_FULL (-4)
+
+/* Grid storage types. */
+#define ORC_F64 0
+#define ORC_F32 1
+#define ORC_BF16 2
+#define ORC_F16 3
+
+/* Regular periodic Cartesian vector grid (paper Sec. 3.2): node (i,j,k) sits at
+ * origin + (i,j,k)*spacing and holds B at data[((i*ny + j)*nz + k)*3 + c]. */
+typedef struct {
+    const void* data;
+    int32_t dtype;
+    int32_t nx, ny, nz;
+    int32_t pad_;
+    double spacing;
+    double origin[3];
+    double scale;       /* multiplies BF16/F16 values; ignored for F32/F64 */
+} orc_field;
+
+/* Interaction tables on x = log10(Lorentz factor): node j at x0 + j/inv_dx.
+ * Species index = Z*(n_max+1) + (A-Z). Values are log10 of a rate in 1/m.
+ * has_* == 0 marks a species whose rate is identically zero. */
+typedef struct {
+    int32_t z_max, n_max, n_nodes, pad_;
+    double x0, inv_dx;
+    const double* log10_loss;   /* continuous-loss rate 1/lambda_loss  [species][n_nodes] */
+    const double* log10_pd;     /* photo-disintegration rate            [species][n_nodes] */
+    const uint8_t* has_loss;
+    const uint8_t* has_pd;
+} orc_tables;
+
+typedef struct {
+    double tol;          /* Cash-Karp error tolerance */
+    double hmin, hmax;   /* propagation step limits, m */
+    double dmax;         /* trajectory-length limit (observer), m */
+    uint64_t seed;       /* Philox key */
+    int64_t max_steps;   /* accepted steps per particle per call; <= 0: no limit */
+    int32_t n_threads;   /* <= 0: one */
+    int32_t pad_;
+} orc_params;
+
+/* Particle state, structure of arrays, `capacity` slots; slots [0, n) are in use. */
+typedef struct {
+    double *x, *y, *z, *ux, *uy, *uz, *E, *s, *hprop, *tau, *u0x, *u0y, *u0z;
+    int32_t *A, *Z, *n_int, *status, *grid_id;
+    int64_t *uid, *n_steps, *n_att;
+    int64_t capacity;
+    int64_t n;
+} orc_state;
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+double orc_uniform(uint64_t seed, uint64_t uid, uint32_t k, uint32_t tag);
+double orc_exp(double x);
+double orc_log(double x);
+void orc_field_value(const orc_field* f, const double x[3], double B[3]);
+void orc_deriv(const orc_field* f, double kappa, const double y[6], double k[6]);
+void orc_ck_attempt(const orc_field* f, double kappa, const double y[6], const double k1[6],
+                    double h, double y5[6], double err[6]);
+double orc_error_ratio(const double err[6], double h, double tol);
+int orc_rates(const orc_tables* t, int32_t A, int32_t Z, double E, double* r_loss, double* r_pd);
+int orc_inject(orc_state* st, int64_t first, int64_t count, uint64_t seed, const orc_tables* t);
+int orc_propagate(orc_state* st, const orc_field* fields, int32_t n_fields, const orc_tables* t,
+                  const orc_params* p, int64_t stats[4]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

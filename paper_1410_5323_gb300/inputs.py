@@ -1,0 +1,371 @@
+"""Seeded synthetic inputs for the 3D propagation workloads.
+
+This module produces the *inputs* both the CUDA path and the CPU oracle consume:
+turbulent field grids, interaction tables and injected particle batches. It holds
+none of the propagation arithmetic (no stepping, lookup, interpolation or sampling
+of interactions), so it can feed both sides without coupling them.
+
+Paper passages the shapes follow (arXiv:1410.5323):
+  * Sec. 4: vector field on a Cartesian grid initialised with a random turbulent
+    realisation of a Kolmogorov power spectrum (coherence ~500 kpc, 50 kpc cells);
+  * Sec. 4: sources emit isotropically with a power-law spectrum; the mixed
+    composition uses H, He-4, N-14 and Fe-56;
+  * Sec. 2: pair-production loss and photo-disintegration act on the nuclei; the
+    paper's photon-background tables are not available, so closed-form synthetic
+    tables with the same layout stand in for them.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+MPC = 3.0856775814913673e22       # m  (648000/pi au, au = 149597870700 m)
+KPC = MPC / 1000.0
+NANOGAUSS = 1e-13                  # T
+
+# Table geometry: x = log10(Lorentz factor) on [6, 14], 201 nodes, species (Z <= 26, N <= 30).
+TABLE_Z_MAX = 26
+TABLE_N_MAX = 30
+TABLE_NODES = 201
+TABLE_X0 = 6.0
+TABLE_INV_DX = 25.0               # node spacing 0.04 in log10(gamma)
+
+# Synthetic-table closed forms (constants are this project's readings).
+LOSS_L0 = 1000.0 * MPC            # loss length scale of a proton at the break
+LOSS_X_BREAK = 9.6                # log10 gamma of the loss-length minimum (node 90)
+LOSS_SLOPE_LO = -3.0              # d log10(lambda)/d log10(gamma) below the break
+LOSS_SLOPE_HI = 0.5               # ... above the break
+PD_R0 = 1.0 / (5.0 * MPC)         # Fe-56 photo-disintegration rate on the plateau (1/m)
+PD_X_THRESH = 9.0                 # log10 gamma where the plateau starts (node 75)
+PD_SLOPE_LO = 2.0                 # d log10(R)/d log10(gamma) below it
+
+SPECIES = {"H": (1, 1), "He": (4, 2), "N": (14, 7), "Fe": (56, 26)}
+
+
+# --------------------------------------------------------------------------------------
+# Kolmogorov turbulent field (Sec. 4)
+# --------------------------------------------------------------------------------------
+def _mode_integers(n: int) -> np.ndarray:
+    return np.fft.fftfreq(n, d=1.0 / n)   # 0, 1, ..., n/2-1, -n/2, ..., -1
+
+
+def kolmogorov_spectrum(n: int, lmin_cells: float, lmax_cells: float, seed: int) -> np.ndarray:
+    """Complex mode amplitudes F[nx, ny, nz, 3] of one Kolmogorov realisation (unscaled).
+
+    Active modes: integer wavevectors with n/lmax <= |k| <= n/lmin and no component on a
+    Nyquist plane (|k_i| = n/2). Each active mode gets amplitude |k|^(-11/6) (per-mode power
+    |k|^(-11/3), shell power |k|^(-5/3)), a random unit polarisation perpendicular to k (so
+    the field is divergence-free) and a uniform random phase. The spectrum is made Hermitian
+    (F(-k) = conj F(k)) so that the inverse FFT is real.
+    """
+    if n % 2:
+        raise ValueError("grid size must be even")
+    rng = np.random.Generator(np.random.PCG64(seed))
+    k1 = _mode_integers(n)
+    kx, ky, kz = np.meshgrid(k1, k1, k1, indexing="ij")
+    kk = np.sqrt(kx * kx + ky * ky + kz * kz)
+    nyq = -(n // 2)
+    active = (kk >= n / lmax_cells) & (kk <= n / lmin_cells)
+    active &= (kx != nyq) & (ky != nyq) & (kz != nyq)
+    # random polarisation, projected perpendicular to k
+    e = rng.standard_normal((n, n, n, 3))
+    phase = rng.uniform(0.0, 2.0 * np.pi, (n, n, n))
+    safe = np.where(kk > 0, kk, 1.0)
+    khat = np.stack([kx / safe, ky / safe, kz / safe], axis=-1)
+    e = e - np.sum(e * khat, axis=-1, keepdims=True) * khat
+    enorm = np.linalg.norm(e, axis=-1, keepdims=True)
+    e = e / np.where(enorm > 0, enorm, 1.0)
+    amp = np.where(active, safe ** (-11.0 / 6.0), 0.0)
+    F = (amp * np.exp(1j * phase))[..., None] * e
+    # Hermitian symmetry: keep the "positive" half, mirror the other
+    pos = (kx > 0) | ((kx == 0) & (ky > 0)) | ((kx == 0) & (ky == 0) & (kz > 0))
+    mirror = np.roll(np.flip(F, axis=(0, 1, 2)), 1, axis=(0, 1, 2))   # F[(-i) mod n]
+    F = np.where(pos[..., None], F, np.conj(mirror))
+    return F
+
+
+def kolmogorov_grid(n: int, spacing_m: float, lmin_cells: float, lmax_cells: float,
+                    brms_t: float, seed: int) -> np.ndarray:
+    """Real periodic field B[nx, ny, nz, 3] (tesla, float64) with <|B|^2> = brms^2."""
+    F = kolmogorov_spectrum(n, lmin_cells, lmax_cells, seed)
+    B = np.empty((n, n, n, 3), dtype=np.float64)
+    for c in range(3):
+        B[..., c] = np.fft.ifftn(F[..., c]).real
+    del F
+    rms = math.sqrt(float(np.mean(np.sum(B * B, axis=-1))))
+    B *= brms_t / rms
+    return B
+
+
+def kolmogorov_grid_torch(n: int, lmin_cells: float, lmax_cells: float, brms_t: float,
+                          seed: int, device: str = "cuda", out_dtype=None):
+    """Same recipe as :func:`kolmogorov_grid`, built with torch on a device, one
+    component at a time, for grids too large for host FFTs (e.g. 1024^3).
+
+    Randomness comes from a seeded torch generator on that device, so the realisation
+    differs from the numpy one for the same seed but is reproducible on one machine.
+    Returns a tensor [n, n, n, 3] of ``out_dtype`` (default float32) and the FP32 scale
+    that was applied (B = stored * 1 for float32 outputs).
+    """
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    k1 = torch.fft.fftfreq(n, d=1.0 / n, device=device, dtype=torch.float32)
+    out = torch.empty((n, n, n, 3), dtype=out_dtype or torch.float32, device=device)
+    nyq = -(n // 2)
+    # polarisation field e(k), drawn once, projected per component as needed
+    kx = k1.view(n, 1, 1)
+    ky = k1.view(1, n, 1)
+    kz = k1.view(1, 1, n)
+    kk = torch.sqrt(kx * kx + ky * ky + kz * kz)
+    active = (kk >= n / lmax_cells) & (kk <= n / lmin_cells)
+    active &= (kx != nyq) & (ky != nyq) & (kz != nyq)
+    safe = torch.where(kk > 0, kk, torch.ones_like(kk))
+    e = torch.randn((3, n, n, n), generator=g, device=device, dtype=torch.float32)
+    phase = torch.rand((n, n, n), generator=g, device=device, dtype=torch.float32) * (2 * math.pi)
+    kh = (kx / safe, ky / safe, kz / safe)
+    dot = e[0] * kh[0] + e[1] * kh[1] + e[2] * kh[2]
+    for c in range(3):
+        e[c] -= dot * kh[c]
+    del dot
+    en = torch.sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2])
+    en = torch.where(en > 0, en, torch.ones_like(en))
+    amp = torch.where(active, safe ** (-11.0 / 6.0), torch.zeros_like(safe)) / en
+    del en, kk, safe, active
+    pos = (kx > 0) | ((kx == 0) & (ky > 0)) | ((kx == 0) & (ky == 0) & (kz > 0))
+    sumsq = 0.0
+    for c in range(3):
+        Fc = torch.polar(amp * e[c], phase)
+        mirror = torch.roll(torch.flip(Fc, dims=(0, 1, 2)), shifts=(1, 1, 1), dims=(0, 1, 2))
+        Fc = torch.where(pos, Fc, torch.conj(mirror))
+        del mirror
+        Bc = torch.fft.ifftn(Fc).real
+        del Fc
+        sumsq += float(torch.sum(Bc.double() * Bc.double()))
+        out[..., c] = Bc.to(out.dtype)
+        del Bc
+    rms = math.sqrt(sumsq / n ** 3)
+    scale = brms_t / rms
+    return out, scale
+
+
+# --------------------------------------------------------------------------------------
+# Synthetic interaction tables (Sec. 2 processes; closed forms are readings)
+# --------------------------------------------------------------------------------------
+@dataclasses.dataclass
+class TableArrays:
+    z_max: int
+    n_max: int
+    n_nodes: int
+    x0: float
+    inv_dx: float
+    log10_loss: np.ndarray     # [species, n_nodes] float64, log10 of 1/lambda_loss (1/m)
+    log10_pd: np.ndarray       # [species, n_nodes] float64, log10 of the PD rate (1/m)
+    has_loss: np.ndarray       # [species] uint8
+    has_pd: np.ndarray         # [species] uint8
+
+    def species_index(self, A: int, Z: int) -> int:
+        return Z * (self.n_max + 1) + (A - Z)
+
+
+def table_nodes(n_nodes: int = TABLE_NODES, x0: float = TABLE_X0, inv_dx: float = TABLE_INV_DX):
+    return x0 + np.arange(n_nodes, dtype=np.float64) / inv_dx
+
+
+def loss_rate_closed_form(A, Z, x):
+    """1/lambda_loss (1/m) at log10 gamma = x: a broken power law in gamma with its break
+    at 10^9.6; lambda scales as A/Z^2 times 1000 Mpc at the break."""
+    A = np.asarray(A, dtype=np.float64)
+    Z = np.asarray(Z, dtype=np.float64)
+    x = np.asarray(x, dtype=np.float64)
+    slope = np.where(x < LOSS_X_BREAK, LOSS_SLOPE_LO, LOSS_SLOPE_HI)
+    lam = (A / (Z * Z)) * LOSS_L0 * np.power(10.0, slope * (x - LOSS_X_BREAK))
+    return 1.0 / lam
+
+
+def pd_rate_closed_form(A, x):
+    """Photo-disintegration rate (1/m): R0 (A/56) (gamma/10^9)^2 below 10^9, flat above."""
+    A = np.asarray(A, dtype=np.float64)
+    x = np.asarray(x, dtype=np.float64)
+    return PD_R0 * (A / 56.0) * np.power(10.0, PD_SLOPE_LO * np.minimum(x - PD_X_THRESH, 0.0))
+
+
+def synthetic_tables(z_max: int = TABLE_Z_MAX, n_max: int = TABLE_N_MAX,
+                     n_nodes: int = TABLE_NODES, x0: float = TABLE_X0,
+                     inv_dx: float = TABLE_INV_DX) -> TableArrays:
+    x = table_nodes(n_nodes, x0, inv_dx)
+    n_sp = (z_max + 1) * (n_max + 1)
+    ll = np.full((n_sp, n_nodes), -np.inf)
+    lp = np.full((n_sp, n_nodes), -np.inf)
+    hl = np.zeros(n_sp, dtype=np.uint8)
+    hp = np.zeros(n_sp, dtype=np.uint8)
+    for Z in range(z_max + 1):
+        for N in range(n_max + 1):
+            A = Z + N
+            sp = Z * (n_max + 1) + N
+            if A < 1:
+                continue
+            if Z > 0:
+                # log10 of the closed form, written as the linear function of x it is
+                slope = np.where(x < LOSS_X_BREAK, LOSS_SLOPE_LO, LOSS_SLOPE_HI)
+                ll[sp] = -(math.log10(A / (Z * Z) * LOSS_L0) + slope * (x - LOSS_X_BREAK))
+                hl[sp] = 1
+            if A > 1:
+                lp[sp] = math.log10(PD_R0 * A / 56.0) + PD_SLOPE_LO * np.minimum(x - PD_X_THRESH, 0.0)
+                hp[sp] = 1
+    return TableArrays(z_max, n_max, n_nodes, x0, inv_dx, ll, lp, hl, hp)
+
+
+def constant_rate_tables(loss_rate: float = 0.0, pd_rate: float = 0.0,
+                         z_max: int = TABLE_Z_MAX, n_max: int = TABLE_N_MAX) -> TableArrays:
+    """Tables with the same rate at every gamma (for closed-form checks: E(s) = E0 exp(-s R),
+    Poisson interaction counts)."""
+    n_sp = (z_max + 1) * (n_max + 1)
+    ll = np.full((n_sp, TABLE_NODES), -np.inf)
+    lp = np.full((n_sp, TABLE_NODES), -np.inf)
+    hl = np.zeros(n_sp, dtype=np.uint8)
+    hp = np.zeros(n_sp, dtype=np.uint8)
+    for Z in range(z_max + 1):
+        for N in range(n_max + 1):
+            A = Z + N
+            sp = Z * (n_max + 1) + N
+            if A < 1:
+                continue
+            if loss_rate > 0 and Z > 0:
+                ll[sp] = math.log10(loss_rate)
+                hl[sp] = 1
+            if pd_rate > 0 and A > 1:
+                lp[sp] = math.log10(pd_rate)
+                hp[sp] = 1
+    return TableArrays(z_max, n_max, TABLE_NODES, TABLE_X0, TABLE_INV_DX, ll, lp, hl, hp)
+
+
+# --------------------------------------------------------------------------------------
+# Particle batches (Sec. 4: isotropic point emission, power-law spectra)
+# --------------------------------------------------------------------------------------
+@dataclasses.dataclass
+class Particles:
+    x: np.ndarray      # [n, 3] float64, m
+    u: np.ndarray      # [n, 3] float64, unit direction
+    E: np.ndarray      # [n] float64, eV
+    A: np.ndarray      # [n] int32
+    Z: np.ndarray      # [n] int32
+    uid: np.ndarray    # [n] int64, < 2^32
+    grid_id: np.ndarray  # [n] int32
+
+    def __len__(self):
+        return int(self.E.shape[0])
+
+    def take(self, idx) -> "Particles":
+        return Particles(self.x[idx].copy(), self.u[idx].copy(), self.E[idx].copy(),
+                         self.A[idx].copy(), self.Z[idx].copy(), self.uid[idx].copy(),
+                         self.grid_id[idx].copy())
+
+
+def isotropic_directions(n: int, rng: np.random.Generator) -> np.ndarray:
+    w = rng.uniform(-1.0, 1.0, n)
+    phi = rng.uniform(0.0, 2.0 * np.pi, n)
+    sw = np.sqrt(1.0 - w * w)
+    return np.stack([sw * np.cos(phi), sw * np.sin(phi), w], axis=1)
+
+
+def power_law_energies(n: int, rng, e_min: float, e_max: float, index: float) -> np.ndarray:
+    """dN/dE ~ E^-index on [e_min, e_max] by inverse CDF (index != 1)."""
+    u = rng.uniform(0.0, 1.0, n)
+    g = 1.0 - index
+    return (e_min ** g + u * (e_max ** g - e_min ** g)) ** (1.0 / g)
+
+
+def log_uniform_energies(n: int, rng, e_min: float, e_max: float) -> np.ndarray:
+    return np.exp(rng.uniform(math.log(e_min), math.log(e_max), n))
+
+
+def make_particles(n: int, seed: int, species=(("H", 1.0),), energy=("fixed", 1e19),
+                   grid_ids=None, uid_offset: int = 0) -> Particles:
+    """Isotropic emission from the origin. ``species``: (name, fraction) pairs, drawn
+    by fraction; ``energy``: ("fixed", E) | ("power", e_min, e_max, index) |
+    ("loguniform", e_min, e_max)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    names = [s for s, _ in species]
+    frac = np.array([f for _, f in species], dtype=np.float64)
+    frac = frac / frac.sum()
+    pick = rng.choice(len(names), size=n, p=frac) if len(names) > 1 else np.zeros(n, dtype=np.int64)
+    A = np.array([SPECIES[names[i]][0] for i in range(len(names))], dtype=np.int32)[pick]
+    Z = np.array([SPECIES[names[i]][1] for i in range(len(names))], dtype=np.int32)[pick]
+    kind = energy[0]
+    if kind == "fixed":
+        E = np.full(n, float(energy[1]))
+    elif kind == "power":
+        E = power_law_energies(n, rng, energy[1], energy[2], energy[3])
+    elif kind == "loguniform":
+        E = log_uniform_energies(n, rng, energy[1], energy[2])
+    else:
+        raise ValueError(kind)
+    u = isotropic_directions(n, rng)
+    x = np.zeros((n, 3))
+    uid = np.arange(n, dtype=np.int64) + uid_offset
+    gid = np.zeros(n, dtype=np.int32) if grid_ids is None else np.asarray(grid_ids, dtype=np.int32)
+    return Particles(x, u, E, A, Z, uid, gid)
+
+
+# --------------------------------------------------------------------------------------
+# Workloads (sizes and parameters; synthetic stand-ins for the paper's Sec. 4 scenario)
+# --------------------------------------------------------------------------------------
+@dataclasses.dataclass
+class Workload:
+    name: str
+    n_particles: int
+    grid_n: int
+    spacing_m: float
+    lmin_cells: float
+    lmax_cells: float
+    brms_t: float
+    grid_seed: int
+    tol: float
+    hmin_m: float
+    hmax_m: float
+    dmax_m: float
+    species: tuple
+    energy: tuple
+    interactions: bool
+    n_grids: int = 1
+    particle_seed: int = 1
+    rng_seed: int = 1          # Philox key for interaction sampling
+
+
+def workload(name: str) -> Workload:
+    """The five synthetic workloads (turbulent grid, injection, propagation limits)."""
+    common = dict(spacing_m=0.25 * MPC, lmin_cells=2.0, tol=1e-4, hmin_m=1.0 * KPC,
+                  hmax_m=1.0 * MPC, grid_seed=1)
+    if name == "fp64_64cube_1k_protons":
+        return Workload(name, 1024, 64, lmax_cells=32.0, brms_t=1.0 * NANOGAUSS,
+                        dmax_m=100.0 * MPC, species=(("H", 1.0),), energy=("fixed", 1e19),
+                        interactions=False, **common)
+    if name == "fp64_256cube_1M_nuclei":
+        return Workload(name, 1_000_000, 256, lmax_cells=32.0, brms_t=1.0 * NANOGAUSS,
+                        dmax_m=500.0 * MPC,
+                        species=(("H", 0.4), ("He", 0.3), ("N", 0.2), ("Fe", 0.1)),
+                        energy=("power", 1e18, 10 ** 20.5, 2.0), interactions=True, **common)
+    if name == "mixed_1024cube_10M_pFe":
+        return Workload(name, 10_000_000, 1024, lmax_cells=256.0, brms_t=0.5 * NANOGAUSS,
+                        dmax_m=500.0 * MPC, species=(("H", 0.5), ("Fe", 0.5)),
+                        energy=("power", 1e18, 10 ** 20.5, 2.0), interactions=False, **common)
+    if name == "batched_64x128cube_12.8M_protons":
+        return Workload(name, 64 * 200_000, 128, lmax_cells=32.0, brms_t=1.0 * NANOGAUSS,
+                        dmax_m=100.0 * MPC, species=(("H", 1.0),),
+                        energy=("loguniform", 1e17, 10 ** 20.5), interactions=False,
+                        n_grids=64, **common)
+    if name == "adjoint_128cube_4k_protons":
+        return Workload(name, 4096, 128, lmax_cells=32.0, brms_t=1.0 * NANOGAUSS,
+                        dmax_m=1e6 * MPC, species=(("H", 1.0),), energy=("fixed", 10 ** 19.5),
+                        interactions=False, **common)
+    raise KeyError(name)
+
+
+def batched_brms(n_grids: int = 64, seed: int = 1, lo: float = 0.1, hi: float = 10.0) -> np.ndarray:
+    """Per-realisation B_rms (tesla), log-uniform in [lo, hi] nG."""
+    rng = np.random.Generator(np.random.PCG64(seed + 1000))
+    return np.exp(rng.uniform(math.log(lo), math.log(hi), n_grids)) * NANOGAUSS
