@@ -1,0 +1,361 @@
+#!/usr/bin/env python
+"""Benchmark: particle RK-steps/s of the 3D propagation hot path (arXiv:1410.5323, CRPropa 3).
+
+Workload (default): 10^6 nuclei (H/He-4/N-14/Fe-56 = 0.4/0.3/0.2/0.1, E^-2 on
+[1e18, 10^20.5] eV, isotropic from the origin) through a 256^3 FP32 Kolmogorov grid
+(0.25 Mpc cells, l = 2-32 cells, B_rms = 1 nG) with synthetic loss / photo-disintegration
+tables, to 500 Mpc, FP64 form. One bench step = the whole hot path over that batch:
+inject (device-resident columns) + propagate every primary and every secondary to the
+distance limit. value = accepted RK steps of all particles / device time.
+
+Prints one JSON line (rank 0). Synthetic seeded inputs; no datasets.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1410_5323_gb300 import inputs as I  # noqa: E402
+
+METRIC = "particle RK-steps/s (accepted Cash-Karp steps summed over particles / propagate time)"
+UNIT = "steps/s"
+
+# Algorithmic FP64 work of the method (counted from its formulas; each +,-,*,/,sqrt,max one
+# flop, each elementary function one flop):
+#   per attempt: 6 field evaluations x (lookup 69 + Lorentz 12) = 486, stage sums 210,
+#   5th-order update 54, error estimate 60, error norm 15, kappa 2, controller 5  -> 832
+#   per accepted step with tables: bids, gamma0, 2 table interpolations, loss, tau -> 30
+FLOP_PER_ATTEMPT = 832
+FLOP_PER_ACCEPTED_TABLES = 30
+# FP64 pipe of one GB300: 2 FP64 lanes/clk/SM x 152 SMs x 2070 MHz = 6.29e11 ops/s,
+# 1.259e12 FLOP/s counting an FMA as two (the FP64 form issues no FMA: ceiling 0.5).
+FP64_PEAK_TFLOPS = 152 * 2 * 2.070e9 * 2 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="own", choices=["own", "reference"])
+    ap.add_argument("--form", default="fp64", choices=["fp64"])
+    ap.add_argument("--workload", default="fp64_256cube_1M_nuclei")
+    ap.add_argument("--n-particles", type=int, default=0, help="override batch size (testing)")
+    ap.add_argument("--cpu-sample", type=int, default=16384, help="primaries in the oracle sample")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--block-size", type=int, default=0)
+    ap.add_argument("--cadence", type=int, default=0)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------------------
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def build_inputs(w: I.Workload, n: int, rank: int):
+    grid = I.kolmogorov_grid(w.grid_n, w.spacing_m, w.lmin_cells, w.lmax_cells, w.brms_t,
+                             w.grid_seed).astype(np.float32)
+    tables = I.synthetic_tables() if w.interactions else None
+    parts = I.make_particles(n, w.particle_seed + 7919 * rank, w.species, w.energy,
+                             uid_offset=rank * n)
+    return grid, tables, parts
+
+
+def capacity_for(parts) -> int:
+    return int(len(parts) + np.sum(parts.A.astype(np.int64) - 1))
+
+
+class ClockSampler:
+    """nvidia-smi sampling (200 ms) during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(w, grid, tables, parts, sample: int, form_desc: str):
+    """The oracle, as it stands, on a bounded sample of the same workload."""
+    import oracle as O
+
+    sub = parts.take(np.arange(min(sample, len(parts))))
+    cap = capacity_for(sub)
+    st = O.OracleState(cap)
+    ot = O.OracleTables(tables) if tables is not None else None
+    O.inject(st, sub, w.rng_seed, ot)
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    rc, stats = O.propagate(st, [O.OracleField(grid, w.spacing_m)], ot, w.tol, w.hmin_m, w.hmax_m,
+                            w.dmax_m, seed=w.rng_seed, n_threads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": stats["accepted"] / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"first {len(sub)} primaries of the same batch (+{stats['secondaries']} "
+                      f"secondaries), full {w.dmax_m / I.MPC:.0f} Mpc, {stats['accepted']} "
+                      f"accepted steps in {dt:.2f} s ({form_desc} oracle)",
+            "rc": rc}
+
+
+# ---------------------------------------------------------------------------------------
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = I.workload(args.workload)
+    n = args.n_particles or w.n_particles
+    grid, tables, parts = build_inputs(w, n, 0)
+    import oracle as O
+
+    per_step = max(1, args.cpu_sample)
+    times, steps_acc = [], []
+    for it in range(args.warmup + args.steps):
+        lo = (it * per_step) % max(1, n - per_step)
+        sub = parts.take(np.arange(lo, lo + per_step))
+        st = O.OracleState(capacity_for(sub))
+        ot = O.OracleTables(tables) if tables is not None else None
+        O.inject(st, sub, w.rng_seed, ot)
+        t0 = time.perf_counter()
+        rc, stats = O.propagate(st, [O.OracleField(grid, w.spacing_m)], ot, w.tol, w.hmin_m,
+                                w.hmax_m, w.dmax_m, seed=w.rng_seed, n_threads=os.cpu_count() or 1)
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+            steps_acc.append(stats["accepted"])
+    value = sum(steps_acc) / sum(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "batch_per_step": per_step,
+                   "note": "FP64 CPU oracle on a bounded sample of the workload per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count() or 1,
+                         "kind": "oracle",
+                         "sample": f"{per_step} primaries per step (+ secondaries), full distance"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_own(args):
+    import torch
+
+    import paper_1410_5323_gb300 as crp
+
+    ws, rank, local = dist_env()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = I.workload(args.workload)
+    n = args.n_particles or w.n_particles
+    grid, tables, parts = build_inputs(w, n, rank)
+    cap = capacity_for(parts)
+
+    field = crp.Field(grid, w.spacing_m)
+    tabs = crp.Tables(tables) if tables is not None else None
+    sim = crp.Simulation([field], tabs, seed=w.rng_seed, capacity=cap)
+    stream = torch.cuda.current_stream(dev)
+
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    cols = dict(x=(d(parts.x[:, 0]), d(parts.x[:, 1]), d(parts.x[:, 2])),
+                u=(d(parts.u[:, 0]), d(parts.u[:, 1]), d(parts.u[:, 2])),
+                E=d(parts.E), A=d(parts.A), Z=d(parts.Z), uid=d(parts.uid))
+    prm = dict(form=crp.FORM_FP64, block_size=args.block_size, cadence=args.cadence)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def one_step():
+        sim.reset()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.inject(**cols, stream=stream)
+        p0.record(stream)
+        sim.propagate(w.tol, w.hmin_m, w.hmax_m, w.dmax_m, stream=stream, **prm)
+        p1.record(stream)
+        e1.record(stream)
+        rc = sim.sync(0.0, raise_on_error=False)
+        c = sim.counts()
+        return e0.elapsed_time(e1), p0.elapsed_time(p1), c, rc
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        one_step()
+
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    step_ms, prop_ms, accepted, attempted, rcs, secondaries = [], [], 0, 0, [], 0
+    for _ in range(args.steps):
+        flush.zero_()
+        ms, pms, c, rc = one_step()
+        step_ms.append(ms)
+        prop_ms.append(pms)
+        accepted += c["accepted"]
+        attempted += c["attempted"]
+        secondaries += c["secondaries"]
+        rcs.append(rc)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+
+    total_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms, accepted, attempted], dtype=torch.float64, device=dev)
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        total_ms_max, accepted_all, attempted_all = float(mx[0]), float(t[1]), float(t[2])
+    else:
+        total_ms_max, accepted_all, attempted_all = total_ms, float(accepted), float(attempted)
+    value = accepted_all / (total_ms_max * 1e-3)
+
+    # ---- roofline of the dominant kernel (the propagate call, timed live) ----
+    prop_s = sum(prop_ms) * 1e-3
+    flops = FLOP_PER_ATTEMPT * attempted + (FLOP_PER_ACCEPTED_TABLES * accepted if tables is not None else 0)
+    achieved_tflops = flops / prop_s / 1e12
+    roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": None,
+                "kernel": "k_propagate_fp64 (2 launches per call + 4 bookkeeping kernels)",
+                "peak_source": "derived: 152 SM x 2 FP64 lanes/clk x 2070 MHz, FMA=2"}
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        hcols = dict(x=(pin(parts.x[:, 0]), pin(parts.x[:, 1]), pin(parts.x[:, 2])),
+                     u=(pin(parts.u[:, 0]), pin(parts.u[:, 1]), pin(parts.u[:, 2])),
+                     E=pin(parts.E), A=pin(parts.A), Z=pin(parts.Z), uid=pin(parts.uid))
+        h2d = sum(int(t.numel() * t.element_size()) for v in hcols.values()
+                  for t in (v if isinstance(v, tuple) else (v,)))
+        out = sim.observe_buffers(cap, pinned=True)
+        e2e_times, e2e_steps, d2h = [], 0, 0
+        for it in range(1 + args.steps):
+            sim.reset()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sim.inject(**hcols, stream=stream)
+            sim.propagate(w.tol, w.hmin_m, w.hmax_m, w.dmax_m, stream=stream, **prm)
+            sim.sync(0.0, raise_on_error=False)
+            rec = sim.observe(out=out)
+            dt = time.perf_counter() - t0
+            if it >= 1:
+                e2e_times.append(dt)
+                e2e_steps += sim.counts()["accepted"]
+                d2h = sim.observe_bytes(len(rec["uid"]))
+        e2e = {"value": e2e_steps / sum(e2e_times), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, grid, tables, parts, args.cpu_sample, "FP64")
+        cpu.pop("rc", None)
+
+    # our kernels in the timed region, per step: inject init + slot count, prepare,
+    # work-list build, 2 x (propagate + swap)
+    launches_per_step = 2 + 2 + 2 * 2
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "particles_per_gpu": n, "grid": f"{w.grid_n}^3 f32",
+                   "form": args.form, "dmax_mpc": w.dmax_m / I.MPC, "tol": w.tol,
+                   "l2": "inputs larger than L2 (grid 268 MB as float4, state 1.7 GB) and a "
+                         "256 MB flush before every step",
+                   "parallelism": f"dp{ws} (independent particle batches per GPU)"},
+        "accepted_steps_per_step": accepted_all / args.steps,
+        "attempted_steps_per_step": attempted_all / args.steps,
+        "reject_frac": 1.0 - accepted_all / max(attempted_all, 1.0),
+        "secondaries_per_step": secondaries / args.steps,
+        "sync_codes": sorted(set(rcs)),
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_own(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

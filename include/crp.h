@@ -1,0 +1,214 @@
+/*
+ * crp.h -- C ABI of the GB300 3D-mode cosmic-ray propagation library (libcrp.so).
+ *
+ * Method: "Cosmic ray propagation with CRPropa 3" (arXiv:1410.5323). The library
+ * advances batches of independent charged nuclei through a periodic gridded magnetic
+ * field; every particle runs the per-step module sequence of Sec. 3.1 (propagation
+ * with step-size bidding, continuous energy loss, photo-disintegration with nucleon
+ * secondaries, observer) with the 3D deflection of Sec. 2 on the regular grids of
+ * Sec. 3.2.
+ *
+ * Conventions for every entry point:
+ *   - Units: lengths in metres, energies in eV, magnetic field in tesla.
+ *   - Return value: CRP_OK (0) or a negative CRP_ERR_* code; crp_error_string() names
+ *     it and crp_last_error_detail() gives the last failure's text (thread-local).
+ *   - Pointers marked "host or device" are device pointers when the accompanying
+ *     is_device flag is non-zero, host pointers otherwise. The library never keeps a
+ *     caller pointer after the call returns (it copies), except where stated.
+ *   - The library owns the device memory behind every handle; the caller owns every
+ *     buffer it passes in.
+ *   - `stream` is a cudaStream_t passed as void* (NULL: the legacy default stream).
+ *     Calls taking a stream are asynchronous with respect to the host; crp_sync()
+ *     waits and turns the device status word into a return code.
+ *   - There is no CPU fallback: without a usable CUDA device every call that needs
+ *     one returns CRP_ERR_CUDA.
+ */
+#ifndef CRP_H
+#define CRP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------- */
+#define CRP_OK 0
+#define CRP_ERR_INVALID_ARG (-1)   /* bad argument; nothing was changed */
+#define CRP_ERR_OOM (-2)           /* device allocation failed */
+#define CRP_ERR_CUDA (-3)          /* a CUDA runtime call failed (no device, launch error) */
+#define CRP_ERR_QUEUE_FULL (-4)    /* a split found no free particle slot: the parent is
+                                      parked at the start of that step; grow the simulation
+                                      with crp_sim_reserve() and call crp_propagate() again */
+#define CRP_ERR_TIMEOUT (-5)       /* crp_sync() wait limit reached (work still running) */
+#define CRP_ERR_NAN_STATE (-6)     /* a particle state became non-finite; that particle was
+                                      stopped with status CRP_STATUS_NAN */
+#define CRP_ERR_TABLE_RANGE (-7)   /* a species fell outside the interaction tables; that
+                                      particle was stopped with status CRP_STATUS_RANGE */
+
+/* ---- enumerations ------------------------------------------------------------------ */
+#define CRP_DTYPE_F64 0
+#define CRP_DTYPE_F32 1
+#define CRP_DTYPE_BF16 2
+#define CRP_DTYPE_F16 3
+
+#define CRP_FORM_FP64 0     /* FP64 stages, FP64 lookups; bit-identical to the FP64 reading */
+#define CRP_FORM_MIXED 1    /* FP32 local-frame stages, FP64 position and error norm */
+
+#define CRP_STATUS_ACTIVE 0
+#define CRP_STATUS_DONE 1   /* reached the trajectory-length limit (observer) */
+#define CRP_STATUS_NAN 2
+#define CRP_STATUS_RANGE 3
+
+/* Particle-state columns for crp_read_state(). */
+#define CRP_COL_X 0         /* f64 */
+#define CRP_COL_Y 1
+#define CRP_COL_Z 2
+#define CRP_COL_UX 3
+#define CRP_COL_UY 4
+#define CRP_COL_UZ 5
+#define CRP_COL_E 6
+#define CRP_COL_S 7         /* path length travelled, m */
+#define CRP_COL_HPROP 8     /* next propagation-step proposal, m (+inf before the first step) */
+#define CRP_COL_TAU 9       /* remaining optical depth to the next photo-disintegration */
+#define CRP_COL_U0X 10
+#define CRP_COL_U0Y 11
+#define CRP_COL_U0Z 12
+#define CRP_COL_A 13        /* i32 */
+#define CRP_COL_Z_CHARGE 14 /* i32 */
+#define CRP_COL_N_INT 15    /* i32: photo-disintegrations so far */
+#define CRP_COL_STATUS 16   /* i32: CRP_STATUS_* */
+#define CRP_COL_GRID_ID 17  /* i32 */
+#define CRP_COL_UID 18      /* i64 */
+#define CRP_COL_N_STEPS 19  /* i64: accepted steps */
+#define CRP_COL_N_ATT 20    /* i64: attempted Cash-Karp steps */
+#define CRP_N_COLS 21
+
+typedef struct crp_field crp_field;
+typedef struct crp_tables crp_tables;
+typedef struct crp_sim crp_sim;
+
+/* ---- field (Sec. 3.2: regular Cartesian vector grid, periodic) ----------------------
+ * grid: [nx][ny][nz][3] B values (C order, component fastest), dtype CRP_DTYPE_*,
+ * host or device. Node (i,j,k) sits at origin_m + (i,j,k)*spacing_m; the grid repeats
+ * with period (nx,ny,nz)*spacing_m. B = value (F32/F64) or value*scale (BF16/F16).
+ * The library copies the grid into its own device layout (one float4/double4/half4
+ * per node) and keeps nothing of the caller's buffer.
+ * Errors: INVALID_ARG for NULL pointers, non-positive sizes, spacing <= 0, unknown
+ * dtype, or a grid above 2^31 nodes; OOM; CUDA. */
+int crp_field_create(const void* grid, int32_t dtype, int32_t is_device, int32_t nx,
+                     int32_t ny, int32_t nz, double spacing_m, const double origin_m[3],
+                     float scale, crp_field** out);
+int crp_field_destroy(crp_field* field);
+
+/* ---- interaction tables (Sec. 2: pair-production loss, photo-disintegration) --------
+ * Species s = Z*(n_max+1) + (A-Z), Z in [0,z_max], A-Z in [0,n_max]. Row s holds
+ * n_nodes values of log10(rate in 1/m) on x = log10(gamma) = x0 + j/inv_dx, with
+ * gamma = E/(A m_p c^2). log10_loss is the continuous-loss rate 1/lambda_loss,
+ * log10_pd the photo-disintegration rate. has_loss[s] / has_pd[s] == 0 mark
+ * identically-zero rates (the row is then ignored). All pointers are host pointers.
+ * Errors: INVALID_ARG for NULL pointers, n_nodes < 2, inv_dx <= 0, non-finite values
+ * in a flagged row; OOM; CUDA. */
+int crp_tables_create(int32_t z_max, int32_t n_max, int32_t n_nodes, double x0, double inv_dx,
+                      const double* log10_loss, const double* log10_pd,
+                      const uint8_t* has_loss, const uint8_t* has_pd, crp_tables** out);
+int crp_tables_destroy(crp_tables* tables);
+
+/* ---- simulation -----------------------------------------------------------------------
+ * fields: n_fields field handles (a particle's grid_id picks one); tables: NULL for no
+ * interactions; seed: Philox key for interaction sampling; capacity: particle slots
+ * (primaries + secondaries). The handles must outlive the simulation.
+ * Errors: INVALID_ARG (n_fields < 1, NULL field, capacity < 1 or >= 2^31); OOM; CUDA. */
+int crp_sim_create(const crp_field* const* fields, int32_t n_fields, const crp_tables* tables,
+                   uint64_t seed, int64_t capacity, crp_sim** out);
+/* Grow to `capacity` slots, keeping every particle (resumes after CRP_ERR_QUEUE_FULL).
+ * Synchronises the simulation's last stream. */
+int crp_sim_reserve(crp_sim* sim, int64_t capacity);
+int crp_sim_destroy(crp_sim* sim);
+/* Forget every particle (slots, done list, step counters, status word) and keep the
+ * allocations, fields, tables and seed; uids continue from 0 again. Synchronises. */
+int crp_sim_reset(crp_sim* sim);
+
+/* ---- source injection (Sec. 4: sources emit isotropically; positions/directions/
+ * energies come from the caller) ----------------------------------------------------------
+ * Appends n particles after the ones already present. Each needs A >= 1, 0 <= Z <= A,
+ * a species inside the tables (if any), uid < 2^32 (uid == NULL: uids continue the
+ * count of primaries injected so far), 0 <= grid_id < n_fields (grid_id == NULL: 0).
+ * The library initialises s = 0, no step proposal, the first optical depth
+ * tau = -ln U(uid, 0, tag 0) (Philox), u0 = u, counters 0, status active.
+ * Errors: INVALID_ARG (NULL columns, n < 0, capacity exceeded, an invalid particle when
+ * the columns are host pointers; with device columns invalid particles are reported by
+ * crp_sync as INVALID_ARG); CUDA. */
+typedef struct {
+    const double *x, *y, *z;
+    const double *ux, *uy, *uz;
+    const double* E;
+    const int32_t *A, *Z;
+    const int64_t* uid;        /* may be NULL */
+    const int32_t* grid_id;    /* may be NULL */
+    int32_t is_device;
+    int32_t pad_;
+} crp_particles;
+int crp_source_inject(crp_sim* sim, const crp_particles* particles, int64_t n, void* stream);
+
+/* ---- propagation (Sec. 3.1 module sequence; Sec. 2 3D deflection) ----------------------
+ * Advances every active particle until it reaches max_distance_m (status DONE), or has
+ * taken params->max_steps accepted steps in this call (stays active; a later call resumes
+ * it bit-identically), or fails (NAN / RANGE). Secondaries created in the call are
+ * propagated in the same call. Per step: bids h = min(clamp(proposal, min_step_m,
+ * max_step_m), 0.1/R_loss, tau/R_pd, max_distance_m - s); Cash-Karp RK4(5) attempts
+ * until the FP64 error ratio max(|dx|/h, |du|)/tolerance <= 1 (or h <= min_step_m);
+ * continuous loss; photo-disintegration when the interaction bid was the step; observer.
+ * Asynchronous on `stream`. Errors: INVALID_ARG (tolerance <= 0, min_step_m <= 0,
+ * max_step_m < min_step_m, max_distance_m <= 0, unknown form); CUDA (launch failure). */
+typedef struct {
+    int32_t form;            /* CRP_FORM_FP64 or CRP_FORM_MIXED */
+    int32_t block_size;      /* threads per block, multiple of 32; 0: default */
+    int32_t blocks_per_sm;   /* 0: the occupancy limit */
+    int32_t cadence;         /* attempts between refill checks; 0: default (1) */
+    int64_t max_steps;       /* accepted steps per particle per call; <= 0: no limit */
+} crp_params;
+int crp_propagate(crp_sim* sim, const crp_params* params, double tolerance, double min_step_m,
+                  double max_step_m, double max_distance_m, void* stream);
+
+/* Wait for the simulation's last stream (at most timeout_s seconds; <= 0: no limit),
+ * then return the first device-side error as a code: QUEUE_FULL, NAN_STATE,
+ * TABLE_RANGE, INVALID_ARG, or CRP_OK. Clears the reported bits. */
+int crp_sync(crp_sim* sim, double timeout_s);
+
+/* counts[8] = {slots in use, active, done, accepted steps, attempted steps, secondaries
+ * created, propagate kernel launches, device status bits}; the step counters are
+ * cumulative over the simulation. Synchronises. */
+int crp_sim_counts(crp_sim* sim, int64_t counts[8]);
+
+/* Copy `count` entries of column `column` (CRP_COL_*) starting at slot `first` into dst
+ * (host or device). Element type as listed with the CRP_COL_* values. Synchronises when
+ * dst is a host pointer. Errors: INVALID_ARG (range, column). */
+int crp_read_state(crp_sim* sim, int32_t column, void* dst, int32_t dst_is_device,
+                   int64_t first, int64_t count);
+
+/* ---- observer records (Sec. 3.1 observers) ---------------------------------------------
+ * Copies the records of particles that have finished (status != ACTIVE), in the order
+ * they finished, starting at the `first`-th finished particle, at most `capacity`
+ * records; *n_out receives the number written. Caller-allocated columns, host or device. */
+typedef struct {
+    int64_t* uid;
+    int32_t *A, *Z, *n_int, *status;
+    double *E, *x, *y, *z, *ux, *uy, *uz, *u0x, *u0y, *u0z, *s;
+    int64_t *n_steps, *n_att;
+    int32_t is_device;
+    int32_t pad_;
+} crp_observer;
+int crp_observe(crp_sim* sim, const crp_observer* out, int64_t first, int64_t capacity,
+                int64_t* n_out);
+
+const char* crp_error_string(int32_t code);
+const char* crp_last_error_detail(void);
+
+/* Library build identifier, e.g. "crp 1 sm_103a". */
+const char* crp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

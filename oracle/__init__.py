@@ -105,6 +105,8 @@ class OracleField:
             dtype = {np.dtype(np.float64): F64, np.dtype(np.float32): F32}[grid.dtype]
         self.grid = np.ascontiguousarray(grid)
         nx, ny, nz = self.grid.shape[:3]
+        if dtype in (BF16, F16):
+            scale = float(np.float32(scale))      # half-precision grids carry an FP32 scale
         self.c = Field(_ptr(self.grid), dtype, nx, ny, nz, 0, float(spacing),
                        (C.c_double * 3)(*origin), float(scale))
 

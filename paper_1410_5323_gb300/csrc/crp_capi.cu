@@ -1,0 +1,732 @@
+// crp_capi.cu -- the C ABI of libcrp.so (declared in include/crp.h): handles, argument
+// checks, device memory, and the small bookkeeping kernels around the propagate kernels
+// (grid layout, injection initialisation, work-list compaction, list swap, observer gather).
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "crp.h"
+#include "crp_internal.h"
+#include "crp_math.cuh"
+
+static_assert(CRP_STATUS_ACTIVE == crp::CRP_STATUS_ACTIVE_, "status numbering");
+static_assert(CRP_STATUS_DONE == crp::CRP_STATUS_DONE_, "status numbering");
+static_assert(CRP_STATUS_NAN == crp::CRP_STATUS_NAN_, "status numbering");
+static_assert(CRP_STATUS_RANGE == crp::CRP_STATUS_RANGE_, "status numbering");
+
+using namespace crp;
+
+namespace {
+
+thread_local std::string g_detail;
+
+int fail(int code, const std::string& msg) {
+    g_detail = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+    g_detail = std::string(where) + ": " + cudaGetErrorString(e);
+    return (e == cudaErrorMemoryAllocation) ? CRP_ERR_OOM : CRP_ERR_CUDA;
+}
+
+#define CRP_CUDA(call)                                      \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// ---- K1: grid layout (one 4-wide vector per node) --------------------------------------
+template <class In, class Out>
+__global__ void k_layout(const In* __restrict__ in, Out* __restrict__ out, long long n_nodes);
+
+template <>
+__global__ void k_layout<float, float4>(const float* __restrict__ in, float4* __restrict__ out,
+                                         long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = make_float4(in[3 * i], in[3 * i + 1], in[3 * i + 2], 0.0f);
+}
+template <>
+__global__ void k_layout<double, double2>(const double* __restrict__ in, double2* __restrict__ out,
+                                           long long n) {   // two double2 per node
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        out[2 * i] = make_double2(in[3 * i], in[3 * i + 1]);
+        out[2 * i + 1] = make_double2(in[3 * i + 2], 0.0);
+    }
+}
+template <>
+__global__ void k_layout<unsigned short, ushort4>(const unsigned short* __restrict__ in,
+                                                  ushort4* __restrict__ out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = make_ushort4(in[3 * i], in[3 * i + 1], in[3 * i + 2], 0);
+}
+
+// ---- injection: per-particle bookkeeping (Philox tau draw), validation ----------------
+__global__ void k_inject_init(SimState S, long long first, long long n, int uid_given,
+                              int gid_given, unsigned long long uid_base, int n_fields,
+                              int has_tables, int z_max, int n_max, unsigned long long seed,
+                              int32_t* done_list, Counters* C) {
+    const double INF = __longlong_as_double(0x7ff0000000000000LL);
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const long long i = first + k;
+        if (!uid_given) S.uid[i] = (long long)(uid_base + (unsigned long long)k);
+        if (!gid_given) S.grid_id[i] = 0;
+        const int A = S.A[i], Z = S.Z[i];
+        const long long uid = S.uid[i];
+        bool ok = A >= 1 && Z >= 0 && Z <= A && uid >= 0 && uid < (1ll << 32) &&
+                  S.grid_id[i] >= 0 && S.grid_id[i] < n_fields;
+        if (has_tables && (Z > z_max || A - Z > n_max)) ok = false;
+        S.s[i] = 0.0;
+        S.hprop[i] = INF;
+        S.tau[i] = -crp_log(uniform01(seed, (unsigned long long)uid, 0u, 0u));
+        S.u0x[i] = S.ux[i];
+        S.u0y[i] = S.uy[i];
+        S.u0z[i] = S.uz[i];
+        S.n_int[i] = 0;
+        S.n_steps[i] = 0;
+        S.n_att[i] = 0;
+        S.status[i] = ok ? CRP_STATUS_ACTIVE_ : CRP_STATUS_RANGE_;
+        if (!ok) {   // stopped at injection; reported by crp_sync as INVALID_ARG
+            atomicOr(&C->status_bits, BIT_INVALID);
+            const unsigned long long d = atomicAdd(&C->n_done, 1ull);
+            done_list[d] = (int32_t)i;
+        }
+    }
+}
+
+__global__ void k_set_used(Counters* C, unsigned long long n_used, unsigned long long n_prim) {
+    C->n_used = n_used;
+    C->reserve = n_used;
+    C->n_primaries = n_prim;
+}
+
+// ---- propagate bookkeeping ----------------------------------------------------------------
+__global__ void k_prepare(Counters* C) {
+    C->count[0] = 0;
+    C->count[1] = 0;
+    C->head = 0;
+    C->reserve = C->n_used;
+}
+
+// Work list 0 <- slots [0, n_used) with status ACTIVE (warp-aggregated append).
+__global__ void k_build_worklist(const int32_t* __restrict__ status, int32_t* __restrict__ list,
+                                 Counters* C) {
+    const unsigned long long n = *(volatile unsigned long long*)&C->n_used;
+    const int lane = threadIdx.x & 31;
+    for (long long base = blockIdx.x * (long long)blockDim.x; base < (long long)n;
+         base += (long long)gridDim.x * blockDim.x) {
+        const long long i = base + threadIdx.x;
+        const bool act = i < (long long)n && status[i] == CRP_STATUS_ACTIVE_;
+        const unsigned m = __ballot_sync(0xffffffffu, act);
+        if (!m) continue;
+        unsigned long long p0 = 0;
+        if (lane == 0) p0 = atomicAdd(&C->count[0], (unsigned long long)__popc(m));
+        p0 = __shfl_sync(0xffffffffu, p0, 0);
+        if (act) list[p0 + __popc(m & ((1u << lane) - 1u))] = (int32_t)i;
+    }
+}
+
+// After a propagate launch over list `from`: fix the slot count, reset the pop head and
+// the list that the next launch pushes into.
+__global__ void k_swap(Counters* C, long long capacity, int from) {
+    const unsigned long long r = C->reserve;
+    C->n_used = r < (unsigned long long)capacity ? r : (unsigned long long)capacity;
+    C->reserve = C->n_used;
+    C->head = 0;
+    C->count[from] = 0;
+    C->launches += 1;
+}
+
+// ---- observer gather ----------------------------------------------------------------------
+struct ObsCols {
+    int64_t* uid;
+    int32_t *A, *Z, *n_int, *status;
+    double *E, *x, *y, *z, *ux, *uy, *uz, *u0x, *u0y, *u0z, *s;
+    int64_t *n_steps, *n_att;
+};
+
+__global__ void k_observe(SimState S, const int32_t* __restrict__ done, long long first,
+                          long long n, ObsCols o) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int32_t i = done[first + k];
+        if (o.uid) o.uid[k] = S.uid[i];
+        if (o.A) o.A[k] = S.A[i];
+        if (o.Z) o.Z[k] = S.Z[i];
+        if (o.n_int) o.n_int[k] = S.n_int[i];
+        if (o.status) o.status[k] = S.status[i];
+        if (o.E) o.E[k] = S.E[i];
+        if (o.x) o.x[k] = S.x[i];
+        if (o.y) o.y[k] = S.y[i];
+        if (o.z) o.z[k] = S.z[i];
+        if (o.ux) o.ux[k] = S.ux[i];
+        if (o.uy) o.uy[k] = S.uy[i];
+        if (o.uz) o.uz[k] = S.uz[i];
+        if (o.u0x) o.u0x[k] = S.u0x[i];
+        if (o.u0y) o.u0y[k] = S.u0y[i];
+        if (o.u0z) o.u0z[k] = S.u0z[i];
+        if (o.s) o.s[k] = S.s[i];
+        if (o.n_steps) o.n_steps[k] = S.n_steps[i];
+        if (o.n_att) o.n_att[k] = S.n_att[i];
+    }
+}
+
+int grid_for(long long n, int block, int max_blocks) {
+    long long g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > max_blocks) g = max_blocks;
+    return (int)g;
+}
+
+int device_sms() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    return sms;
+}
+
+// Column table for SimState: element size and pointer slot.
+struct ColInfo { int size; };
+const ColInfo kCols[CRP_N_COLS] = {
+    {8}, {8}, {8}, {8}, {8}, {8}, {8}, {8}, {8}, {8}, {8}, {8}, {8},   // f64 0..12
+    {4}, {4}, {4}, {4}, {4},                                           // i32 13..17
+    {8}, {8}, {8}};                                                    // i64 18..20
+
+void** col_ptr(SimState& S, int c) {
+    void** f[CRP_N_COLS] = {(void**)&S.x, (void**)&S.y, (void**)&S.z, (void**)&S.ux,
+                            (void**)&S.uy, (void**)&S.uz, (void**)&S.E, (void**)&S.s,
+                            (void**)&S.hprop, (void**)&S.tau, (void**)&S.u0x, (void**)&S.u0y,
+                            (void**)&S.u0z, (void**)&S.A, (void**)&S.Z, (void**)&S.n_int,
+                            (void**)&S.status, (void**)&S.grid_id, (void**)&S.uid,
+                            (void**)&S.n_steps, (void**)&S.n_att};
+    return f[c];
+}
+
+}  // namespace
+
+// ---- handles ------------------------------------------------------------------------------
+struct crp_field {
+    FieldDev dev;
+    void* mem = nullptr;
+    long long nodes = 0;
+};
+
+struct crp_tables {
+    TablesDev dev;
+    void* mem = nullptr;
+};
+
+struct crp_sim {
+    std::vector<FieldDev> host_fields;
+    FieldDev* d_fields = nullptr;
+    int layout = LAYOUT_F32X4;
+    const crp_tables* tables = nullptr;
+    unsigned long long seed = 0;
+    long long capacity = 0;
+    SimState st{};
+    int32_t* lists[2] = {nullptr, nullptr};
+    int32_t* done_list = nullptr;
+    Counters* ctr = nullptr;
+    cudaStream_t last = nullptr;
+    int sms = 0;
+};
+
+namespace {
+
+void free_state(SimState& S) {
+    for (int c = 0; c < CRP_N_COLS; ++c) {
+        void** p = col_ptr(S, c);
+        if (*p) cudaFree(*p);
+        *p = nullptr;
+    }
+}
+
+int alloc_state(SimState& S, long long cap) {
+    for (int c = 0; c < CRP_N_COLS; ++c) {
+        void** p = col_ptr(S, c);
+        cudaError_t e = cudaMalloc(p, (size_t)cap * kCols[c].size);
+        if (e != cudaSuccess) {
+            free_state(S);
+            return cuda_fail(e, "cudaMalloc(state)");
+        }
+    }
+    return CRP_OK;
+}
+
+int sync_stream(crp_sim* s) {
+    cudaError_t e = cudaStreamSynchronize(s->last);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return CRP_OK;
+}
+
+int read_counters(crp_sim* s, Counters* h) {
+    int rc = sync_stream(s);
+    if (rc) return rc;
+    CRP_CUDA(cudaMemcpy(h, s->ctr, sizeof(Counters), cudaMemcpyDeviceToHost));
+    return CRP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* crp_version(void) { return "crp 1 sm_103a"; }
+
+const char* crp_error_string(int32_t code) {
+    switch (code) {
+    case CRP_OK: return "ok";
+    case CRP_ERR_INVALID_ARG: return "invalid argument";
+    case CRP_ERR_OOM: return "device allocation failed";
+    case CRP_ERR_CUDA: return "CUDA runtime error";
+    case CRP_ERR_QUEUE_FULL: return "secondary queue full (resumable after crp_sim_reserve)";
+    case CRP_ERR_TIMEOUT: return "wait limit reached";
+    case CRP_ERR_NAN_STATE: return "non-finite particle state";
+    case CRP_ERR_TABLE_RANGE: return "species outside the interaction tables";
+    default: return "unknown error";
+    }
+}
+
+const char* crp_last_error_detail(void) { return g_detail.c_str(); }
+
+int crp_field_create(const void* grid, int32_t dtype, int32_t is_device, int32_t nx, int32_t ny,
+                     int32_t nz, double spacing_m, const double origin_m[3], float scale,
+                     crp_field** out) {
+    if (!out) return fail(CRP_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!grid || !origin_m) return fail(CRP_ERR_INVALID_ARG, "grid or origin is NULL");
+    if (nx < 1 || ny < 1 || nz < 1) return fail(CRP_ERR_INVALID_ARG, "grid sizes must be >= 1");
+    const long long nodes = (long long)nx * ny * nz;
+    if (nodes >= (1ll << 31)) return fail(CRP_ERR_INVALID_ARG, "grid above 2^31 nodes");
+    if (!(spacing_m > 0.0) || !std::isfinite(spacing_m))
+        return fail(CRP_ERR_INVALID_ARG, "spacing must be finite and > 0");
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(origin_m[a])) return fail(CRP_ERR_INVALID_ARG, "origin not finite");
+    int elem, layout, out_elem;
+    switch (dtype) {
+    case CRP_DTYPE_F64: elem = 8; layout = LAYOUT_F64X4; out_elem = 32; break;
+    case CRP_DTYPE_F32: elem = 4; layout = LAYOUT_F32X4; out_elem = 16; break;
+    case CRP_DTYPE_BF16: elem = 2; layout = LAYOUT_BF16X4; out_elem = 8; break;
+    case CRP_DTYPE_F16: elem = 2; layout = LAYOUT_F16X4; out_elem = 8; break;
+    default: return fail(CRP_ERR_INVALID_ARG, "unknown dtype");
+    }
+    if ((dtype == CRP_DTYPE_BF16 || dtype == CRP_DTYPE_F16) && !(std::isfinite(scale) && scale != 0.0f))
+        return fail(CRP_ERR_INVALID_ARG, "scale must be finite and non-zero");
+    int ndev = 0;
+    CRP_CUDA(cudaGetDeviceCount(&ndev));
+    const size_t in_bytes = (size_t)nodes * 3 * elem;
+    const void* src = grid;
+    void* staging = nullptr;
+    if (!is_device) {
+        CRP_CUDA(cudaMalloc(&staging, in_bytes));
+        cudaError_t e = cudaMemcpy(staging, grid, in_bytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { cudaFree(staging); return cuda_fail(e, "cudaMemcpy(grid)"); }
+        src = staging;
+    }
+    crp_field* f = new crp_field();
+    cudaError_t e = cudaMalloc(&f->mem, (size_t)nodes * out_elem);
+    if (e != cudaSuccess) {
+        if (staging) cudaFree(staging);
+        delete f;
+        return cuda_fail(e, "cudaMalloc(field)");
+    }
+    const int block = 256;
+    const int gridn = grid_for(nodes, block, 65535);
+    switch (dtype) {
+    case CRP_DTYPE_F64: k_layout<double, double2><<<gridn, block>>>((const double*)src, (double2*)f->mem, nodes); break;
+    case CRP_DTYPE_F32: k_layout<float, float4><<<gridn, block>>>((const float*)src, (float4*)f->mem, nodes); break;
+    default: k_layout<unsigned short, ushort4><<<gridn, block>>>((const unsigned short*)src, (ushort4*)f->mem, nodes); break;
+    }
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (staging) cudaFree(staging);
+    if (e != cudaSuccess) {
+        cudaFree(f->mem);
+        delete f;
+        return cuda_fail(e, "field layout kernel");
+    }
+    f->nodes = nodes;
+    FieldDev& d = f->dev;
+    d.data = f->mem;
+    d.layout = layout;
+    d.nx = nx; d.ny = ny; d.nz = nz;
+    d.pow2 = (is_pow2(nx) && is_pow2(ny) && is_pow2(nz)) ? 1 : 0;
+    d.inv_spacing = 1.0 / spacing_m;
+    d.spacing = spacing_m;
+    d.ox = origin_m[0]; d.oy = origin_m[1]; d.oz = origin_m[2];
+    d.scale = (dtype == CRP_DTYPE_BF16 || dtype == CRP_DTYPE_F16) ? (double)scale : 1.0;
+    *out = f;
+    return CRP_OK;
+}
+
+int crp_field_destroy(crp_field* field) {
+    if (!field) return fail(CRP_ERR_INVALID_ARG, "field is NULL");
+    if (field->mem) cudaFree(field->mem);
+    delete field;
+    return CRP_OK;
+}
+
+int crp_tables_create(int32_t z_max, int32_t n_max, int32_t n_nodes, double x0, double inv_dx,
+                      const double* log10_loss, const double* log10_pd, const uint8_t* has_loss,
+                      const uint8_t* has_pd, crp_tables** out) {
+    if (!out) return fail(CRP_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!log10_loss || !log10_pd || !has_loss || !has_pd)
+        return fail(CRP_ERR_INVALID_ARG, "NULL table pointer");
+    if (z_max < 0 || n_max < 0 || n_nodes < 2 || !(inv_dx > 0.0) || !std::isfinite(x0))
+        return fail(CRP_ERR_INVALID_ARG, "bad table geometry");
+    const long long n_sp = (long long)(z_max + 1) * (n_max + 1);
+    for (long long sp = 0; sp < n_sp; ++sp) {
+        for (int j = 0; j < n_nodes; ++j) {
+            if (has_loss[sp] && !std::isfinite(log10_loss[sp * n_nodes + j]))
+                return fail(CRP_ERR_INVALID_ARG, "non-finite value in a loss row");
+            if (has_pd[sp] && !std::isfinite(log10_pd[sp * n_nodes + j]))
+                return fail(CRP_ERR_INVALID_ARG, "non-finite value in a PD row");
+        }
+    }
+    int ndev = 0;
+    CRP_CUDA(cudaGetDeviceCount(&ndev));
+    const size_t vb = (size_t)n_sp * n_nodes * sizeof(double);
+    const size_t total = 2 * vb + 2 * (size_t)n_sp + 64;
+    crp_tables* t = new crp_tables();
+    cudaError_t e = cudaMalloc(&t->mem, total);
+    if (e != cudaSuccess) { delete t; return cuda_fail(e, "cudaMalloc(tables)"); }
+    char* base = (char*)t->mem;
+    e = cudaMemcpy(base, log10_loss, vb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(base + vb, log10_pd, vb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(base + 2 * vb, has_loss, n_sp, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(base + 2 * vb + n_sp, has_pd, n_sp, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { cudaFree(t->mem); delete t; return cuda_fail(e, "cudaMemcpy(tables)"); }
+    TablesDev& d = t->dev;
+    d.loss = (const double*)base;
+    d.pd = (const double*)(base + vb);
+    d.has_loss = (const uint8_t*)(base + 2 * vb);
+    d.has_pd = (const uint8_t*)(base + 2 * vb + n_sp);
+    d.z_max = z_max; d.n_max = n_max; d.n_nodes = n_nodes;
+    d.x0 = x0; d.inv_dx = inv_dx;
+    *out = t;
+    return CRP_OK;
+}
+
+int crp_tables_destroy(crp_tables* tables) {
+    if (!tables) return fail(CRP_ERR_INVALID_ARG, "tables is NULL");
+    if (tables->mem) cudaFree(tables->mem);
+    delete tables;
+    return CRP_OK;
+}
+
+int crp_sim_create(const crp_field* const* fields, int32_t n_fields, const crp_tables* tables,
+                   uint64_t seed, int64_t capacity, crp_sim** out) {
+    if (!out) return fail(CRP_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!fields || n_fields < 1) return fail(CRP_ERR_INVALID_ARG, "need at least one field");
+    for (int i = 0; i < n_fields; ++i)
+        if (!fields[i]) return fail(CRP_ERR_INVALID_ARG, "NULL field handle");
+    if (capacity < 1 || capacity >= (1ll << 31)) return fail(CRP_ERR_INVALID_ARG, "capacity out of range");
+    const int layout = fields[0]->dev.layout;
+    for (int i = 1; i < n_fields; ++i)
+        if (fields[i]->dev.layout != layout)
+            return fail(CRP_ERR_INVALID_ARG, "all fields of a simulation need the same dtype");
+    int ndev = 0;
+    CRP_CUDA(cudaGetDeviceCount(&ndev));
+    crp_sim* s = new crp_sim();
+    s->layout = layout;
+    s->tables = tables;
+    s->seed = seed;
+    s->capacity = capacity;
+    s->sms = device_sms();
+    for (int i = 0; i < n_fields; ++i) s->host_fields.push_back(fields[i]->dev);
+    int rc = alloc_state(s->st, capacity);
+    cudaError_t e = cudaSuccess;
+    if (rc == CRP_OK) e = cudaMalloc(&s->d_fields, sizeof(FieldDev) * n_fields);
+    if (rc == CRP_OK && e == cudaSuccess)
+        e = cudaMemcpy(s->d_fields, s->host_fields.data(), sizeof(FieldDev) * n_fields, cudaMemcpyHostToDevice);
+    if (rc == CRP_OK && e == cudaSuccess) e = cudaMalloc(&s->lists[0], sizeof(int32_t) * capacity);
+    if (rc == CRP_OK && e == cudaSuccess) e = cudaMalloc(&s->lists[1], sizeof(int32_t) * capacity);
+    if (rc == CRP_OK && e == cudaSuccess) e = cudaMalloc(&s->done_list, sizeof(int32_t) * capacity);
+    if (rc == CRP_OK && e == cudaSuccess) e = cudaMalloc(&s->ctr, sizeof(Counters));
+    if (rc == CRP_OK && e == cudaSuccess) e = cudaMemset(s->ctr, 0, sizeof(Counters));
+    if (rc != CRP_OK || e != cudaSuccess) {
+        crp_sim_destroy(s);
+        return rc != CRP_OK ? rc : cuda_fail(e, "crp_sim_create allocations");
+    }
+    *out = s;
+    return CRP_OK;
+}
+
+int crp_sim_destroy(crp_sim* s) {
+    if (!s) return fail(CRP_ERR_INVALID_ARG, "sim is NULL");
+    if (s->last) cudaStreamSynchronize(s->last);
+    free_state(s->st);
+    if (s->d_fields) cudaFree(s->d_fields);
+    if (s->lists[0]) cudaFree(s->lists[0]);
+    if (s->lists[1]) cudaFree(s->lists[1]);
+    if (s->done_list) cudaFree(s->done_list);
+    if (s->ctr) cudaFree(s->ctr);
+    delete s;
+    return CRP_OK;
+}
+
+int crp_sim_reset(crp_sim* s) {
+    if (!s) return fail(CRP_ERR_INVALID_ARG, "sim is NULL");
+    int rc = sync_stream(s);
+    if (rc) return rc;
+    CRP_CUDA(cudaMemset(s->ctr, 0, sizeof(Counters)));
+    CRP_CUDA(cudaDeviceSynchronize());
+    return CRP_OK;
+}
+
+int crp_sim_reserve(crp_sim* s, int64_t capacity) {
+    if (!s) return fail(CRP_ERR_INVALID_ARG, "sim is NULL");
+    if (capacity >= (1ll << 31)) return fail(CRP_ERR_INVALID_ARG, "capacity out of range");
+    if (capacity <= s->capacity) return CRP_OK;
+    Counters h;
+    int rc = read_counters(s, &h);
+    if (rc) return rc;
+    SimState ns{};
+    rc = alloc_state(ns, capacity);
+    if (rc) return rc;
+    int32_t *l0 = nullptr, *l1 = nullptr, *dl = nullptr;
+    cudaError_t e = cudaMalloc(&l0, sizeof(int32_t) * capacity);
+    if (e == cudaSuccess) e = cudaMalloc(&l1, sizeof(int32_t) * capacity);
+    if (e == cudaSuccess) e = cudaMalloc(&dl, sizeof(int32_t) * capacity);
+    for (int c = 0; c < CRP_N_COLS && e == cudaSuccess; ++c)
+        e = cudaMemcpy(*col_ptr(ns, c), *col_ptr(s->st, c), (size_t)h.n_used * kCols[c].size,
+                       cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(dl, s->done_list, sizeof(int32_t) * h.n_done, cudaMemcpyDeviceToDevice);
+    if (e != cudaSuccess) {
+        free_state(ns);
+        if (l0) cudaFree(l0);
+        if (l1) cudaFree(l1);
+        if (dl) cudaFree(dl);
+        return cuda_fail(e, "crp_sim_reserve");
+    }
+    free_state(s->st);
+    cudaFree(s->lists[0]);
+    cudaFree(s->lists[1]);
+    cudaFree(s->done_list);
+    s->st = ns;
+    s->lists[0] = l0;
+    s->lists[1] = l1;
+    s->done_list = dl;
+    s->capacity = capacity;
+    return CRP_OK;
+}
+
+int crp_source_inject(crp_sim* s, const crp_particles* p, int64_t n, void* stream) {
+    if (!s || !p) return fail(CRP_ERR_INVALID_ARG, "sim or particles is NULL");
+    if (n < 0) return fail(CRP_ERR_INVALID_ARG, "n < 0");
+    if (n == 0) return CRP_OK;
+    if (!p->x || !p->y || !p->z || !p->ux || !p->uy || !p->uz || !p->E || !p->A || !p->Z)
+        return fail(CRP_ERR_INVALID_ARG, "NULL particle column");
+    Counters h;
+    int rc = read_counters(s, &h);
+    if (rc) return rc;
+    if ((long long)h.n_used + n > s->capacity)
+        return fail(CRP_ERR_INVALID_ARG, "injection exceeds the simulation capacity");
+    const int n_fields = (int)s->host_fields.size();
+    const TablesDev* tab = s->tables ? &s->tables->dev : nullptr;
+    if (!p->is_device) {   // host columns: validate before touching the device
+        for (long long i = 0; i < n; ++i) {
+            const int A = p->A[i], Z = p->Z[i];
+            if (A < 1 || Z < 0 || Z > A) return fail(CRP_ERR_INVALID_ARG, "particle with invalid A/Z");
+            if (tab && (Z > tab->z_max || A - Z > tab->n_max))
+                return fail(CRP_ERR_INVALID_ARG, "species outside the interaction tables");
+            const long long uid = p->uid ? p->uid[i] : (long long)(h.n_primaries + i);
+            if (uid < 0 || uid >= (1ll << 32)) return fail(CRP_ERR_INVALID_ARG, "uid outside [0, 2^32)");
+            if (p->grid_id && (p->grid_id[i] < 0 || p->grid_id[i] >= n_fields))
+                return fail(CRP_ERR_INVALID_ARG, "grid_id out of range");
+        }
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const cudaMemcpyKind kind = p->is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const long long f = (long long)h.n_used;
+    struct { const void* src; int col; } cp[] = {
+        {p->x, CRP_COL_X}, {p->y, CRP_COL_Y}, {p->z, CRP_COL_Z}, {p->ux, CRP_COL_UX},
+        {p->uy, CRP_COL_UY}, {p->uz, CRP_COL_UZ}, {p->E, CRP_COL_E}, {p->A, CRP_COL_A},
+        {p->Z, CRP_COL_Z_CHARGE}, {p->uid, CRP_COL_UID}, {p->grid_id, CRP_COL_GRID_ID}};
+    for (auto& c : cp) {
+        if (!c.src) continue;
+        char* dst = (char*)*col_ptr(s->st, c.col) + f * kCols[c.col].size;
+        CRP_CUDA(cudaMemcpyAsync(dst, c.src, (size_t)n * kCols[c.col].size, kind, st));
+    }
+    const int block = 256;
+    k_inject_init<<<grid_for(n, block, 4096), block, 0, st>>>(
+        s->st, f, n, p->uid ? 1 : 0, p->grid_id ? 1 : 0, h.n_primaries, n_fields, tab ? 1 : 0,
+        tab ? tab->z_max : 0, tab ? tab->n_max : 0, s->seed, s->done_list, s->ctr);
+    CRP_CUDA(cudaGetLastError());
+    k_set_used<<<1, 1, 0, st>>>(s->ctr, h.n_used + n, h.n_primaries + (p->uid ? 0 : n));
+    CRP_CUDA(cudaGetLastError());
+    s->last = st;
+    return CRP_OK;
+}
+
+int crp_propagate(crp_sim* s, const crp_params* prm, double tol, double hmin, double hmax,
+                  double dmax, void* stream) {
+    if (!s || !prm) return fail(CRP_ERR_INVALID_ARG, "sim or params is NULL");
+    if (!(tol > 0.0) || !(hmin > 0.0) || !(hmax >= hmin) || !(dmax > 0.0) || !std::isfinite(hmax) ||
+        !std::isfinite(dmax))
+        return fail(CRP_ERR_INVALID_ARG, "need tolerance > 0, 0 < min_step <= max_step, max_distance > 0");
+    if (prm->form != CRP_FORM_FP64) return fail(CRP_ERR_INVALID_ARG, "unknown or unavailable form");
+    const int block = prm->block_size > 0 ? prm->block_size : 128;
+    if (block % 32 || block > 256) return fail(CRP_ERR_INVALID_ARG, "block_size must be a multiple of 32, <= 256");
+    int bps = prm->blocks_per_sm;
+    if (bps <= 0) {
+        int occ = 0;
+        if (propagate_fp64_occupancy(s->layout, block, &occ) != 0 || occ < 1) occ = 1;
+        bps = occ;
+    }
+    const int grid = (s->sms > 0 ? s->sms : 1) * bps;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    PropArgs a{};
+    a.st = s->st;
+    a.fields = s->d_fields;
+    a.n_fields = (int)s->host_fields.size();
+    a.has_tables = s->tables ? 1 : 0;
+    if (s->tables) a.tab = s->tables->dev;
+    a.tol = tol; a.hmin = hmin; a.hmax = hmax; a.dmax = dmax;
+    a.seed = s->seed;
+    a.max_steps = prm->max_steps;
+    a.capacity = s->capacity;
+    a.cadence = prm->cadence > 0 ? prm->cadence : 1;
+    a.lists[0] = s->lists[0];
+    a.lists[1] = s->lists[1];
+    a.done_list = s->done_list;
+    a.ctr = s->ctr;
+    k_prepare<<<1, 1, 0, st>>>(s->ctr);
+    CRP_CUDA(cudaGetLastError());
+    k_build_worklist<<<(s->sms > 0 ? s->sms : 1) * 4, 256, 0, st>>>(s->st.status, s->lists[0], s->ctr);
+    CRP_CUDA(cudaGetLastError());
+    // generation 1: the work list; generation 2: secondaries created by it (nucleons, which
+    // never split, so two launches finish the call)
+    for (int gen = 0; gen < 2; ++gen) {
+        a.list = gen;
+        int e = launch_propagate_fp64(a, s->layout, grid, block, st);
+        if (e) return cuda_fail((cudaError_t)e, "propagate kernel launch");
+        k_swap<<<1, 1, 0, st>>>(s->ctr, s->capacity, gen);
+        CRP_CUDA(cudaGetLastError());
+    }
+    s->last = st;
+    return CRP_OK;
+}
+
+int crp_sync(crp_sim* s, double timeout_s) {
+    if (!s) return fail(CRP_ERR_INVALID_ARG, "sim is NULL");
+    if (timeout_s > 0) {
+        const auto t0 = std::chrono::steady_clock::now();
+        for (;;) {
+            cudaError_t e = cudaStreamQuery(s->last);
+            if (e == cudaSuccess) break;
+            if (e != cudaErrorNotReady) return cuda_fail(e, "cudaStreamQuery");
+            const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            if (dt > timeout_s) return fail(CRP_ERR_TIMEOUT, "crp_sync wait limit reached");
+            std::this_thread::sleep_for(std::chrono::microseconds(200));
+        }
+    }
+    Counters h;
+    int rc = read_counters(s, &h);
+    if (rc) return rc;
+    const unsigned b = h.status_bits;
+    if (b) {
+        unsigned zero = 0;
+        CRP_CUDA(cudaMemcpy(&s->ctr->status_bits, &zero, sizeof zero, cudaMemcpyHostToDevice));
+    }
+    if (b & BIT_QUEUE_FULL) return fail(CRP_ERR_QUEUE_FULL, "secondary queue full");
+    if (b & BIT_NAN) return fail(CRP_ERR_NAN_STATE, "non-finite particle state");
+    if (b & BIT_RANGE) return fail(CRP_ERR_TABLE_RANGE, "species outside tables");
+    if (b & BIT_INVALID) return fail(CRP_ERR_INVALID_ARG, "invalid particle in injection");
+    return CRP_OK;
+}
+
+int crp_sim_counts(crp_sim* s, int64_t counts[8]) {
+    if (!s || !counts) return fail(CRP_ERR_INVALID_ARG, "NULL argument");
+    Counters h;
+    int rc = read_counters(s, &h);
+    if (rc) return rc;
+    counts[0] = (int64_t)h.n_used;
+    counts[1] = (int64_t)(h.n_used - h.n_done);
+    counts[2] = (int64_t)h.n_done;
+    counts[3] = (int64_t)h.accepted;
+    counts[4] = (int64_t)h.attempted;
+    counts[5] = (int64_t)h.secondaries;
+    counts[6] = (int64_t)h.launches;
+    counts[7] = (int64_t)h.status_bits;
+    return CRP_OK;
+}
+
+int crp_read_state(crp_sim* s, int32_t column, void* dst, int32_t dst_is_device, int64_t first,
+                   int64_t count) {
+    if (!s || !dst) return fail(CRP_ERR_INVALID_ARG, "NULL argument");
+    if (column < 0 || column >= CRP_N_COLS) return fail(CRP_ERR_INVALID_ARG, "unknown column");
+    if (first < 0 || count < 0 || first + count > s->capacity)
+        return fail(CRP_ERR_INVALID_ARG, "slot range outside the simulation");
+    int rc = sync_stream(s);
+    if (rc) return rc;
+    const char* src = (const char*)*col_ptr(s->st, column) + first * kCols[column].size;
+    CRP_CUDA(cudaMemcpy(dst, src, (size_t)count * kCols[column].size,
+                        dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
+    return CRP_OK;
+}
+
+int crp_observe(crp_sim* s, const crp_observer* o, int64_t first, int64_t capacity, int64_t* n_out) {
+    if (!s || !o || !n_out) return fail(CRP_ERR_INVALID_ARG, "NULL argument");
+    if (first < 0 || capacity < 0) return fail(CRP_ERR_INVALID_ARG, "negative range");
+    *n_out = 0;
+    Counters h;
+    int rc = read_counters(s, &h);
+    if (rc) return rc;
+    long long n = (long long)h.n_done - first;
+    if (n <= 0) return CRP_OK;
+    if (n > capacity) n = capacity;
+    ObsCols d{o->uid, o->A, o->Z, o->n_int, o->status, o->E, o->x, o->y, o->z, o->ux, o->uy,
+              o->uz, o->u0x, o->u0y, o->u0z, o->s, o->n_steps, o->n_att};
+    void* tmp = nullptr;
+    ObsCols t = d;
+    if (!o->is_device) {   // gather on the device into one staging block, then copy out
+        size_t off = 0;
+        const size_t sz8 = (size_t)n * 8, sz4 = (size_t)n * 4;
+        CRP_CUDA(cudaMalloc(&tmp, 13 * sz8 + 4 * sz4 + 2 * sz8));
+        char* b = (char*)tmp;
+        auto take8 = [&](void* want) -> void* { if (!want) return nullptr; void* r = b + off; off += sz8; return r; };
+        auto take4 = [&](void* want) -> void* { if (!want) return nullptr; void* r = b + off; off += sz4; return r; };
+        t.uid = (int64_t*)take8(d.uid);
+        t.E = (double*)take8(d.E); t.x = (double*)take8(d.x); t.y = (double*)take8(d.y);
+        t.z = (double*)take8(d.z); t.ux = (double*)take8(d.ux); t.uy = (double*)take8(d.uy);
+        t.uz = (double*)take8(d.uz); t.u0x = (double*)take8(d.u0x); t.u0y = (double*)take8(d.u0y);
+        t.u0z = (double*)take8(d.u0z); t.s = (double*)take8(d.s);
+        t.n_steps = (int64_t*)take8(d.n_steps); t.n_att = (int64_t*)take8(d.n_att);
+        t.A = (int32_t*)take4(d.A); t.Z = (int32_t*)take4(d.Z);
+        t.n_int = (int32_t*)take4(d.n_int); t.status = (int32_t*)take4(d.status);
+    }
+    k_observe<<<grid_for(n, 256, 4096), 256>>>(s->st, s->done_list, first, n, t);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess && !o->is_device) {
+        struct { void* dst; void* src; size_t sz; } cps[] = {
+            {d.uid, t.uid, 8}, {d.E, t.E, 8}, {d.x, t.x, 8}, {d.y, t.y, 8}, {d.z, t.z, 8},
+            {d.ux, t.ux, 8}, {d.uy, t.uy, 8}, {d.uz, t.uz, 8}, {d.u0x, t.u0x, 8},
+            {d.u0y, t.u0y, 8}, {d.u0z, t.u0z, 8}, {d.s, t.s, 8}, {d.n_steps, t.n_steps, 8},
+            {d.n_att, t.n_att, 8}, {d.A, t.A, 4}, {d.Z, t.Z, 4}, {d.n_int, t.n_int, 4},
+            {d.status, t.status, 4}};
+        for (auto& c : cps)
+            if (c.dst && e == cudaSuccess) e = cudaMemcpy(c.dst, c.src, (size_t)n * c.sz, cudaMemcpyDeviceToHost);
+    }
+    if (tmp) cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(e, "crp_observe");
+    *n_out = n;
+    return CRP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,89 @@
+// crp_internal.h -- device-side data structures shared by the host library (crp_capi.cu)
+// and the kernels. Not part of the public ABI.
+#pragma once
+#include <cstdint>
+
+namespace crp {
+
+// Grid layouts in device memory: one 4-wide vector per node, node index
+// (i*ny + j)*nz + k, the 4th lane unused (padding keeps every corner one aligned load).
+enum Layout : int32_t { LAYOUT_F32X4 = 0, LAYOUT_F64X4 = 1, LAYOUT_BF16X4 = 2, LAYOUT_F16X4 = 3 };
+
+struct FieldDev {
+    const void* data;
+    int32_t layout;
+    int32_t nx, ny, nz;
+    int32_t pow2;            // 1 if nx, ny, nz are all powers of two
+    int32_t pad_;
+    double inv_spacing;      // 1/spacing, rounded once
+    double spacing;
+    double ox, oy, oz;
+    double scale;            // BF16/F16 multiplier (1 otherwise)
+};
+
+struct TablesDev {
+    const double* loss;      // [species][n_nodes] log10 rate
+    const double* pd;
+    const uint8_t* has_loss;
+    const uint8_t* has_pd;
+    int32_t z_max, n_max, n_nodes, pad_;
+    double x0, inv_dx;
+};
+
+struct SimState {            // structure of arrays, `capacity` slots
+    double *x, *y, *z, *ux, *uy, *uz, *E, *s, *hprop, *tau, *u0x, *u0y, *u0z;
+    int32_t *A, *Z, *n_int, *status, *grid_id;
+    int64_t *uid, *n_steps, *n_att;
+};
+
+// Particle status values (same numbers as CRP_STATUS_* in the public header).
+constexpr int32_t CRP_STATUS_ACTIVE_ = 0;
+constexpr int32_t CRP_STATUS_DONE_ = 1;
+constexpr int32_t CRP_STATUS_NAN_ = 2;
+constexpr int32_t CRP_STATUS_RANGE_ = 3;
+
+// Device status bits.
+enum : uint32_t {
+    BIT_QUEUE_FULL = 1u,
+    BIT_NAN = 2u,
+    BIT_RANGE = 4u,
+    BIT_INVALID = 8u,
+};
+
+struct Counters {
+    unsigned long long n_used;       // slots in use
+    unsigned long long reserve;      // slot reservation counter during a launch
+    unsigned long long count[2];     // entries in work list 0 / 1
+    unsigned long long head;         // next position to pop from the list being processed
+    unsigned long long n_done;       // entries in the done list
+    unsigned long long accepted;     // cumulative accepted steps
+    unsigned long long attempted;    // cumulative attempted steps
+    unsigned long long secondaries;  // cumulative secondaries created
+    unsigned long long launches;     // propagate kernel launches
+    unsigned long long n_primaries;  // primaries injected (default uids)
+    unsigned int status_bits;
+    unsigned int pad_;
+};
+
+struct PropArgs {
+    SimState st;
+    const FieldDev* fields;
+    int32_t n_fields;
+    int32_t has_tables;
+    TablesDev tab;
+    double tol, hmin, hmax, dmax;
+    unsigned long long seed;
+    long long max_steps;
+    long long capacity;
+    int32_t cadence;
+    int32_t list;                    // process list `list`, push secondaries to 1 - list
+    int32_t* lists[2];
+    int32_t* done_list;
+    Counters* ctr;
+};
+
+// Launchers (defined in the kernel translation units).
+int launch_propagate_fp64(const PropArgs& a, int layout, int grid, int block, void* stream);
+int propagate_fp64_occupancy(int layout, int block, int* blocks_per_sm);
+
+}  // namespace crp

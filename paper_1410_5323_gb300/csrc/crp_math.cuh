@@ -1,0 +1,137 @@
+// crp_math.cuh -- device arithmetic of the method that must reproduce the stated FP64
+// reading bit for bit: Philox4x32-10 streams, exp/log by the stated reduction + series,
+// table interpolation. Translation units that include this for the FP64 form are
+// compiled with --fmad=false so every operation below is one IEEE-rounded operation.
+#pragma once
+#include <cstdint>
+#include "crp_internal.h"
+
+namespace crp {
+
+constexpr double kC = 299792458.0;          // speed of light, m/s
+constexpr double kMpC2 = 938272088.16;      // proton rest energy, eV (CODATA 2018)
+
+// ---- Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11) ---------------------------
+struct U4 { uint32_t a, b, c, d; };
+
+__device__ __forceinline__ U4 philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                       uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+    return {c0, c1, c2, c3};
+}
+
+// U in (0,1): 52 random bits m = (w0 << 20) | (w1 >> 12), U = (m + 1/2) 2^-52 (exact).
+__device__ __forceinline__ double uniform01(unsigned long long seed, unsigned long long uid,
+                                            uint32_t k, uint32_t tag) {
+    const U4 w = philox10((uint32_t)uid, (uint32_t)(uid >> 32), k, tag, (uint32_t)seed,
+                          (uint32_t)(seed >> 32));
+    const unsigned long long m = ((unsigned long long)w.a << 20) | (unsigned long long)(w.b >> 12);
+    return __dmul_rn(__dadd_rn((double)m, 0.5), 0x1p-52);
+}
+
+// Removed nucleon is a proton iff (w0 mod A) < Z, w0 from counter (uid, k, tag 1).
+__device__ __forceinline__ int nucleon_proton(unsigned long long seed, unsigned long long uid,
+                                              uint32_t k, int A, int Z) {
+    const U4 w = philox10((uint32_t)uid, (uint32_t)(uid >> 32), k, 1u, (uint32_t)seed,
+                          (uint32_t)(seed >> 32));
+    return (int)(w.a % (uint32_t)A) < Z;
+}
+
+// ---- exp / log: Cody & Waite reduction, ln 2 = head (32 bits) + tail ------------------
+constexpr double kLn2Hi = 0x1.62e42feep-1;
+constexpr double kLn2Lo = 0x1.a39ef35793c76p-33;
+constexpr double kInvLn2 = 0x1.71547652b82fep+0;
+constexpr double kSqrtHalf = 0x1.6a09e667f3bcdp-1;
+constexpr double kLn10 = 0x1.26bb1bbb55516p+1;
+constexpr double kInvLn10 = 0.4342944819032518;
+
+// exp(x) = 2^n e^r, |r| <= ln2/2, e^r by Taylor through r^14/14! in Horner order.
+__device__ __forceinline__ double crp_exp(double x) {
+    if (x != x) return x;
+    if (x > 709.782712893384) return __longlong_as_double(0x7ff0000000000000LL);
+    if (x < -745.1332191019412) return 0.0;
+    const double n = floor(__dadd_rn(__dmul_rn(x, kInvLn2), 0.5));
+    const double r = __dsub_rn(__dsub_rn(x, __dmul_rn(n, kLn2Hi)), __dmul_rn(n, kLn2Lo));
+    double p = 1.0 / 87178291200.0;
+    p = __dadd_rn(__dmul_rn(p, r), 1.0 / 6227020800.0);
+    p = __dadd_rn(__dmul_rn(p, r), 1.0 / 479001600.0);
+    p = __dadd_rn(__dmul_rn(p, r), 1.0 / 39916800.0);
+    p = __dadd_rn(__dmul_rn(p, r), 1.0 / 3628800.0);
+    p = __dadd_rn(__dmul_rn(p, r), 1.0 / 362880.0);
+    p = __dadd_rn(__dmul_rn(p, r), 1.0 / 40320.0);
+    p = __dadd_rn(__dmul_rn(p, r), 1.0 / 5040.0);
+    p = __dadd_rn(__dmul_rn(p, r), 1.0 / 720.0);
+    p = __dadd_rn(__dmul_rn(p, r), 1.0 / 120.0);
+    p = __dadd_rn(__dmul_rn(p, r), 1.0 / 24.0);
+    p = __dadd_rn(__dmul_rn(p, r), 1.0 / 6.0);
+    p = __dadd_rn(__dmul_rn(p, r), 0.5);
+    p = __dadd_rn(__dmul_rn(p, r), 1.0);
+    p = __dadd_rn(__dmul_rn(p, r), 1.0);
+    return ldexp(p, (int)n);
+}
+
+// log(x) = e ln2 + 2 atanh(s), s = (m-1)/(m+1), m in [sqrt(1/2), sqrt(2)), through s^23/23.
+__device__ __forceinline__ double crp_log(double x) {
+    if (x != x) return x;
+    if (x < 0.0) return __longlong_as_double(0x7ff8000000000000LL);
+    if (x == 0.0) return __longlong_as_double(0xfff0000000000000LL);
+    if (isinf(x)) return x;
+    int e;
+    double m = frexp(x, &e);
+    if (m < kSqrtHalf) { m = __dmul_rn(m, 2.0); e = e - 1; }
+    const double s = __ddiv_rn(__dsub_rn(m, 1.0), __dadd_rn(m, 1.0));
+    const double s2 = __dmul_rn(s, s);
+    double p = 1.0 / 23.0;
+    p = __dadd_rn(__dmul_rn(p, s2), 1.0 / 21.0);
+    p = __dadd_rn(__dmul_rn(p, s2), 1.0 / 19.0);
+    p = __dadd_rn(__dmul_rn(p, s2), 1.0 / 17.0);
+    p = __dadd_rn(__dmul_rn(p, s2), 1.0 / 15.0);
+    p = __dadd_rn(__dmul_rn(p, s2), 1.0 / 13.0);
+    p = __dadd_rn(__dmul_rn(p, s2), 1.0 / 11.0);
+    p = __dadd_rn(__dmul_rn(p, s2), 1.0 / 9.0);
+    p = __dadd_rn(__dmul_rn(p, s2), 1.0 / 7.0);
+    p = __dadd_rn(__dmul_rn(p, s2), 1.0 / 5.0);
+    p = __dadd_rn(__dmul_rn(p, s2), 1.0 / 3.0);
+    const double t = __dmul_rn(s2, p);
+    const double log_m = __dadd_rn(__dmul_rn(2.0, s), __dmul_rn(__dmul_rn(2.0, s), t));
+    const double de = (double)e;
+    return __dadd_rn(__dmul_rn(de, kLn2Hi), __dadd_rn(__dmul_rn(de, kLn2Lo), log_m));
+}
+
+// ---- tabulated rates at gamma0 = E/(A m_p c^2) ------------------------------------------
+// Returns false if the species lies outside the tables.
+__device__ __forceinline__ bool table_rates(const TablesDev& t, int A, int Z, double E,
+                                            double& r_loss, double& r_pd) {
+    r_loss = 0.0;
+    r_pd = 0.0;
+    const int N = A - Z;
+    if (Z < 0 || N < 0 || Z > t.z_max || N > t.n_max) return false;
+    const long long sp = (long long)Z * (t.n_max + 1) + N;
+    const double gamma0 = __ddiv_rn(E, __dmul_rn((double)A, kMpC2));
+    const double x = __dmul_rn(crp_log(gamma0), kInvLn10);
+    double tt = __dmul_rn(__dsub_rn(x, t.x0), t.inv_dx);
+    tt = fmin(fmax(tt, 0.0), (double)(t.n_nodes - 1));
+    long long j = (long long)floor(tt);
+    if (j > t.n_nodes - 2) j = t.n_nodes - 2;
+    const double fr = __dsub_rn(tt, (double)j);
+    if (t.has_loss[sp]) {
+        const double* T = t.loss + sp * t.n_nodes;
+        const double a = __ldg(T + j), b = __ldg(T + j + 1);
+        r_loss = crp_exp(__dmul_rn(__dadd_rn(a, __dmul_rn(fr, __dsub_rn(b, a))), kLn10));
+    }
+    if (t.has_pd[sp]) {
+        const double* T = t.pd + sp * t.n_nodes;
+        const double a = __ldg(T + j), b = __ldg(T + j + 1);
+        r_pd = crp_exp(__dmul_rn(__dadd_rn(a, __dmul_rn(fr, __dsub_rn(b, a))), kLn10));
+    }
+    return true;
+}
+
+}  // namespace crp
