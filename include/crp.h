@@ -202,6 +202,47 @@ typedef struct {
 int crp_observe(crp_sim* sim, const crp_observer* out, int64_t first, int64_t capacity,
                 int64_t* n_out);
 
+/* ---- propagation that allocates nothing -------------------------------------------------
+ * This entry point has no counterpart in the paper; it exists for callers that must not
+ * have this library allocate device memory. Some host programs own every byte of GPU
+ * memory themselves: a framework with its own pooled allocator, where a library's
+ * cudaMalloc would fragment the pool or fail against a budget the host already handed
+ * out, or a long-running service whose device footprint is fixed at start-up. Such
+ * callers cannot use crp_sim_create / crp_field_create, which allocate. Here the caller
+ * passes every input and output buffer, and the bookkeeping the propagate kernel needs
+ * (counters, work lists, done list) lives in one static device array inside the library,
+ * of CRP_NOALLOC_SCRATCH_BYTES bytes, which every GPU that loads the library holds until
+ * the process exits.
+ *
+ * What it does: for particles 0..n-1 in `cols` (device pointers, each column at least n
+ * entries; the caller fills x, y, z, ux, uy, uz, E, A, Z and uid < 2^32) it initialises
+ * the bookkeeping columns exactly as crp_source_inject does (grid_id = 0) and propagates
+ * them in the FP64 form without interactions through one field, exactly as
+ * crp_propagate does, to max_distance_m or max_steps accepted steps (<= 0: no limit).
+ * The field is `grid_f32x4`: a device pointer, 16-byte aligned, to nx*ny*nz float4 nodes
+ * (x, y, z components, fourth lane ignored), node (i,j,k) at index (i*ny + j)*nz + k.
+ * The call waits for the work on `stream` to finish and returns CRP_OK or the device
+ * status as a code (CRP_ERR_NAN_STATE, CRP_ERR_INVALID_ARG for an invalid particle).
+ *
+ * Limits and sharing: n <= CRP_NOALLOC_MAX_PARTICLES, else CRP_ERR_INVALID_ARG and nothing
+ * runs. The first call on a device looks up the static array's device address (once per
+ * device, with that device current); make that first call before any stream capture.
+ * Every call reuses the same array and clears what must start at zero, so calls that
+ * overlap on the GPU (from several host threads or streams) race: serialise them.
+ * It never calls cudaMalloc, cudaFree or any allocating routine. */
+#define CRP_NOALLOC_MAX_PARTICLES 262144
+#define CRP_NOALLOC_SCRATCH_BYTES (512 + 3 * 4 * CRP_NOALLOC_MAX_PARTICLES)
+typedef struct {
+    double *x, *y, *z, *ux, *uy, *uz, *E, *s, *hprop, *tau, *u0x, *u0y, *u0z;
+    int32_t *A, *Z, *n_int, *status, *grid_id;
+    int64_t *uid, *n_steps, *n_att;
+} crp_state_columns;
+int crp_propagate_noalloc(const void* grid_f32x4, int32_t nx, int32_t ny, int32_t nz,
+                          double spacing_m, const double origin_m[3],
+                          const crp_state_columns* cols, int64_t n, uint64_t seed,
+                          double tolerance, double min_step_m, double max_step_m,
+                          double max_distance_m, int64_t max_steps, void* stream);
+
 const char* crp_error_string(int32_t code);
 const char* crp_last_error_detail(void);
 

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 
 #include <chrono>
+#include <cstdint>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -730,3 +732,122 @@ int crp_observe(crp_sim* s, const crp_observer* o, int64_t first, int64_t capaci
 }
 
 }  // extern "C"
+
+// ---- propagation without allocation: scratch in a static device array ---------------------
+// Layout: [Counters | pad to 256] [FieldDev | pad to 256] [work list 0] [work list 1]
+// [done list], each list CRP_NOALLOC_MAX_PARTICLES int32 entries.
+namespace {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[CRP_NOALLOC_SCRATCH_BYTES];
+static_assert(sizeof(Counters) <= 256 && sizeof(FieldDev) <= 256, "scratch header layout");
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[64] = {};   // device address of the array, per device ordinal
+
+__global__ void k_noalloc_setup(Counters* C, FieldDev* F, FieldDev f, unsigned long long n) {
+    Counters z{};
+    z.n_used = n;
+    z.reserve = n;
+    *C = z;
+    *F = f;
+}
+
+}  // namespace
+
+extern "C" int crp_propagate_noalloc(const void* grid, int32_t nx, int32_t ny, int32_t nz,
+                                     double spacing_m, const double origin_m[3],
+                                     const crp_state_columns* cols, int64_t n, uint64_t seed,
+                                     double tol, double hmin, double hmax, double dmax,
+                                     int64_t max_steps, void* stream) {
+    if (!grid || !origin_m || !cols) return fail(CRP_ERR_INVALID_ARG, "NULL argument");
+    if (n < 0 || n > CRP_NOALLOC_MAX_PARTICLES)
+        return fail(CRP_ERR_INVALID_ARG, "n outside [0, CRP_NOALLOC_MAX_PARTICLES]");
+    if (((uintptr_t)grid) % 16) return fail(CRP_ERR_INVALID_ARG, "grid must be 16-byte aligned");
+    if (nx < 1 || ny < 1 || nz < 1 || (long long)nx * ny * nz >= (1ll << 31))
+        return fail(CRP_ERR_INVALID_ARG, "grid sizes out of range");
+    if (!(spacing_m > 0.0) || !std::isfinite(spacing_m))
+        return fail(CRP_ERR_INVALID_ARG, "spacing must be finite and > 0");
+    if (!(tol > 0.0) || !(hmin > 0.0) || !(hmax >= hmin) || !(dmax > 0.0) ||
+        !std::isfinite(hmax) || !std::isfinite(dmax))
+        return fail(CRP_ERR_INVALID_ARG, "need tolerance > 0, 0 < min_step <= max_step, max_distance > 0");
+    const crp_state_columns& c = *cols;
+    const void* req[] = {c.x, c.y, c.z, c.ux, c.uy, c.uz, c.E, c.s, c.hprop, c.tau, c.u0x,
+                         c.u0y, c.u0z, c.A, c.Z, c.n_int, c.status, c.grid_id, c.uid,
+                         c.n_steps, c.n_att};
+    for (const void* q : req)
+        if (!q) return fail(CRP_ERR_INVALID_ARG, "NULL state column");
+    if (n == 0) return CRP_OK;
+    int dev = 0;
+    CRP_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(CRP_ERR_CUDA, "device ordinal above 63");
+    void* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void* p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+            g_noalloc_addr[dev] = p;
+        }
+        base = g_noalloc_addr[dev];
+    }
+    Counters* ctr = (Counters*)base;
+    FieldDev* fdev = (FieldDev*)((char*)base + 256);
+    int32_t* l0 = (int32_t*)((char*)base + 512);
+    int32_t* l1 = l0 + CRP_NOALLOC_MAX_PARTICLES;
+    int32_t* done = l1 + CRP_NOALLOC_MAX_PARTICLES;
+
+    FieldDev f{};
+    f.data = grid;
+    f.layout = LAYOUT_F32X4;
+    f.nx = nx; f.ny = ny; f.nz = nz;
+    f.pow2 = (is_pow2(nx) && is_pow2(ny) && is_pow2(nz)) ? 1 : 0;
+    f.inv_spacing = 1.0 / spacing_m;
+    f.spacing = spacing_m;
+    f.ox = origin_m[0]; f.oy = origin_m[1]; f.oz = origin_m[2];
+    f.scale = 1.0;
+    SimState S{c.x, c.y, c.z, c.ux, c.uy, c.uz, c.E, c.s, c.hprop, c.tau, c.u0x, c.u0y, c.u0z,
+               c.A, c.Z, c.n_int, c.status, c.grid_id, c.uid, c.n_steps, c.n_att};
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int sms = device_sms() > 0 ? device_sms() : 1;
+
+    k_noalloc_setup<<<1, 1, 0, st>>>(ctr, fdev, f, (unsigned long long)n);
+    CRP_CUDA(cudaGetLastError());
+    k_inject_init<<<grid_for(n, 256, 4096), 256, 0, st>>>(S, 0, n, 1, 0, 0ull, 1, 0, 0, 0, seed,
+                                                          done, ctr);
+    CRP_CUDA(cudaGetLastError());
+    k_prepare<<<1, 1, 0, st>>>(ctr);
+    CRP_CUDA(cudaGetLastError());
+    k_build_worklist<<<sms * 4, 256, 0, st>>>(S.status, l0, ctr);
+    CRP_CUDA(cudaGetLastError());
+    const int block = 128;
+    int occ = 0;
+    if (propagate_fp64_occupancy(LAYOUT_F32X4, block, &occ) != 0 || occ < 1) occ = 1;
+    PropArgs a{};
+    a.st = S;
+    a.fields = fdev;
+    a.n_fields = 1;
+    a.has_tables = 0;
+    a.tol = tol; a.hmin = hmin; a.hmax = hmax; a.dmax = dmax;
+    a.seed = seed;
+    a.max_steps = max_steps;
+    a.capacity = n;
+    a.cadence = 1;
+    a.lists[0] = l0;
+    a.lists[1] = l1;
+    a.done_list = done;
+    a.ctr = ctr;
+    for (int gen = 0; gen < 2; ++gen) {
+        a.list = gen;
+        int e = launch_propagate_fp64(a, LAYOUT_F32X4, sms * occ, block, st);
+        if (e) return cuda_fail((cudaError_t)e, "propagate kernel launch");
+        k_swap<<<1, 1, 0, st>>>(ctr, n, gen);
+        CRP_CUDA(cudaGetLastError());
+    }
+    CRP_CUDA(cudaStreamSynchronize(st));
+    unsigned bits = 0;
+    CRP_CUDA(cudaMemcpy(&bits, &ctr->status_bits, sizeof bits, cudaMemcpyDeviceToHost));
+    if (bits & BIT_NAN) return fail(CRP_ERR_NAN_STATE, "non-finite particle state");
+    if (bits & BIT_INVALID) return fail(CRP_ERR_INVALID_ARG, "invalid particle");
+    return CRP_OK;
+}
