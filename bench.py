@@ -42,6 +42,14 @@ FLOP_PER_ACCEPTED_TABLES = 30
 # FP64 pipe of one GB300: 2 FP64 lanes/clk/SM x 152 SMs x 2070 MHz = 6.29e11 ops/s,
 # 1.259e12 FLOP/s counting an FMA as two (the FP64 form issues no FMA: ceiling 0.5).
 FP64_PEAK_TFLOPS = 152 * 2 * 2.070e9 * 2 / 1e12
+FP64_OPS_PEAK_T = 152 * 2 * 2.070e9 / 1e12          # FP64 pipe instructions (T ops/s)
+FP32_PEAK_TFLOPS = 152 * 128 * 2.070e9 * 2 / 1e12   # FFMA lanes x 2
+# Mixed form: FP64 ops that remain per attempt (6 widenings, 2 x (mul + 2 fma), max, compare)
+# and per accepted step (path length add, distance bid, widen h, compare), the FP32 flops
+# per attempt (6 x (lookup 60 + Lorentz 9) + stages 120 + update/error 66 + ratio 12).
+MIXED_FP64_OPS_PER_ATTEMPT = 14
+MIXED_FP64_OPS_PER_ACCEPTED = 5
+MIXED_FP32_FLOP_PER_ATTEMPT = 612
 
 
 def parse():
@@ -50,7 +58,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
-    ap.add_argument("--form", default="fp64", choices=["fp64"])
+    ap.add_argument("--form", default="fp64", choices=["fp64", "mixed"],
+                    help="form whose throughput is `value`; the other form is reported under `forms`")
+    ap.add_argument("--no-other-form", action="store_true")
     ap.add_argument("--workload", default="fp64_256cube_1M_nuclei")
     ap.add_argument("--n-particles", type=int, default=0, help="override batch size (testing)")
     ap.add_argument("--cpu-sample", type=int, default=16384, help="primaries in the oracle sample")
@@ -147,11 +157,52 @@ def cpu_baseline(w, grid, tables, parts, sample: int, form_desc: str):
     rc, stats = O.propagate(st, [O.OracleField(grid, w.spacing_m)], ot, w.tol, w.hmin_m, w.hmax_m,
                             w.dmax_m, seed=w.rng_seed, n_threads=threads)
     dt = time.perf_counter() - t0
-    return {"value": stats["accepted"] / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"first {len(sub)} primaries of the same batch (+{stats['secondaries']} "
-                      f"secondaries), full {w.dmax_m / I.MPC:.0f} Mpc, {stats['accepted']} "
-                      f"accepted steps in {dt:.2f} s ({form_desc} oracle)",
-            "rc": rc}
+    return ({"value": stats["accepted"] / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+             "sample": f"first {len(sub)} primaries of the same batch (+{stats['secondaries']} "
+                       f"secondaries), full {w.dmax_m / I.MPC:.0f} Mpc, {stats['accepted']} "
+                       f"accepted steps in {dt:.2f} s ({form_desc} oracle)",
+             "rc": rc}, st.snapshot())
+
+
+def roofline_for(form, attempted, accepted, tables, prop_s):
+    """Roofline of the propagate kernel for one form, from the live CUDA-event time."""
+    if form == "fp64":
+        flops = FLOP_PER_ATTEMPT * attempted + (FLOP_PER_ACCEPTED_TABLES * accepted if tables else 0)
+        ach = flops / prop_s / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                "kernel": "k_propagate_fp64 (2 launches per call + 4 bookkeeping kernels)",
+                "peak_source": "derived: 152 SM x 2 FP64 lanes/clk x 2070 MHz, FMA=2 (of derived)"}
+    ops64 = MIXED_FP64_OPS_PER_ATTEMPT * attempted + MIXED_FP64_OPS_PER_ACCEPTED * accepted
+    ach = ops64 / prop_s / 1e12
+    return {"bound": "alu", "achieved": ach, "peak": FP64_OPS_PEAK_T, "unit": "TFLOP/s",
+            "frac": ach / FP64_OPS_PEAK_T, "traffic": None,
+            "kernel": "k_propagate_mixed (2 launches per call + 4 bookkeeping kernels)",
+            "peak_source": "derived: FP64 pipe 152 SM x 2 lanes/clk x 2070 MHz = 0.629 T ops/s; "
+                           "the residual FP64 ops (error norm, path length) bind this form",
+            "fp32_flop_per_attempt": MIXED_FP32_FLOP_PER_ATTEMPT,
+            "fp32_achieved_tflops": MIXED_FP32_FLOP_PER_ATTEMPT * attempted / prop_s / 1e12,
+            "fp32_peak_tflops": FP32_PEAK_TFLOPS}
+
+
+def mixed_error_statement(w, grid, tables, parts, mixed_state, oracle_state, sim, crp):
+    """Mixed form vs the FP64 oracle on the oracle sample: KS at full distance on the
+    deflection angle and log arrival energy of the sampled primaries."""
+    from scipy import stats
+
+    def defl(d, sel):
+        u = np.stack([d["ux"], d["uy"], d["uz"]], 1)[sel]
+        u0 = np.stack([d["u0x"], d["u0y"], d["u0z"]], 1)[sel]
+        return np.degrees(np.arctan2(np.linalg.norm(np.cross(u, u0), axis=1), np.sum(u * u0, 1)))
+
+    n_s = int(np.sum(oracle_state["uid"] < 2 ** 32))
+    sel_m = mixed_state["uid"] < int(np.min(mixed_state["uid"])) + n_s
+    sel_o = oracle_state["uid"] < 2 ** 32
+    ks_defl = stats.ks_2samp(defl(mixed_state, sel_m), defl(oracle_state, sel_o)).pvalue
+    ks_E = stats.ks_2samp(np.log10(mixed_state["E"][sel_m]), np.log10(oracle_state["E"][sel_o])).pvalue
+    return {"sample_primaries": n_s, "distance_mpc": w.dmax_m / I.MPC,
+            "ks_p_deflection": float(ks_defl), "ks_p_log_energy": float(ks_E),
+            "note": "per-particle angles are chaotic beyond ~15 Mpc (1-ulp floor); see DESIGN.md"}
 
 
 # ---------------------------------------------------------------------------------------
@@ -223,14 +274,15 @@ def run_own(args):
     cols = dict(x=(d(parts.x[:, 0]), d(parts.x[:, 1]), d(parts.x[:, 2])),
                 u=(d(parts.u[:, 0]), d(parts.u[:, 1]), d(parts.u[:, 2])),
                 E=d(parts.E), A=d(parts.A), Z=d(parts.Z), uid=d(parts.uid))
-    prm = dict(form=crp.FORM_FP64, block_size=args.block_size, cadence=args.cadence)
+    form_id = {"fp64": crp.FORM_FP64, "mixed": crp.FORM_MIXED}
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2
 
     def barrier():
         if dist is not None:
             dist.barrier()
 
-    def one_step():
+    def one_step(form):
+        prm = dict(form=form_id[form], block_size=args.block_size, cadence=args.cadence)
         sim.reset()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -246,47 +298,62 @@ def run_own(args):
         c = sim.counts()
         return e0.elapsed_time(e1), p0.elapsed_time(p1), c, rc
 
-    for _ in range(args.warmup):
-        flush.zero_()
-        one_step()
+    def measure(form, with_clocks):
+        for _ in range(args.warmup):
+            flush.zero_()
+            one_step(form)
+        clocks = ClockSampler(local) if with_clocks else None
+        barrier()
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+        r = dict(step_ms=[], prop_ms=[], accepted=0, attempted=0, rcs=[], secondaries=0)
+        for _ in range(args.steps):
+            flush.zero_()
+            ms, pms, c, rc = one_step(form)
+            r["step_ms"].append(ms)
+            r["prop_ms"].append(pms)
+            r["accepted"] += c["accepted"]
+            r["attempted"] += c["attempted"]
+            r["secondaries"] += c["secondaries"]
+            r["rcs"].append(rc)
+        torch.cuda.synchronize()
+        barrier()
+        r["clocks"] = clocks.stop() if clocks else None
+        total_ms = sum(r["step_ms"])
+        if dist is not None:
+            t = torch.tensor([total_ms, r["accepted"], r["attempted"]], dtype=torch.float64, device=dev)
+            mx = t.clone()
+            dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+            dist.all_reduce(t, op=dist.ReduceOp.SUM)
+            r["total_ms_max"], r["accepted_all"], r["attempted_all"] = float(mx[0]), float(t[1]), float(t[2])
+        else:
+            r["total_ms_max"], r["accepted_all"], r["attempted_all"] = total_ms, float(r["accepted"]), float(r["attempted"])
+        r["value"] = r["accepted_all"] / (r["total_ms_max"] * 1e-3)
+        return r
 
-    clocks = ClockSampler(local)
-    barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    step_ms, prop_ms, accepted, attempted, rcs, secondaries = [], [], 0, 0, [], 0
-    for _ in range(args.steps):
-        flush.zero_()
-        ms, pms, c, rc = one_step()
-        step_ms.append(ms)
-        prop_ms.append(pms)
-        accepted += c["accepted"]
-        attempted += c["attempted"]
-        secondaries += c["secondaries"]
-        rcs.append(rc)
-    torch.cuda.synchronize()
-    barrier()
-    clk = clocks.stop()
+    main = measure(args.form, True)
+    other_form = "mixed" if args.form == "fp64" else "fp64"
+    other = None if args.no_other_form else measure(other_form, False)
+    # the error statement needs mixed-form results in the simulation state
+    last_is_mixed = (other is not None and other_form == "mixed") or (other is None and args.form == "mixed")
+    if not last_is_mixed and args.form == "mixed":
+        one_step("mixed")
+        last_is_mixed = True
+    n_sample = min(args.cpu_sample, n)
+    last_state = ({k: sim.read(k, 0, n_sample) for k in crp.COLUMNS} if last_is_mixed else None)
 
-    total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms, accepted, attempted], dtype=torch.float64, device=dev)
-        mx = t.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        total_ms_max, accepted_all, attempted_all = float(mx[0]), float(t[1]), float(t[2])
-    else:
-        total_ms_max, accepted_all, attempted_all = total_ms, float(accepted), float(attempted)
-    value = accepted_all / (total_ms_max * 1e-3)
+    value = main["value"]
+    clk = main["clocks"]
+    accepted, attempted, secondaries = main["accepted"], main["attempted"], main["secondaries"]
+    accepted_all, attempted_all = main["accepted_all"], main["attempted_all"]
+    total_ms_max, rcs = main["total_ms_max"], main["rcs"]
+    prop_ms = main["prop_ms"]
+    prm = dict(form=form_id[args.form], block_size=args.block_size, cadence=args.cadence)
 
     # ---- roofline of the dominant kernel (the propagate call, timed live) ----
     prop_s = sum(prop_ms) * 1e-3
-    flops = FLOP_PER_ATTEMPT * attempted + (FLOP_PER_ACCEPTED_TABLES * accepted if tables is not None else 0)
-    achieved_tflops = flops / prop_s / 1e12
-    roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": None,
-                "kernel": "k_propagate_fp64 (2 launches per call + 4 bookkeeping kernels)",
-                "peak_source": "derived: 152 SM x 2 FP64 lanes/clk x 2070 MHz, FMA=2"}
+    roofline = roofline_for(args.form, attempted, accepted, tables is not None, prop_s)
 
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
@@ -299,7 +366,7 @@ def run_own(args):
                   for t in (v if isinstance(v, tuple) else (v,)))
         out = sim.observe_buffers(cap, pinned=True)
         e2e_times, e2e_steps, d2h = [], 0, 0
-        for it in range(1 + args.steps):
+        for _ in range(args.steps):          # the device path is already warm
             sim.reset()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -307,18 +374,30 @@ def run_own(args):
             sim.propagate(w.tol, w.hmin_m, w.hmax_m, w.dmax_m, stream=stream, **prm)
             sim.sync(0.0, raise_on_error=False)
             rec = sim.observe(out=out)
-            dt = time.perf_counter() - t0
-            if it >= 1:
-                e2e_times.append(dt)
-                e2e_steps += sim.counts()["accepted"]
-                d2h = sim.observe_bytes(len(rec["uid"]))
+            e2e_times.append(time.perf_counter() - t0)
+            e2e_steps += sim.counts()["accepted"]
+            d2h = sim.observe_bytes(len(rec["uid"]))
         e2e = {"value": e2e_steps / sum(e2e_times), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
-    cpu = None
+    cpu, forms = None, None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w, grid, tables, parts, args.cpu_sample, "FP64")
+        cpu, oracle_state = cpu_baseline(w, grid, tables, parts, args.cpu_sample, "FP64")
         cpu.pop("rc", None)
+        if last_state is not None:
+            forms_err = mixed_error_statement(w, grid, tables, parts, last_state, oracle_state, sim, crp)
+        else:
+            forms_err = None
+    else:
+        forms_err = None
+    if other is not None:
+        forms = {args.form: {"value": value, "unit": UNIT},
+                 other_form: {"value": other["value"], "unit": UNIT,
+                              "reject_frac": 1.0 - other["accepted_all"] / max(other["attempted_all"], 1.0),
+                              "roofline": roofline_for(other_form, other["attempted"], other["accepted"],
+                                                       tables is not None, sum(other["prop_ms"]) * 1e-3)},
+                 "mixed_over_fp64": (other["value"] / value) if other_form == "mixed" else (value / other["value"]),
+                 "mixed_error_vs_fp64_oracle": forms_err}
 
     # our kernels in the timed region, per step: inject init + slot count, prepare,
     # work-list build, 2 x (propagate + swap)
@@ -326,7 +405,9 @@ def run_own(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.form == "fp64" else "f32 stages / f64 norm+path / double-float position",
+        "data": "synthetic",
         "config": {"workload": w.name, "particles_per_gpu": n, "grid": f"{w.grid_n}^3 f32",
                    "form": args.form, "dmax_mpc": w.dmax_m / I.MPC, "tol": w.tol,
                    "l2": "inputs larger than L2 (grid 268 MB as float4, state 1.7 GB) and a "
@@ -338,6 +419,7 @@ def run_own(args):
         "secondaries_per_step": secondaries / args.steps,
         "sync_codes": sorted(set(rcs)),
         "roofline": roofline,
+        "forms": forms,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,

@@ -26,6 +26,7 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE
 SOURCES = [
     ("crp_capi.cu", []),
     ("propagate_fp64.cu", ["--fmad=false"]),
+    ("propagate_mixed.cu", []),
 ]
 
 

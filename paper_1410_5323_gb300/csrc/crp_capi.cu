@@ -400,21 +400,32 @@ int crp_tables_create(int32_t z_max, int32_t n_max, int32_t n_nodes, double x0, 
     int ndev = 0;
     CRP_CUDA(cudaGetDeviceCount(&ndev));
     const size_t vb = (size_t)n_sp * n_nodes * sizeof(double);
-    const size_t total = 2 * vb + 2 * (size_t)n_sp + 64;
+    const size_t fb = (size_t)n_sp * n_nodes * sizeof(float);
+    const size_t total = 2 * vb + 2 * fb + 2 * (size_t)n_sp + 64;
+    std::vector<float> lf((size_t)n_sp * n_nodes), pf((size_t)n_sp * n_nodes);
+    for (size_t i = 0; i < lf.size(); ++i) {
+        lf[i] = (float)log10_loss[i];
+        pf[i] = (float)log10_pd[i];
+    }
     crp_tables* t = new crp_tables();
     cudaError_t e = cudaMalloc(&t->mem, total);
     if (e != cudaSuccess) { delete t; return cuda_fail(e, "cudaMalloc(tables)"); }
     char* base = (char*)t->mem;
     e = cudaMemcpy(base, log10_loss, vb, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(base + vb, log10_pd, vb, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(base + 2 * vb, has_loss, n_sp, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(base + 2 * vb + n_sp, has_pd, n_sp, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(base + 2 * vb, lf.data(), fb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(base + 2 * vb + fb, pf.data(), fb, cudaMemcpyHostToDevice);
+    char* flags = base + 2 * vb + 2 * fb;
+    if (e == cudaSuccess) e = cudaMemcpy(flags, has_loss, n_sp, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(flags + n_sp, has_pd, n_sp, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { cudaFree(t->mem); delete t; return cuda_fail(e, "cudaMemcpy(tables)"); }
     TablesDev& d = t->dev;
     d.loss = (const double*)base;
     d.pd = (const double*)(base + vb);
-    d.has_loss = (const uint8_t*)(base + 2 * vb);
-    d.has_pd = (const uint8_t*)(base + 2 * vb + n_sp);
+    d.loss_f = (const float*)(base + 2 * vb);
+    d.pd_f = (const float*)(base + 2 * vb + fb);
+    d.has_loss = (const uint8_t*)flags;
+    d.has_pd = (const uint8_t*)(flags + n_sp);
     d.z_max = z_max; d.n_max = n_max; d.n_nodes = n_nodes;
     d.x0 = x0; d.inv_dx = inv_dx;
     *out = t;
@@ -581,13 +592,19 @@ int crp_propagate(crp_sim* s, const crp_params* prm, double tol, double hmin, do
     if (!(tol > 0.0) || !(hmin > 0.0) || !(hmax >= hmin) || !(dmax > 0.0) || !std::isfinite(hmax) ||
         !std::isfinite(dmax))
         return fail(CRP_ERR_INVALID_ARG, "need tolerance > 0, 0 < min_step <= max_step, max_distance > 0");
-    if (prm->form != CRP_FORM_FP64) return fail(CRP_ERR_INVALID_ARG, "unknown or unavailable form");
+    if (prm->form != CRP_FORM_FP64 && prm->form != CRP_FORM_MIXED)
+        return fail(CRP_ERR_INVALID_ARG, "unknown form");
+    if (prm->form == CRP_FORM_MIXED && s->layout != LAYOUT_F32X4 && s->layout != LAYOUT_BF16X4)
+        return fail(CRP_ERR_INVALID_ARG, "the mixed form reads FP32 or BF16 grids");
+    const bool mixed = prm->form == CRP_FORM_MIXED;
     const int block = prm->block_size > 0 ? prm->block_size : 128;
     if (block % 32 || block > 256) return fail(CRP_ERR_INVALID_ARG, "block_size must be a multiple of 32, <= 256");
     int bps = prm->blocks_per_sm;
     if (bps <= 0) {
         int occ = 0;
-        if (propagate_fp64_occupancy(s->layout, block, &occ) != 0 || occ < 1) occ = 1;
+        const int oe = mixed ? propagate_mixed_occupancy(s->layout, block, &occ)
+                             : propagate_fp64_occupancy(s->layout, block, &occ);
+        if (oe != 0 || occ < 1) occ = 1;
         bps = occ;
     }
     const int grid = (s->sms > 0 ? s->sms : 1) * bps;
@@ -615,7 +632,8 @@ int crp_propagate(crp_sim* s, const crp_params* prm, double tol, double hmin, do
     // never split, so two launches finish the call)
     for (int gen = 0; gen < 2; ++gen) {
         a.list = gen;
-        int e = launch_propagate_fp64(a, s->layout, grid, block, st);
+        int e = mixed ? launch_propagate_mixed(a, s->layout, grid, block, st)
+                      : launch_propagate_fp64(a, s->layout, grid, block, st);
         if (e) return cuda_fail((cudaError_t)e, "propagate kernel launch");
         k_swap<<<1, 1, 0, st>>>(s->ctr, s->capacity, gen);
         CRP_CUDA(cudaGetLastError());

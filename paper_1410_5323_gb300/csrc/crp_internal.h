@@ -24,6 +24,8 @@ struct FieldDev {
 struct TablesDev {
     const double* loss;      // [species][n_nodes] log10 rate
     const double* pd;
+    const float* loss_f;     // FP32 copies (precision form)
+    const float* pd_f;
     const uint8_t* has_loss;
     const uint8_t* has_pd;
     int32_t z_max, n_max, n_nodes, pad_;
@@ -85,5 +87,7 @@ struct PropArgs {
 // Launchers (defined in the kernel translation units).
 int launch_propagate_fp64(const PropArgs& a, int layout, int grid, int block, void* stream);
 int propagate_fp64_occupancy(int layout, int block, int* blocks_per_sm);
+int launch_propagate_mixed(const PropArgs& a, int layout, int grid, int block, void* stream);
+int propagate_mixed_occupancy(int layout, int block, int* blocks_per_sm);
 
 }  // namespace crp

@@ -1,0 +1,448 @@
+// propagate_mixed.cu -- precision form of the propagation hot path (arXiv:1410.5323,
+// Sec. 3.1 module sequence, Sec. 2 3D deflection, Sec. 3.2 regular grids).
+//
+// Same persistent warp-per-particle-batch structure and module sequence as the FP64
+// form, with the arithmetic moved to where GB300 is fast (FP32 is 64x FP64 here):
+//   * lengths in grid-cell units; Cash-Karp stages in FP32 in a local frame: offsets from
+//     the step-start cell, so stage positions stay O(1) and FP32 keeps ~1e-7 of a cell;
+//   * the position itself is a double-float (hi + lo FP32 pair, TwoSum) in cell units,
+//     which resolves 1 kpc steps at 500 Mpc without any FP64 instruction;
+//   * the step-error norm and the accept/reject decision stay FP64: the six FP32 error
+//     components are widened and their squared norms compared against tol^2 in FP64
+//     (|dx|/h is computed as |sum_i e_i u_i|, so no division by h is needed);
+//   * path length s stays FP64 so the observer lands exactly on the distance limit;
+//   * continuous loss and interaction rates in FP32 from FP32 copies of the tables; the
+//     Philox streams and the nucleon rule are the same integers as in the FP64 form.
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+
+#include "crp_internal.h"
+#include "crp_math.cuh"
+
+namespace crp {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+constexpr float A21 = 1.0f / 5.0f;
+constexpr float A31 = 3.0f / 40.0f, A32 = 9.0f / 40.0f;
+constexpr float A41 = 3.0f / 10.0f, A42 = -9.0f / 10.0f, A43 = 6.0f / 5.0f;
+constexpr float A51 = -11.0f / 54.0f, A52 = 5.0f / 2.0f, A53 = -70.0f / 27.0f, A54 = 35.0f / 27.0f;
+constexpr float A61 = 1631.0f / 55296.0f, A62 = 175.0f / 512.0f, A63 = 575.0f / 13824.0f,
+                A64 = 44275.0f / 110592.0f, A65 = 253.0f / 4096.0f;
+constexpr float B1 = 37.0f / 378.0f, B3 = 250.0f / 621.0f, B4 = 125.0f / 594.0f, B6 = 512.0f / 1771.0f;
+constexpr float E1 = -277.0f / 64512.0f, E3 = 6925.0f / 370944.0f, E4 = -6925.0f / 202752.0f,
+                E5 = -277.0f / 14336.0f, E6 = 277.0f / 7084.0f;
+
+struct F3 { float x, y, z; };
+struct DF { float hi, lo; };
+
+// a + b with the rounding error carried in lo (Knuth TwoSum, then renormalise).
+__device__ __forceinline__ DF df_add(DF a, float b) {
+    const float s = a.hi + b;
+    const float bb = s - a.hi;
+    const float e = (a.hi - (s - bb)) + (b - bb) + a.lo;
+    const float hi = s + e;
+    return {hi, e - (hi - s)};
+}
+
+// floor of hi + lo and the fraction in [0, 1).
+__device__ __forceinline__ void df_floor(DF a, int& i, float& f) {
+    const float fl = floorf(a.hi);
+    f = (a.hi - fl) + a.lo;
+    i = (int)fl;
+    if (f < 0.0f) { f += 1.0f; i -= 1; }
+    else if (f >= 1.0f) { f -= 1.0f; i += 1; }
+}
+
+__device__ __forceinline__ int wrap(int i, int n, int pow2) {
+    if (pow2) return i & (n - 1);
+    int a = i % n;
+    return a < 0 ? a + n : a;
+}
+
+// Field-local description in FP32.
+struct FieldF {
+    const void* data;
+    int nx, ny, nz, pow2;
+    float scale;
+};
+
+template <int L>
+__device__ __forceinline__ F3 corner_f(const FieldF& F, int node) {
+    if constexpr (L == LAYOUT_F32X4) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(F.data) + node);
+        return {v.x, v.y, v.z};
+    } else {
+        const ushort4 v = __ldg(reinterpret_cast<const ushort4*>(F.data) + node);
+        return {__uint_as_float((unsigned)v.x << 16), __uint_as_float((unsigned)v.y << 16),
+                __uint_as_float((unsigned)v.z << 16)};
+    }
+}
+
+// Trilinear periodic lookup at (base cell b, fraction f0) + offset p (cells).
+template <int L>
+__device__ __forceinline__ F3 field_f(const FieldF& F, int bx, int by, int bz, F3 f0, F3 p) {
+    const float tx = f0.x + p.x, ty = f0.y + p.y, tz = f0.z + p.z;
+    const float cx = floorf(tx), cy = floorf(ty), cz = floorf(tz);
+    const float fx = tx - cx, fy = ty - cy, fz = tz - cz;
+    const int ix = wrap(bx + (int)cx, F.nx, F.pow2), iy = wrap(by + (int)cy, F.ny, F.pow2),
+              iz = wrap(bz + (int)cz, F.nz, F.pow2);
+    const int ix1 = ix + 1 == F.nx ? 0 : ix + 1, iy1 = iy + 1 == F.ny ? 0 : iy + 1,
+              iz1 = iz + 1 == F.nz ? 0 : iz + 1;
+    const int r00 = (ix * F.ny + iy) * F.nz, r01 = (ix * F.ny + iy1) * F.nz;
+    const int r10 = (ix1 * F.ny + iy) * F.nz, r11 = (ix1 * F.ny + iy1) * F.nz;
+    const F3 g0 = corner_f<L>(F, r00 + iz), g1 = corner_f<L>(F, r00 + iz1);
+    const F3 g2 = corner_f<L>(F, r01 + iz), g3 = corner_f<L>(F, r01 + iz1);
+    const F3 g4 = corner_f<L>(F, r10 + iz), g5 = corner_f<L>(F, r10 + iz1);
+    const F3 g6 = corner_f<L>(F, r11 + iz), g7 = corner_f<L>(F, r11 + iz1);
+    const float gx = 1.0f - fx, gy = 1.0f - fy, gz = 1.0f - fz;
+    const float w00 = gx * gy, w01 = gx * fy, w10 = fx * gy, w11 = fx * fy;
+    float w;
+    F3 B;
+    w = w00 * gz; B.x = w * g0.x;          B.y = w * g0.y;          B.z = w * g0.z;
+    w = w00 * fz; B.x = fmaf(w, g1.x, B.x); B.y = fmaf(w, g1.y, B.y); B.z = fmaf(w, g1.z, B.z);
+    w = w01 * gz; B.x = fmaf(w, g2.x, B.x); B.y = fmaf(w, g2.y, B.y); B.z = fmaf(w, g2.z, B.z);
+    w = w01 * fz; B.x = fmaf(w, g3.x, B.x); B.y = fmaf(w, g3.y, B.y); B.z = fmaf(w, g3.z, B.z);
+    w = w10 * gz; B.x = fmaf(w, g4.x, B.x); B.y = fmaf(w, g4.y, B.y); B.z = fmaf(w, g4.z, B.z);
+    w = w10 * fz; B.x = fmaf(w, g5.x, B.x); B.y = fmaf(w, g5.y, B.y); B.z = fmaf(w, g5.z, B.z);
+    w = w11 * gz; B.x = fmaf(w, g6.x, B.x); B.y = fmaf(w, g6.y, B.y); B.z = fmaf(w, g6.z, B.z);
+    w = w11 * fz; B.x = fmaf(w, g7.x, B.x); B.y = fmaf(w, g7.y, B.y); B.z = fmaf(w, g7.z, B.z);
+    if constexpr (L != LAYOUT_F32X4) { B.x *= F.scale; B.y *= F.scale; B.z *= F.scale; }
+    return B;
+}
+
+struct Y { F3 p, u; };   // local position offset (cells) and direction
+
+template <int L>
+__device__ __forceinline__ Y deriv_f(const FieldF& F, int bx, int by, int bz, F3 f0, float kappa,
+                                     const Y& y) {
+    const F3 B = field_f<L>(F, bx, by, bz, f0, y.p);
+    Y k;
+    k.p = y.u;
+    k.u.x = kappa * (y.u.y * B.z - y.u.z * B.y);
+    k.u.y = kappa * (y.u.z * B.x - y.u.x * B.z);
+    k.u.z = kappa * (y.u.x * B.y - y.u.y * B.x);
+    return k;
+}
+
+__device__ __forceinline__ float clampf_(float v, float lo, float hi) { return fminf(fmaxf(v, lo), hi); }
+
+// r2^p for r2 > 0 (controller exponents on the squared ratio).
+__device__ __forceinline__ float powf_pos(float r2, float p) { return exp2f(p * __log2f(r2)); }
+
+__device__ __forceinline__ bool fin3(F3 a) { return isfinite(a.x) && isfinite(a.y) && isfinite(a.z); }
+
+template <int L>
+__global__ void __launch_bounds__(256) k_propagate_mixed(const PropArgs a) {
+    const int lane = threadIdx.x & 31;
+    Counters* C = a.ctr;
+    const int32_t* work = a.lists[a.list];
+    int32_t* next = a.lists[1 - a.list];
+    const unsigned long long n_work = *(volatile unsigned long long*)&C->count[a.list];
+    const float INF = __int_as_float(0x7f800000);
+    const SimState& S = a.st;
+    const double tol2 = a.tol * a.tol;
+    const float inv_tol2 = (float)(1.0 / tol2);
+
+    int slot = -1;
+    // particle state (cell units)
+    DF Rx{0, 0}, Ry{0, 0}, Rz{0, 0};
+    F3 u{0, 0, 0};
+    double E = 0, s_c = 0;
+    float hprop = 0, tau = 0;
+    int A = 0, Z = 0, n_int = 0, gid = 0;
+    unsigned long long uid = 0;
+    long long n_steps = 0, n_att = 0, taken = 0;
+    // field of the current particle
+    FieldF F{};
+    double sp = 1.0, inv_sp = 1.0, ox = 0, oy = 0, oz = 0, dmax_c = 0;
+    float hmin_c = 0, hmax_c = 0, sp_f = 1.0f;
+    // step state
+    bool new_step = true;
+    int bx = 0, by = 0, bz = 0;
+    F3 f0{0, 0, 0};
+    float h = 0, h_first = 0, h_propc = 0, h_int = 0, h_dist = 0, rl = 0, rpd = 0, kappa = 0;
+    int rejected = 0;
+    long long att_step = 0;
+    unsigned long long acc_tot = 0, att_tot = 0, sec_tot = 0;
+    unsigned bits = 0;
+
+    auto to_x = [&](DF r, double o) { return o + ((double)r.hi + (double)r.lo) * sp; };
+    auto from_x = [&](double x, double o) {
+        const double rr = (x - o) * inv_sp;
+        const float hi = (float)rr;
+        return DF{hi, (float)(rr - (double)hi)};
+    };
+    auto store = [&](int status, bool exact_end) {
+        S.x[slot] = to_x(Rx, ox); S.y[slot] = to_x(Ry, oy); S.z[slot] = to_x(Rz, oz);
+        S.ux[slot] = u.x; S.uy[slot] = u.y; S.uz[slot] = u.z;
+        S.E[slot] = E;
+        S.s[slot] = exact_end ? a.dmax : s_c * sp;
+        S.hprop[slot] = (double)hprop * sp;
+        S.tau[slot] = tau;
+        S.A[slot] = A; S.Z[slot] = Z; S.n_int[slot] = n_int; S.status[slot] = status;
+        S.n_steps[slot] = n_steps; S.n_att[slot] = n_att;
+        if (status != CRP_STATUS_ACTIVE_) {
+            const unsigned long long d = atomicAdd(&C->n_done, 1ull);
+            a.done_list[d] = slot;
+        }
+        slot = -1;
+    };
+
+    for (;;) {
+        const bool idle = slot < 0;
+        const unsigned im = __ballot_sync(kFull, idle);
+        if (im) {
+            unsigned long long base = n_work;
+            if (lane == 0 && *(volatile unsigned long long*)&C->head < n_work)
+                base = atomicAdd(&C->head, (unsigned long long)__popc(im));
+            base = __shfl_sync(kFull, base, 0);
+            if (idle) {
+                const unsigned long long pos = base + __popc(im & ((1u << lane) - 1u));
+                if (pos < n_work) {
+                    slot = work[pos];
+                    gid = S.grid_id[slot];
+                    const FieldDev& G = a.fields[gid];
+                    F.data = G.data; F.nx = G.nx; F.ny = G.ny; F.nz = G.nz; F.pow2 = G.pow2;
+                    F.scale = (float)G.scale;
+                    sp = G.spacing; inv_sp = G.inv_spacing; sp_f = (float)sp;
+                    ox = G.ox; oy = G.oy; oz = G.oz;
+                    hmin_c = (float)(a.hmin * inv_sp);
+                    hmax_c = (float)(a.hmax * inv_sp);
+                    dmax_c = a.dmax * inv_sp;
+                    Rx = from_x(S.x[slot], ox); Ry = from_x(S.y[slot], oy); Rz = from_x(S.z[slot], oz);
+                    u = {(float)S.ux[slot], (float)S.uy[slot], (float)S.uz[slot]};
+                    E = S.E[slot];
+                    s_c = S.s[slot] * inv_sp;
+                    hprop = (float)(S.hprop[slot] * inv_sp);
+                    tau = (float)S.tau[slot];
+                    A = S.A[slot]; Z = S.Z[slot]; n_int = S.n_int[slot];
+                    uid = (unsigned long long)S.uid[slot];
+                    n_steps = S.n_steps[slot]; n_att = S.n_att[slot];
+                    taken = 0;
+                    new_step = true;
+                }
+            }
+        }
+        if (__ballot_sync(kFull, slot >= 0) == 0) break;
+
+        for (int it = 0; it < a.cadence; ++it) {
+            if (slot < 0) continue;
+            if (new_step) {
+                // rates at gamma0 (FP32 tables), per cell
+                rl = 0.0f;
+                rpd = 0.0f;
+                if (a.has_tables) {
+                    const TablesDev& T = a.tab;
+                    const int N = A - Z;
+                    if (Z < 0 || N < 0 || Z > T.z_max || N > T.n_max) {
+                        bits |= BIT_RANGE;
+                        store(CRP_STATUS_RANGE_, false);
+                        continue;
+                    }
+                    const int sp_i = Z * (T.n_max + 1) + N;
+                    const float g0 = (float)E / ((float)A * (float)kMpC2);
+                    float t = (log10f(g0) - (float)T.x0) * (float)T.inv_dx;
+                    t = clampf_(t, 0.0f, (float)(T.n_nodes - 1));
+                    int j = (int)floorf(t);
+                    if (j > T.n_nodes - 2) j = T.n_nodes - 2;
+                    const float fr = t - (float)j;
+                    if (T.has_loss[sp_i]) {
+                        const float* R = T.loss_f + (long long)sp_i * T.n_nodes;
+                        const float v0 = __ldg(R + j), v1 = __ldg(R + j + 1);
+                        rl = exp10f(fmaf(fr, v1 - v0, v0)) * sp_f;
+                    }
+                    if (T.has_pd[sp_i]) {
+                        const float* R = T.pd_f + (long long)sp_i * T.n_nodes;
+                        const float v0 = __ldg(R + j), v1 = __ldg(R + j + 1);
+                        rpd = exp10f(fmaf(fr, v1 - v0, v0)) * sp_f;
+                    }
+                }
+                h_propc = clampf_(hprop, hmin_c, hmax_c);
+                const float h_loss = rl > 0.0f ? 0.1f / rl : INF;
+                h_int = rpd > 0.0f ? fmaxf(tau, 0.0f) / rpd : INF;
+                h_dist = (float)(dmax_c - s_c);
+                h = h_propc;
+                if (h_loss < h) h = h_loss;
+                if (h_int < h) h = h_int;
+                if (h_dist < h) h = h_dist;
+                h_first = h;
+                rejected = 0;
+                att_step = 0;
+                kappa = (float)Z * (float)(kC * sp) / (float)E;
+                df_floor(Rx, bx, f0.x);
+                df_floor(Ry, by, f0.y);
+                df_floor(Rz, bz, f0.z);
+                new_step = false;
+            }
+            // ---- one Cash-Karp attempt in the local frame (FP32) ----
+            const Y y0{{0.0f, 0.0f, 0.0f}, u};
+            const Y k1 = deriv_f<L>(F, bx, by, bz, f0, kappa, y0);
+            Y t;
+#define STG(expr)                                                                              \
+            t.p.x = h * (expr(p.x)); t.p.y = h * (expr(p.y)); t.p.z = h * (expr(p.z));         \
+            t.u.x = fmaf(h, (expr(u.x)), u.x); t.u.y = fmaf(h, (expr(u.y)), u.y);               \
+            t.u.z = fmaf(h, (expr(u.z)), u.z);
+#define S2(c) (A21 * k1.c)
+            STG(S2)
+            const Y k2 = deriv_f<L>(F, bx, by, bz, f0, kappa, t);
+#define S3(c) (A31 * k1.c + A32 * k2.c)
+            STG(S3)
+            const Y k3 = deriv_f<L>(F, bx, by, bz, f0, kappa, t);
+#define S4(c) (A41 * k1.c + A42 * k2.c + A43 * k3.c)
+            STG(S4)
+            const Y k4 = deriv_f<L>(F, bx, by, bz, f0, kappa, t);
+#define S5(c) (A51 * k1.c + A52 * k2.c + A53 * k3.c + A54 * k4.c)
+            STG(S5)
+            const Y k5 = deriv_f<L>(F, bx, by, bz, f0, kappa, t);
+#define S6(c) (A61 * k1.c + A62 * k2.c + A63 * k3.c + A64 * k4.c + A65 * k5.c)
+            STG(S6)
+            const Y k6 = deriv_f<L>(F, bx, by, bz, f0, kappa, t);
+#define SB(c) (B1 * k1.c + B3 * k3.c + B4 * k4.c + B6 * k6.c)
+#define SE(c) (E1 * k1.c + E3 * k3.c + E4 * k4.c + E5 * k5.c + E6 * k6.c)
+            const F3 dp{h * SB(p.x), h * SB(p.y), h * SB(p.z)};
+            const F3 un{fmaf(h, SB(u.x), u.x), fmaf(h, SB(u.y), u.y), fmaf(h, SB(u.z), u.z)};
+            const F3 ex{SE(p.x), SE(p.y), SE(p.z)};                  // |dx| / h
+            const F3 eu{h * SE(u.x), h * SE(u.y), h * SE(u.z)};      // |du|
+#undef STG
+#undef S2
+#undef S3
+#undef S4
+#undef S5
+#undef S6
+#undef SB
+#undef SE
+            att_step += 1;
+            // ---- FP64 error norm and accept/reject ----
+            const double qx = fma((double)ex.z, (double)ex.z,
+                                  fma((double)ex.y, (double)ex.y, (double)ex.x * (double)ex.x));
+            const double qu = fma((double)eu.z, (double)eu.z,
+                                  fma((double)eu.y, (double)eu.y, (double)eu.x * (double)eu.x));
+            const bool accept = (fmax(qx, qu) <= tol2) || (h <= hmin_c);
+            const float r2 = fmaxf(ex.x * ex.x + ex.y * ex.y + ex.z * ex.z,
+                                   eu.x * eu.x + eu.y * eu.y + eu.z * eu.z) * inv_tol2;
+            if (!accept) {
+                const float shrink = clampf_(0.95f * powf_pos(r2, -0.125f), 0.1f, 1.0f);
+                h = fmaxf(h * shrink, hmin_c);
+                rejected = 1;
+                continue;
+            }
+            if (!(fin3(dp) && fin3(un))) {
+                n_att += att_step;
+                att_tot += att_step;
+                bits |= BIT_NAN;
+                store(CRP_STATUS_NAN_, false);
+                continue;
+            }
+            const bool fires = (rpd > 0.0f && h == h_int);
+            unsigned long long q = 0;
+            if (fires) {
+                q = atomicAdd(&C->reserve, 1ull);
+                if (q >= (unsigned long long)a.capacity) {
+                    bits |= BIT_QUEUE_FULL;
+                    store(CRP_STATUS_ACTIVE_, false);
+                    continue;
+                }
+            }
+            // ---- accept ----
+            n_att += att_step;
+            att_tot += att_step;
+            Rx = df_add(Rx, dp.x);
+            Ry = df_add(Ry, dp.y);
+            Rz = df_add(Rz, dp.z);
+            u = un;
+            bool done = (h == h_dist);
+            s_c = s_c + (double)h;
+            if (s_c >= dmax_c) done = true;
+            if (done) s_c = dmax_c;
+            n_steps += 1;
+            acc_tot += 1;
+            taken += 1;
+            const float grow = (r2 == 0.0f) ? 5.0f : clampf_(0.95f * powf_pos(r2, -0.1f), 0.2f, 5.0f);
+            float hnext = h * grow;
+            if (!rejected && h_first < h_propc) hnext = fmaxf(hnext, h_propc);
+            hprop = clampf_(hnext, hmin_c, hmax_c);
+            if (rl > 0.0f) E = E * (double)__expf(-h * rl);
+            if (rpd > 0.0f) {
+                if (fires) {
+                    const unsigned kk = (unsigned)(n_int + 1);
+                    const int dz = nucleon_proton(a.seed, uid, kk, A, Z) ? 1 : 0;
+                    const double E_sec = E / (double)A;
+                    const double E_par = E * (double)(A - 1) / (double)A;
+                    const long long qs = (long long)q;
+                    const unsigned long long uid2 = (1ull << 32) + uid * 64ull + kk;
+                    S.x[qs] = to_x(Rx, ox); S.y[qs] = to_x(Ry, oy); S.z[qs] = to_x(Rz, oz);
+                    S.ux[qs] = u.x; S.uy[qs] = u.y; S.uz[qs] = u.z;
+                    S.E[qs] = E_sec;
+                    S.s[qs] = done ? a.dmax : s_c * sp;
+                    S.hprop[qs] = __longlong_as_double(0x7ff0000000000000LL);
+                    S.tau[qs] = -crp_log(uniform01(a.seed, uid2, 0u, 0u));
+                    S.u0x[qs] = S.u0x[slot]; S.u0y[qs] = S.u0y[slot]; S.u0z[qs] = S.u0z[slot];
+                    S.A[qs] = 1; S.Z[qs] = dz; S.n_int[qs] = 0; S.grid_id[qs] = gid;
+                    S.uid[qs] = (long long)uid2;
+                    S.n_steps[qs] = 0; S.n_att[qs] = 0;
+                    S.status[qs] = done ? CRP_STATUS_DONE_ : CRP_STATUS_ACTIVE_;
+                    if (done) {
+                        const unsigned long long d = atomicAdd(&C->n_done, 1ull);
+                        a.done_list[d] = (int32_t)qs;
+                    } else {
+                        const unsigned long long p = atomicAdd(&C->count[1 - a.list], 1ull);
+                        next[p] = (int32_t)qs;
+                    }
+                    sec_tot += 1;
+                    A = A - 1;
+                    Z = Z - dz;
+                    E = E_par;
+                    n_int = (int)kk;
+                    tau = (float)(-crp_log(uniform01(a.seed, uid, kk, 0u)));
+                } else {
+                    tau = tau - h * rpd;
+                }
+            }
+            new_step = true;
+            if (done) {
+                store(CRP_STATUS_DONE_, true);
+            } else if (a.max_steps > 0 && taken >= a.max_steps) {
+                store(CRP_STATUS_ACTIVE_, false);
+            }
+        }
+    }
+
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        acc_tot += __shfl_xor_sync(kFull, acc_tot, o);
+        att_tot += __shfl_xor_sync(kFull, att_tot, o);
+        sec_tot += __shfl_xor_sync(kFull, sec_tot, o);
+        bits |= __shfl_xor_sync(kFull, bits, o);
+    }
+    if (lane == 0) {
+        if (acc_tot) atomicAdd(&C->accepted, acc_tot);
+        if (att_tot) atomicAdd(&C->attempted, att_tot);
+        if (sec_tot) atomicAdd(&C->secondaries, sec_tot);
+        if (bits) atomicOr(&C->status_bits, bits);
+    }
+}
+
+}  // namespace
+
+int launch_propagate_mixed(const PropArgs& a, int layout, int grid, int block, void* stream) {
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    switch (layout) {
+    case LAYOUT_F32X4: k_propagate_mixed<LAYOUT_F32X4><<<grid, block, 0, st>>>(a); break;
+    case LAYOUT_BF16X4: k_propagate_mixed<LAYOUT_BF16X4><<<grid, block, 0, st>>>(a); break;
+    default: return (int)cudaErrorInvalidValue;
+    }
+    return (int)cudaGetLastError();
+}
+
+int propagate_mixed_occupancy(int layout, int block, int* blocks_per_sm) {
+    cudaError_t e = cudaErrorInvalidValue;
+    if (layout == LAYOUT_F32X4)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_propagate_mixed<LAYOUT_F32X4>, block, 0);
+    else if (layout == LAYOUT_BF16X4)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_propagate_mixed<LAYOUT_BF16X4>, block, 0);
+    return (int)e;
+}
+
+}  // namespace crp

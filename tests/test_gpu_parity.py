@@ -247,3 +247,28 @@ def test_invalid_arguments_rejected():
         sim.propagate(-1.0, I.KPC, I.MPC, I.MPC)
     with pytest.raises(crp.CrpError):
         sim.propagate(1e-4, I.MPC, I.KPC, I.MPC)   # max step below min step
+
+
+def test_full_size_workload_sampled_bit_identical(oracle_lib):
+    """The whole 10^6-nuclei 256^3 batch in the launch configuration the benchmark times;
+    256 primaries spread over the batch, with every secondary they produced, are checked bit
+    for bit against the oracle run on those primaries alone (particles are independent)."""
+    w = I.workload("fp64_256cube_1M_nuclei")
+    g = I.kolmogorov_grid(w.grid_n, w.spacing_m, w.lmin_cells, w.lmax_cells, w.brms_t,
+                          w.grid_seed).astype(np.float32)
+    t = I.synthetic_tables()
+    p = I.make_particles(w.n_particles, w.particle_seed, w.species, w.energy)
+    cap = int(len(p) + np.sum(p.A.astype(np.int64) - 1))
+    sim, rc = run_gpu([g], p, t, w.tol, w.hmin_m, w.hmax_m, w.dmax_m, seed=w.rng_seed, capacity=cap)
+    assert rc == 0
+    gs = sim.state()
+    pick = np.sort(np.random.default_rng(0).choice(len(p), 256, replace=False))
+    sub = p.take(pick)
+    st, orc = run_oracle([g], sub, t, w.tol, w.hmin_m, w.hmax_m, w.dmax_m, seed=w.rng_seed,
+                         capacity=int(256 * 56))
+    assert orc == 0
+    o = st.snapshot()
+    root = np.where(gs["uid"] < 2 ** 32, gs["uid"], (gs["uid"] - 2 ** 32) // 64)
+    keep = np.isin(root, pick)
+    assert_bit_identical({k: v[keep] for k, v in gs.items()}, o)
+    assert np.all(gs["status"] == O.DONE)
