@@ -68,6 +68,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--block-size", type=int, default=0)
     ap.add_argument("--cadence", type=int, default=0)
+    ap.add_argument("--order", type=int, default=0, help="work-list order (CRP_ORDER_*); 0: default")
+    ap.add_argument("--slice-steps", type=int, default=-1,
+                    help="> 0: graph loop of slices of this many steps; 0: one call; -1: workload default")
     return ap.parse_args()
 
 
@@ -80,12 +83,28 @@ def dist_env():
 
 
 def build_inputs(w: I.Workload, n: int, rank: int):
+    """Field grids (list), tables, particles of the workload (this rank's batch)."""
+    tables = I.synthetic_tables() if w.interactions else None
+    if w.n_grids > 1:
+        grids, _ = I.batched_grids(w)
+        per = max(1, n // w.n_grids)
+        parts = I.batched_particles(w, per, seed=w.particle_seed + 7919 * rank)
+        parts.uid[:] += rank * len(parts)
+        return grids, tables, parts
     grid = I.kolmogorov_grid(w.grid_n, w.spacing_m, w.lmin_cells, w.lmax_cells, w.brms_t,
                              w.grid_seed).astype(np.float32)
-    tables = I.synthetic_tables() if w.interactions else None
     parts = I.make_particles(n, w.particle_seed + 7919 * rank, w.species, w.energy,
                              uid_offset=rank * n)
-    return grid, tables, parts
+    return [grid], tables, parts
+
+
+def oracle_sample_index(w: I.Workload, n_total: int, sample: int) -> np.ndarray:
+    """Primaries the oracle reruns: the first ones, or the first of every realisation."""
+    if w.n_grids > 1:
+        per_grid = n_total // w.n_grids
+        k = max(1, min(per_grid, sample // w.n_grids))
+        return (np.arange(w.n_grids)[:, None] * per_grid + np.arange(k)[None, :]).ravel()
+    return np.arange(min(sample, n_total))
 
 
 def capacity_for(parts) -> int:
@@ -143,22 +162,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(w, grid, tables, parts, sample: int, form_desc: str):
+def cpu_baseline(w, grids, tables, parts, sample: int, form_desc: str):
     """The oracle, as it stands, on a bounded sample of the same workload."""
     import oracle as O
 
-    sub = parts.take(np.arange(min(sample, len(parts))))
+    sub = parts.take(oracle_sample_index(w, len(parts), sample))
     cap = capacity_for(sub)
     st = O.OracleState(cap)
     ot = O.OracleTables(tables) if tables is not None else None
     O.inject(st, sub, w.rng_seed, ot)
     threads = os.cpu_count() or 1
     t0 = time.perf_counter()
-    rc, stats = O.propagate(st, [O.OracleField(grid, w.spacing_m)], ot, w.tol, w.hmin_m, w.hmax_m,
-                            w.dmax_m, seed=w.rng_seed, n_threads=threads)
+    rc, stats = O.propagate(st, [O.OracleField(g, w.spacing_m) for g in grids], ot, w.tol,
+                            w.hmin_m, w.hmax_m, w.dmax_m, seed=w.rng_seed, n_threads=threads)
     dt = time.perf_counter() - t0
     return ({"value": stats["accepted"] / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-             "sample": f"first {len(sub)} primaries of the same batch (+{stats['secondaries']} "
+             "sample": f"{len(sub)} primaries of the same batch (+{stats['secondaries']} "
                        f"secondaries), full {w.dmax_m / I.MPC:.0f} Mpc, {stats['accepted']} "
                        f"accepted steps in {dt:.2f} s ({form_desc} oracle)",
              "rc": rc}, st.snapshot())
@@ -185,7 +204,7 @@ def roofline_for(form, attempted, accepted, tables, prop_s):
             "fp32_peak_tflops": FP32_PEAK_TFLOPS}
 
 
-def mixed_error_statement(w, grid, tables, parts, mixed_state, oracle_state, sim, crp):
+def mixed_error_statement(w, mixed_state, oracle_state):
     """Mixed form vs the FP64 oracle on the oracle sample: KS at full distance on the
     deflection angle and log arrival energy of the sampled primaries."""
     from scipy import stats
@@ -196,7 +215,7 @@ def mixed_error_statement(w, grid, tables, parts, mixed_state, oracle_state, sim
         return np.degrees(np.arctan2(np.linalg.norm(np.cross(u, u0), axis=1), np.sum(u * u0, 1)))
 
     n_s = int(np.sum(oracle_state["uid"] < 2 ** 32))
-    sel_m = mixed_state["uid"] < int(np.min(mixed_state["uid"])) + n_s
+    sel_m = mixed_state["uid"] < 2 ** 32
     sel_o = oracle_state["uid"] < 2 ** 32
     ks_defl = stats.ks_2samp(defl(mixed_state, sel_m), defl(oracle_state, sel_o)).pvalue
     ks_E = stats.ks_2samp(np.log10(mixed_state["E"][sel_m]), np.log10(oracle_state["E"][sel_o])).pvalue
@@ -212,20 +231,22 @@ def run_reference(args):
         return 0
     w = I.workload(args.workload)
     n = args.n_particles or w.n_particles
-    grid, tables, parts = build_inputs(w, n, 0)
+    grids, tables, parts = build_inputs(w, n, 0)
     import oracle as O
 
     per_step = max(1, args.cpu_sample)
     times, steps_acc = [], []
     for it in range(args.warmup + args.steps):
-        lo = (it * per_step) % max(1, n - per_step)
-        sub = parts.take(np.arange(lo, lo + per_step))
+        lo = (it * per_step) % max(1, len(parts) - per_step)
+        sub = parts.take(np.arange(lo, lo + per_step) if w.n_grids == 1 else
+                         np.random.default_rng(it).choice(len(parts), per_step, replace=False))
         st = O.OracleState(capacity_for(sub))
         ot = O.OracleTables(tables) if tables is not None else None
         O.inject(st, sub, w.rng_seed, ot)
         t0 = time.perf_counter()
-        rc, stats = O.propagate(st, [O.OracleField(grid, w.spacing_m)], ot, w.tol, w.hmin_m,
-                                w.hmax_m, w.dmax_m, seed=w.rng_seed, n_threads=os.cpu_count() or 1)
+        rc, stats = O.propagate(st, [O.OracleField(g, w.spacing_m) for g in grids], ot, w.tol,
+                                w.hmin_m, w.hmax_m, w.dmax_m, seed=w.rng_seed,
+                                n_threads=os.cpu_count() or 1)
         dt = time.perf_counter() - t0
         if it >= args.warmup:
             times.append(dt)
@@ -262,19 +283,29 @@ def run_own(args):
     dev = torch.device("cuda", local)
     w = I.workload(args.workload)
     n = args.n_particles or w.n_particles
-    grid, tables, parts = build_inputs(w, n, rank)
+    grids, tables, parts = build_inputs(w, n, rank)
+    n = len(parts)
     cap = capacity_for(parts)
 
-    field = crp.Field(grid, w.spacing_m)
+    fields = [crp.Field(g, w.spacing_m) for g in grids]
     tabs = crp.Tables(tables) if tables is not None else None
-    sim = crp.Simulation([field], tabs, seed=w.rng_seed, capacity=cap)
+    sim = crp.Simulation(fields, tabs, seed=w.rng_seed, capacity=cap)
+    slice_steps = args.slice_steps if args.slice_steps >= 0 else (16000 if w.n_grids > 1 else 0)
+    order = args.order or (3 if w.n_grids > 1 else 2)
     stream = torch.cuda.current_stream(dev)
 
     d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     cols = dict(x=(d(parts.x[:, 0]), d(parts.x[:, 1]), d(parts.x[:, 2])),
                 u=(d(parts.u[:, 0]), d(parts.u[:, 1]), d(parts.u[:, 2])),
-                E=d(parts.E), A=d(parts.A), Z=d(parts.Z), uid=d(parts.uid))
+                E=d(parts.E), A=d(parts.A), Z=d(parts.Z), uid=d(parts.uid), grid_id=d(parts.grid_id))
     form_id = {"fp64": crp.FORM_FP64, "mixed": crp.FORM_MIXED}
+
+    def run_propagate(prm):
+        if slice_steps > 0:
+            sim.propagate_loop(w.tol, w.hmin_m, w.hmax_m, w.dmax_m, max_steps=slice_steps,
+                               stream=stream, **prm)
+        else:
+            sim.propagate(w.tol, w.hmin_m, w.hmax_m, w.dmax_m, stream=stream, **prm)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2
 
     def barrier():
@@ -282,7 +313,7 @@ def run_own(args):
             dist.barrier()
 
     def one_step(form):
-        prm = dict(form=form_id[form], block_size=args.block_size, cadence=args.cadence)
+        prm = dict(form=form_id[form], block_size=args.block_size, cadence=args.cadence, order=order)
         sim.reset()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -291,7 +322,7 @@ def run_own(args):
         e0.record(stream)
         sim.inject(**cols, stream=stream)
         p0.record(stream)
-        sim.propagate(w.tol, w.hmin_m, w.hmax_m, w.dmax_m, stream=stream, **prm)
+        run_propagate(prm)
         p1.record(stream)
         e1.record(stream)
         rc = sim.sync(0.0, raise_on_error=False)
@@ -307,7 +338,7 @@ def run_own(args):
         torch.cuda.synchronize()
         if clocks:
             clocks.start()
-        r = dict(step_ms=[], prop_ms=[], accepted=0, attempted=0, rcs=[], secondaries=0)
+        r = dict(step_ms=[], prop_ms=[], accepted=0, attempted=0, rcs=[], secondaries=0, launches=0)
         for _ in range(args.steps):
             flush.zero_()
             ms, pms, c, rc = one_step(form)
@@ -316,6 +347,7 @@ def run_own(args):
             r["accepted"] += c["accepted"]
             r["attempted"] += c["attempted"]
             r["secondaries"] += c["secondaries"]
+            r["launches"] += c["launches"]
             r["rcs"].append(rc)
         torch.cuda.synchronize()
         barrier()
@@ -340,8 +372,9 @@ def run_own(args):
     if not last_is_mixed and args.form == "mixed":
         one_step("mixed")
         last_is_mixed = True
-    n_sample = min(args.cpu_sample, n)
-    last_state = ({k: sim.read(k, 0, n_sample) for k in crp.COLUMNS} if last_is_mixed else None)
+    sample_idx = oracle_sample_index(w, n, args.cpu_sample)
+    last_state = ({k: sim.read(k, 0, int(sample_idx[-1]) + 1)[sample_idx] for k in crp.COLUMNS}
+                  if last_is_mixed else None)
 
     value = main["value"]
     clk = main["clocks"]
@@ -349,7 +382,7 @@ def run_own(args):
     accepted_all, attempted_all = main["accepted_all"], main["attempted_all"]
     total_ms_max, rcs = main["total_ms_max"], main["rcs"]
     prop_ms = main["prop_ms"]
-    prm = dict(form=form_id[args.form], block_size=args.block_size, cadence=args.cadence)
+    prm = dict(form=form_id[args.form], block_size=args.block_size, cadence=args.cadence, order=order)
 
     # ---- roofline of the dominant kernel (the propagate call, timed live) ----
     prop_s = sum(prop_ms) * 1e-3
@@ -361,7 +394,8 @@ def run_own(args):
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
         hcols = dict(x=(pin(parts.x[:, 0]), pin(parts.x[:, 1]), pin(parts.x[:, 2])),
                      u=(pin(parts.u[:, 0]), pin(parts.u[:, 1]), pin(parts.u[:, 2])),
-                     E=pin(parts.E), A=pin(parts.A), Z=pin(parts.Z), uid=pin(parts.uid))
+                     E=pin(parts.E), A=pin(parts.A), Z=pin(parts.Z), uid=pin(parts.uid),
+                     grid_id=pin(parts.grid_id))
         h2d = sum(int(t.numel() * t.element_size()) for v in hcols.values()
                   for t in (v if isinstance(v, tuple) else (v,)))
         out = sim.observe_buffers(cap, pinned=True)
@@ -371,7 +405,7 @@ def run_own(args):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             sim.inject(**hcols, stream=stream)
-            sim.propagate(w.tol, w.hmin_m, w.hmax_m, w.dmax_m, stream=stream, **prm)
+            run_propagate(prm)
             sim.sync(0.0, raise_on_error=False)
             rec = sim.observe(out=out)
             e2e_times.append(time.perf_counter() - t0)
@@ -382,10 +416,10 @@ def run_own(args):
 
     cpu, forms = None, None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu, oracle_state = cpu_baseline(w, grid, tables, parts, args.cpu_sample, "FP64")
+        cpu, oracle_state = cpu_baseline(w, grids, tables, parts, args.cpu_sample, "FP64")
         cpu.pop("rc", None)
         if last_state is not None:
-            forms_err = mixed_error_statement(w, grid, tables, parts, last_state, oracle_state, sim, crp)
+            forms_err = mixed_error_statement(w, last_state, oracle_state)
         else:
             forms_err = None
     else:
@@ -399,16 +433,21 @@ def run_own(args):
                  "mixed_over_fp64": (other["value"] / value) if other_form == "mixed" else (value / other["value"]),
                  "mixed_error_vs_fp64_oracle": forms_err}
 
-    # our kernels in the timed region, per step: inject init + slot count, prepare,
-    # work-list build, 2 x (propagate + swap)
-    launches_per_step = 2 + 2 + 2 * 2
+    # our kernels in the timed region: per step inject init + slot count; per propagate slice
+    # prepare + work-list build (1 kernel, or 3 for the ordered builds) + 2 x (propagate + swap);
+    # the graph loop adds an init kernel per step and a condition kernel per slice.
+    slices = main["launches"] / 2
+    per_slice = 1 + (1 if order == 1 else 3) + 4 + (1 if slice_steps > 0 else 0)
+    gpu_launches = int(2 * args.steps + slices * per_slice + (args.steps if slice_steps > 0 else 0))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.form == "fp64" else "f32 stages / f64 norm+path / double-float position",
         "data": "synthetic",
-        "config": {"workload": w.name, "particles_per_gpu": n, "grid": f"{w.grid_n}^3 f32",
+        "config": {"workload": w.name, "particles_per_gpu": n,
+                   "grid": f"{w.n_grids} x {w.grid_n}^3 f32", "order": order,
+                   "slice_steps": slice_steps,
                    "form": args.form, "dmax_mpc": w.dmax_m / I.MPC, "tol": w.tol,
                    "l2": "inputs larger than L2 (grid 268 MB as float4, state 1.7 GB) and a "
                          "256 MB flush before every step",
@@ -422,7 +461,7 @@ def run_own(args):
         "forms": forms,
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": launches_per_step * args.steps,
+        "gpu_launches": gpu_launches,
         "clocks": clk,
     }
     if rank == 0:

@@ -167,9 +167,34 @@ typedef struct {
     int32_t blocks_per_sm;   /* 0: the occupancy limit */
     int32_t cadence;         /* attempts between refill checks; 0: default (1) */
     int64_t max_steps;       /* accepted steps per particle per call; <= 0: no limit */
+    int32_t order;           /* work-list order: CRP_ORDER_* (0: default = CRP_ORDER_COST) */
+    int32_t pickup;          /* secondaries created in a launch: CRP_PICKUP_* (0: default = OFF) */
 } crp_params;
+/* Scheduling choices (never change a particle's result, only when it runs). */
+#define CRP_ORDER_DEFAULT 0
+#define CRP_ORDER_SLOT 1         /* slot (injection) order */
+#define CRP_ORDER_COST 2         /* lowest rigidity E/Z first: expected longest first */
+#define CRP_ORDER_GRID 3         /* by grid_id, then lowest rigidity first: concurrent particles
+                                    share field realisations (cache locality over many grids) */
+#define CRP_PICKUP_DEFAULT 0
+#define CRP_PICKUP_OFF 1         /* secondaries wait for the second launch */
+#define CRP_PICKUP_ON 2          /* idle warps take secondaries pushed earlier in the launch */
 int crp_propagate(crp_sim* sim, const crp_params* params, double tolerance, double min_step_m,
                   double max_step_m, double max_distance_m, void* stream);
+
+/* The batching form of the propagation: slices of params->max_steps accepted steps per
+ * particle (must be > 0 to make slices; <= 0 runs everything in one slice), repeated on the
+ * device until no particle is active, the device status word reports an error, a slice
+ * made no progress, or max_slices slices ran. Between slices the work list is rebuilt from
+ * the active particles, so long-lived particles are packed into full warps again. The whole
+ * loop is one CUDA graph (a conditional while node around the captured propagate sequence),
+ * built on the first call and reused while the arguments and the simulation's buffers are
+ * unchanged: one graph launch, no host round trip per slice. Results are the same as
+ * repeated crp_propagate calls with the same max_steps. Asynchronous on `stream`.
+ * Errors: as crp_propagate; INVALID_ARG for max_slices < 1; CUDA. */
+int crp_propagate_loop(crp_sim* sim, const crp_params* params, double tolerance,
+                       double min_step_m, double max_step_m, double max_distance_m,
+                       int32_t max_slices, void* stream);
 
 /* Wait for the simulation's last stream (at most timeout_s seconds; <= 0: no limit),
  * then return the first device-side error as a code: QUEUE_FULL, NAN_STATE,

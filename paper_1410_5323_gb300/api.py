@@ -15,6 +15,8 @@ ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_QUEUE_FULL = -1, -2, -3, -4
 ERR_TIMEOUT, ERR_NAN_STATE, ERR_TABLE_RANGE = -5, -6, -7
 DTYPE_F64, DTYPE_F32, DTYPE_BF16, DTYPE_F16 = 0, 1, 2, 3
 FORM_FP64, FORM_MIXED = 0, 1
+ORDER_DEFAULT, ORDER_SLOT, ORDER_COST, ORDER_GRID = 0, 1, 2, 3
+PICKUP_DEFAULT, PICKUP_OFF, PICKUP_ON = 0, 1, 2
 STATUS_ACTIVE, STATUS_DONE, STATUS_NAN, STATUS_RANGE = 0, 1, 2, 3
 
 # column name -> (id, numpy dtype)
@@ -44,7 +46,8 @@ class _Particles(C.Structure):
 
 class _Params(C.Structure):
     _fields_ = [("form", C.c_int32), ("block_size", C.c_int32), ("blocks_per_sm", C.c_int32),
-                ("cadence", C.c_int32), ("max_steps", C.c_int64)]
+                ("cadence", C.c_int32), ("max_steps", C.c_int64), ("order", C.c_int32),
+                ("pickup", C.c_int32)]
 
 
 _OBS_I64 = ("uid",)
@@ -81,6 +84,7 @@ def lib() -> C.CDLL:
             "crp_sim_reset": ([p], C.c_int),
             "crp_source_inject": ([p, p, i64, p], C.c_int),
             "crp_propagate": ([p, p, d, d, d, d, p], C.c_int),
+            "crp_propagate_loop": ([p, p, d, d, d, d, i32, p], C.c_int),
             "crp_sync": ([p, d], C.c_int),
             "crp_sim_counts": ([p, p], C.c_int),
             "crp_read_state": ([p, i32, p, i32, i64, i64], C.c_int),
@@ -233,10 +237,20 @@ class Simulation:
     def propagate(self, tolerance: float, min_step_m: float, max_step_m: float,
                   max_distance_m: float, form: int = FORM_FP64, max_steps: int = 0,
                   block_size: int = 0, blocks_per_sm: int = 0, cadence: int = 0,
-                  stream=None) -> None:
-        prm = _Params(form, block_size, blocks_per_sm, cadence, max_steps)
+                  order: int = 0, pickup: int = 0, stream=None) -> None:
+        prm = _Params(form, block_size, blocks_per_sm, cadence, max_steps, order, pickup)
         _check(lib().crp_propagate(self._h, C.byref(prm), tolerance, min_step_m, max_step_m,
                                    max_distance_m, _stream_ptr(stream)), "crp_propagate")
+
+    def propagate_loop(self, tolerance: float, min_step_m: float, max_step_m: float,
+                       max_distance_m: float, max_steps: int, max_slices: int = 1 << 20,
+                       form: int = FORM_FP64, block_size: int = 0, blocks_per_sm: int = 0,
+                       cadence: int = 0, order: int = 0, pickup: int = 0, stream=None) -> None:
+        """Slices of max_steps accepted steps until done, as one device-side graph loop."""
+        prm = _Params(form, block_size, blocks_per_sm, cadence, max_steps, order, pickup)
+        _check(lib().crp_propagate_loop(self._h, C.byref(prm), tolerance, min_step_m, max_step_m,
+                                        max_distance_m, int(max_slices), _stream_ptr(stream)),
+               "crp_propagate_loop")
 
     def sync(self, timeout_s: float = 0.0, raise_on_error: bool = True) -> int:
         rc = lib().crp_sync(self._h, timeout_s)

@@ -118,11 +118,103 @@ __global__ void k_set_used(Counters* C, unsigned long long n_used, unsigned long
 __global__ void k_prepare(Counters* C) {
     C->count[0] = 0;
     C->count[1] = 0;
-    C->head = 0;
+    C->head[0] = 0;
+    C->head[1] = 0;
     C->reserve = C->n_used;
 }
 
-// Work list 0 <- slots [0, n_used) with status ACTIVE (warp-aggregated append).
+// ---- work list in order of expected cost (longest first) ------------------------------
+// Bucket by rigidity E/Z (step size grows with the gyro-radius, so low rigidity means many
+// steps): 4 buckets per octave from 2^50 V, neutral particles last. A counting sort:
+// histogram, exclusive scan, scatter with one atomic per (warp, bucket).
+constexpr int kBuckets = 64;
+
+__device__ __forceinline__ int cost_bucket(double E, int Z) {
+    if (Z <= 0) return kBuckets - 1;
+    const float b = 4.0f * (__log2f((float)E / (float)Z) - 50.0f);
+    return b < 0.0f ? 0 : (b > (float)(kBuckets - 2) ? kBuckets - 2 : (int)b);
+}
+
+__device__ __forceinline__ int sort_key(double E, int Z, int gid, int grid_major) {
+    return grid_major ? gid * kBuckets + cost_bucket(E, Z) : cost_bucket(E, Z);
+}
+
+__global__ void k_cost_hist(const int32_t* __restrict__ status, const double* __restrict__ E,
+                            const int32_t* __restrict__ Zc, const int32_t* __restrict__ gid,
+                            int grid_major, int n_buckets, int use_shared,
+                            unsigned* __restrict__ hist, const Counters* C) {
+    extern __shared__ unsigned sh[];
+    if (use_shared) {
+        for (int b = threadIdx.x; b < n_buckets; b += blockDim.x) sh[b] = 0;
+        __syncthreads();
+    }
+    const long long n = (long long)*(volatile const unsigned long long*)&C->n_used;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (status[i] != CRP_STATUS_ACTIVE_) continue;
+        const int k = sort_key(E[i], Zc[i], gid[i], grid_major);
+        if (use_shared) atomicAdd(&sh[k], 1u);
+        else atomicAdd(&hist[k], 1u);
+    }
+    if (use_shared) {
+        __syncthreads();
+        for (int b = threadIdx.x; b < n_buckets; b += blockDim.x)
+            if (sh[b]) atomicAdd(&hist[b], sh[b]);
+    }
+}
+
+// Exclusive scan of the histogram (one block of 1024 threads), clearing it for next time.
+__global__ void k_cost_scan(unsigned* hist, unsigned* offs, int n_buckets, Counters* C) {
+    __shared__ unsigned part[1024];
+    const int t = threadIdx.x;
+    const int chunk = (n_buckets + blockDim.x - 1) / blockDim.x;
+    const int b0 = t * chunk, b1 = min(b0 + chunk, n_buckets);
+    unsigned sum = 0;
+    for (int b = b0; b < b1; ++b) sum += hist[b];
+    part[t] = sum;
+    __syncthreads();
+    if (t == 0) {
+        unsigned acc = 0;
+        for (int k = 0; k < (int)blockDim.x; ++k) {
+            const unsigned v = part[k];
+            part[k] = acc;
+            acc += v;
+        }
+        C->count[0] = acc;
+    }
+    __syncthreads();
+    unsigned acc = part[t];
+    for (int b = b0; b < b1; ++b) {
+        offs[b] = acc;
+        acc += hist[b];
+        hist[b] = 0;
+    }
+}
+
+__global__ void k_cost_scatter(const int32_t* __restrict__ status, const double* __restrict__ E,
+                               const int32_t* __restrict__ Zc, const int32_t* __restrict__ gid,
+                               int grid_major, unsigned* __restrict__ offs,
+                               int32_t* __restrict__ list, const Counters* C) {
+    const long long n = (long long)*(volatile const unsigned long long*)&C->n_used;
+    const int lane = threadIdx.x & 31;
+    for (long long base = blockIdx.x * (long long)blockDim.x; base < n;
+         base += (long long)gridDim.x * blockDim.x) {
+        const long long i = base + threadIdx.x;
+        const bool act = i < n && status[i] == CRP_STATUS_ACTIVE_;
+        const int b = act ? sort_key(E[i], Zc[i], gid[i], grid_major) : -1;
+        const unsigned grp = __match_any_sync(0xffffffffu, b);
+        if (act) {
+            const int leader = __ffs(grp) - 1;
+            unsigned p0 = 0;
+            if (lane == leader) p0 = atomicAdd(&offs[b], (unsigned)__popc(grp));
+            p0 = __shfl_sync(grp, p0, leader);
+            list[p0 + __popc(grp & ((1u << lane) - 1u))] = (int32_t)i;
+        }
+    }
+}
+
+// Work list 0 <- slots [0, n_used) with status ACTIVE, in slot order within each warp
+// (warp-aggregated append).
 __global__ void k_build_worklist(const int32_t* __restrict__ status, int32_t* __restrict__ list,
                                  Counters* C) {
     const unsigned long long n = *(volatile unsigned long long*)&C->n_used;
@@ -146,7 +238,7 @@ __global__ void k_swap(Counters* C, long long capacity, int from) {
     const unsigned long long r = C->reserve;
     C->n_used = r < (unsigned long long)capacity ? r : (unsigned long long)capacity;
     C->reserve = C->n_used;
-    C->head = 0;
+    C->head[from] = 0;      // the other list keeps its head: the next launch continues it
     C->count[from] = 0;
     C->launches += 1;
 }
@@ -219,6 +311,15 @@ void** col_ptr(SimState& S, int c) {
 }  // namespace
 
 // ---- handles ------------------------------------------------------------------------------
+namespace {
+// One validated propagate call: kernel arguments and launch shape.
+struct Plan {
+    PropArgs a{};
+    int grid = 0, block = 0, order = 0, mixed = 0, n_buckets = 0;
+};
+
+}  // namespace
+
 struct crp_field {
     FieldDev dev;
     void* mem = nullptr;
@@ -241,7 +342,12 @@ struct crp_sim {
     int32_t* lists[2] = {nullptr, nullptr};
     int32_t* done_list = nullptr;
     Counters* ctr = nullptr;
+    unsigned* sort_scratch = nullptr;   // [hist n_buckets][offsets n_buckets]
     cudaStream_t last = nullptr;
+    cudaGraph_t loop_graph = nullptr;   // crp_propagate_loop, cached for one plan
+    cudaGraphExec_t loop_exec = nullptr;
+    Plan loop_plan{};
+    int loop_max_slices = 0;
     int sms = 0;
 };
 
@@ -470,6 +576,9 @@ int crp_sim_create(const crp_field* const* fields, int32_t n_fields, const crp_t
     if (rc == CRP_OK && e == cudaSuccess) e = cudaMalloc(&s->done_list, sizeof(int32_t) * capacity);
     if (rc == CRP_OK && e == cudaSuccess) e = cudaMalloc(&s->ctr, sizeof(Counters));
     if (rc == CRP_OK && e == cudaSuccess) e = cudaMemset(s->ctr, 0, sizeof(Counters));
+    const size_t sort_bytes = 2 * (size_t)kBuckets * n_fields * sizeof(unsigned);
+    if (rc == CRP_OK && e == cudaSuccess) e = cudaMalloc(&s->sort_scratch, sort_bytes);
+    if (rc == CRP_OK && e == cudaSuccess) e = cudaMemset(s->sort_scratch, 0, sort_bytes);
     if (rc != CRP_OK || e != cudaSuccess) {
         crp_sim_destroy(s);
         return rc != CRP_OK ? rc : cuda_fail(e, "crp_sim_create allocations");
@@ -487,6 +596,9 @@ int crp_sim_destroy(crp_sim* s) {
     if (s->lists[1]) cudaFree(s->lists[1]);
     if (s->done_list) cudaFree(s->done_list);
     if (s->ctr) cudaFree(s->ctr);
+    if (s->sort_scratch) cudaFree(s->sort_scratch);
+    if (s->loop_exec) cudaGraphExecDestroy(s->loop_exec);
+    if (s->loop_graph) cudaGraphDestroy(s->loop_graph);
     delete s;
     return CRP_OK;
 }
@@ -586,8 +698,12 @@ int crp_source_inject(crp_sim* s, const crp_particles* p, int64_t n, void* strea
     return CRP_OK;
 }
 
-int crp_propagate(crp_sim* s, const crp_params* prm, double tol, double hmin, double hmax,
-                  double dmax, void* stream) {
+}  // extern "C"
+
+namespace {
+
+int make_plan(crp_sim* s, const crp_params* prm, double tol, double hmin, double hmax,
+              double dmax, Plan& P) {
     if (!s || !prm) return fail(CRP_ERR_INVALID_ARG, "sim or params is NULL");
     if (!(tol > 0.0) || !(hmin > 0.0) || !(hmax >= hmin) || !(dmax > 0.0) || !std::isfinite(hmax) ||
         !std::isfinite(dmax))
@@ -597,6 +713,11 @@ int crp_propagate(crp_sim* s, const crp_params* prm, double tol, double hmin, do
     if (prm->form == CRP_FORM_MIXED && s->layout != LAYOUT_F32X4 && s->layout != LAYOUT_BF16X4)
         return fail(CRP_ERR_INVALID_ARG, "the mixed form reads FP32 or BF16 grids");
     const bool mixed = prm->form == CRP_FORM_MIXED;
+    const int order = prm->order == CRP_ORDER_DEFAULT ? CRP_ORDER_COST : prm->order;
+    const int pickup = prm->pickup == CRP_PICKUP_DEFAULT ? CRP_PICKUP_OFF : prm->pickup;
+    if (order != CRP_ORDER_SLOT && order != CRP_ORDER_COST && order != CRP_ORDER_GRID)
+        return fail(CRP_ERR_INVALID_ARG, "unknown order");
+    if (pickup != CRP_PICKUP_OFF && pickup != CRP_PICKUP_ON) return fail(CRP_ERR_INVALID_ARG, "unknown pickup");
     const int block = prm->block_size > 0 ? prm->block_size : 128;
     if (block % 32 || block > 256) return fail(CRP_ERR_INVALID_ARG, "block_size must be a multiple of 32, <= 256");
     int bps = prm->blocks_per_sm;
@@ -607,9 +728,12 @@ int crp_propagate(crp_sim* s, const crp_params* prm, double tol, double hmin, do
         if (oe != 0 || occ < 1) occ = 1;
         bps = occ;
     }
-    const int grid = (s->sms > 0 ? s->sms : 1) * bps;
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    PropArgs a{};
+    P.grid = (s->sms > 0 ? s->sms : 1) * bps;
+    P.block = block;
+    P.order = order;
+    P.mixed = mixed ? 1 : 0;
+    P.n_buckets = order == CRP_ORDER_GRID ? kBuckets * (int)s->host_fields.size() : kBuckets;
+    PropArgs& a = P.a;
     a.st = s->st;
     a.fields = s->d_fields;
     a.n_fields = (int)s->host_fields.size();
@@ -620,24 +744,136 @@ int crp_propagate(crp_sim* s, const crp_params* prm, double tol, double hmin, do
     a.max_steps = prm->max_steps;
     a.capacity = s->capacity;
     a.cadence = prm->cadence > 0 ? prm->cadence : 1;
+    a.pickup = pickup == CRP_PICKUP_ON ? 1 : 0;
     a.lists[0] = s->lists[0];
     a.lists[1] = s->lists[1];
     a.done_list = s->done_list;
     a.ctr = s->ctr;
+    return CRP_OK;
+}
+
+// The launch sequence of one propagate call (no host synchronisation; capturable).
+int enqueue(crp_sim* s, const Plan& P, cudaStream_t st) {
+    PropArgs a = P.a;
     k_prepare<<<1, 1, 0, st>>>(s->ctr);
     CRP_CUDA(cudaGetLastError());
-    k_build_worklist<<<(s->sms > 0 ? s->sms : 1) * 4, 256, 0, st>>>(s->st.status, s->lists[0], s->ctr);
+    const int sgrid = (s->sms > 0 ? s->sms : 1) * 4;
+    if (P.order == CRP_ORDER_SLOT) {
+        k_build_worklist<<<sgrid, 256, 0, st>>>(s->st.status, s->lists[0], s->ctr);
+    } else {
+        const int grid_major = P.order == CRP_ORDER_GRID ? 1 : 0;
+        unsigned* hist = s->sort_scratch;
+        unsigned* offs = s->sort_scratch + P.n_buckets;
+        const size_t shm = (size_t)P.n_buckets * sizeof(unsigned);
+        k_cost_hist<<<sgrid, 256, shm <= 48 * 1024 ? shm : 0, st>>>(
+            s->st.status, s->st.E, s->st.Z, s->st.grid_id, grid_major, P.n_buckets,
+            shm <= 48 * 1024 ? 1 : 0, hist, s->ctr);
+        k_cost_scan<<<1, 1024, 0, st>>>(hist, offs, P.n_buckets, s->ctr);
+        k_cost_scatter<<<sgrid, 256, 0, st>>>(s->st.status, s->st.E, s->st.Z, s->st.grid_id,
+                                              grid_major, offs, s->lists[0], s->ctr);
+    }
     CRP_CUDA(cudaGetLastError());
-    // generation 1: the work list; generation 2: secondaries created by it (nucleons, which
-    // never split, so two launches finish the call)
+    // generation 1: the work list (and, with pickup, secondaries it pushes once the list
+    // runs dry); generation 2: the secondaries left. Nucleon secondaries never split, so two
+    // launches finish the call. The push list starts filled with -1.
     for (int gen = 0; gen < 2; ++gen) {
+        if (a.pickup) CRP_CUDA(cudaMemsetAsync(s->lists[1 - gen], 0xff, sizeof(int32_t) * s->capacity, st));
         a.list = gen;
-        int e = mixed ? launch_propagate_mixed(a, s->layout, grid, block, st)
-                      : launch_propagate_fp64(a, s->layout, grid, block, st);
+        int e = P.mixed ? launch_propagate_mixed(a, s->layout, P.grid, P.block, st)
+                        : launch_propagate_fp64(a, s->layout, P.grid, P.block, st);
         if (e) return cuda_fail((cudaError_t)e, "propagate kernel launch");
         k_swap<<<1, 1, 0, st>>>(s->ctr, s->capacity, gen);
         CRP_CUDA(cudaGetLastError());
     }
+    return CRP_OK;
+}
+
+// Device-side loop control for crp_propagate_loop.
+__global__ void k_loop_init(Counters* C) {
+    C->slices = 0;
+    C->prev_accepted = C->accepted;
+}
+
+__global__ void k_loop_cond(Counters* C, cudaGraphConditionalHandle h, long long max_slices) {
+    C->slices += 1;
+    const bool active = C->n_used > C->n_done;
+    const bool progressed = C->accepted != C->prev_accepted;
+    C->prev_accepted = C->accepted;
+    const bool go = active && C->status_bits == 0 && progressed && (long long)C->slices < max_slices;
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+bool same_plan(const Plan& x, const Plan& y) {
+    return std::memcmp(&x.a, &y.a, sizeof(PropArgs)) == 0 && x.grid == y.grid &&
+           x.block == y.block && x.order == y.order && x.mixed == y.mixed && x.n_buckets == y.n_buckets;
+}
+
+}  // namespace
+
+extern "C" {
+
+int crp_propagate(crp_sim* s, const crp_params* prm, double tol, double hmin, double hmax,
+                  double dmax, void* stream) {
+    Plan P;
+    int rc = make_plan(s, prm, tol, hmin, hmax, dmax, P);
+    if (rc) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    rc = enqueue(s, P, st);
+    if (rc) return rc;
+    s->last = st;
+    return CRP_OK;
+}
+
+int crp_propagate_loop(crp_sim* s, const crp_params* prm, double tol, double hmin, double hmax,
+                       double dmax, int32_t max_slices, void* stream) {
+    Plan P;
+    int rc = make_plan(s, prm, tol, hmin, hmax, dmax, P);
+    if (rc) return rc;
+    if (max_slices < 1) return fail(CRP_ERR_INVALID_ARG, "max_slices must be >= 1");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (!s->loop_exec || !same_plan(P, s->loop_plan) || s->loop_max_slices != max_slices) {
+        if (s->loop_exec) { cudaGraphExecDestroy(s->loop_exec); s->loop_exec = nullptr; }
+        if (s->loop_graph) { cudaGraphDestroy(s->loop_graph); s->loop_graph = nullptr; }
+        cudaGraph_t g = nullptr;
+        CRP_CUDA(cudaGraphCreate(&g, 0));
+        s->loop_graph = g;
+        // init node
+        cudaKernelNodeParams kp{};
+        Counters* ctr = s->ctr;
+        void* init_args[] = {&ctr};
+        kp.func = (void*)k_loop_init;
+        kp.gridDim = dim3(1);
+        kp.blockDim = dim3(1);
+        kp.kernelParams = init_args;
+        cudaGraphNode_t init_node;
+        CRP_CUDA(cudaGraphAddKernelNode(&init_node, g, nullptr, 0, &kp));
+        // while node; its body is the captured propagate sequence plus the condition kernel
+        cudaGraphConditionalHandle h;
+        CRP_CUDA(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t cond_node;
+        CRP_CUDA(cudaGraphAddNode(&cond_node, g, &init_node, nullptr, 1, &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        cudaStream_t cs;
+        CRP_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaError_t e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+        if (e != cudaSuccess) { cudaStreamDestroy(cs); return cuda_fail(e, "cudaStreamBeginCaptureToGraph"); }
+        rc = enqueue(s, P, cs);
+        k_loop_cond<<<1, 1, 0, cs>>>(s->ctr, h, (long long)max_slices);
+        cudaGraph_t captured = nullptr;
+        e = cudaStreamEndCapture(cs, &captured);
+        cudaStreamDestroy(cs);
+        if (rc) return rc;
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        CRP_CUDA(cudaGraphInstantiate(&s->loop_exec, g, 0));
+        s->loop_plan = P;
+        s->loop_max_slices = max_slices;
+    }
+    CRP_CUDA(cudaGraphLaunch(s->loop_exec, st));
     s->last = st;
     return CRP_OK;
 }
@@ -667,6 +903,7 @@ int crp_sync(crp_sim* s, double timeout_s) {
     if (b & BIT_NAN) return fail(CRP_ERR_NAN_STATE, "non-finite particle state");
     if (b & BIT_RANGE) return fail(CRP_ERR_TABLE_RANGE, "species outside tables");
     if (b & BIT_INVALID) return fail(CRP_ERR_INVALID_ARG, "invalid particle in injection");
+    if (b & BIT_TIMEOUT) return fail(CRP_ERR_TIMEOUT, "a pushed secondary never appeared in its list");
     return CRP_OK;
 }
 

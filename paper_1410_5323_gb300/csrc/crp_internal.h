@@ -50,19 +50,22 @@ enum : uint32_t {
     BIT_NAN = 2u,
     BIT_RANGE = 4u,
     BIT_INVALID = 8u,
+    BIT_TIMEOUT = 16u,
 };
 
 struct Counters {
     unsigned long long n_used;       // slots in use
     unsigned long long reserve;      // slot reservation counter during a launch
     unsigned long long count[2];     // entries in work list 0 / 1
-    unsigned long long head;         // next position to pop from the list being processed
+    unsigned long long head[2];      // next position to pop, per work list
     unsigned long long n_done;       // entries in the done list
     unsigned long long accepted;     // cumulative accepted steps
     unsigned long long attempted;    // cumulative attempted steps
     unsigned long long secondaries;  // cumulative secondaries created
     unsigned long long launches;     // propagate kernel launches
     unsigned long long n_primaries;  // primaries injected (default uids)
+    unsigned long long slices;       // slices run by the current propagate loop
+    unsigned long long prev_accepted;
     unsigned int status_bits;
     unsigned int pad_;
 };
@@ -78,6 +81,7 @@ struct PropArgs {
     long long max_steps;
     long long capacity;
     int32_t cadence;
+    int32_t pickup;                  // take secondaries pushed during the launch
     int32_t list;                    // process list `list`, push secondaries to 1 - list
     int32_t* lists[2];
     int32_t* done_list;

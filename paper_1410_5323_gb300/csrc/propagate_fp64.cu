@@ -15,6 +15,7 @@
 
 #include "crp_internal.h"
 #include "crp_math.cuh"
+#include "crp_sched.cuh"
 
 namespace crp {
 namespace {
@@ -179,8 +180,6 @@ template <int L>
 __global__ void __launch_bounds__(256) k_propagate_fp64(const PropArgs a) {
     const int lane = threadIdx.x & 31;
     Counters* C = a.ctr;
-    const int32_t* work = a.lists[a.list];
-    int32_t* next = a.lists[1 - a.list];
     const unsigned long long n_work = *(volatile unsigned long long*)&C->count[a.list];
     const double INF = __longlong_as_double(0x7ff0000000000000LL);
     const SimState& S = a.st;
@@ -214,26 +213,17 @@ __global__ void __launch_bounds__(256) k_propagate_fp64(const PropArgs a) {
     for (;;) {
         // ---- refill idle lanes from the work list (one atomic per warp) ----
         const bool idle = slot < 0;
-        const unsigned im = __ballot_sync(kFull, idle);
-        if (im) {
-            unsigned long long base = n_work;
-            if (lane == 0 && *(volatile unsigned long long*)&C->head < n_work)
-                base = atomicAdd(&C->head, (unsigned long long)__popc(im));
-            base = __shfl_sync(kFull, base, 0);
-            if (idle) {
-                const unsigned long long pos = base + __popc(im & ((1u << lane) - 1u));
-                if (pos < n_work) {
-                    slot = work[pos];
-                    y.x = S.x[slot]; y.y = S.y[slot]; y.z = S.z[slot];
-                    y.ux = S.ux[slot]; y.uy = S.uy[slot]; y.uz = S.uz[slot];
-                    E = S.E[slot]; s = S.s[slot]; hprop = S.hprop[slot]; tau = S.tau[slot];
-                    A = S.A[slot]; Z = S.Z[slot]; n_int = S.n_int[slot]; gid = S.grid_id[slot];
-                    uid = (unsigned long long)S.uid[slot];
-                    n_steps = S.n_steps[slot]; n_att = S.n_att[slot];
-                    taken = 0;
-                    new_step = true;
-                }
-            }
+        const int popped = sched_pop(a, idle, lane, n_work, bits);
+        if (popped >= 0) {
+            slot = popped;
+            y.x = __ldcg(&S.x[slot]); y.y = __ldcg(&S.y[slot]); y.z = __ldcg(&S.z[slot]);
+            y.ux = __ldcg(&S.ux[slot]); y.uy = __ldcg(&S.uy[slot]); y.uz = __ldcg(&S.uz[slot]);
+            E = __ldcg(&S.E[slot]); s = __ldcg(&S.s[slot]); hprop = __ldcg(&S.hprop[slot]); tau = __ldcg(&S.tau[slot]);
+            A = __ldcg(&S.A[slot]); Z = __ldcg(&S.Z[slot]); n_int = __ldcg(&S.n_int[slot]); gid = __ldcg(&S.grid_id[slot]);
+            uid = (unsigned long long)__ldcg(&S.uid[slot]);
+            n_steps = __ldcg(&S.n_steps[slot]); n_att = __ldcg(&S.n_att[slot]);
+            taken = 0;
+            new_step = true;
         }
         if (__ballot_sync(kFull, slot >= 0) == 0) break;
 
@@ -333,8 +323,7 @@ __global__ void __launch_bounds__(256) k_propagate_fp64(const PropArgs a) {
                         const unsigned long long d = atomicAdd(&C->n_done, 1ull);
                         a.done_list[d] = (int32_t)qs;
                     } else {
-                        const unsigned long long p = atomicAdd(&C->count[1 - a.list], 1ull);
-                        next[p] = (int32_t)qs;
+                        sched_push(a, (int32_t)qs);
                     }
                     sec_tot += 1;
                     A = A - 1;

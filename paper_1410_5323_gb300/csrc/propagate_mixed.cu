@@ -18,6 +18,7 @@
 
 #include "crp_internal.h"
 #include "crp_math.cuh"
+#include "crp_sched.cuh"
 
 namespace crp {
 namespace {
@@ -133,12 +134,17 @@ __device__ __forceinline__ float powf_pos(float r2, float p) { return exp2f(p * 
 
 __device__ __forceinline__ bool fin3(F3 a) { return isfinite(a.x) && isfinite(a.y) && isfinite(a.z); }
 
+// Register cap (more resident warps to hide gather latency); a build-time tuning knob.
+#ifdef CRP_MIXED_MAXNREG
+#define CRP_MIXED_BOUNDS __maxnreg__(CRP_MIXED_MAXNREG)
+#else
+#define CRP_MIXED_BOUNDS __launch_bounds__(256)
+#endif
+
 template <int L>
-__global__ void __launch_bounds__(256) k_propagate_mixed(const PropArgs a) {
+__global__ void CRP_MIXED_BOUNDS k_propagate_mixed(const PropArgs a) {
     const int lane = threadIdx.x & 31;
     Counters* C = a.ctr;
-    const int32_t* work = a.lists[a.list];
-    int32_t* next = a.lists[1 - a.list];
     const unsigned long long n_work = *(volatile unsigned long long*)&C->count[a.list];
     const float INF = __int_as_float(0x7f800000);
     const SimState& S = a.st;
@@ -192,38 +198,29 @@ __global__ void __launch_bounds__(256) k_propagate_mixed(const PropArgs a) {
 
     for (;;) {
         const bool idle = slot < 0;
-        const unsigned im = __ballot_sync(kFull, idle);
-        if (im) {
-            unsigned long long base = n_work;
-            if (lane == 0 && *(volatile unsigned long long*)&C->head < n_work)
-                base = atomicAdd(&C->head, (unsigned long long)__popc(im));
-            base = __shfl_sync(kFull, base, 0);
-            if (idle) {
-                const unsigned long long pos = base + __popc(im & ((1u << lane) - 1u));
-                if (pos < n_work) {
-                    slot = work[pos];
-                    gid = S.grid_id[slot];
-                    const FieldDev& G = a.fields[gid];
-                    F.data = G.data; F.nx = G.nx; F.ny = G.ny; F.nz = G.nz; F.pow2 = G.pow2;
-                    F.scale = (float)G.scale;
-                    sp = G.spacing; inv_sp = G.inv_spacing; sp_f = (float)sp;
-                    ox = G.ox; oy = G.oy; oz = G.oz;
-                    hmin_c = (float)(a.hmin * inv_sp);
-                    hmax_c = (float)(a.hmax * inv_sp);
-                    dmax_c = a.dmax * inv_sp;
-                    Rx = from_x(S.x[slot], ox); Ry = from_x(S.y[slot], oy); Rz = from_x(S.z[slot], oz);
-                    u = {(float)S.ux[slot], (float)S.uy[slot], (float)S.uz[slot]};
-                    E = S.E[slot];
-                    s_c = S.s[slot] * inv_sp;
-                    hprop = (float)(S.hprop[slot] * inv_sp);
-                    tau = (float)S.tau[slot];
-                    A = S.A[slot]; Z = S.Z[slot]; n_int = S.n_int[slot];
-                    uid = (unsigned long long)S.uid[slot];
-                    n_steps = S.n_steps[slot]; n_att = S.n_att[slot];
-                    taken = 0;
-                    new_step = true;
-                }
-            }
+        const int popped = sched_pop(a, idle, lane, n_work, bits);
+        if (popped >= 0) {
+            slot = popped;
+            gid = __ldcg(&S.grid_id[slot]);
+            const FieldDev& G = a.fields[gid];
+            F.data = G.data; F.nx = G.nx; F.ny = G.ny; F.nz = G.nz; F.pow2 = G.pow2;
+            F.scale = (float)G.scale;
+            sp = G.spacing; inv_sp = G.inv_spacing; sp_f = (float)sp;
+            ox = G.ox; oy = G.oy; oz = G.oz;
+            hmin_c = (float)(a.hmin * inv_sp);
+            hmax_c = (float)(a.hmax * inv_sp);
+            dmax_c = a.dmax * inv_sp;
+            Rx = from_x(__ldcg(&S.x[slot]), ox); Ry = from_x(__ldcg(&S.y[slot]), oy); Rz = from_x(__ldcg(&S.z[slot]), oz);
+            u = {(float)__ldcg(&S.ux[slot]), (float)__ldcg(&S.uy[slot]), (float)__ldcg(&S.uz[slot])};
+            E = __ldcg(&S.E[slot]);
+            s_c = __ldcg(&S.s[slot]) * inv_sp;
+            hprop = (float)(__ldcg(&S.hprop[slot]) * inv_sp);
+            tau = (float)__ldcg(&S.tau[slot]);
+            A = __ldcg(&S.A[slot]); Z = __ldcg(&S.Z[slot]); n_int = __ldcg(&S.n_int[slot]);
+            uid = (unsigned long long)__ldcg(&S.uid[slot]);
+            n_steps = __ldcg(&S.n_steps[slot]); n_att = __ldcg(&S.n_att[slot]);
+            taken = 0;
+            new_step = true;
         }
         if (__ballot_sync(kFull, slot >= 0) == 0) break;
 
@@ -387,8 +384,7 @@ __global__ void __launch_bounds__(256) k_propagate_mixed(const PropArgs a) {
                         const unsigned long long d = atomicAdd(&C->n_done, 1ull);
                         a.done_list[d] = (int32_t)qs;
                     } else {
-                        const unsigned long long p = atomicAdd(&C->count[1 - a.list], 1ull);
-                        next[p] = (int32_t)qs;
+                        sched_push(a, (int32_t)qs);
                     }
                     sec_tot += 1;
                     A = A - 1;

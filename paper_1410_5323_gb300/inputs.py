@@ -369,3 +369,21 @@ def batched_brms(n_grids: int = 64, seed: int = 1, lo: float = 0.1, hi: float = 
     """Per-realisation B_rms (tesla), log-uniform in [lo, hi] nG."""
     rng = np.random.Generator(np.random.PCG64(seed + 1000))
     return np.exp(rng.uniform(math.log(lo), math.log(hi), n_grids)) * NANOGAUSS
+
+
+def batched_grids(w: Workload, n_grids: int | None = None, grid_n: int | None = None):
+    """Field realisations of the batching workload: seeds 1..n, B_rms log-uniform in
+    [0.1, 10] nG, each an FP32 [n, n, n, 3] Kolmogorov grid."""
+    n_grids = n_grids or w.n_grids
+    grid_n = grid_n or w.grid_n
+    brms = batched_brms(n_grids)
+    return [kolmogorov_grid(grid_n, w.spacing_m, w.lmin_cells, w.lmax_cells, float(brms[i]),
+                            i + 1).astype(np.float32) for i in range(n_grids)], brms
+
+
+def batched_particles(w: Workload, n_per_grid: int, n_grids: int | None = None, seed: int = 1):
+    """Protons, log-uniform energies, n_per_grid per realisation (grid_id = i // n_per_grid)."""
+    n_grids = n_grids or w.n_grids
+    n = n_per_grid * n_grids
+    gid = np.repeat(np.arange(n_grids, dtype=np.int32), n_per_grid)
+    return make_particles(n, seed, w.species, w.energy, grid_ids=gid)
