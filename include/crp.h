@@ -52,7 +52,10 @@ extern "C" {
 #define CRP_DTYPE_BF16 2
 #define CRP_DTYPE_F16 3
 
-#define CRP_FORM_FP64 0     /* FP64 stages, FP64 lookups; bit-identical to the FP64 reading */
+#define CRP_FORM_FP64 0     /* FP64 stages, FP64 lookups; bit-identical to the FP64 reading. On
+                               first use it builds an FP64 copy of each FP32/BF16/F16 grid
+                               (32 B per node, kept with the field) so that no widening runs
+                               on the FP64 pipe per lookup */
 #define CRP_FORM_MIXED 1    /* FP32 local-frame stages, FP64 position and error norm */
 
 #define CRP_STATUS_ACTIVE 0
@@ -226,6 +229,39 @@ typedef struct {
 } crp_observer;
 int crp_observe(crp_sim* sim, const crp_observer* out, int64_t first, int64_t capacity,
                 int64_t* n_out);
+
+/* ---- differentiation through a frozen step sequence (Sec. 2 deflection, Sec. 3.2 grid) --
+ * The FP64 propagation module alone (no loss, interactions or distance limit) for n
+ * particles through one field: crp_adjoint_forward records the accepted step sizes h_n of
+ * n_steps steps with the adaptive Cash-Karp controller and checkpoints (x, u) every
+ * checkpoint_every steps; crp_adjoint_backward differentiates the map with the recorded h_n
+ * held fixed (the controller is not differentiated), recomputing each segment from its
+ * checkpoint. Initial momenta p0 are in eV/c: E = |p0|, u0 = p0/E, kappa = Z c / E.
+ * All array arguments are device pointers; [n][3] arrays are row-major.
+ * Memory owned by the handle: 8 B x n x (n_steps + 6 (n_steps / checkpoint_every + 1) +
+ * 6 (checkpoint_every + 1) + 20). */
+typedef struct crp_adjoint crp_adjoint;
+int crp_adjoint_create(const crp_field* field, int64_t n, int32_t n_steps,
+                       int32_t checkpoint_every, crp_adjoint** out);
+int crp_adjoint_destroy(crp_adjoint* adj);
+/* x0, p0: [n][3]; Z: [n]; outputs xT, uT: [n][3] after n_steps accepted steps. */
+int crp_adjoint_forward(crp_adjoint* adj, const double* x0, const double* p0, const int32_t* Z,
+                        double tolerance, double min_step_m, double max_step_m, double* xT,
+                        double* uT, void* stream);
+/* The recorded step sequence again, on `field` (NULL: the handle's; otherwise same grid
+ * geometry) and/or from other initial momenta p0 ([n][3], NULL: the recorded ones), x0 as
+ * recorded. For finite differences and sensitivity studies. cell_hash (may be NULL) receives
+ * per particle a hash of the cell of every stage lookup: the trilinear field is only
+ * continuous across cell faces, so a difference quotient is a derivative only where the
+ * perturbed replays visit the same cells. */
+int crp_adjoint_replay(crp_adjoint* adj, const crp_field* field, const double* p0, double* xT,
+                       double* uT, uint64_t* cell_hash, void* stream);
+/* uT_bar = dL/du_T [n][3]. grid_bar: [nx][ny][nz][3] FP64, accumulated (the caller zeroes
+ * it); p0_bar = dL/dp0 [n][3]; x0_bar = dL/dx0 [n][3] (may be NULL). */
+int crp_adjoint_backward(crp_adjoint* adj, const double* uT_bar, double* grid_bar, double* p0_bar,
+                         double* x0_bar, void* stream);
+/* Recorded step sizes, [n_steps][n] (host or device). */
+int crp_adjoint_read_steps(crp_adjoint* adj, double* h, int32_t is_device);
 
 /* ---- propagation that allocates nothing -------------------------------------------------
  * This entry point has no counterpart in the paper; it exists for callers that must not

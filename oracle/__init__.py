@@ -243,3 +243,47 @@ def exp(x: float) -> float:
 
 def log(x: float) -> float:
     return lib().orc_log(x)
+
+
+# ---- frozen-step differentiation ------------------------------------------------------
+def _sigs():
+    L = lib()
+    if not getattr(L, "_adj_sigs", False):
+        p, d, i32 = C.c_void_p, C.c_double, C.c_int32
+        L.orc_record_steps.argtypes = [p, d, p, d, d, d, i32, p, p]
+        L.orc_record_steps.restype = C.c_int
+        L.orc_frozen_forward.argtypes = [p, d, p, p, i32, p]
+        L.orc_adjoint.argtypes = [p, d, p, p, i32, p, p, p, p]
+        L._adj_sigs = True
+    return L
+
+
+def record_steps(field: OracleField, kappa: float, y0, tol: float, hmin: float, hmax: float,
+                 n_steps: int):
+    """Accepted step sizes of the propagation module alone; returns (h[n], y_T)."""
+    y = np.ascontiguousarray(y0, dtype=np.float64)
+    h = np.zeros(n_steps)
+    yT = np.zeros(6)
+    _sigs().orc_record_steps(C.byref(field.c), kappa, _ptr(y), tol, hmin, hmax, n_steps, _ptr(h), _ptr(yT))
+    return h, yT
+
+
+def frozen_forward(field: OracleField, kappa: float, y0, h) -> np.ndarray:
+    y = np.ascontiguousarray(y0, dtype=np.float64)
+    hh = np.ascontiguousarray(h, dtype=np.float64)
+    yT = np.zeros(6)
+    _sigs().orc_frozen_forward(C.byref(field.c), kappa, _ptr(y), _ptr(hh), len(hh), _ptr(yT))
+    return yT
+
+
+def adjoint(field: OracleField, kappa: float, y0, h, lamT, grid_bar: np.ndarray | None = None):
+    """Reverse pass; returns (y0_bar, kappa_bar); grid_bar ([nx,ny,nz,3] float64) accumulates."""
+    y = np.ascontiguousarray(y0, dtype=np.float64)
+    hh = np.ascontiguousarray(h, dtype=np.float64)
+    lam = np.ascontiguousarray(lamT, dtype=np.float64)
+    yb = np.zeros(6)
+    kb = C.c_double()
+    gp = None if grid_bar is None else _ptr(grid_bar)
+    _sigs().orc_adjoint(C.byref(field.c), kappa, _ptr(y), _ptr(hh), len(hh), _ptr(lam), gp, _ptr(yb),
+                        C.byref(kb))
+    return yb, kb.value

@@ -555,3 +555,191 @@ int orc_propagate(orc_state* st, const orc_field* fields, int32_t n_fields, cons
     }
     return job.queue_full ? ORC_ERR_QUEUE_FULL : ORC_OK;
 }
+
+
+/* ==== frozen-step differentiation =====================================================
+ * The controller and the bids are not differentiated: the accepted step sizes h_n of a
+ * forward run are recorded and the map y_{n+1} = y_n + h_n sum_i b_i k_i (5th-order
+ * Cash-Karp solution) is differentiated exactly for fixed h_n. */
+
+/* Accepted steps of the propagation module alone (no distance, loss or interaction bids),
+ * with the same attempt loop and controller as orc_propagate. */
+int orc_record_steps(const orc_field* f, double kappa, const double y0[6], double tol, double hmin,
+                     double hmax, int32_t n_steps, double* h_out, double yT[6])
+{
+    double y[6];
+    for (int c = 0; c < 6; ++c) y[c] = y0[c];
+    double hprop = INFINITY;
+    for (int32_t n = 0; n < n_steps; ++n) {
+        double h_prop = fmin(fmax(hprop, hmin), hmax);
+        double h = h_prop;
+        double k1[6], y5[6], err[6], r;
+        orc_deriv(f, kappa, y, k1);
+        int rejected = 0;
+        for (;;) {
+            orc_ck_attempt(f, kappa, y, k1, h, y5, err);
+            r = orc_error_ratio(err, h, tol);
+            if (r <= 1.0 || h <= hmin) break;
+            double shrink = clamp(0.95 * orc_exp(-0.25 * orc_log(r)), 0.1, 1.0);
+            h = fmax(h * shrink, hmin);
+            rejected = 1;
+        }
+        for (int c = 0; c < 6; ++c) y[c] = y5[c];
+        h_out[n] = h;
+        double grow = (r == 0.0) ? 5.0 : clamp(0.95 * orc_exp(-0.2 * orc_log(r)), 0.2, 5.0);
+        double hnext = h * grow;
+        if (!rejected && h < h_prop) hnext = fmax(hnext, h_prop);
+        hprop = clamp(hnext, hmin, hmax);
+    }
+    for (int c = 0; c < 6; ++c) yT[c] = y[c];
+    return 0;
+}
+
+/* One frozen step: the Cash-Karp 5th-order update with step h. */
+static void frozen_step(const orc_field* f, double kappa, double y[6], double h)
+{
+    double k1[6], y5[6], err[6];
+    orc_deriv(f, kappa, y, k1);
+    orc_ck_attempt(f, kappa, y, k1, h, y5, err);
+    for (int c = 0; c < 6; ++c) y[c] = y5[c];
+}
+
+void orc_frozen_forward(const orc_field* f, double kappa, const double y0[6], const double* h,
+                        int32_t n_steps, double yT[6])
+{
+    double y[6];
+    for (int c = 0; c < 6; ++c) y[c] = y0[c];
+    for (int32_t n = 0; n < n_steps; ++n) frozen_step(f, kappa, y, h[n]);
+    for (int c = 0; c < 6; ++c) yT[c] = y[c];
+}
+
+/* Trilinear lookup with the corner weights, their x-derivatives and the grid indices. */
+typedef struct {
+    double B[3];
+    double w[8];            /* corner weights, corner order 000, 001, ..., 111 */
+    double dw[8][3];        /* d w / d x_a */
+    int64_t node[8];
+    double G[8][3];
+} orc_lookup;
+
+static void lookup_full(const orc_field* f, const double x[3], orc_lookup* L)
+{
+    double inv = 1.0 / f->spacing;
+    int64_t dims[3] = {f->nx, f->ny, f->nz};
+    int64_t idx[3][2];
+    double w[3][2], dwd[3][2];
+    for (int a = 0; a < 3; ++a) {
+        double r = (x[a] - f->origin[a]) * inv;
+        double fl = floor(r);
+        double fr = r - fl;
+        int64_t i = (int64_t)fl;
+        int64_t n = dims[a];
+        int64_t i0 = ((i % n) + n) % n;
+        idx[a][0] = i0;
+        idx[a][1] = (i0 + 1) % n;
+        w[a][0] = 1.0 - fr;
+        w[a][1] = fr;
+        dwd[a][0] = -inv;
+        dwd[a][1] = inv;
+    }
+    L->B[0] = 0.0; L->B[1] = 0.0; L->B[2] = 0.0;
+    int c8 = 0;
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            for (int c = 0; c < 2; ++c, ++c8) {
+                double wt = (w[0][a] * w[1][b]) * w[2][c];
+                L->w[c8] = wt;
+                L->dw[c8][0] = (dwd[0][a] * w[1][b]) * w[2][c];
+                L->dw[c8][1] = (w[0][a] * dwd[1][b]) * w[2][c];
+                L->dw[c8][2] = (w[0][a] * w[1][b]) * dwd[2][c];
+                L->node[c8] = (idx[0][a] * f->ny + idx[1][b]) * f->nz + idx[2][c];
+                for (int q = 0; q < 3; ++q) {
+                    L->G[c8][q] = grid_at(f, idx[0][a], idx[1][b], idx[2][c], q);
+                    L->B[q] = L->B[q] + wt * L->G[c8][q];
+                }
+            }
+}
+
+/* Vector-Jacobian product of f(Y) = (u, kappa u x B(x)) with kbar = (abar, bbar):
+ *   Bbar = kappa (bbar x u);  kappa_bar += bbar . (u x B);
+ *   Ybar_u = abar + kappa (B x bbar);  Ybar_x[a] = sum_c dw_c/dx_a (G_c . Bbar);
+ *   grid_bar[c] += w_c Bbar. */
+static void vjp_f(const orc_field* f, double kappa, const double Y[6], const double kb[6],
+                  double Yb[6], double* grid_bar, double* kappa_bar)
+{
+    orc_lookup L;
+    lookup_full(f, Y, &L);
+    const double* u = Y + 3;
+    const double* bb = kb + 3;
+    double Bb[3];
+    Bb[0] = kappa * (bb[1] * u[2] - bb[2] * u[1]);
+    Bb[1] = kappa * (bb[2] * u[0] - bb[0] * u[2]);
+    Bb[2] = kappa * (bb[0] * u[1] - bb[1] * u[0]);
+    double uxB0 = u[1] * L.B[2] - u[2] * L.B[1];
+    double uxB1 = u[2] * L.B[0] - u[0] * L.B[2];
+    double uxB2 = u[0] * L.B[1] - u[1] * L.B[0];
+    *kappa_bar = *kappa_bar + ((bb[0] * uxB0 + bb[1] * uxB1) + bb[2] * uxB2);
+    Yb[3] = kb[0] + kappa * (L.B[1] * bb[2] - L.B[2] * bb[1]);
+    Yb[4] = kb[1] + kappa * (L.B[2] * bb[0] - L.B[0] * bb[2]);
+    Yb[5] = kb[2] + kappa * (L.B[0] * bb[1] - L.B[1] * bb[0]);
+    Yb[0] = 0.0; Yb[1] = 0.0; Yb[2] = 0.0;
+    for (int c = 0; c < 8; ++c) {
+        double gB = (L.G[c][0] * Bb[0] + L.G[c][1] * Bb[1]) + L.G[c][2] * Bb[2];
+        for (int a = 0; a < 3; ++a) Yb[a] = Yb[a] + L.dw[c][a] * gB;
+        if (grid_bar)
+            for (int q = 0; q < 3; ++q)
+                grid_bar[L.node[c] * 3 + q] = grid_bar[L.node[c] * 3 + q] + L.w[c] * Bb[q];
+    }
+}
+
+/* Reverse pass through the recorded steps. lamT = dL/dy_T; grid_bar ([nx][ny][nz][3]) is
+ * accumulated; y0_bar = dL/dy_0; kappa_bar = dL/dkappa (kappa is one constant per particle). */
+void orc_adjoint(const orc_field* f, double kappa, const double y0[6], const double* h,
+                 int32_t n_steps, const double lamT[6], double* grid_bar, double y0_bar[6],
+                 double* kappa_bar)
+{
+    double* ys = (double*)malloc(sizeof(double) * 6 * (size_t)(n_steps + 1));
+    for (int c = 0; c < 6; ++c) ys[c] = y0[c];
+    for (int32_t n = 0; n < n_steps; ++n) {
+        for (int c = 0; c < 6; ++c) ys[6 * (n + 1) + c] = ys[6 * n + c];
+        frozen_step(f, kappa, ys + 6 * (n + 1), h[n]);
+    }
+    double lam[6];
+    for (int c = 0; c < 6; ++c) lam[c] = lamT[c];
+    *kappa_bar = 0.0;
+    for (int32_t n = n_steps - 1; n >= 0; --n) {
+        const double* y = ys + 6 * n;
+        const double hn = h[n];
+        /* stage states Y_1..Y_6 of this step */
+        double k[6][6], Y[6][6];
+        for (int c = 0; c < 6; ++c) Y[0][c] = y[c];
+        orc_deriv(f, kappa, Y[0], k[0]);
+        for (int i = 1; i < 6; ++i) {
+            for (int c = 0; c < 6; ++c) {
+                double acc = CK_A[i][0] * k[0][c];
+                for (int j = 1; j < i; ++j) acc = acc + CK_A[i][j] * k[j][c];
+                Y[i][c] = y[c] + hn * acc;
+            }
+            orc_deriv(f, kappa, Y[i], k[i]);
+        }
+        /* adjoint of y' = y + h sum_i b_i k_i and of the stage sums, stages in reverse */
+        double kb[6][6], yb[6];
+        for (int i = 0; i < 6; ++i) {
+            double hb = hn * CK_B5[i];
+            for (int c = 0; c < 6; ++c) kb[i][c] = hb * lam[c];
+        }
+        for (int c = 0; c < 6; ++c) yb[c] = lam[c];
+        for (int i = 5; i >= 0; --i) {
+            double Yb[6];
+            vjp_f(f, kappa, Y[i], kb[i], Yb, grid_bar, kappa_bar);
+            for (int c = 0; c < 6; ++c) yb[c] = yb[c] + Yb[c];
+            for (int j = 0; j < i; ++j) {
+                double ha = hn * CK_A[i][j];
+                for (int c = 0; c < 6; ++c) kb[j][c] = kb[j][c] + ha * Yb[c];
+            }
+        }
+        for (int c = 0; c < 6; ++c) lam[c] = yb[c];
+    }
+    for (int c = 0; c < 6; ++c) y0_bar[c] = lam[c];
+    free(ys);
+}

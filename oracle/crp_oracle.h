@@ -94,6 +94,16 @@ int orc_inject(orc_state* st, int64_t first, int64_t count, uint64_t seed, const
 int orc_propagate(orc_state* st, const orc_field* fields, int32_t n_fields, const orc_tables* t,
                   const orc_params* p, int64_t stats[4]);
 
+/* Frozen-step differentiation (adjoint of the Cash-Karp map with recorded steps).
+ * y = (x, u); kappa = Z c / E. */
+int orc_record_steps(const orc_field* f, double kappa, const double y0[6], double tol, double hmin,
+                     double hmax, int32_t n_steps, double* h_out, double yT[6]);
+void orc_frozen_forward(const orc_field* f, double kappa, const double y0[6], const double* h,
+                        int32_t n_steps, double yT[6]);
+void orc_adjoint(const orc_field* f, double kappa, const double y0[6], const double* h,
+                 int32_t n_steps, const double lamT[6], double* grid_bar, double y0_bar[6],
+                 double* kappa_bar);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,6 +27,7 @@ SOURCES = [
     ("crp_capi.cu", []),
     ("propagate_fp64.cu", ["--fmad=false"]),
     ("propagate_mixed.cu", []),
+    ("adjoint.cu", ["--fmad=false"]),
 ]
 
 

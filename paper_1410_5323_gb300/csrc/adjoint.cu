@@ -1,0 +1,324 @@
+// adjoint.cu -- differentiation form of the propagation (arXiv:1410.5323 3D deflection,
+// Sec. 2; regular grids, Sec. 3.2): reverse mode through a frozen step sequence.
+//
+// A forward pass with the adaptive Cash-Karp controller records the accepted step sizes
+// h_n and checkpoints y = (x, u) every K steps. The map y_{n+1} = y_n + h_n sum_i b_i k_i
+// is then differentiated exactly for fixed h_n: per segment of K steps the states are
+// recomputed from the checkpoint, and the steps are reversed stage by stage with the
+// vector-Jacobian product of f(y) = (u, kappa u x B(x)), which also yields dL/dkappa and
+// scatters dL/dB into the grid gradient through the trilinear weights (FP64 atomics).
+// Compiled with --fmad=false; per-particle arithmetic follows the oracle's order.
+#include <cuda_runtime.h>
+
+#include "crp_fp64.cuh"
+#include "crp_internal.h"
+#include "crp_math.cuh"
+
+namespace crp {
+namespace {
+
+using namespace fp64;
+
+__device__ __forceinline__ void load6(const double* a, long long n, long long i, Y6& y) {
+    y.x = a[0 * n + i]; y.y = a[1 * n + i]; y.z = a[2 * n + i];
+    y.ux = a[3 * n + i]; y.uy = a[4 * n + i]; y.uz = a[5 * n + i];
+}
+__device__ __forceinline__ void store6(double* a, long long n, long long i, const Y6& y) {
+    a[0 * n + i] = y.x; a[1 * n + i] = y.y; a[2 * n + i] = y.z;
+    a[3 * n + i] = y.ux; a[4 * n + i] = y.uy; a[5 * n + i] = y.uz;
+}
+
+// E = |p0| ((p_x^2 + p_y^2) + p_z^2, then sqrt), u0 = p0 / E, kappa = (Z c) / E; positions
+// are copied from x0 unless it is NULL (then the position rows of y0 are left as they are).
+__global__ void k_adj_init(const double* __restrict__ x0, const double* __restrict__ p0,
+                           const int32_t* __restrict__ Z, double* __restrict__ y0,
+                           double* __restrict__ kappa, double* __restrict__ E, long long n) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double px = p0[3 * i], py = p0[3 * i + 1], pz = p0[3 * i + 2];
+    const double e = sqrt((px * px + py * py) + pz * pz);
+    if (x0) {
+        y0[0 * n + i] = x0[3 * i]; y0[1 * n + i] = x0[3 * i + 1]; y0[2 * n + i] = x0[3 * i + 2];
+    }
+    y0[3 * n + i] = px / e; y0[4 * n + i] = py / e; y0[5 * n + i] = pz / e;
+    E[i] = e;
+    kappa[i] = (double)Z[i] * kC / e;
+}
+
+// Forward with the propagation module's controller only; records h_n and checkpoints.
+template <int L>
+__global__ void k_adj_record(FieldDev F, const double* __restrict__ y0, const double* __restrict__ kap,
+                             double tol, double hmin, double hmax, int n_steps, int K,
+                             double* __restrict__ h_out, double* __restrict__ ck,
+                             double* __restrict__ xT, double* __restrict__ uT, long long n) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Y6 y;
+    load6(y0, n, i, y);
+    const double kappa = kap[i];
+    double hprop = __longlong_as_double(0x7ff0000000000000LL);
+    for (int m = 0; m < n_steps; ++m) {
+        if (m % K == 0) store6(ck + (long long)(m / K) * 6 * n, n, i, y);
+        const double h_prop = clampd(hprop, hmin, hmax);
+        double h = h_prop;
+        const Y6 k1 = deriv<L>(F, kappa, y);
+        Y6 y5, err;
+        double r;
+        int rejected = 0;
+        for (;;) {
+            ck_attempt<L>(F, kappa, y, k1, h, y5, err);
+            r = error_ratio(err, h, tol);
+            if (r <= 1.0 || h <= hmin) break;
+            const double shrink = clampd(0.95 * crp_exp(-0.25 * crp_log(r)), 0.1, 1.0);
+            h = fmax(h * shrink, hmin);
+            rejected = 1;
+        }
+        y = y5;
+        h_out[(long long)m * n + i] = h;
+        const double grow = (r == 0.0) ? 5.0 : clampd(0.95 * crp_exp(-0.2 * crp_log(r)), 0.2, 5.0);
+        double hnext = h * grow;
+        if (!rejected && h < h_prop) hnext = fmax(hnext, h_prop);
+        hprop = clampd(hnext, hmin, hmax);
+    }
+    xT[3 * i] = y.x; xT[3 * i + 1] = y.y; xT[3 * i + 2] = y.z;
+    uT[3 * i] = y.ux; uT[3 * i + 1] = y.uy; uT[3 * i + 2] = y.uz;
+}
+
+template <int L, bool H = false>
+__device__ __forceinline__ void frozen_step(const FieldDev& F, double kappa, Y6& y, double h,
+                                            unsigned long long* hh = nullptr) {
+    const Y6 k1 = deriv<L, H>(F, kappa, y, hh);
+    Y6 y5, err;
+    ck_attempt<L, H>(F, kappa, y, k1, h, y5, err, hh);
+    y = y5;
+}
+
+// Frozen replay; with H also the hash of every cell its stages looked up (two replays with
+// equal hashes stayed inside the same cells, where the map is smooth).
+template <int L, bool H>
+__global__ void k_adj_replay(FieldDev F, const double* __restrict__ y0, const double* __restrict__ kap,
+                             const double* __restrict__ h, int n_steps, double* __restrict__ xT,
+                             double* __restrict__ uT, unsigned long long* __restrict__ cell_hash,
+                             long long n) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Y6 y;
+    load6(y0, n, i, y);
+    const double kappa = kap[i];
+    unsigned long long hh = 0;
+    for (int m = 0; m < n_steps; ++m) frozen_step<L, H>(F, kappa, y, h[(long long)m * n + i], &hh);
+    xT[3 * i] = y.x; xT[3 * i + 1] = y.y; xT[3 * i + 2] = y.z;
+    uT[3 * i] = y.ux; uT[3 * i + 1] = y.uy; uT[3 * i + 2] = y.uz;
+    if (H) cell_hash[i] = hh;
+}
+
+// Full lookup: B, corner weights, their x-derivatives, nodes and corner values; corner order
+// 000, 001, ..., 111; dw_c/dx_a = (d w_a) * w_b * w_c with d(1 - f) = -1/spacing, d f = 1/spacing.
+template <int L>
+__device__ __forceinline__ void lookup_full(const FieldDev& F, const Y6& Y, double B[3], double w[8],
+                                            double dw[8][3], long long node[8], double G[8][3]) {
+    long long ix[2], iy[2], iz[2];
+    double wx[2], wy[2], wz[2];
+    axis(Y.x, F.ox, F.inv_spacing, F.nx, F.pow2, ix[0], ix[1], wx[0], wx[1]);
+    axis(Y.y, F.oy, F.inv_spacing, F.ny, F.pow2, iy[0], iy[1], wy[0], wy[1]);
+    axis(Y.z, F.oz, F.inv_spacing, F.nz, F.pow2, iz[0], iz[1], wz[0], wz[1]);
+    const double dd[2] = {-F.inv_spacing, F.inv_spacing};
+    B[0] = 0.0; B[1] = 0.0; B[2] = 0.0;
+    int c8 = 0;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int c = 0; c < 2; ++c, ++c8) {
+                const double wt = (wx[a] * wy[b]) * wz[c];
+                w[c8] = wt;
+                dw[c8][0] = (dd[a] * wy[b]) * wz[c];
+                dw[c8][1] = (wx[a] * dd[b]) * wz[c];
+                dw[c8][2] = (wx[a] * wy[b]) * dd[c];
+                node[c8] = (ix[a] * F.ny + iy[b]) * F.nz + iz[c];
+                const V3 g = corner<L>(F, node[c8]);
+                G[c8][0] = g.x; G[c8][1] = g.y; G[c8][2] = g.z;
+                B[0] = B[0] + wt * g.x;
+                B[1] = B[1] + wt * g.y;
+                B[2] = B[2] + wt * g.z;
+            }
+}
+
+// Vector-Jacobian product of f at stage state Y with cotangent kb (see the file comment).
+template <int L>
+__device__ __forceinline__ void vjp_f(const FieldDev& F, double kappa, const Y6& Y, const Y6& kb,
+                                      Y6& Yb, double* __restrict__ grid_bar, double& kappa_bar) {
+    double B[3], w[8], dw[8][3], G[8][3];
+    long long node[8];
+    lookup_full<L>(F, Y, B, w, dw, node, G);
+    const double Bb0 = kappa * (kb.uy * Y.uz - kb.uz * Y.uy);
+    const double Bb1 = kappa * (kb.uz * Y.ux - kb.ux * Y.uz);
+    const double Bb2 = kappa * (kb.ux * Y.uy - kb.uy * Y.ux);
+    const double uxB0 = Y.uy * B[2] - Y.uz * B[1];
+    const double uxB1 = Y.uz * B[0] - Y.ux * B[2];
+    const double uxB2 = Y.ux * B[1] - Y.uy * B[0];
+    kappa_bar = kappa_bar + ((kb.ux * uxB0 + kb.uy * uxB1) + kb.uz * uxB2);
+    Yb.ux = kb.x + kappa * (B[1] * kb.uz - B[2] * kb.uy);
+    Yb.uy = kb.y + kappa * (B[2] * kb.ux - B[0] * kb.uz);
+    Yb.uz = kb.z + kappa * (B[0] * kb.uy - B[1] * kb.ux);
+    Yb.x = 0.0; Yb.y = 0.0; Yb.z = 0.0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const double gB = (G[c][0] * Bb0 + G[c][1] * Bb1) + G[c][2] * Bb2;
+        Yb.x = Yb.x + dw[c][0] * gB;
+        Yb.y = Yb.y + dw[c][1] * gB;
+        Yb.z = Yb.z + dw[c][2] * gB;
+        double* gp = grid_bar + node[c] * 3;
+        atomicAdd(gp + 0, w[c] * Bb0);
+        atomicAdd(gp + 1, w[c] * Bb1);
+        atomicAdd(gp + 2, w[c] * Bb2);
+    }
+}
+
+__device__ __forceinline__ void axpy6(Y6& acc, double s, const Y6& v) {
+    acc.x = acc.x + s * v.x; acc.y = acc.y + s * v.y; acc.z = acc.z + s * v.z;
+    acc.ux = acc.ux + s * v.ux; acc.uy = acc.uy + s * v.uy; acc.uz = acc.uz + s * v.uz;
+}
+__device__ __forceinline__ Y6 scale6(double s, const Y6& v) {
+    return {s * v.x, s * v.y, s * v.z, s * v.ux, s * v.uy, s * v.uz};
+}
+__device__ __forceinline__ void add6(Y6& acc, const Y6& v) {
+    acc.x = acc.x + v.x; acc.y = acc.y + v.y; acc.z = acc.z + v.z;
+    acc.ux = acc.ux + v.ux; acc.uy = acc.uy + v.uy; acc.uz = acc.uz + v.uz;
+}
+
+__constant__ double cA[6][5] = {
+    {0.0, 0.0, 0.0, 0.0, 0.0},
+    {1.0 / 5.0, 0.0, 0.0, 0.0, 0.0},
+    {3.0 / 40.0, 9.0 / 40.0, 0.0, 0.0, 0.0},
+    {3.0 / 10.0, -9.0 / 10.0, 6.0 / 5.0, 0.0, 0.0},
+    {-11.0 / 54.0, 5.0 / 2.0, -70.0 / 27.0, 35.0 / 27.0, 0.0},
+    {1631.0 / 55296.0, 175.0 / 512.0, 575.0 / 13824.0, 44275.0 / 110592.0, 253.0 / 4096.0}};
+__constant__ double cB5[6] = {37.0 / 378.0, 0.0, 250.0 / 621.0, 125.0 / 594.0, 0.0, 512.0 / 1771.0};
+
+// One reverse step: lam = dL/dy_{m+1} in, dL/dy_m out; y = y_m.
+template <int L>
+__device__ void adjoint_step(const FieldDev& F, double kappa, const Y6& y, double hn, Y6& lam,
+                             double* __restrict__ grid_bar, double& kappa_bar) {
+    Y6 Y[6], k[6];
+    Y[0] = y;
+    k[0] = deriv<L>(F, kappa, y);
+    for (int i = 1; i < 6; ++i) {
+        // acc = A[i][0] k1; acc = acc + A[i][j] k_j (j < i), as in the stage sums
+        Y6 acc = scale6(cA[i][0], k[0]);
+        for (int j = 1; j < i; ++j) axpy6(acc, cA[i][j], k[j]);
+        Y[i] = {y.x + hn * acc.x, y.y + hn * acc.y, y.z + hn * acc.z,
+                y.ux + hn * acc.ux, y.uy + hn * acc.uy, y.uz + hn * acc.uz};
+        k[i] = deriv<L>(F, kappa, Y[i]);
+    }
+    Y6 kb[6];
+    for (int i = 0; i < 6; ++i) kb[i] = scale6(hn * cB5[i], lam);
+    Y6 yb = lam;
+    for (int i = 5; i >= 0; --i) {
+        Y6 Yb;
+        vjp_f<L>(F, kappa, Y[i], kb[i], Yb, grid_bar, kappa_bar);
+        add6(yb, Yb);
+        for (int j = 0; j < i; ++j) axpy6(kb[j], hn * cA[i][j], Yb);
+    }
+    lam = yb;
+}
+
+template <int L>
+__global__ void k_adj_backward(FieldDev F, const double* __restrict__ kap, const double* __restrict__ h,
+                               const double* __restrict__ ck, double* __restrict__ seg, int n_steps,
+                               int K, const double* __restrict__ uT_bar, double* __restrict__ grid_bar,
+                               double* __restrict__ y0_bar, double* __restrict__ kappa_bar_out,
+                               long long n) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double kappa = kap[i];
+    Y6 lam{0.0, 0.0, 0.0, uT_bar[3 * i], uT_bar[3 * i + 1], uT_bar[3 * i + 2]};
+    double kappa_bar = 0.0;
+    const int n_seg = (n_steps + K - 1) / K;
+    for (int sg = n_seg - 1; sg >= 0; --sg) {
+        const int m0 = sg * K, m1 = min(m0 + K, n_steps);
+        Y6 y;
+        load6(ck + (long long)sg * 6 * n, n, i, y);
+        store6(seg, n, i, y);
+        for (int m = m0; m < m1; ++m) {          // recompute the segment from its checkpoint
+            frozen_step<L>(F, kappa, y, h[(long long)m * n + i]);
+            store6(seg + (long long)(m - m0 + 1) * 6 * n, n, i, y);
+        }
+        for (int m = m1 - 1; m >= m0; --m) {
+            Y6 ym;
+            load6(seg + (long long)(m - m0) * 6 * n, n, i, ym);
+            adjoint_step<L>(F, kappa, ym, h[(long long)m * n + i], lam, grid_bar, kappa_bar);
+        }
+    }
+    store6(y0_bar, n, i, lam);
+    kappa_bar_out[i] = kappa_bar;
+}
+
+// dL/dp0 = (ubar0 - (u0 . ubar0) u0) / E + Ebar u0 with Ebar = -(kappa_bar * kappa) / E;
+// dL/dx0 = xbar0.
+__global__ void k_adj_p0bar(const double* __restrict__ y0, const double* __restrict__ kap,
+                            const double* __restrict__ E, const double* __restrict__ y0_bar,
+                            const double* __restrict__ kappa_bar, double* __restrict__ p0_bar,
+                            double* __restrict__ x0_bar, long long n) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Y6 y, yb;
+    load6(y0, n, i, y);
+    load6(y0_bar, n, i, yb);
+    const double e = E[i];
+    const double dot = (y.ux * yb.ux + y.uy * yb.uy) + y.uz * yb.uz;
+    const double Eb = -(kappa_bar[i] * kap[i]) / e;
+    p0_bar[3 * i] = (yb.ux - dot * y.ux) / e + Eb * y.ux;
+    p0_bar[3 * i + 1] = (yb.uy - dot * y.uy) / e + Eb * y.uy;
+    p0_bar[3 * i + 2] = (yb.uz - dot * y.uz) / e + Eb * y.uz;
+    if (x0_bar) {
+        x0_bar[3 * i] = yb.x; x0_bar[3 * i + 1] = yb.y; x0_bar[3 * i + 2] = yb.z;
+    }
+}
+
+int blocks(long long n) { return (int)((n + 127) / 128); }
+
+}  // namespace
+
+int adj_init(const double* x0, const double* p0, const int32_t* Z, double* y0, double* kappa,
+             double* E, long long n, void* stream) {
+    k_adj_init<<<blocks(n), 128, 0, (cudaStream_t)stream>>>(x0, p0, Z, y0, kappa, E, n);
+    return (int)cudaGetLastError();
+}
+
+int adj_record(const FieldDev& F, const double* y0, const double* kappa, double tol, double hmin,
+               double hmax, int n_steps, int K, double* h, double* ck, double* xT, double* uT,
+               long long n, void* stream) {
+    k_adj_record<LAYOUT_F64X4><<<blocks(n), 128, 0, (cudaStream_t)stream>>>(
+        F, y0, kappa, tol, hmin, hmax, n_steps, K, h, ck, xT, uT, n);
+    return (int)cudaGetLastError();
+}
+
+int adj_replay(const FieldDev& F, const double* y0, const double* kappa, const double* h, int n_steps,
+               double* xT, double* uT, unsigned long long* cell_hash, long long n, void* stream) {
+    if (cell_hash)
+        k_adj_replay<LAYOUT_F64X4, true><<<blocks(n), 128, 0, (cudaStream_t)stream>>>(
+            F, y0, kappa, h, n_steps, xT, uT, cell_hash, n);
+    else
+        k_adj_replay<LAYOUT_F64X4, false><<<blocks(n), 128, 0, (cudaStream_t)stream>>>(
+            F, y0, kappa, h, n_steps, xT, uT, nullptr, n);
+    return (int)cudaGetLastError();
+}
+
+int adj_backward(const FieldDev& F, const double* kappa, const double* h, const double* ck,
+                 double* seg, int n_steps, int K, const double* uT_bar, double* grid_bar,
+                 double* y0_bar, double* kappa_bar, long long n, void* stream) {
+    k_adj_backward<LAYOUT_F64X4><<<blocks(n), 128, 0, (cudaStream_t)stream>>>(
+        F, kappa, h, ck, seg, n_steps, K, uT_bar, grid_bar, y0_bar, kappa_bar, n);
+    return (int)cudaGetLastError();
+}
+
+int adj_p0bar(const double* y0, const double* kappa, const double* E, const double* y0_bar,
+              const double* kappa_bar, double* p0_bar, double* x0_bar, long long n, void* stream) {
+    k_adj_p0bar<<<blocks(n), 128, 0, (cudaStream_t)stream>>>(y0, kappa, E, y0_bar, kappa_bar, p0_bar,
+                                                             x0_bar, n);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace crp

@@ -1,6 +1,7 @@
 // crp_capi.cu -- the C ABI of libcrp.so (declared in include/crp.h): handles, argument
 // checks, device memory, and the small bookkeeping kernels around the propagate kernels
 // (grid layout, injection initialisation, work-list compaction, list swap, observer gather).
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -72,6 +73,32 @@ __global__ void k_layout<unsigned short, ushort4>(const unsigned short* __restri
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
         out[i] = make_ushort4(in[3 * i], in[3 * i + 1], in[3 * i + 2], 0);
+}
+
+// Widen a 4-wide FP32 / BF16 / F16 node layout to FP64 pairs (x, y | z, 0), with the exact
+// per-corner expression the FP64 kernel would otherwise evaluate on every lookup.
+__global__ void k_widen(const void* __restrict__ in, int layout, double scale,
+                        double2* __restrict__ out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        double x, y, z;
+        if (layout == LAYOUT_F32X4) {
+            const float4 v = reinterpret_cast<const float4*>(in)[i];
+            x = (double)v.x; y = (double)v.y; z = (double)v.z;
+        } else if (layout == LAYOUT_BF16X4) {
+            const ushort4 v = reinterpret_cast<const ushort4*>(in)[i];
+            x = (double)__uint_as_float((unsigned)v.x << 16) * scale;
+            y = (double)__uint_as_float((unsigned)v.y << 16) * scale;
+            z = (double)__uint_as_float((unsigned)v.z << 16) * scale;
+        } else {
+            const ushort4 v = reinterpret_cast<const ushort4*>(in)[i];
+            x = (double)__half2float(__ushort_as_half(v.x)) * scale;
+            y = (double)__half2float(__ushort_as_half(v.y)) * scale;
+            z = (double)__half2float(__ushort_as_half(v.z)) * scale;
+        }
+        out[2 * i] = make_double2(x, y);
+        out[2 * i + 1] = make_double2(z, 0.0);
+    }
 }
 
 // ---- injection: per-particle bookkeeping (Philox tau draw), validation ----------------
@@ -315,7 +342,7 @@ namespace {
 // One validated propagate call: kernel arguments and launch shape.
 struct Plan {
     PropArgs a{};
-    int grid = 0, block = 0, order = 0, mixed = 0, n_buckets = 0;
+    int grid = 0, block = 0, order = 0, mixed = 0, n_buckets = 0, layout = 0;
 };
 
 }  // namespace
@@ -324,6 +351,8 @@ struct crp_field {
     FieldDev dev;
     void* mem = nullptr;
     long long nodes = 0;
+    void* mem64 = nullptr;   // FP64 copy for the FP64 form (built on first use)
+    FieldDev dev64{};
 };
 
 struct crp_tables {
@@ -333,7 +362,9 @@ struct crp_tables {
 
 struct crp_sim {
     std::vector<FieldDev> host_fields;
+    std::vector<crp_field*> handles;
     FieldDev* d_fields = nullptr;
+    FieldDev* d_fields64 = nullptr;     // FP64 copies, for the FP64 form
     int layout = LAYOUT_F32X4;
     const crp_tables* tables = nullptr;
     unsigned long long seed = 0;
@@ -481,6 +512,7 @@ int crp_field_create(const void* grid, int32_t dtype, int32_t is_device, int32_t
 int crp_field_destroy(crp_field* field) {
     if (!field) return fail(CRP_ERR_INVALID_ARG, "field is NULL");
     if (field->mem) cudaFree(field->mem);
+    if (field->mem64) cudaFree(field->mem64);
     delete field;
     return CRP_OK;
 }
@@ -565,7 +597,10 @@ int crp_sim_create(const crp_field* const* fields, int32_t n_fields, const crp_t
     s->seed = seed;
     s->capacity = capacity;
     s->sms = device_sms();
-    for (int i = 0; i < n_fields; ++i) s->host_fields.push_back(fields[i]->dev);
+    for (int i = 0; i < n_fields; ++i) {
+        s->host_fields.push_back(fields[i]->dev);
+        s->handles.push_back(const_cast<crp_field*>(fields[i]));
+    }
     int rc = alloc_state(s->st, capacity);
     cudaError_t e = cudaSuccess;
     if (rc == CRP_OK) e = cudaMalloc(&s->d_fields, sizeof(FieldDev) * n_fields);
@@ -592,6 +627,7 @@ int crp_sim_destroy(crp_sim* s) {
     if (s->last) cudaStreamSynchronize(s->last);
     free_state(s->st);
     if (s->d_fields) cudaFree(s->d_fields);
+    if (s->d_fields64) cudaFree(s->d_fields64);
     if (s->lists[0]) cudaFree(s->lists[0]);
     if (s->lists[1]) cudaFree(s->lists[1]);
     if (s->done_list) cudaFree(s->done_list);
@@ -702,6 +738,36 @@ int crp_source_inject(crp_sim* s, const crp_particles* p, int64_t n, void* strea
 
 namespace {
 
+// Build (once per field) the FP64 copies and this simulation's descriptor array for them.
+int ensure_fp64_fields(crp_sim* s) {
+    if (s->d_fields64) return CRP_OK;
+    int rc = sync_stream(s);
+    if (rc) return rc;
+    std::vector<FieldDev> d64;
+    for (crp_field* f : s->handles) {
+        if (!f->mem64) {
+            void* m = nullptr;
+            CRP_CUDA(cudaMalloc(&m, (size_t)f->nodes * 32));
+            k_widen<<<grid_for(f->nodes, 256, 65535), 256>>>(f->mem, f->dev.layout, f->dev.scale,
+                                                             (double2*)m, f->nodes);
+            cudaError_t e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+            if (e != cudaSuccess) { cudaFree(m); return cuda_fail(e, "field widening"); }
+            f->mem64 = m;
+            f->dev64 = f->dev;
+            f->dev64.data = m;
+            f->dev64.layout = LAYOUT_F64X4;
+        }
+        d64.push_back(f->dev64);
+    }
+    void* d = nullptr;
+    CRP_CUDA(cudaMalloc(&d, sizeof(FieldDev) * d64.size()));
+    cudaError_t e = cudaMemcpy(d, d64.data(), sizeof(FieldDev) * d64.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { cudaFree(d); return cuda_fail(e, "cudaMemcpy(fields64)"); }
+    s->d_fields64 = (FieldDev*)d;
+    return CRP_OK;
+}
+
 int make_plan(crp_sim* s, const crp_params* prm, double tol, double hmin, double hmax,
               double dmax, Plan& P) {
     if (!s || !prm) return fail(CRP_ERR_INVALID_ARG, "sim or params is NULL");
@@ -720,11 +786,20 @@ int make_plan(crp_sim* s, const crp_params* prm, double tol, double hmin, double
     if (pickup != CRP_PICKUP_OFF && pickup != CRP_PICKUP_ON) return fail(CRP_ERR_INVALID_ARG, "unknown pickup");
     const int block = prm->block_size > 0 ? prm->block_size : 128;
     if (block % 32 || block > 256) return fail(CRP_ERR_INVALID_ARG, "block_size must be a multiple of 32, <= 256");
+    // the FP64 form reads FP64 copies of the grids (no per-corner widening on the FP64 pipe)
+    const FieldDev* fields = s->d_fields;
+    int layout = s->layout;
+    if (!mixed && layout != LAYOUT_F64X4) {
+        int rc = ensure_fp64_fields(s);
+        if (rc) return rc;
+        fields = s->d_fields64;
+        layout = LAYOUT_F64X4;
+    }
     int bps = prm->blocks_per_sm;
     if (bps <= 0) {
         int occ = 0;
-        const int oe = mixed ? propagate_mixed_occupancy(s->layout, block, &occ)
-                             : propagate_fp64_occupancy(s->layout, block, &occ);
+        const int oe = mixed ? propagate_mixed_occupancy(layout, block, &occ)
+                             : propagate_fp64_occupancy(layout, block, &occ);
         if (oe != 0 || occ < 1) occ = 1;
         bps = occ;
     }
@@ -732,10 +807,11 @@ int make_plan(crp_sim* s, const crp_params* prm, double tol, double hmin, double
     P.block = block;
     P.order = order;
     P.mixed = mixed ? 1 : 0;
+    P.layout = layout;
     P.n_buckets = order == CRP_ORDER_GRID ? kBuckets * (int)s->host_fields.size() : kBuckets;
     PropArgs& a = P.a;
     a.st = s->st;
-    a.fields = s->d_fields;
+    a.fields = fields;
     a.n_fields = (int)s->host_fields.size();
     a.has_tables = s->tables ? 1 : 0;
     if (s->tables) a.tab = s->tables->dev;
@@ -762,8 +838,11 @@ int enqueue(crp_sim* s, const Plan& P, cudaStream_t st) {
         k_build_worklist<<<sgrid, 256, 0, st>>>(s->st.status, s->lists[0], s->ctr);
     } else {
         const int grid_major = P.order == CRP_ORDER_GRID ? 1 : 0;
+        // fixed regions sized for the largest bucket count: [hist | offsets]; the scan leaves
+        // hist zeroed for the next build, whatever order that build uses
+        const int max_buckets = kBuckets * (int)s->host_fields.size();
         unsigned* hist = s->sort_scratch;
-        unsigned* offs = s->sort_scratch + P.n_buckets;
+        unsigned* offs = s->sort_scratch + max_buckets;
         const size_t shm = (size_t)P.n_buckets * sizeof(unsigned);
         k_cost_hist<<<sgrid, 256, shm <= 48 * 1024 ? shm : 0, st>>>(
             s->st.status, s->st.E, s->st.Z, s->st.grid_id, grid_major, P.n_buckets,
@@ -779,8 +858,8 @@ int enqueue(crp_sim* s, const Plan& P, cudaStream_t st) {
     for (int gen = 0; gen < 2; ++gen) {
         if (a.pickup) CRP_CUDA(cudaMemsetAsync(s->lists[1 - gen], 0xff, sizeof(int32_t) * s->capacity, st));
         a.list = gen;
-        int e = P.mixed ? launch_propagate_mixed(a, s->layout, P.grid, P.block, st)
-                        : launch_propagate_fp64(a, s->layout, P.grid, P.block, st);
+        int e = P.mixed ? launch_propagate_mixed(a, P.layout, P.grid, P.block, st)
+                        : launch_propagate_fp64(a, P.layout, P.grid, P.block, st);
         if (e) return cuda_fail((cudaError_t)e, "propagate kernel launch");
         k_swap<<<1, 1, 0, st>>>(s->ctr, s->capacity, gen);
         CRP_CUDA(cudaGetLastError());
@@ -805,7 +884,8 @@ __global__ void k_loop_cond(Counters* C, cudaGraphConditionalHandle h, long long
 
 bool same_plan(const Plan& x, const Plan& y) {
     return std::memcmp(&x.a, &y.a, sizeof(PropArgs)) == 0 && x.grid == y.grid &&
-           x.block == y.block && x.order == y.order && x.mixed == y.mixed && x.n_buckets == y.n_buckets;
+           x.block == y.block && x.order == y.order && x.mixed == y.mixed && x.n_buckets == y.n_buckets &&
+           x.layout == y.layout;
 }
 
 }  // namespace
@@ -904,6 +984,7 @@ int crp_sync(crp_sim* s, double timeout_s) {
     if (b & BIT_RANGE) return fail(CRP_ERR_TABLE_RANGE, "species outside tables");
     if (b & BIT_INVALID) return fail(CRP_ERR_INVALID_ARG, "invalid particle in injection");
     if (b & BIT_TIMEOUT) return fail(CRP_ERR_TIMEOUT, "a pushed secondary never appeared in its list");
+    if (b & BIT_BOUNDS) return fail(CRP_ERR_CUDA, "a work-list entry or grid id was out of range (skipped)");
     return CRP_OK;
 }
 
@@ -1106,3 +1187,153 @@ extern "C" int crp_propagate_noalloc(const void* grid, int32_t nx, int32_t ny, i
     if (bits & BIT_INVALID) return fail(CRP_ERR_INVALID_ARG, "invalid particle");
     return CRP_OK;
 }
+
+// ---- differentiation through a frozen step sequence -----------------------------------------
+struct crp_adjoint {
+    crp_field* field = nullptr;
+    long long n = 0;
+    int n_steps = 0, K = 0, n_ck = 0;
+    double *y0 = nullptr, *kappa = nullptr, *E = nullptr, *h = nullptr, *ck = nullptr;
+    double *seg = nullptr, *y0_bar = nullptr, *kappa_bar = nullptr, *y0_tmp = nullptr;
+    double *kappa_tmp = nullptr, *E_tmp = nullptr;
+    int32_t* Z = nullptr;
+    bool recorded = false;
+};
+
+namespace {
+
+int field_fp64_desc(crp_field* f, FieldDev& out) {
+    if (f->dev.layout == LAYOUT_F64X4) { out = f->dev; return CRP_OK; }
+    if (!f->mem64) {
+        void* m = nullptr;
+        CRP_CUDA(cudaMalloc(&m, (size_t)f->nodes * 32));
+        k_widen<<<grid_for(f->nodes, 256, 65535), 256>>>(f->mem, f->dev.layout, f->dev.scale,
+                                                         (double2*)m, f->nodes);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) { cudaFree(m); return cuda_fail(e, "field widening"); }
+        f->mem64 = m;
+        f->dev64 = f->dev;
+        f->dev64.data = m;
+        f->dev64.layout = LAYOUT_F64X4;
+    }
+    out = f->dev64;
+    return CRP_OK;
+}
+
+void adj_free(crp_adjoint* a) {
+    double* ds[] = {a->y0, a->kappa, a->E, a->h, a->ck, a->seg, a->y0_bar, a->kappa_bar, a->y0_tmp,
+                    a->kappa_tmp, a->E_tmp};
+    for (double* p : ds)
+        if (p) cudaFree(p);
+    if (a->Z) cudaFree(a->Z);
+}
+
+}  // namespace
+
+extern "C" {
+
+int crp_adjoint_create(const crp_field* field, int64_t n, int32_t n_steps, int32_t K, crp_adjoint** out) {
+    if (!out) return fail(CRP_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!field || n < 1 || n_steps < 1 || K < 1) return fail(CRP_ERR_INVALID_ARG, "need field, n >= 1, n_steps >= 1, checkpoint_every >= 1");
+    crp_adjoint* a = new crp_adjoint();
+    a->field = const_cast<crp_field*>(field);
+    a->n = n;
+    a->n_steps = n_steps;
+    a->K = K;
+    a->n_ck = (n_steps + K - 1) / K;
+    struct { double** p; size_t count; } al[] = {
+        {&a->y0, 6 * (size_t)n}, {&a->kappa, (size_t)n}, {&a->E, (size_t)n},
+        {&a->h, (size_t)n_steps * n}, {&a->ck, (size_t)a->n_ck * 6 * n}, {&a->seg, (size_t)(K + 1) * 6 * n},
+        {&a->y0_bar, 6 * (size_t)n}, {&a->kappa_bar, (size_t)n}, {&a->y0_tmp, 6 * (size_t)n},
+        {&a->kappa_tmp, (size_t)n}, {&a->E_tmp, (size_t)n}};
+    for (auto& q : al) {
+        cudaError_t e = cudaMalloc(q.p, q.count * sizeof(double));
+        if (e != cudaSuccess) { adj_free(a); delete a; return cuda_fail(e, "cudaMalloc(adjoint)"); }
+    }
+    cudaError_t e = cudaMalloc(&a->Z, sizeof(int32_t) * n);
+    if (e != cudaSuccess) { adj_free(a); delete a; return cuda_fail(e, "cudaMalloc(adjoint Z)"); }
+    FieldDev F;
+    int rc = field_fp64_desc(a->field, F);
+    if (rc) { adj_free(a); delete a; return rc; }
+    *out = a;
+    return CRP_OK;
+}
+
+int crp_adjoint_destroy(crp_adjoint* a) {
+    if (!a) return fail(CRP_ERR_INVALID_ARG, "adjoint is NULL");
+    cudaDeviceSynchronize();
+    adj_free(a);
+    delete a;
+    return CRP_OK;
+}
+
+int crp_adjoint_forward(crp_adjoint* a, const double* x0, const double* p0, const int32_t* Z,
+                        double tol, double hmin, double hmax, double* xT, double* uT, void* stream) {
+    if (!a || !x0 || !p0 || !Z || !xT || !uT) return fail(CRP_ERR_INVALID_ARG, "NULL argument");
+    if (!(tol > 0.0) || !(hmin > 0.0) || !(hmax >= hmin) || !std::isfinite(hmax))
+        return fail(CRP_ERR_INVALID_ARG, "need tolerance > 0 and 0 < min_step <= max_step");
+    FieldDev F;
+    int rc = field_fp64_desc(a->field, F);
+    if (rc) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    CRP_CUDA(cudaMemcpyAsync(a->Z, Z, sizeof(int32_t) * a->n, cudaMemcpyDeviceToDevice, st));
+    int e = adj_init(x0, p0, a->Z, a->y0, a->kappa, a->E, a->n, st);
+    if (e) return cuda_fail((cudaError_t)e, "adjoint init");
+    e = adj_record(F, a->y0, a->kappa, tol, hmin, hmax, a->n_steps, a->K, a->h, a->ck, xT, uT, a->n, st);
+    if (e) return cuda_fail((cudaError_t)e, "adjoint forward");
+    a->recorded = true;
+    return CRP_OK;
+}
+
+int crp_adjoint_replay(crp_adjoint* a, const crp_field* field, const double* p0, double* xT,
+                       double* uT, uint64_t* cell_hash, void* stream) {
+    if (!a || !xT || !uT) return fail(CRP_ERR_INVALID_ARG, "NULL argument");
+    if (!a->recorded) return fail(CRP_ERR_INVALID_ARG, "no recorded forward pass");
+    crp_field* f = field ? const_cast<crp_field*>(field) : a->field;
+    if (f->dev.nx != a->field->dev.nx || f->dev.ny != a->field->dev.ny || f->dev.nz != a->field->dev.nz)
+        return fail(CRP_ERR_INVALID_ARG, "replay field has another grid geometry");
+    FieldDev F;
+    int rc = field_fp64_desc(f, F);
+    if (rc) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const double* y0 = a->y0;
+    const double* kap = a->kappa;
+    if (p0) {   // new directions and kappa; positions as recorded
+        CRP_CUDA(cudaMemcpyAsync(a->y0_tmp, a->y0, sizeof(double) * 3 * a->n, cudaMemcpyDeviceToDevice, st));
+        int e = adj_init(nullptr, p0, a->Z, a->y0_tmp, a->kappa_tmp, a->E_tmp, a->n, st);
+        if (e) return cuda_fail((cudaError_t)e, "replay init");
+        y0 = a->y0_tmp;
+        kap = a->kappa_tmp;
+    }
+    int e = adj_replay(F, y0, kap, a->h, a->n_steps, xT, uT, (unsigned long long*)cell_hash, a->n, st);
+    if (e) return cuda_fail((cudaError_t)e, "adjoint replay");
+    return CRP_OK;
+}
+
+int crp_adjoint_backward(crp_adjoint* a, const double* uT_bar, double* grid_bar, double* p0_bar,
+                         double* x0_bar, void* stream) {
+    if (!a || !uT_bar || !grid_bar || !p0_bar) return fail(CRP_ERR_INVALID_ARG, "NULL argument");
+    if (!a->recorded) return fail(CRP_ERR_INVALID_ARG, "no recorded forward pass");
+    FieldDev F;
+    int rc = field_fp64_desc(a->field, F);
+    if (rc) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int e = adj_backward(F, a->kappa, a->h, a->ck, a->seg, a->n_steps, a->K, uT_bar, grid_bar,
+                         a->y0_bar, a->kappa_bar, a->n, st);
+    if (e) return cuda_fail((cudaError_t)e, "adjoint backward");
+    e = adj_p0bar(a->y0, a->kappa, a->E, a->y0_bar, a->kappa_bar, p0_bar, x0_bar, a->n, st);
+    if (e) return cuda_fail((cudaError_t)e, "adjoint p0 gradient");
+    return CRP_OK;
+}
+
+int crp_adjoint_read_steps(crp_adjoint* a, double* h, int32_t is_device) {
+    if (!a || !h) return fail(CRP_ERR_INVALID_ARG, "NULL argument");
+    CRP_CUDA(cudaDeviceSynchronize());
+    CRP_CUDA(cudaMemcpy(h, a->h, sizeof(double) * a->n * a->n_steps,
+                        is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
+    return CRP_OK;
+}
+
+}  // extern "C"

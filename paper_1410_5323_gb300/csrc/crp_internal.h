@@ -51,6 +51,7 @@ enum : uint32_t {
     BIT_RANGE = 4u,
     BIT_INVALID = 8u,
     BIT_TIMEOUT = 16u,
+    BIT_BOUNDS = 32u,       // a work-list entry or grid id out of range (skipped)
 };
 
 struct Counters {
@@ -93,5 +94,20 @@ int launch_propagate_fp64(const PropArgs& a, int layout, int grid, int block, vo
 int propagate_fp64_occupancy(int layout, int block, int* blocks_per_sm);
 int launch_propagate_mixed(const PropArgs& a, int layout, int grid, int block, void* stream);
 int propagate_mixed_occupancy(int layout, int block, int* blocks_per_sm);
+
+// Adjoint launchers (adjoint.cu). Arrays are component-major [component][n] for y,
+// [step][n] for h, [checkpoint][6][n] for checkpoints.
+int adj_init(const double* x0, const double* p0, const int32_t* Z, double* y0, double* kappa,
+             double* E, long long n, void* stream);
+int adj_record(const FieldDev& F, const double* y0, const double* kappa, double tol, double hmin,
+               double hmax, int n_steps, int K, double* h, double* ck, double* xT, double* uT,
+               long long n, void* stream);
+int adj_replay(const FieldDev& F, const double* y0, const double* kappa, const double* h, int n_steps,
+               double* xT, double* uT, unsigned long long* cell_hash, long long n, void* stream);
+int adj_backward(const FieldDev& F, const double* kappa, const double* h, const double* ck,
+                 double* seg, int n_steps, int K, const double* uT_bar, double* grid_bar,
+                 double* y0_bar, double* kappa_bar, long long n, void* stream);
+int adj_p0bar(const double* y0, const double* kappa, const double* E, const double* y0_bar,
+              const double* kappa_bar, double* p0_bar, double* x0_bar, long long n, void* stream);
 
 }  // namespace crp

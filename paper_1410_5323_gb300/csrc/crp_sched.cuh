@@ -65,10 +65,15 @@ __device__ __forceinline__ int sched_pop(const PropArgs& a, bool idle, int lane,
     const unsigned rank = (unsigned)__popc(im & ((1u << lane) - 1u));
     if (rank >= got) return -1;
     const unsigned long long pos = base + rank;
-    if (from == 0) return a.lists[L][pos];
+    if (from == 0) {
+        const int32_t v = a.lists[L][pos];
+        if (v < 0 || v >= a.capacity) { bits |= BIT_BOUNDS; return -1; }
+        return v;
+    }
     cuda::atomic_ref<int32_t, cuda::thread_scope_device> e(a.lists[P][pos]);
     for (int t = 0; t < kPublishWaitLimit; ++t) {
         const int32_t v = e.load(cuda::memory_order_acquire);
+        if (v >= a.capacity) { bits |= BIT_BOUNDS; return -1; }
         if (v >= 0) return v;
         __nanosleep(64);
     }

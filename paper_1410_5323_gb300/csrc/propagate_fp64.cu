@@ -16,165 +16,12 @@
 #include "crp_internal.h"
 #include "crp_math.cuh"
 #include "crp_sched.cuh"
+#include "crp_fp64.cuh"
 
 namespace crp {
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
-
-// Cash & Karp (1990) tableau; b - b* reduced to single rationals.
-constexpr double A21 = 1.0 / 5.0;
-constexpr double A31 = 3.0 / 40.0, A32 = 9.0 / 40.0;
-constexpr double A41 = 3.0 / 10.0, A42 = -9.0 / 10.0, A43 = 6.0 / 5.0;
-constexpr double A51 = -11.0 / 54.0, A52 = 5.0 / 2.0, A53 = -70.0 / 27.0, A54 = 35.0 / 27.0;
-constexpr double A61 = 1631.0 / 55296.0, A62 = 175.0 / 512.0, A63 = 575.0 / 13824.0,
-                 A64 = 44275.0 / 110592.0, A65 = 253.0 / 4096.0;
-constexpr double B1 = 37.0 / 378.0, B3 = 250.0 / 621.0, B4 = 125.0 / 594.0, B6 = 512.0 / 1771.0;
-constexpr double E1 = -277.0 / 64512.0, E3 = 6925.0 / 370944.0, E4 = -6925.0 / 202752.0,
-                 E5 = -277.0 / 14336.0, E6 = 277.0 / 7084.0;
-
-struct V3 { double x, y, z; };
-
-template <int L>
-__device__ __forceinline__ V3 corner(const FieldDev& F, long long node) {
-    V3 g;
-    if constexpr (L == LAYOUT_F32X4) {
-        const float4 v = __ldg(reinterpret_cast<const float4*>(F.data) + node);
-        g.x = (double)v.x; g.y = (double)v.y; g.z = (double)v.z;
-    } else if constexpr (L == LAYOUT_F64X4) {
-        const double2* p = reinterpret_cast<const double2*>(F.data) + 2 * node;
-        const double2 a = __ldg(p), b = __ldg(p + 1);
-        g.x = a.x; g.y = a.y; g.z = b.x;
-    } else if constexpr (L == LAYOUT_BF16X4) {
-        const ushort4 v = __ldg(reinterpret_cast<const ushort4*>(F.data) + node);
-        g.x = (double)__uint_as_float((unsigned)v.x << 16) * F.scale;
-        g.y = (double)__uint_as_float((unsigned)v.y << 16) * F.scale;
-        g.z = (double)__uint_as_float((unsigned)v.z << 16) * F.scale;
-    } else {
-        const ushort4 v = __ldg(reinterpret_cast<const ushort4*>(F.data) + node);
-        g.x = (double)__half2float(__ushort_as_half(v.x)) * F.scale;
-        g.y = (double)__half2float(__ushort_as_half(v.y)) * F.scale;
-        g.z = (double)__half2float(__ushort_as_half(v.z)) * F.scale;
-    }
-    return g;
-}
-
-// One axis of the periodic lookup: r = (x - o)*(1/spacing), i0 = floor(r) mod n, weights.
-__device__ __forceinline__ void axis(double x, double o, double inv, int n, int pow2,
-                                     long long& i0, long long& i1, double& w0, double& w1) {
-    const double r = (x - o) * inv;
-    const double fl = floor(r);
-    const double fr = r - fl;
-    const long long i = (long long)fl;
-    long long a;
-    if (pow2) a = i & (long long)(n - 1);
-    else { a = i % n; if (a < 0) a += n; }
-    i0 = a;
-    i1 = (a + 1 == n) ? 0 : a + 1;
-    w0 = 1.0 - fr;
-    w1 = fr;
-}
-
-// Trilinear periodic lookup; corners summed in the order 000, 001, ..., 111 (x, y, z),
-// weight ((w_x * w_y) * w_z).
-template <int L>
-__device__ __forceinline__ V3 field_b(const FieldDev& F, double x, double y, double z) {
-    long long ix0, ix1, iy0, iy1, iz0, iz1;
-    double wx0, wx1, wy0, wy1, wz0, wz1;
-    axis(x, F.ox, F.inv_spacing, F.nx, F.pow2, ix0, ix1, wx0, wx1);
-    axis(y, F.oy, F.inv_spacing, F.ny, F.pow2, iy0, iy1, wy0, wy1);
-    axis(z, F.oz, F.inv_spacing, F.nz, F.pow2, iz0, iz1, wz0, wz1);
-    const long long ny = F.ny, nz = F.nz;
-    const long long r00 = (ix0 * ny + iy0) * nz, r01 = (ix0 * ny + iy1) * nz;
-    const long long r10 = (ix1 * ny + iy0) * nz, r11 = (ix1 * ny + iy1) * nz;
-    const V3 g0 = corner<L>(F, r00 + iz0), g1 = corner<L>(F, r00 + iz1);
-    const V3 g2 = corner<L>(F, r01 + iz0), g3 = corner<L>(F, r01 + iz1);
-    const V3 g4 = corner<L>(F, r10 + iz0), g5 = corner<L>(F, r10 + iz1);
-    const V3 g6 = corner<L>(F, r11 + iz0), g7 = corner<L>(F, r11 + iz1);
-    const double w00 = wx0 * wy0, w01 = wx0 * wy1, w10 = wx1 * wy0, w11 = wx1 * wy1;
-    double t;
-    V3 B;
-    t = w00 * wz0; B.x = t * g0.x;       B.y = t * g0.y;       B.z = t * g0.z;
-    t = w00 * wz1; B.x = B.x + t * g1.x; B.y = B.y + t * g1.y; B.z = B.z + t * g1.z;
-    t = w01 * wz0; B.x = B.x + t * g2.x; B.y = B.y + t * g2.y; B.z = B.z + t * g2.z;
-    t = w01 * wz1; B.x = B.x + t * g3.x; B.y = B.y + t * g3.y; B.z = B.z + t * g3.z;
-    t = w10 * wz0; B.x = B.x + t * g4.x; B.y = B.y + t * g4.y; B.z = B.z + t * g4.z;
-    t = w10 * wz1; B.x = B.x + t * g5.x; B.y = B.y + t * g5.y; B.z = B.z + t * g5.z;
-    t = w11 * wz0; B.x = B.x + t * g6.x; B.y = B.y + t * g6.y; B.z = B.z + t * g6.z;
-    t = w11 * wz1; B.x = B.x + t * g7.x; B.y = B.y + t * g7.y; B.z = B.z + t * g7.z;
-    return B;
-}
-
-struct Y6 { double x, y, z, ux, uy, uz; };
-
-// f(y) = (u, kappa u x B(x))
-template <int L>
-__device__ __forceinline__ Y6 deriv(const FieldDev& F, double kappa, const Y6& y) {
-    const V3 B = field_b<L>(F, y.x, y.y, y.z);
-    Y6 k;
-    k.x = y.ux; k.y = y.uy; k.z = y.uz;
-    k.ux = kappa * (y.uy * B.z - y.uz * B.y);
-    k.uy = kappa * (y.uz * B.x - y.ux * B.z);
-    k.uz = kappa * (y.ux * B.y - y.uy * B.x);
-    return k;
-}
-
-#define CRP_STAGE(dst, expr)                                                           \
-    do {                                                                               \
-        dst.x = y.x + h * (expr(x));  dst.y = y.y + h * (expr(y));                      \
-        dst.z = y.z + h * (expr(z));  dst.ux = y.ux + h * (expr(ux));                   \
-        dst.uy = y.uy + h * (expr(uy)); dst.uz = y.uz + h * (expr(uz));                 \
-    } while (0)
-
-// One Cash-Karp attempt of size h from y with k1 = f(y).
-template <int L>
-__device__ __forceinline__ void ck_attempt(const FieldDev& F, double kappa, const Y6& y,
-                                           const Y6& k1, double h, Y6& y5, Y6& err) {
-    Y6 t;
-#define S2(c) (A21 * k1.c)
-    CRP_STAGE(t, S2);
-    const Y6 k2 = deriv<L>(F, kappa, t);
-#define S3(c) (A31 * k1.c + A32 * k2.c)
-    CRP_STAGE(t, S3);
-    const Y6 k3 = deriv<L>(F, kappa, t);
-#define S4(c) (A41 * k1.c + A42 * k2.c + A43 * k3.c)
-    CRP_STAGE(t, S4);
-    const Y6 k4 = deriv<L>(F, kappa, t);
-#define S5(c) (A51 * k1.c + A52 * k2.c + A53 * k3.c + A54 * k4.c)
-    CRP_STAGE(t, S5);
-    const Y6 k5 = deriv<L>(F, kappa, t);
-#define S6(c) (A61 * k1.c + A62 * k2.c + A63 * k3.c + A64 * k4.c + A65 * k5.c)
-    CRP_STAGE(t, S6);
-    const Y6 k6 = deriv<L>(F, kappa, t);
-#define SB(c) (B1 * k1.c + B3 * k3.c + B4 * k4.c + B6 * k6.c)
-    CRP_STAGE(y5, SB);
-#define SE(c) (h * (E1 * k1.c + E3 * k3.c + E4 * k4.c + E5 * k5.c + E6 * k6.c))
-    err.x = SE(x); err.y = SE(y); err.z = SE(z);
-    err.ux = SE(ux); err.uy = SE(uy); err.uz = SE(uz);
-#undef S2
-#undef S3
-#undef S4
-#undef S5
-#undef S6
-#undef SB
-#undef SE
-}
-
-__device__ __forceinline__ double error_ratio(const Y6& e, double h, double tol) {
-    if (h == 0.0) return 0.0;
-    const double ex = sqrt((e.x * e.x + e.y * e.y) + e.z * e.z) / h;
-    const double eu = sqrt((e.ux * e.ux + e.uy * e.uy) + e.uz * e.uz);
-    return fmax(ex, eu) / tol;
-}
-
-__device__ __forceinline__ double clampd(double v, double lo, double hi) {
-    return fmin(fmax(v, lo), hi);
-}
-
-__device__ __forceinline__ bool finite6(const Y6& y) {
-    return isfinite(y.x) && isfinite(y.y) && isfinite(y.z) && isfinite(y.ux) &&
-           isfinite(y.uy) && isfinite(y.uz);
-}
+using namespace fp64;
 
 template <int L>
 __global__ void __launch_bounds__(256) k_propagate_fp64(const PropArgs a) {
@@ -224,6 +71,7 @@ __global__ void __launch_bounds__(256) k_propagate_fp64(const PropArgs a) {
             n_steps = __ldcg(&S.n_steps[slot]); n_att = __ldcg(&S.n_att[slot]);
             taken = 0;
             new_step = true;
+            if (gid < 0 || gid >= a.n_fields) { bits |= BIT_BOUNDS; slot = -1; }
         }
         if (__ballot_sync(kFull, slot >= 0) == 0) break;
 

@@ -202,6 +202,9 @@ __global__ void CRP_MIXED_BOUNDS k_propagate_mixed(const PropArgs a) {
         if (popped >= 0) {
             slot = popped;
             gid = __ldcg(&S.grid_id[slot]);
+            if (gid < 0 || gid >= a.n_fields) { bits |= BIT_BOUNDS; gid = 0; slot = -1; }
+        }
+        if (slot >= 0 && popped >= 0) {
             const FieldDev& G = a.fields[gid];
             F.data = G.data; F.nx = G.nx; F.ny = G.ny; F.nz = G.nz; F.pow2 = G.pow2;
             F.scale = (float)G.scale;

@@ -142,3 +142,22 @@ def test_full_size_batched_workload_sampled(oracle_lib):
 
     assert np.all(gs["s"] == w.dmax_m)
     assert stats.ks_2samp(defl(gs), defl(o)).pvalue > 0.01
+
+
+def test_switching_orders_on_one_simulation(small_batch):
+    """Consecutive calls with different work-list orders on the same simulation (the sort
+    scratch is reused) give the same bits as a fresh simulation."""
+    w, grids, p = small_batch
+    ref = _sim(grids, p)
+    ref.propagate(w.tol, w.hmin_m, w.hmax_m, 8 * I.MPC)
+    ref.sync(120.0)
+    R = by_uid(ref.state())
+    sim = _sim(grids, p)
+    for order in (2, 3, 2, 1, 3):
+        sim.reset()
+        sim.inject(p)
+        sim.propagate(w.tol, w.hmin_m, w.hmax_m, 8 * I.MPC, order=order)
+        assert sim.sync(120.0, raise_on_error=False) == 0
+        S = by_uid(sim.state())
+        for k in R:
+            assert np.array_equal(R[k], S[k]), (order, k)
