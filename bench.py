@@ -58,8 +58,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
-    ap.add_argument("--form", default="fp64", choices=["fp64", "mixed"],
-                    help="form whose throughput is `value`; the other form is reported under `forms`")
+    ap.add_argument("--form", default=None, choices=["fp64", "mixed"],
+                    help="form whose throughput is `value` (default: fp64 for the FP64 workload, "
+                         "mixed for the precision and batching workloads); the other form is "
+                         "reported under `forms` for the FP64 workload")
     ap.add_argument("--no-other-form", action="store_true")
     ap.add_argument("--workload", default="fp64_256cube_1M_nuclei")
     ap.add_argument("--n-particles", type=int, default=0, help="override batch size (testing)")
@@ -82,20 +84,47 @@ def dist_env():
     return ws, rank, local
 
 
+class GridInput:
+    """One field grid in the form both sides need: the library's Field and the oracle's."""
+
+    def __init__(self, grid=None, bf16=None, scale=1.0):
+        self.grid, self.bf16, self.scale = grid, bf16, scale
+
+    def field(self, crp, spacing):
+        if self.bf16 is not None:
+            return crp.Field(self.bf16, spacing, scale=self.scale)
+        return crp.Field(self.grid, spacing)
+
+    def oracle_field(self, O, spacing):
+        if self.bf16 is not None:
+            import torch
+
+            bits = self.bf16.view(torch.int16).cpu().numpy().view(np.uint16)
+            return O.OracleField(bits, spacing, scale=self.scale, dtype=O.BF16)
+        return O.OracleField(self.grid, spacing)
+
+
 def build_inputs(w: I.Workload, n: int, rank: int):
-    """Field grids (list), tables, particles of the workload (this rank's batch)."""
+    """Field grids (list of GridInput), tables, particles of the workload (this rank's batch)."""
     tables = I.synthetic_tables() if w.interactions else None
+    if w.grid_n >= 512:     # generated and quantised on the device (BF16 + one FP32 scale)
+        B = I.kolmogorov_grid_torch(w.grid_n, w.lmin_cells, w.lmax_cells, w.brms_t, w.grid_seed)
+        q, scale = I.quantize_bf16(B)
+        del B
+        parts = I.make_particles(n, w.particle_seed + 7919 * rank, w.species, w.energy,
+                                 uid_offset=rank * n)
+        return [GridInput(bf16=q, scale=scale)], tables, parts
     if w.n_grids > 1:
         grids, _ = I.batched_grids(w)
         per = max(1, n // w.n_grids)
         parts = I.batched_particles(w, per, seed=w.particle_seed + 7919 * rank)
         parts.uid[:] += rank * len(parts)
-        return grids, tables, parts
+        return [GridInput(grid=g) for g in grids], tables, parts
     grid = I.kolmogorov_grid(w.grid_n, w.spacing_m, w.lmin_cells, w.lmax_cells, w.brms_t,
                              w.grid_seed).astype(np.float32)
     parts = I.make_particles(n, w.particle_seed + 7919 * rank, w.species, w.energy,
                              uid_offset=rank * n)
-    return [grid], tables, parts
+    return [GridInput(grid=grid)], tables, parts
 
 
 def oracle_sample_index(w: I.Workload, n_total: int, sample: int) -> np.ndarray:
@@ -173,7 +202,7 @@ def cpu_baseline(w, grids, tables, parts, sample: int, form_desc: str):
     O.inject(st, sub, w.rng_seed, ot)
     threads = os.cpu_count() or 1
     t0 = time.perf_counter()
-    rc, stats = O.propagate(st, [O.OracleField(g, w.spacing_m) for g in grids], ot, w.tol,
+    rc, stats = O.propagate(st, [g.oracle_field(O, w.spacing_m) for g in grids], ot, w.tol,
                             w.hmin_m, w.hmax_m, w.dmax_m, seed=w.rng_seed, n_threads=threads)
     dt = time.perf_counter() - t0
     return ({"value": stats["accepted"] / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
@@ -244,7 +273,7 @@ def run_reference(args):
         ot = O.OracleTables(tables) if tables is not None else None
         O.inject(st, sub, w.rng_seed, ot)
         t0 = time.perf_counter()
-        rc, stats = O.propagate(st, [O.OracleField(g, w.spacing_m) for g in grids], ot, w.tol,
+        rc, stats = O.propagate(st, [g.oracle_field(O, w.spacing_m) for g in grids], ot, w.tol,
                                 w.hmin_m, w.hmax_m, w.dmax_m, seed=w.rng_seed,
                                 n_threads=os.cpu_count() or 1)
         dt = time.perf_counter() - t0
@@ -287,10 +316,11 @@ def run_own(args):
     n = len(parts)
     cap = capacity_for(parts)
 
-    fields = [crp.Field(g, w.spacing_m) for g in grids]
+    fields = [g.field(crp, w.spacing_m) for g in grids]
     tabs = crp.Tables(tables) if tables is not None else None
     sim = crp.Simulation(fields, tabs, seed=w.rng_seed, capacity=cap)
     slice_steps = args.slice_steps if args.slice_steps >= 0 else (16000 if w.n_grids > 1 else 0)
+    grid_bytes = sum(int(np.prod(f.shape)) for f in fields) * (8 if w.grid_n >= 512 else 16)
     order = args.order or (3 if w.n_grids > 1 else 2)
     stream = torch.cuda.current_stream(dev)
 
@@ -446,11 +476,12 @@ def run_own(args):
         "dtype": "f64" if args.form == "fp64" else "f32 stages / f64 norm+path / double-float position",
         "data": "synthetic",
         "config": {"workload": w.name, "particles_per_gpu": n,
-                   "grid": f"{w.n_grids} x {w.grid_n}^3 f32", "order": order,
+                   "grid": f"{w.n_grids} x {w.grid_n}^3 " + ("bf16 + fp32 scale" if w.grid_n >= 512 else "f32"),
+                   "order": order,
                    "slice_steps": slice_steps,
                    "form": args.form, "dmax_mpc": w.dmax_m / I.MPC, "tol": w.tol,
-                   "l2": "inputs larger than L2 (grid 268 MB as float4, state 1.7 GB) and a "
-                         "256 MB flush before every step",
+                   "l2": f"inputs larger than L2 (grids {grid_bytes / 1e6:.0f} MB in device layout, "
+                         f"particle state {cap * 170 / 1e9:.2f} GB) and a 256 MB flush before every step",
                    "parallelism": f"dp{ws} (independent particle batches per GPU)"},
         "accepted_steps_per_step": accepted_all / args.steps,
         "attempted_steps_per_step": attempted_all / args.steps,
@@ -473,6 +504,11 @@ def run_own(args):
 
 def main():
     args = parse()
+    w = I.workload(args.workload)
+    if args.form is None:
+        args.form = "fp64" if w.name.startswith("fp64") else "mixed"
+        if not w.name.startswith("fp64"):
+            args.no_other_form = True
     if args.impl == "reference":
         return run_reference(args)
     return run_own(args)

@@ -100,30 +100,28 @@ def kolmogorov_grid(n: int, spacing_m: float, lmin_cells: float, lmax_cells: flo
 
 
 def kolmogorov_grid_torch(n: int, lmin_cells: float, lmax_cells: float, brms_t: float,
-                          seed: int, device: str = "cuda", out_dtype=None):
-    """Same recipe as :func:`kolmogorov_grid`, built with torch on a device, one
-    component at a time, for grids too large for host FFTs (e.g. 1024^3).
+                          seed: int, device: str = "cuda"):
+    """Same recipe as :func:`kolmogorov_grid`, built with torch one component at a time
+    (for grids too large for host FFTs, e.g. 1024^3 on the GPU). FP32 spectrum and FFT.
 
     Randomness comes from a seeded torch generator on that device, so the realisation
     differs from the numpy one for the same seed but is reproducible on one machine.
-    Returns a tensor [n, n, n, 3] of ``out_dtype`` (default float32) and the FP32 scale
-    that was applied (B = stored * 1 for float32 outputs).
+    Returns B [n, n, n, 3] float32 (tesla) with <|B|^2> = brms^2.
     """
     import torch
 
+    if n % 2:
+        raise ValueError("grid size must be even")
     g = torch.Generator(device=device)
     g.manual_seed(int(seed))
     k1 = torch.fft.fftfreq(n, d=1.0 / n, device=device, dtype=torch.float32)
-    out = torch.empty((n, n, n, 3), dtype=out_dtype or torch.float32, device=device)
-    nyq = -(n // 2)
-    # polarisation field e(k), drawn once, projected per component as needed
-    kx = k1.view(n, 1, 1)
-    ky = k1.view(1, n, 1)
-    kz = k1.view(1, 1, n)
+    kx, ky, kz = k1.view(n, 1, 1), k1.view(1, n, 1), k1.view(1, 1, n)
     kk = torch.sqrt(kx * kx + ky * ky + kz * kz)
+    nyq = -(n // 2)
     active = (kk >= n / lmax_cells) & (kk <= n / lmin_cells)
     active &= (kx != nyq) & (ky != nyq) & (kz != nyq)
     safe = torch.where(kk > 0, kk, torch.ones_like(kk))
+    # random polarisation perpendicular to k, unit length, times |k|^(-11/6)
     e = torch.randn((3, n, n, n), generator=g, device=device, dtype=torch.float32)
     phase = torch.rand((n, n, n), generator=g, device=device, dtype=torch.float32) * (2 * math.pi)
     kh = (kx / safe, ky / safe, kz / safe)
@@ -132,24 +130,39 @@ def kolmogorov_grid_torch(n: int, lmin_cells: float, lmax_cells: float, brms_t: 
         e[c] -= dot * kh[c]
     del dot
     en = torch.sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2])
-    en = torch.where(en > 0, en, torch.ones_like(en))
-    amp = torch.where(active, safe ** (-11.0 / 6.0), torch.zeros_like(safe)) / en
+    amp = torch.where(active, safe ** (-11.0 / 6.0) / torch.where(en > 0, en, torch.ones_like(en)),
+                      torch.zeros_like(safe))
     del en, kk, safe, active
     pos = (kx > 0) | ((kx == 0) & (ky > 0)) | ((kx == 0) & (ky == 0) & (kz > 0))
+    cos_p, sin_p = torch.cos(phase), torch.sin(phase)
+    del phase
+    out = torch.empty((n, n, n, 3), dtype=torch.float32, device=device)
     sumsq = 0.0
     for c in range(3):
-        Fc = torch.polar(amp * e[c], phase)
+        a = amp * e[c]
+        Fc = torch.complex(a * cos_p, a * sin_p)
+        del a
         mirror = torch.roll(torch.flip(Fc, dims=(0, 1, 2)), shifts=(1, 1, 1), dims=(0, 1, 2))
         Fc = torch.where(pos, Fc, torch.conj(mirror))
         del mirror
         Bc = torch.fft.ifftn(Fc).real
         del Fc
-        sumsq += float(torch.sum(Bc.double() * Bc.double()))
-        out[..., c] = Bc.to(out.dtype)
+        sumsq += float(torch.sum(Bc.double() ** 2))
+        out[..., c] = Bc
         del Bc
-    rms = math.sqrt(sumsq / n ** 3)
-    scale = brms_t / rms
-    return out, scale
+    out *= float(brms_t / math.sqrt(sumsq / n ** 3))
+    return out
+
+
+def quantize_bf16(B, scale: float | None = None):
+    """BF16 storage with one FP32 scale: B ~= scale * stored. Returns (stored bfloat16 tensor,
+    scale as a Python float that is exactly an FP32 value). Default scale: the rms of |B|."""
+    import torch
+
+    if scale is None:
+        scale = float(torch.sqrt(torch.mean(torch.sum(B.double() ** 2, dim=-1))))
+    scale = float(np.float32(scale))
+    return (B * (1.0 / scale)).to(torch.bfloat16), scale
 
 
 # --------------------------------------------------------------------------------------

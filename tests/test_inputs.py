@@ -88,3 +88,30 @@ def test_synthetic_table_layout():
     assert x[0] == 6.0 and abs(x[-1] - 14.0) < 1e-14 and abs(x[90] - 9.6) < 1e-14 and abs(x[75] - 9.0) < 1e-14
     assert t.has_loss[t.species_index(1, 0)] == 0 and t.has_pd[t.species_index(1, 1)] == 0
     assert t.has_loss[t.species_index(56, 26)] == 1 and t.has_pd[t.species_index(56, 26)] == 1
+
+
+def test_torch_kolmogorov_recipe_on_cpu():
+    """The device generator used for 1024^3 grids: same band, slope, divergence and rms."""
+    torch = __import__("pytest").importorskip("torch")
+    n, lmin, lmax = 32, 2.0, 16.0
+    B = I.kolmogorov_grid_torch(n, lmin, lmax, 2e-13, 5, device="cpu").double().numpy()
+    assert math.sqrt(np.mean(np.sum(B * B, -1))) == __import__("pytest").approx(2e-13, rel=1e-5)
+    F, kx, ky, kz = _spectrum_of(B)
+    kk = np.sqrt(kx ** 2 + ky ** 2 + kz ** 2)
+    P = np.sum(np.abs(F) ** 2, -1)
+    nyq = (kx == -n // 2) | (ky == -n // 2) | (kz == -n // 2)
+    band = (kk >= n / lmax) & (kk <= n / lmin) & ~nyq
+    assert np.max(P[~band]) < 1e-9 * np.max(P)
+    ratio = P[band] * kk[band] ** (11.0 / 3.0)
+    assert np.max(np.abs(ratio / ratio.mean() - 1)) < 1e-3        # FP32 spectrum
+    div = kx * F[..., 0] + ky * F[..., 1] + kz * F[..., 2]
+    assert np.max(np.abs(div)) < 1e-5 * np.max(np.sqrt(kk ** 2 * P))
+
+
+def test_bf16_quantization_scale_is_fp32_and_values_close():
+    torch = __import__("pytest").importorskip("torch")
+    B = torch.from_numpy(I.kolmogorov_grid(16, 1.0, 2, 8, 3e-13, 2).astype(np.float32))
+    q, scale = I.quantize_bf16(B)
+    assert q.dtype == torch.bfloat16 and scale == float(np.float32(scale))
+    err = (q.float() * scale - B).abs().max() / B.abs().max()
+    assert err < 2 ** -8
