@@ -50,6 +50,10 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2.070e9 * 2 / 1e12   # FFMA lanes x 2
 MIXED_FP64_OPS_PER_ATTEMPT = 14
 MIXED_FP64_OPS_PER_ACCEPTED = 5
 MIXED_FP32_FLOP_PER_ATTEMPT = 612
+# DRAM bytes (read + write) per attempted step of the propagate kernels, measured by ncu on
+# the 10^6-nuclei workload at reduced batch (both launches of one call; profiles/
+# k_propagate_*_256cube_1M_nuclei.md); traffic of a call = this x its attempts.
+DRAM_BYTES_PER_ATTEMPT = {"fp64": 140.5, "mixed": 92.7}
 
 
 def parse():
@@ -65,6 +69,7 @@ def parse():
     ap.add_argument("--no-other-form", action="store_true")
     ap.add_argument("--workload", default="fp64_256cube_1M_nuclei")
     ap.add_argument("--n-particles", type=int, default=0, help="override batch size (testing)")
+    ap.add_argument("--grid-n", type=int, default=0, help="override grid size (profiling)")
     ap.add_argument("--cpu-sample", type=int, default=16384, help="primaries in the oracle sample")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -77,6 +82,14 @@ def parse():
 
 
 # ---------------------------------------------------------------------------------------
+def workload_for(args) -> I.Workload:
+    w = I.workload(args.workload)
+    if args.grid_n:
+        w.grid_n = args.grid_n
+        w.name = f"{w.name} (grid {args.grid_n}^3)"
+    return w
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -212,19 +225,26 @@ def cpu_baseline(w, grids, tables, parts, sample: int, form_desc: str):
              "rc": rc}, st.snapshot())
 
 
-def roofline_for(form, attempted, accepted, tables, prop_s):
+def traffic_for(form, attempted, calls):
+    """DRAM bytes per propagate call (both launches), from the measured bytes per attempt."""
+    if form not in DRAM_BYTES_PER_ATTEMPT or calls <= 0:
+        return None
+    return DRAM_BYTES_PER_ATTEMPT[form] * attempted / calls
+
+
+def roofline_for(form, attempted, accepted, tables, prop_s, calls=1):
     """Roofline of the propagate kernel for one form, from the live CUDA-event time."""
     if form == "fp64":
         flops = FLOP_PER_ATTEMPT * attempted + (FLOP_PER_ACCEPTED_TABLES * accepted if tables else 0)
         ach = flops / prop_s / 1e12
         return {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                "frac": ach / FP64_PEAK_TFLOPS, "traffic": traffic_for(form, attempted, calls),
                 "kernel": "k_propagate_fp64 (2 launches per call + 4 bookkeeping kernels)",
                 "peak_source": "derived: 152 SM x 2 FP64 lanes/clk x 2070 MHz, FMA=2 (of derived)"}
     ops64 = MIXED_FP64_OPS_PER_ATTEMPT * attempted + MIXED_FP64_OPS_PER_ACCEPTED * accepted
     ach = ops64 / prop_s / 1e12
     return {"bound": "alu", "achieved": ach, "peak": FP64_OPS_PEAK_T, "unit": "TFLOP/s",
-            "frac": ach / FP64_OPS_PEAK_T, "traffic": None,
+            "frac": ach / FP64_OPS_PEAK_T, "traffic": traffic_for(form, attempted, calls),
             "kernel": "k_propagate_mixed (2 launches per call + 4 bookkeeping kernels)",
             "peak_source": "derived: FP64 pipe 152 SM x 2 lanes/clk x 2070 MHz = 0.629 T ops/s; "
                            "the residual FP64 ops (error norm, path length) bind this form",
@@ -258,7 +278,7 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    w = I.workload(args.workload)
+    w = workload_for(args)
     n = args.n_particles or w.n_particles
     grids, tables, parts = build_inputs(w, n, 0)
     import oracle as O
@@ -310,7 +330,7 @@ def run_own(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = I.workload(args.workload)
+    w = workload_for(args)
     n = args.n_particles or w.n_particles
     grids, tables, parts = build_inputs(w, n, rank)
     n = len(parts)
@@ -416,7 +436,10 @@ def run_own(args):
 
     # ---- roofline of the dominant kernel (the propagate call, timed live) ----
     prop_s = sum(prop_ms) * 1e-3
-    roofline = roofline_for(args.form, attempted, accepted, tables is not None, prop_s)
+    roofline = roofline_for(args.form, attempted, accepted, tables is not None, prop_s,
+                            calls=args.steps)
+    if w.name != "fp64_256cube_1M_nuclei":
+        roofline["traffic"] = None      # the traffic figures were measured on that workload
 
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
@@ -459,7 +482,8 @@ def run_own(args):
                  other_form: {"value": other["value"], "unit": UNIT,
                               "reject_frac": 1.0 - other["accepted_all"] / max(other["attempted_all"], 1.0),
                               "roofline": roofline_for(other_form, other["attempted"], other["accepted"],
-                                                       tables is not None, sum(other["prop_ms"]) * 1e-3)},
+                                                       tables is not None, sum(other["prop_ms"]) * 1e-3,
+                                                       calls=args.steps)},
                  "mixed_over_fp64": (other["value"] / value) if other_form == "mixed" else (value / other["value"]),
                  "mixed_error_vs_fp64_oracle": forms_err}
 
@@ -504,7 +528,7 @@ def run_own(args):
 
 def main():
     args = parse()
-    w = I.workload(args.workload)
+    w = workload_for(args)
     if args.form is None:
         args.form = "fp64" if w.name.startswith("fp64") else "mixed"
         if not w.name.startswith("fp64"):

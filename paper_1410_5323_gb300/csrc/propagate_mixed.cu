@@ -81,14 +81,26 @@ __device__ __forceinline__ F3 corner_f(const FieldF& F, int node) {
     }
 }
 
+// floor(t) and t - floor(t) without conversion instructions, exact for |t| < 2^22:
+// adding 1.5 * 2^23 rounds t to an integer held in the low mantissa bits.
+__device__ __forceinline__ int floor_frac(float t, float& frac) {
+    const float big = __fadd_rn(t, 12582912.0f);
+    const float n = __fsub_rn(big, 12582912.0f);      // t rounded to nearest (exact)
+    int i = __float_as_int(big) - 0x4B400000;
+    float f = __fsub_rn(t, n);                        // exact, in [-0.5, 0.5]
+    if (f < 0.0f) { f = __fadd_rn(f, 1.0f); i -= 1; }
+    frac = f;
+    return i;
+}
+
 // Trilinear periodic lookup at (base cell b, fraction f0) + offset p (cells).
 template <int L>
 __device__ __forceinline__ F3 field_f(const FieldF& F, int bx, int by, int bz, F3 f0, F3 p) {
-    const float tx = f0.x + p.x, ty = f0.y + p.y, tz = f0.z + p.z;
-    const float cx = floorf(tx), cy = floorf(ty), cz = floorf(tz);
-    const float fx = tx - cx, fy = ty - cy, fz = tz - cz;
-    const int ix = wrap(bx + (int)cx, F.nx, F.pow2), iy = wrap(by + (int)cy, F.ny, F.pow2),
-              iz = wrap(bz + (int)cz, F.nz, F.pow2);
+    float fx, fy, fz;
+    const int cx = floor_frac(f0.x + p.x, fx), cy = floor_frac(f0.y + p.y, fy),
+              cz = floor_frac(f0.z + p.z, fz);
+    const int ix = wrap(bx + cx, F.nx, F.pow2), iy = wrap(by + cy, F.ny, F.pow2),
+              iz = wrap(bz + cz, F.nz, F.pow2);
     const int ix1 = ix + 1 == F.nx ? 0 : ix + 1, iy1 = iy + 1 == F.ny ? 0 : iy + 1,
               iz1 = iz + 1 == F.nz ? 0 : iz + 1;
     const int r00 = (ix * F.ny + iy) * F.nz, r01 = (ix * F.ny + iy1) * F.nz;
@@ -163,7 +175,7 @@ __global__ void CRP_MIXED_BOUNDS k_propagate_mixed(const PropArgs a) {
     // field of the current particle
     FieldF F{};
     double sp = 1.0, inv_sp = 1.0, ox = 0, oy = 0, oz = 0, dmax_c = 0;
-    float hmin_c = 0, hmax_c = 0, sp_f = 1.0f;
+    float hmin_c = 0, hmax_c = 0, sp_f = 1.0f, csp_f = 1.0f;
     // step state
     bool new_step = true;
     int bx = 0, by = 0, bz = 0;
@@ -208,7 +220,7 @@ __global__ void CRP_MIXED_BOUNDS k_propagate_mixed(const PropArgs a) {
             const FieldDev& G = a.fields[gid];
             F.data = G.data; F.nx = G.nx; F.ny = G.ny; F.nz = G.nz; F.pow2 = G.pow2;
             F.scale = (float)G.scale;
-            sp = G.spacing; inv_sp = G.inv_spacing; sp_f = (float)sp;
+            sp = G.spacing; inv_sp = G.inv_spacing; sp_f = (float)sp; csp_f = (float)(kC * sp);
             ox = G.ox; oy = G.oy; oz = G.oz;
             hmin_c = (float)(a.hmin * inv_sp);
             hmax_c = (float)(a.hmax * inv_sp);
@@ -270,7 +282,7 @@ __global__ void CRP_MIXED_BOUNDS k_propagate_mixed(const PropArgs a) {
                 h_first = h;
                 rejected = 0;
                 att_step = 0;
-                kappa = (float)Z * (float)(kC * sp) / (float)E;
+                kappa = (float)Z * csp_f / (float)E;
                 df_floor(Rx, bx, f0.x);
                 df_floor(Ry, by, f0.y);
                 df_floor(Rz, bz, f0.z);
