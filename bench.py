@@ -149,6 +149,19 @@ def oracle_sample_index(w: I.Workload, n_total: int, sample: int) -> np.ndarray:
     return np.arange(min(sample, n_total))
 
 
+def aggregate(dist, total_ms: float, accepted: float, attempted: float, device):
+    """Whole-job figures over ranks: the slowest rank's time, the sum of the steps."""
+    if dist is None:
+        return float(total_ms), float(accepted), float(attempted)
+    import torch
+
+    t = torch.tensor([total_ms, accepted, attempted], dtype=torch.float64, device=device)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(t[1]), float(t[2])
+
+
 def capacity_for(parts) -> int:
     return int(len(parts) + np.sum(parts.A.astype(np.int64) - 1))
 
@@ -402,15 +415,8 @@ def run_own(args):
         torch.cuda.synchronize()
         barrier()
         r["clocks"] = clocks.stop() if clocks else None
-        total_ms = sum(r["step_ms"])
-        if dist is not None:
-            t = torch.tensor([total_ms, r["accepted"], r["attempted"]], dtype=torch.float64, device=dev)
-            mx = t.clone()
-            dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-            dist.all_reduce(t, op=dist.ReduceOp.SUM)
-            r["total_ms_max"], r["accepted_all"], r["attempted_all"] = float(mx[0]), float(t[1]), float(t[2])
-        else:
-            r["total_ms_max"], r["accepted_all"], r["attempted_all"] = total_ms, float(r["accepted"]), float(r["attempted"])
+        r["total_ms_max"], r["accepted_all"], r["attempted_all"] = aggregate(
+            dist, sum(r["step_ms"]), r["accepted"], r["attempted"], dev)
         r["value"] = r["accepted_all"] / (r["total_ms_max"] * 1e-3)
         return r
 
@@ -526,8 +532,63 @@ def run_own(args):
     return 0
 
 
+def run_adjoint(args):
+    """Differentiation workload: record the steps of n particles, then the reverse pass.
+    value = frozen steps differentiated per second (n x n_steps / (forward + backward))."""
+    import torch
+
+    import paper_1410_5323_gb300 as crp
+    from paper_1410_5323_gb300.adjoint import Adjoint, direction_loss, perturbed_targets
+
+    w = workload_for(args)
+    n = args.n_particles or w.n_particles
+    n_steps, K = 2000, 64
+    g = I.kolmogorov_grid(w.grid_n, w.spacing_m, w.lmin_cells, w.lmax_cells, w.brms_t,
+                          w.grid_seed).astype(np.float32)
+    p = I.make_particles(n, w.particle_seed, w.species, w.energy)
+    dev = torch.device("cuda")
+    field = crp.Field(torch.from_numpy(g).to(dev), w.spacing_m)
+    adj = Adjoint(field, n, n_steps, K)
+    x0 = torch.from_numpy(p.x).to(dev)
+    p0 = torch.from_numpy(p.u * p.E[:, None]).to(dev)
+    Z = torch.from_numpy(p.Z).to(dev)
+    fwd_ms, bwd_ms = [], []
+    for it in range(args.warmup + args.steps):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record()
+        _, uT = adj.forward(x0, p0, Z, w.tol, w.hmin_m, w.hmax_m)
+        e1.record()
+        t = perturbed_targets(uT)
+        u = uT.clone().requires_grad_(True)
+        direction_loss(u, t).backward()
+        e1b = torch.cuda.Event(enable_timing=True)
+        e1b.record()
+        adj.backward(u.grad, g.shape)
+        e2.record()
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            fwd_ms.append(e0.elapsed_time(e1))
+            bwd_ms.append(e1b.elapsed_time(e2))
+    steps = n * n_steps
+    value = steps * args.steps / ((sum(fwd_ms) + sum(bwd_ms)) * 1e-3)
+    line = {
+        "metric": "frozen particle-steps differentiated/s (recorded forward + checkpointed reverse pass)",
+        "value": value, "unit": "steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": (sum(fwd_ms) + sum(bwd_ms)) / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "particles": n, "frozen_steps": n_steps, "checkpoint_every": K,
+                   "grid": f"{w.grid_n}^3 f32 (read as its FP64 copy)"},
+        "forward_ms": sum(fwd_ms) / args.steps, "backward_ms": sum(bwd_ms) / args.steps,
+        "gpu_launches": 2 + 2 * args.steps,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload.startswith("adjoint"):
+        return run_adjoint(args)
     w = workload_for(args)
     if args.form is None:
         args.form = "fp64" if w.name.startswith("fp64") else "mixed"
