@@ -35,7 +35,10 @@ def build(force: bool = False) -> str:
 class Field(C.Structure):
     _fields_ = [("data", C.c_void_p), ("dtype", C.c_int32), ("nx", C.c_int32),
                 ("ny", C.c_int32), ("nz", C.c_int32), ("pad_", C.c_int32),
-                ("spacing", C.c_double), ("origin", C.c_double * 3), ("scale", C.c_double)]
+                ("spacing", C.c_double), ("origin", C.c_double * 3), ("scale", C.c_double),
+                ("mod_data", C.c_void_p), ("mod_dtype", C.c_int32), ("mod_nx", C.c_int32),
+                ("mod_ny", C.c_int32), ("mod_nz", C.c_int32), ("mod_spacing", C.c_double),
+                ("mod_origin", C.c_double * 3)]
 
 
 class Tables(C.Structure):
@@ -78,6 +81,8 @@ def lib():
         L.orc_log.argtypes = [d]
         L.orc_log.restype = d
         L.orc_field_value.argtypes = [p, p, p]
+        L.orc_modulation_value.argtypes = [p, p]
+        L.orc_modulation_value.restype = d
         L.orc_deriv.argtypes = [p, d, p, p]
         L.orc_ck_attempt.argtypes = [p, d, p, p, d, p, p]
         L.orc_error_ratio.argtypes = [p, d, d]
@@ -100,15 +105,21 @@ class OracleField:
     """Keeps the grid array alive next to its C descriptor."""
 
     def __init__(self, grid: np.ndarray, spacing: float, origin=(0.0, 0.0, 0.0), scale: float = 1.0,
-                 dtype: int | None = None):
+                 dtype: int | None = None, modulation: np.ndarray | None = None,
+                 mod_spacing: float = 1.0, mod_origin=(0.0, 0.0, 0.0)):
         if dtype is None:
             dtype = {np.dtype(np.float64): F64, np.dtype(np.float32): F32}[grid.dtype]
         self.grid = np.ascontiguousarray(grid)
         nx, ny, nz = self.grid.shape[:3]
         if dtype in (BF16, F16):
             scale = float(np.float32(scale))      # half-precision grids carry an FP32 scale
+        self.mod = None if modulation is None else np.ascontiguousarray(modulation)
+        mdt = 0 if self.mod is None else {np.dtype(np.float64): F64, np.dtype(np.float32): F32}[self.mod.dtype]
+        mshape = (0, 0, 0) if self.mod is None else self.mod.shape[:3]
         self.c = Field(_ptr(self.grid), dtype, nx, ny, nz, 0, float(spacing),
-                       (C.c_double * 3)(*origin), float(scale))
+                       (C.c_double * 3)(*origin), float(scale),
+                       None if self.mod is None else _ptr(self.mod), mdt, *mshape,
+                       float(mod_spacing), (C.c_double * 3)(*mod_origin))
 
 
 class OracleTables:
@@ -195,6 +206,11 @@ def field_value(field: OracleField, x) -> np.ndarray:
     B = np.zeros(3)
     lib().orc_field_value(C.byref(field.c), _ptr(xa), _ptr(B))
     return B
+
+
+def modulation_value(field: OracleField, x) -> float:
+    xa = np.ascontiguousarray(x, dtype=np.float64)
+    return lib().orc_modulation_value(C.byref(field.c), _ptr(xa))
 
 
 def deriv(field: OracleField, kappa: float, y) -> np.ndarray:

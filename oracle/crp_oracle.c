@@ -185,6 +185,39 @@ static double grid_at(const orc_field* f, int64_t i, int64_t j, int64_t k, int c
     }
 }
 
+/* Modulation (Sec. 3.2): the scalar grid interpolated trilinearly, periodic over its own
+ * extent, corners summed in the order 000, ..., 111 with weight ((w_x * w_y) * w_z). */
+double orc_modulation_value(const orc_field* f, const double x[3])
+{
+    double inv = 1.0 / f->mod_spacing;
+    int64_t dims[3] = {f->mod_nx, f->mod_ny, f->mod_nz};
+    int64_t idx[3][2];
+    double w[3][2];
+    for (int a = 0; a < 3; ++a) {
+        double r = (x[a] - f->mod_origin[a]) * inv;
+        double fl = floor(r);
+        double fr = r - fl;
+        int64_t i = (int64_t)fl;
+        int64_t n = dims[a];
+        int64_t i0 = ((i % n) + n) % n;
+        idx[a][0] = i0;
+        idx[a][1] = (i0 + 1) % n;
+        w[a][0] = 1.0 - fr;
+        w[a][1] = fr;
+    }
+    double m = 0.0;
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            for (int c = 0; c < 2; ++c) {
+                double wt = (w[0][a] * w[1][b]) * w[2][c];
+                int64_t k = (idx[0][a] * f->mod_ny + idx[1][b]) * f->mod_nz + idx[2][c];
+                double v = f->mod_dtype == ORC_F64 ? ((const double*)f->mod_data)[k]
+                                                   : (double)((const float*)f->mod_data)[k];
+                m = m + wt * v;
+            }
+    return m;
+}
+
 /* Fractional index r = (x - origin) * (1/spacing); cell i0 = floor(r) wrapped modulo n;
  * weights (1 - f, f) with f = r - floor(r). B is the sum over the 8 cell corners, taken
  * in the order (a,b,c) = 000, 001, 010, ..., 111, of ((w_x,a * w_y,b) * w_z,c) * B_corner. */
@@ -214,6 +247,10 @@ void orc_field_value(const orc_field* f, const double x[3], double B[3])
                 for (int q = 0; q < 3; ++q)
                     B[q] = B[q] + wt * grid_at(f, idx[0][a], idx[1][b], idx[2][c], q);
             }
+    if (f->mod_data) {
+        double m = orc_modulation_value(f, x);
+        for (int q = 0; q < 3; ++q) B[q] = m * B[q];
+    }
 }
 
 /* ---- equation of motion (Sec. 2, 3D deflections) -------------------------------- */

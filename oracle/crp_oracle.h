@@ -47,6 +47,14 @@ typedef struct {
     double spacing;
     double origin[3];
     double scale;       /* multiplies BF16/F16 values; ignored for F32/F64 */
+    /* Optional modulation (Sec. 3.2 modulated grids): a scalar periodic grid M, node (i,j,k)
+     * at mod_origin + (i,j,k)*mod_spacing holding mod_data[(i*mod_ny + j)*mod_nz + k]
+     * (F32 or F64); B(x) = M(x) * b(x) with both interpolated trilinearly. NULL: none. */
+    const void* mod_data;
+    int32_t mod_dtype;
+    int32_t mod_nx, mod_ny, mod_nz;
+    double mod_spacing;
+    double mod_origin[3];
 } orc_field;
 
 /* Interaction tables on x = log10(Lorentz factor): node j at x0 + j/inv_dx.
@@ -85,6 +93,7 @@ double orc_uniform(uint64_t seed, uint64_t uid, uint32_t k, uint32_t tag);
 double orc_exp(double x);
 double orc_log(double x);
 void orc_field_value(const orc_field* f, const double x[3], double B[3]);
+double orc_modulation_value(const orc_field* f, const double x[3]);
 void orc_deriv(const orc_field* f, double kappa, const double y[6], double k[6]);
 void orc_ck_attempt(const orc_field* f, double kappa, const double y[6], const double k1[6],
                     double h, double y5[6], double err[6]);
