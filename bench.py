@@ -50,10 +50,18 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2.070e9 * 2 / 1e12   # FFMA lanes x 2
 MIXED_FP64_OPS_PER_ATTEMPT = 14
 MIXED_FP64_OPS_PER_ACCEPTED = 5
 MIXED_FP32_FLOP_PER_ATTEMPT = 612
-# DRAM bytes (read + write) per attempted step of the propagate kernels, measured by ncu on
-# the 10^6-nuclei workload at reduced batch (both launches of one call; profiles/
-# k_propagate_*_256cube_1M_nuclei.md); traffic of a call = this x its attempts.
-DRAM_BYTES_PER_ATTEMPT = {"fp64": 140.5, "mixed": 92.7}
+# Modulated fields add one scalar trilinear lookup per field evaluation: FP64 form 6 x
+# (axes 12, weights 12, 8 products, 7 sums, 3 products m*B) = 252 per attempt; mixed form
+# 6 x 38 FP32 flops per attempt and, per accepted step, the step-start modulation cell in
+# FP64 (3 x (2 widenings, 3 add, 1 mul, floor, 2 conversions, 1 mul)) = 33 FP64 ops.
+MOD_FLOP_PER_ATTEMPT = 252
+MIXED_MOD_FP64_OPS_PER_ACCEPTED = 33
+MIXED_MOD_FP32_FLOP_PER_ATTEMPT = 228
+# DRAM bytes (read + write) per attempted step of the propagate kernels, measured by ncu at
+# reduced batch (both launches of one call; the summaries under profiles/ name the command);
+# traffic of a call = this x its attempts. Keyed by (workload, form).
+DRAM_BYTES_PER_ATTEMPT = {("fp64_256cube_1M_nuclei", "fp64"): 140.5,
+                          ("fp64_256cube_1M_nuclei", "mixed"): 92.7}
 
 
 def parse():
@@ -100,21 +108,27 @@ def dist_env():
 class GridInput:
     """One field grid in the form both sides need: the library's Field and the oracle's."""
 
-    def __init__(self, grid=None, bf16=None, scale=1.0):
+    def __init__(self, grid=None, bf16=None, scale=1.0, mod=None, mod_spacing=1.0):
         self.grid, self.bf16, self.scale = grid, bf16, scale
+        self.mod, self.mod_spacing = mod, mod_spacing
 
     def field(self, crp, spacing):
         if self.bf16 is not None:
-            return crp.Field(self.bf16, spacing, scale=self.scale)
-        return crp.Field(self.grid, spacing)
+            f = crp.Field(self.bf16, spacing, scale=self.scale)
+        else:
+            f = crp.Field(self.grid, spacing)
+        if self.mod is not None:
+            f.modulate(self.mod, self.mod_spacing)
+        return f
 
     def oracle_field(self, O, spacing):
+        mkw = dict(modulation=self.mod, mod_spacing=self.mod_spacing)
         if self.bf16 is not None:
             import torch
 
             bits = self.bf16.view(torch.int16).cpu().numpy().view(np.uint16)
-            return O.OracleField(bits, spacing, scale=self.scale, dtype=O.BF16)
-        return O.OracleField(self.grid, spacing)
+            return O.OracleField(bits, spacing, scale=self.scale, dtype=O.BF16, **mkw)
+        return O.OracleField(self.grid, spacing, **mkw)
 
 
 def build_inputs(w: I.Workload, n: int, rank: int):
@@ -137,6 +151,12 @@ def build_inputs(w: I.Workload, n: int, rank: int):
                              w.grid_seed).astype(np.float32)
     parts = I.make_particles(n, w.particle_seed + 7919 * rank, w.species, w.energy,
                              uid_offset=rank * n)
+    if w.mod_n:             # modulated field; sources follow the matter density
+        rho = I.density_field(w.mod_n, w.mod_lmin_cells, w.mod_lmax_cells, w.mod_sigma_ln, w.mod_seed)
+        mod = I.modulation_from_density(rho)
+        parts.x[:] = I.density_positions(n, rho, w.mod_spacing_m, w.particle_seed + 7919 * rank)
+        del rho
+        return [GridInput(grid=grid, mod=mod, mod_spacing=w.mod_spacing_m)], tables, parts
     return [GridInput(grid=grid)], tables, parts
 
 
@@ -238,31 +258,36 @@ def cpu_baseline(w, grids, tables, parts, sample: int, form_desc: str):
              "rc": rc}, st.snapshot())
 
 
-def traffic_for(form, attempted, calls):
+def traffic_for(workload, form, attempted, calls):
     """DRAM bytes per propagate call (both launches), from the measured bytes per attempt."""
-    if form not in DRAM_BYTES_PER_ATTEMPT or calls <= 0:
+    key = (workload, form)
+    if key not in DRAM_BYTES_PER_ATTEMPT or calls <= 0:
         return None
-    return DRAM_BYTES_PER_ATTEMPT[form] * attempted / calls
+    return DRAM_BYTES_PER_ATTEMPT[key] * attempted / calls
 
 
-def roofline_for(form, attempted, accepted, tables, prop_s, calls=1):
+def roofline_for(form, attempted, accepted, tables, prop_s, calls=1, workload="", modulated=False):
     """Roofline of the propagate kernel for one form, from the live CUDA-event time."""
     if form == "fp64":
-        flops = FLOP_PER_ATTEMPT * attempted + (FLOP_PER_ACCEPTED_TABLES * accepted if tables else 0)
+        per_att = FLOP_PER_ATTEMPT + (MOD_FLOP_PER_ATTEMPT if modulated else 0)
+        flops = per_att * attempted + (FLOP_PER_ACCEPTED_TABLES * accepted if tables else 0)
         ach = flops / prop_s / 1e12
         return {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP64_PEAK_TFLOPS, "traffic": traffic_for(form, attempted, calls),
+                "frac": ach / FP64_PEAK_TFLOPS, "traffic": traffic_for(workload, form, attempted, calls),
                 "kernel": "k_propagate_fp64 (2 launches per call + 4 bookkeeping kernels)",
+                "flop_per_attempt": per_att,
                 "peak_source": "derived: 152 SM x 2 FP64 lanes/clk x 2070 MHz, FMA=2 (of derived)"}
-    ops64 = MIXED_FP64_OPS_PER_ATTEMPT * attempted + MIXED_FP64_OPS_PER_ACCEPTED * accepted
+    per_acc = MIXED_FP64_OPS_PER_ACCEPTED + (MIXED_MOD_FP64_OPS_PER_ACCEPTED if modulated else 0)
+    fp32_att = MIXED_FP32_FLOP_PER_ATTEMPT + (MIXED_MOD_FP32_FLOP_PER_ATTEMPT if modulated else 0)
+    ops64 = MIXED_FP64_OPS_PER_ATTEMPT * attempted + per_acc * accepted
     ach = ops64 / prop_s / 1e12
     return {"bound": "alu", "achieved": ach, "peak": FP64_OPS_PEAK_T, "unit": "TFLOP/s",
-            "frac": ach / FP64_OPS_PEAK_T, "traffic": traffic_for(form, attempted, calls),
+            "frac": ach / FP64_OPS_PEAK_T, "traffic": traffic_for(workload, form, attempted, calls),
             "kernel": "k_propagate_mixed (2 launches per call + 4 bookkeeping kernels)",
             "peak_source": "derived: FP64 pipe 152 SM x 2 lanes/clk x 2070 MHz = 0.629 T ops/s; "
                            "the residual FP64 ops (error norm, path length) bind this form",
-            "fp32_flop_per_attempt": MIXED_FP32_FLOP_PER_ATTEMPT,
-            "fp32_achieved_tflops": MIXED_FP32_FLOP_PER_ATTEMPT * attempted / prop_s / 1e12,
+            "fp32_flop_per_attempt": fp32_att,
+            "fp32_achieved_tflops": fp32_att * attempted / prop_s / 1e12,
             "fp32_peak_tflops": FP32_PEAK_TFLOPS}
 
 
@@ -354,6 +379,7 @@ def run_own(args):
     sim = crp.Simulation(fields, tabs, seed=w.rng_seed, capacity=cap)
     slice_steps = args.slice_steps if args.slice_steps >= 0 else (16000 if w.n_grids > 1 else 0)
     grid_bytes = sum(int(np.prod(f.shape)) for f in fields) * (8 if w.grid_n >= 512 else 16)
+    grid_bytes += sum(int(g.mod.size) * 4 for g in grids if g.mod is not None)
     order = args.order or (3 if w.n_grids > 1 else 2)
     stream = torch.cuda.current_stream(dev)
 
@@ -442,10 +468,9 @@ def run_own(args):
 
     # ---- roofline of the dominant kernel (the propagate call, timed live) ----
     prop_s = sum(prop_ms) * 1e-3
+    modulated = bool(w.mod_n)
     roofline = roofline_for(args.form, attempted, accepted, tables is not None, prop_s,
-                            calls=args.steps)
-    if w.name != "fp64_256cube_1M_nuclei":
-        roofline["traffic"] = None      # the traffic figures were measured on that workload
+                            calls=args.steps, workload=w.name, modulated=modulated)
 
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
@@ -489,7 +514,8 @@ def run_own(args):
                               "reject_frac": 1.0 - other["accepted_all"] / max(other["attempted_all"], 1.0),
                               "roofline": roofline_for(other_form, other["attempted"], other["accepted"],
                                                        tables is not None, sum(other["prop_ms"]) * 1e-3,
-                                                       calls=args.steps)},
+                                                       calls=args.steps, workload=w.name,
+                                                       modulated=modulated)},
                  "mixed_over_fp64": (other["value"] / value) if other_form == "mixed" else (value / other["value"]),
                  "mixed_error_vs_fp64_oracle": forms_err}
 
@@ -506,7 +532,9 @@ def run_own(args):
         "dtype": "f64" if args.form == "fp64" else "f32 stages / f64 norm+path / double-float position",
         "data": "synthetic",
         "config": {"workload": w.name, "particles_per_gpu": n,
-                   "grid": f"{w.n_grids} x {w.grid_n}^3 " + ("bf16 + fp32 scale" if w.grid_n >= 512 else "f32"),
+                   "grid": f"{w.n_grids} x {w.grid_n}^3 " + ("bf16 + fp32 scale" if w.grid_n >= 512 else "f32")
+                           + (f" x modulation {w.mod_n}^3 f32 ({w.mod_spacing_m / I.KPC:.0f} kpc; vector "
+                              f"{w.spacing_m / I.KPC:.0f} kpc)" if w.mod_n else ""),
                    "order": order,
                    "slice_steps": slice_steps,
                    "form": args.form, "dmax_mpc": w.dmax_m / I.MPC, "tol": w.tol,
@@ -591,8 +619,9 @@ def main():
         return run_adjoint(args)
     w = workload_for(args)
     if args.form is None:
-        args.form = "fp64" if w.name.startswith("fp64") else "mixed"
-        if not w.name.startswith("fp64"):
+        both = w.name.startswith("fp64") or w.mod_n > 0
+        args.form = "fp64" if both else "mixed"
+        if not both:
             args.no_other_form = True
     if args.impl == "reference":
         return run_reference(args)

@@ -104,6 +104,23 @@ int crp_field_create(const void* grid, int32_t dtype, int32_t is_device, int32_t
                      float scale, crp_field** out);
 int crp_field_destroy(crp_field* field);
 
+/* Modulated grid (Sec. 3.2, used so in Sec. 4): a small high-resolution vector grid b,
+ * repeated periodically, times a large low-resolution scalar grid M that carries the
+ * large-scale structure: B(x) = M(x) * b(x). M is interpolated trilinearly and periodically
+ * over its own extent, exactly like b: fractional index r = (x - origin_m) / spacing_m per
+ * axis, corners 000..111 weighted ((w_x w_y) w_z), and the product is taken after both
+ * lookups (the FP64 form evaluates m * B_c for each component c).
+ * mod: nx*ny*nz FP32 values (dtype must be CRP_DTYPE_F32), node (i,j,k) at (i*ny + j)*nz + k,
+ * host (is_device = 0) or device memory; copied, the caller keeps ownership. A field takes
+ * one modulation for its lifetime; simulations created from the field before this call keep
+ * the unmodulated field. All fields of one simulation are modulated, or none (crp_sim_create
+ * returns INVALID_ARG otherwise). The adjoint entry points reject modulated fields.
+ * Errors: INVALID_ARG (NULL pointer, dtype not F32, sizes < 1, above 2^31 nodes, spacing
+ * <= 0 or not finite, origin not finite, field already modulated); OOM; CUDA. */
+int crp_field_modulate(crp_field* field, const void* mod, int32_t dtype, int32_t is_device,
+                       int32_t nx, int32_t ny, int32_t nz, double spacing_m,
+                       const double origin_m[3]);
+
 /* ---- interaction tables (Sec. 2: pair-production loss, photo-disintegration) --------
  * Species s = Z*(n_max+1) + (A-Z), Z in [0,z_max], A-Z in [0,n_max]. Row s holds
  * n_nodes values of log10(rate in 1/m) on x = log10(gamma) = x0 + j/inv_dx, with

@@ -76,6 +76,7 @@ def lib() -> C.CDLL:
         sig = {
             "crp_field_create": ([p, i32, i32, i32, i32, i32, d, p, f, p], C.c_int),
             "crp_field_destroy": ([p], C.c_int),
+            "crp_field_modulate": ([p, p, i32, i32, i32, i32, i32, d, p], C.c_int),
             "crp_tables_create": ([i32, i32, i32, d, d, p, p, p, p, p], C.c_int),
             "crp_tables_destroy": ([p], C.c_int),
             "crp_sim_create": ([p, i32, p, u64, i64, p], C.c_int),
@@ -157,6 +158,22 @@ class Field:
         self._h = h
         self.shape = (nx, ny, nz)
         self.spacing = float(spacing_m)
+        self.modulated = False
+
+    def modulate(self, mod, spacing_m: float, origin_m=(0.0, 0.0, 0.0)) -> "Field":
+        """Attach a scalar modulation grid (paper Sec. 3.2 modulated grids): the field
+        becomes M(x) b(x). ``mod``: [nx, ny, nz] float32 numpy array or torch tensor."""
+        name = str(mod.dtype)
+        if name not in ("float32", "torch.float32"):
+            raise TypeError("modulation grids are float32")
+        nx, ny, nz = (int(v) for v in mod.shape[:3])
+        ptr, dev, keep = _buf(mod)
+        org = (C.c_double * 3)(*origin_m)
+        _check(lib().crp_field_modulate(self._h, ptr, DTYPE_F32, dev, nx, ny, nz, float(spacing_m), org),
+               "crp_field_modulate")
+        del keep
+        self.modulated = True
+        return self
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:

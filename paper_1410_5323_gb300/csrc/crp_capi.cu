@@ -342,7 +342,7 @@ namespace {
 // One validated propagate call: kernel arguments and launch shape.
 struct Plan {
     PropArgs a{};
-    int grid = 0, block = 0, order = 0, mixed = 0, n_buckets = 0, layout = 0;
+    int grid = 0, block = 0, order = 0, mixed = 0, n_buckets = 0, layout = 0, mod = 0;
 };
 
 }  // namespace
@@ -353,6 +353,7 @@ struct crp_field {
     long long nodes = 0;
     void* mem64 = nullptr;   // FP64 copy for the FP64 form (built on first use)
     FieldDev dev64{};
+    void* modmem = nullptr;  // modulation grid, FP32 (crp_field_modulate)
 };
 
 struct crp_tables {
@@ -366,6 +367,7 @@ struct crp_sim {
     FieldDev* d_fields = nullptr;
     FieldDev* d_fields64 = nullptr;     // FP64 copies, for the FP64 form
     int layout = LAYOUT_F32X4;
+    int mod = 0;                        // 1: every field carries a modulation grid
     const crp_tables* tables = nullptr;
     unsigned long long seed = 0;
     long long capacity = 0;
@@ -505,7 +507,36 @@ int crp_field_create(const void* grid, int32_t dtype, int32_t is_device, int32_t
     d.spacing = spacing_m;
     d.ox = origin_m[0]; d.oy = origin_m[1]; d.oz = origin_m[2];
     d.scale = (dtype == CRP_DTYPE_BF16 || dtype == CRP_DTYPE_F16) ? (double)scale : 1.0;
+    d.mod = nullptr;
     *out = f;
+    return CRP_OK;
+}
+
+int crp_field_modulate(crp_field* field, const void* mod, int32_t dtype, int32_t is_device,
+                       int32_t nx, int32_t ny, int32_t nz, double spacing_m, const double origin_m[3]) {
+    if (!field || !mod || !origin_m) return fail(CRP_ERR_INVALID_ARG, "field, modulation or origin is NULL");
+    if (dtype != CRP_DTYPE_F32) return fail(CRP_ERR_INVALID_ARG, "modulation grids are FP32");
+    if (nx < 1 || ny < 1 || nz < 1) return fail(CRP_ERR_INVALID_ARG, "grid sizes must be >= 1");
+    const long long nodes = (long long)nx * ny * nz;
+    if (nodes >= (1ll << 31)) return fail(CRP_ERR_INVALID_ARG, "grid above 2^31 nodes");
+    if (!(spacing_m > 0.0) || !std::isfinite(spacing_m))
+        return fail(CRP_ERR_INVALID_ARG, "spacing must be finite and > 0");
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(origin_m[a])) return fail(CRP_ERR_INVALID_ARG, "origin not finite");
+    if (field->modmem) return fail(CRP_ERR_INVALID_ARG, "field already modulated");
+    void* m = nullptr;
+    CRP_CUDA(cudaMalloc(&m, (size_t)nodes * sizeof(float)));
+    cudaError_t e = cudaMemcpy(m, mod, (size_t)nodes * sizeof(float),
+                               is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { cudaFree(m); return cuda_fail(e, "cudaMemcpy(modulation)"); }
+    field->modmem = m;
+    FieldDev& d = field->dev;
+    d.mod = (const float*)m;
+    d.mnx = nx; d.mny = ny; d.mnz = nz;
+    d.mpow2 = (is_pow2(nx) && is_pow2(ny) && is_pow2(nz)) ? 1 : 0;
+    d.m_inv_spacing = 1.0 / spacing_m;
+    d.m_spacing = spacing_m;
+    d.mox = origin_m[0]; d.moy = origin_m[1]; d.moz = origin_m[2];
     return CRP_OK;
 }
 
@@ -513,6 +544,7 @@ int crp_field_destroy(crp_field* field) {
     if (!field) return fail(CRP_ERR_INVALID_ARG, "field is NULL");
     if (field->mem) cudaFree(field->mem);
     if (field->mem64) cudaFree(field->mem64);
+    if (field->modmem) cudaFree(field->modmem);
     delete field;
     return CRP_OK;
 }
@@ -586,13 +618,18 @@ int crp_sim_create(const crp_field* const* fields, int32_t n_fields, const crp_t
         if (!fields[i]) return fail(CRP_ERR_INVALID_ARG, "NULL field handle");
     if (capacity < 1 || capacity >= (1ll << 31)) return fail(CRP_ERR_INVALID_ARG, "capacity out of range");
     const int layout = fields[0]->dev.layout;
-    for (int i = 1; i < n_fields; ++i)
+    const int mod = fields[0]->dev.mod ? 1 : 0;
+    for (int i = 1; i < n_fields; ++i) {
         if (fields[i]->dev.layout != layout)
             return fail(CRP_ERR_INVALID_ARG, "all fields of a simulation need the same dtype");
+        if ((fields[i]->dev.mod ? 1 : 0) != mod)
+            return fail(CRP_ERR_INVALID_ARG, "all fields of a simulation are modulated, or none");
+    }
     int ndev = 0;
     CRP_CUDA(cudaGetDeviceCount(&ndev));
     crp_sim* s = new crp_sim();
     s->layout = layout;
+    s->mod = mod;
     s->tables = tables;
     s->seed = seed;
     s->capacity = capacity;
@@ -738,27 +775,43 @@ int crp_source_inject(crp_sim* s, const crp_particles* p, int64_t n, void* strea
 
 namespace {
 
+// FP64 descriptor of a field: the field itself for FP64 grids, else an FP64 copy of the
+// vector grid (built on first use) with the field's geometry and modulation.
+int field_fp64_desc(crp_field* f, FieldDev& out) {
+    if (f->dev.layout == LAYOUT_F64X4) { out = f->dev; return CRP_OK; }
+    if (!f->mem64) {
+        void* m = nullptr;
+        CRP_CUDA(cudaMalloc(&m, (size_t)f->nodes * 32));
+        k_widen<<<grid_for(f->nodes, 256, 65535), 256>>>(f->mem, f->dev.layout, f->dev.scale,
+                                                         (double2*)m, f->nodes);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) { cudaFree(m); return cuda_fail(e, "field widening"); }
+        f->mem64 = m;
+    }
+    out = f->dev;
+    out.data = f->mem64;
+    out.layout = LAYOUT_F64X4;
+    f->dev64 = out;
+    return CRP_OK;
+}
+
 // Build (once per field) the FP64 copies and this simulation's descriptor array for them.
 int ensure_fp64_fields(crp_sim* s) {
     if (s->d_fields64) return CRP_OK;
     int rc = sync_stream(s);
     if (rc) return rc;
     std::vector<FieldDev> d64;
-    for (crp_field* f : s->handles) {
-        if (!f->mem64) {
-            void* m = nullptr;
-            CRP_CUDA(cudaMalloc(&m, (size_t)f->nodes * 32));
-            k_widen<<<grid_for(f->nodes, 256, 65535), 256>>>(f->mem, f->dev.layout, f->dev.scale,
-                                                             (double2*)m, f->nodes);
-            cudaError_t e = cudaGetLastError();
-            if (e == cudaSuccess) e = cudaDeviceSynchronize();
-            if (e != cudaSuccess) { cudaFree(m); return cuda_fail(e, "field widening"); }
-            f->mem64 = m;
-            f->dev64 = f->dev;
-            f->dev64.data = m;
-            f->dev64.layout = LAYOUT_F64X4;
-        }
-        d64.push_back(f->dev64);
+    for (size_t i = 0; i < s->handles.size(); ++i) {
+        FieldDev F;
+        rc = field_fp64_desc(s->handles[i], F);
+        if (rc) return rc;
+        // the modulation as it was when the simulation was created
+        const FieldDev& H = s->host_fields[i];
+        F.mod = H.mod; F.mnx = H.mnx; F.mny = H.mny; F.mnz = H.mnz; F.mpow2 = H.mpow2;
+        F.m_inv_spacing = H.m_inv_spacing; F.m_spacing = H.m_spacing;
+        F.mox = H.mox; F.moy = H.moy; F.moz = H.moz;
+        d64.push_back(F);
     }
     void* d = nullptr;
     CRP_CUDA(cudaMalloc(&d, sizeof(FieldDev) * d64.size()));
@@ -798,8 +851,8 @@ int make_plan(crp_sim* s, const crp_params* prm, double tol, double hmin, double
     int bps = prm->blocks_per_sm;
     if (bps <= 0) {
         int occ = 0;
-        const int oe = mixed ? propagate_mixed_occupancy(layout, block, &occ)
-                             : propagate_fp64_occupancy(layout, block, &occ);
+        const int oe = mixed ? propagate_mixed_occupancy(layout, s->mod, block, &occ)
+                             : propagate_fp64_occupancy(layout, s->mod, block, &occ);
         if (oe != 0 || occ < 1) occ = 1;
         bps = occ;
     }
@@ -808,6 +861,7 @@ int make_plan(crp_sim* s, const crp_params* prm, double tol, double hmin, double
     P.order = order;
     P.mixed = mixed ? 1 : 0;
     P.layout = layout;
+    P.mod = s->mod;
     P.n_buckets = order == CRP_ORDER_GRID ? kBuckets * (int)s->host_fields.size() : kBuckets;
     PropArgs& a = P.a;
     a.st = s->st;
@@ -858,8 +912,8 @@ int enqueue(crp_sim* s, const Plan& P, cudaStream_t st) {
     for (int gen = 0; gen < 2; ++gen) {
         if (a.pickup) CRP_CUDA(cudaMemsetAsync(s->lists[1 - gen], 0xff, sizeof(int32_t) * s->capacity, st));
         a.list = gen;
-        int e = P.mixed ? launch_propagate_mixed(a, P.layout, P.grid, P.block, st)
-                        : launch_propagate_fp64(a, P.layout, P.grid, P.block, st);
+        int e = P.mixed ? launch_propagate_mixed(a, P.layout, P.mod, P.grid, P.block, st)
+                        : launch_propagate_fp64(a, P.layout, P.mod, P.grid, P.block, st);
         if (e) return cuda_fail((cudaError_t)e, "propagate kernel launch");
         k_swap<<<1, 1, 0, st>>>(s->ctr, s->capacity, gen);
         CRP_CUDA(cudaGetLastError());
@@ -1158,7 +1212,7 @@ extern "C" int crp_propagate_noalloc(const void* grid, int32_t nx, int32_t ny, i
     CRP_CUDA(cudaGetLastError());
     const int block = 128;
     int occ = 0;
-    if (propagate_fp64_occupancy(LAYOUT_F32X4, block, &occ) != 0 || occ < 1) occ = 1;
+    if (propagate_fp64_occupancy(LAYOUT_F32X4, 0, block, &occ) != 0 || occ < 1) occ = 1;
     PropArgs a{};
     a.st = S;
     a.fields = fdev;
@@ -1175,7 +1229,7 @@ extern "C" int crp_propagate_noalloc(const void* grid, int32_t nx, int32_t ny, i
     a.ctr = ctr;
     for (int gen = 0; gen < 2; ++gen) {
         a.list = gen;
-        int e = launch_propagate_fp64(a, LAYOUT_F32X4, sms * occ, block, st);
+        int e = launch_propagate_fp64(a, LAYOUT_F32X4, 0, sms * occ, block, st);
         if (e) return cuda_fail((cudaError_t)e, "propagate kernel launch");
         k_swap<<<1, 1, 0, st>>>(ctr, n, gen);
         CRP_CUDA(cudaGetLastError());
@@ -1202,25 +1256,6 @@ struct crp_adjoint {
 
 namespace {
 
-int field_fp64_desc(crp_field* f, FieldDev& out) {
-    if (f->dev.layout == LAYOUT_F64X4) { out = f->dev; return CRP_OK; }
-    if (!f->mem64) {
-        void* m = nullptr;
-        CRP_CUDA(cudaMalloc(&m, (size_t)f->nodes * 32));
-        k_widen<<<grid_for(f->nodes, 256, 65535), 256>>>(f->mem, f->dev.layout, f->dev.scale,
-                                                         (double2*)m, f->nodes);
-        cudaError_t e = cudaGetLastError();
-        if (e == cudaSuccess) e = cudaDeviceSynchronize();
-        if (e != cudaSuccess) { cudaFree(m); return cuda_fail(e, "field widening"); }
-        f->mem64 = m;
-        f->dev64 = f->dev;
-        f->dev64.data = m;
-        f->dev64.layout = LAYOUT_F64X4;
-    }
-    out = f->dev64;
-    return CRP_OK;
-}
-
 void adj_free(crp_adjoint* a) {
     double* ds[] = {a->y0, a->kappa, a->E, a->h, a->ck, a->seg, a->y0_bar, a->kappa_bar, a->y0_tmp,
                     a->kappa_tmp, a->E_tmp};
@@ -1237,6 +1272,7 @@ int crp_adjoint_create(const crp_field* field, int64_t n, int32_t n_steps, int32
     if (!out) return fail(CRP_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!field || n < 1 || n_steps < 1 || K < 1) return fail(CRP_ERR_INVALID_ARG, "need field, n >= 1, n_steps >= 1, checkpoint_every >= 1");
+    if (field->dev.mod) return fail(CRP_ERR_INVALID_ARG, "the adjoint takes unmodulated fields");
     crp_adjoint* a = new crp_adjoint();
     a->field = const_cast<crp_field*>(field);
     a->n = n;
@@ -1294,6 +1330,7 @@ int crp_adjoint_replay(crp_adjoint* a, const crp_field* field, const double* p0,
     crp_field* f = field ? const_cast<crp_field*>(field) : a->field;
     if (f->dev.nx != a->field->dev.nx || f->dev.ny != a->field->dev.ny || f->dev.nz != a->field->dev.nz)
         return fail(CRP_ERR_INVALID_ARG, "replay field has another grid geometry");
+    if (f->dev.mod) return fail(CRP_ERR_INVALID_ARG, "the adjoint takes unmodulated fields");
     FieldDev F;
     int rc = field_fp64_desc(f, F);
     if (rc) return rc;

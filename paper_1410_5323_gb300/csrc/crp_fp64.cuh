@@ -66,11 +66,39 @@ __device__ __forceinline__ void axis(double x, double o, double inv, int n, int 
     w1 = fr;
 }
 
+// Modulation value M(x): scalar periodic trilinear lookup on the modulation grid, corners
+// in the order 000, 001, ..., 111, weight ((w_x * w_y) * w_z).
+__device__ __forceinline__ double modulation(const FieldDev& F, double x, double y, double z) {
+    long long ix0, ix1, iy0, iy1, iz0, iz1;
+    double wx0, wx1, wy0, wy1, wz0, wz1;
+    axis(x, F.mox, F.m_inv_spacing, F.mnx, F.mpow2, ix0, ix1, wx0, wx1);
+    axis(y, F.moy, F.m_inv_spacing, F.mny, F.mpow2, iy0, iy1, wy0, wy1);
+    axis(z, F.moz, F.m_inv_spacing, F.mnz, F.mpow2, iz0, iz1, wz0, wz1);
+    const long long ny = F.mny, nz = F.mnz;
+    const float* M = F.mod;
+    const long long r00 = (ix0 * ny + iy0) * nz, r01 = (ix0 * ny + iy1) * nz;
+    const long long r10 = (ix1 * ny + iy0) * nz, r11 = (ix1 * ny + iy1) * nz;
+    const double m0 = (double)__ldg(M + r00 + iz0), m1 = (double)__ldg(M + r00 + iz1);
+    const double m2 = (double)__ldg(M + r01 + iz0), m3 = (double)__ldg(M + r01 + iz1);
+    const double m4 = (double)__ldg(M + r10 + iz0), m5 = (double)__ldg(M + r10 + iz1);
+    const double m6 = (double)__ldg(M + r11 + iz0), m7 = (double)__ldg(M + r11 + iz1);
+    const double w00 = wx0 * wy0, w01 = wx0 * wy1, w10 = wx1 * wy0, w11 = wx1 * wy1;
+    double m = (w00 * wz0) * m0;
+    m = m + (w00 * wz1) * m1;
+    m = m + (w01 * wz0) * m2;
+    m = m + (w01 * wz1) * m3;
+    m = m + (w10 * wz0) * m4;
+    m = m + (w10 * wz1) * m5;
+    m = m + (w11 * wz0) * m6;
+    m = m + (w11 * wz1) * m7;
+    return m;
+}
+
 // Trilinear periodic lookup; corners summed in the order 000, 001, ..., 111 (x, y, z),
-// weight ((w_x * w_y) * w_z).
+// weight ((w_x * w_y) * w_z). With M, the result is scaled by the modulation value.
 // With H, every lookup also folds its cell index into *hh (the visited-cell sequence of a
 // trajectory; no effect on the arithmetic).
-template <int L, bool H = false>
+template <int L, bool H = false, bool M = false>
 __device__ __forceinline__ V3 field_b(const FieldDev& F, double x, double y, double z,
                                       unsigned long long* hh = nullptr) {
     long long ix0, ix1, iy0, iy1, iz0, iz1;
@@ -97,16 +125,20 @@ __device__ __forceinline__ V3 field_b(const FieldDev& F, double x, double y, dou
     t = w10 * wz1; B.x = B.x + t * g5.x; B.y = B.y + t * g5.y; B.z = B.z + t * g5.z;
     t = w11 * wz0; B.x = B.x + t * g6.x; B.y = B.y + t * g6.y; B.z = B.z + t * g6.z;
     t = w11 * wz1; B.x = B.x + t * g7.x; B.y = B.y + t * g7.y; B.z = B.z + t * g7.z;
+    if constexpr (M) {
+        const double m = modulation(F, x, y, z);
+        B.x = m * B.x; B.y = m * B.y; B.z = m * B.z;
+    }
     return B;
 }
 
 struct Y6 { double x, y, z, ux, uy, uz; };
 
 // f(y) = (u, kappa u x B(x))
-template <int L, bool H = false>
+template <int L, bool H = false, bool M = false>
 __device__ __forceinline__ Y6 deriv(const FieldDev& F, double kappa, const Y6& y,
                                     unsigned long long* hh = nullptr) {
-    const V3 B = field_b<L, H>(F, y.x, y.y, y.z, hh);
+    const V3 B = field_b<L, H, M>(F, y.x, y.y, y.z, hh);
     Y6 k;
     k.x = y.ux; k.y = y.uy; k.z = y.uz;
     k.ux = kappa * (y.uy * B.z - y.uz * B.y);
@@ -123,26 +155,26 @@ __device__ __forceinline__ Y6 deriv(const FieldDev& F, double kappa, const Y6& y
     } while (0)
 
 // One Cash-Karp attempt of size h from y with k1 = f(y).
-template <int L, bool H = false>
+template <int L, bool H = false, bool M = false>
 __device__ __forceinline__ void ck_attempt(const FieldDev& F, double kappa, const Y6& y,
                                            const Y6& k1, double h, Y6& y5, Y6& err,
                                            unsigned long long* hh = nullptr) {
     Y6 t;
 #define S2(c) (A21 * k1.c)
     CRP_STAGE(t, S2);
-    const Y6 k2 = deriv<L, H>(F, kappa, t, hh);
+    const Y6 k2 = deriv<L, H, M>(F, kappa, t, hh);
 #define S3(c) (A31 * k1.c + A32 * k2.c)
     CRP_STAGE(t, S3);
-    const Y6 k3 = deriv<L, H>(F, kappa, t, hh);
+    const Y6 k3 = deriv<L, H, M>(F, kappa, t, hh);
 #define S4(c) (A41 * k1.c + A42 * k2.c + A43 * k3.c)
     CRP_STAGE(t, S4);
-    const Y6 k4 = deriv<L, H>(F, kappa, t, hh);
+    const Y6 k4 = deriv<L, H, M>(F, kappa, t, hh);
 #define S5(c) (A51 * k1.c + A52 * k2.c + A53 * k3.c + A54 * k4.c)
     CRP_STAGE(t, S5);
-    const Y6 k5 = deriv<L, H>(F, kappa, t, hh);
+    const Y6 k5 = deriv<L, H, M>(F, kappa, t, hh);
 #define S6(c) (A61 * k1.c + A62 * k2.c + A63 * k3.c + A64 * k4.c + A65 * k5.c)
     CRP_STAGE(t, S6);
-    const Y6 k6 = deriv<L, H>(F, kappa, t, hh);
+    const Y6 k6 = deriv<L, H, M>(F, kappa, t, hh);
 #define SB(c) (B1 * k1.c + B3 * k3.c + B4 * k4.c + B6 * k6.c)
     CRP_STAGE(y5, SB);
 #define SE(c) (h * (E1 * k1.c + E3 * k3.c + E4 * k4.c + E5 * k5.c + E6 * k6.c))

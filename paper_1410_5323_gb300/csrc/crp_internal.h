@@ -19,6 +19,12 @@ struct FieldDev {
     double spacing;
     double ox, oy, oz;
     double scale;            // BF16/F16 multiplier (1 otherwise)
+    // Modulation grid (Sec. 3.2 modulated grids): B(x) = M(x) b(x) with M a scalar FP32
+    // periodic grid, node (i,j,k) at (i*mny + j)*mnz + k; nullptr when the field has none.
+    const float* mod;
+    int32_t mnx, mny, mnz, mpow2;
+    double m_inv_spacing, m_spacing;
+    double mox, moy, moz;
 };
 
 struct TablesDev {
@@ -90,10 +96,11 @@ struct PropArgs {
 };
 
 // Launchers (defined in the kernel translation units).
-int launch_propagate_fp64(const PropArgs& a, int layout, int grid, int block, void* stream);
-int propagate_fp64_occupancy(int layout, int block, int* blocks_per_sm);
-int launch_propagate_mixed(const PropArgs& a, int layout, int grid, int block, void* stream);
-int propagate_mixed_occupancy(int layout, int block, int* blocks_per_sm);
+// `mod`: 1 for simulations whose fields carry a modulation grid.
+int launch_propagate_fp64(const PropArgs& a, int layout, int mod, int grid, int block, void* stream);
+int propagate_fp64_occupancy(int layout, int mod, int block, int* blocks_per_sm);
+int launch_propagate_mixed(const PropArgs& a, int layout, int mod, int grid, int block, void* stream);
+int propagate_mixed_occupancy(int layout, int mod, int block, int* blocks_per_sm);
 
 // Adjoint launchers (adjoint.cu). Arrays are component-major [component][n] for y,
 // [step][n] for h, [checkpoint][6][n] for checkpoints.

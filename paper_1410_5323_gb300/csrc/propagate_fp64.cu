@@ -23,7 +23,7 @@ namespace {
 
 using namespace fp64;
 
-template <int L>
+template <int L, bool M>
 __global__ void __launch_bounds__(256) k_propagate_fp64(const PropArgs a) {
     const int lane = threadIdx.x & 31;
     Counters* C = a.ctr;
@@ -105,9 +105,9 @@ __global__ void __launch_bounds__(256) k_propagate_fp64(const PropArgs a) {
             }
             // ---- propagation: one Cash-Karp attempt ----
             const double kappa = (double)Z * kC / E;
-            const Y6 k1 = deriv<L>(F, kappa, y);
+            const Y6 k1 = deriv<L, false, M>(F, kappa, y);
             Y6 y5, err;
-            ck_attempt<L>(F, kappa, y, k1, h, y5, err);
+            ck_attempt<L, false, M>(F, kappa, y, k1, h, y5, err);
             att_step += 1;
             const double r = error_ratio(err, h, a.tol);
             if (!(r <= 1.0 || h <= a.hmin)) {
@@ -211,36 +211,35 @@ __global__ void __launch_bounds__(256) k_propagate_fp64(const PropArgs a) {
 
 }  // namespace
 
-int launch_propagate_fp64(const PropArgs& a, int layout, int grid, int block, void* stream) {
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    switch (layout) {
-    case LAYOUT_F32X4: k_propagate_fp64<LAYOUT_F32X4><<<grid, block, 0, st>>>(a); break;
-    case LAYOUT_F64X4: k_propagate_fp64<LAYOUT_F64X4><<<grid, block, 0, st>>>(a); break;
-    case LAYOUT_BF16X4: k_propagate_fp64<LAYOUT_BF16X4><<<grid, block, 0, st>>>(a); break;
-    case LAYOUT_F16X4: k_propagate_fp64<LAYOUT_F16X4><<<grid, block, 0, st>>>(a); break;
-    default: return -1;
+// Kernel for (layout, modulated): the FP64 form reads FP64 or FP32 vector grids; a
+// modulated field is read through its FP64 copy only.
+template <typename Fn>
+int with_fp64_kernel(int layout, int mod, Fn&& fn) {
+    if (mod) {
+        if (layout != LAYOUT_F64X4) return (int)cudaErrorInvalidValue;
+        return fn(k_propagate_fp64<LAYOUT_F64X4, true>);
     }
-    return (int)cudaGetLastError();
+    switch (layout) {
+    case LAYOUT_F32X4: return fn(k_propagate_fp64<LAYOUT_F32X4, false>);
+    case LAYOUT_F64X4: return fn(k_propagate_fp64<LAYOUT_F64X4, false>);
+    case LAYOUT_BF16X4: return fn(k_propagate_fp64<LAYOUT_BF16X4, false>);
+    case LAYOUT_F16X4: return fn(k_propagate_fp64<LAYOUT_F16X4, false>);
+    default: return (int)cudaErrorInvalidValue;
+    }
 }
 
-int propagate_fp64_occupancy(int layout, int block, int* blocks_per_sm) {
-    cudaError_t e = cudaErrorInvalidValue;
-    switch (layout) {
-    case LAYOUT_F32X4:
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_propagate_fp64<LAYOUT_F32X4>, block, 0);
-        break;
-    case LAYOUT_F64X4:
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_propagate_fp64<LAYOUT_F64X4>, block, 0);
-        break;
-    case LAYOUT_BF16X4:
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_propagate_fp64<LAYOUT_BF16X4>, block, 0);
-        break;
-    case LAYOUT_F16X4:
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_propagate_fp64<LAYOUT_F16X4>, block, 0);
-        break;
-    default: break;
-    }
-    return (int)e;
+int launch_propagate_fp64(const PropArgs& a, int layout, int mod, int grid, int block, void* stream) {
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    return with_fp64_kernel(layout, mod, [&](void (*k)(const PropArgs)) {
+        k<<<grid, block, 0, st>>>(a);
+        return (int)cudaGetLastError();
+    });
+}
+
+int propagate_fp64_occupancy(int layout, int mod, int block, int* blocks_per_sm) {
+    return with_fp64_kernel(layout, mod, [&](void (*k)(const PropArgs)) {
+        return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, block, 0);
+    });
 }
 
 }  // namespace crp

@@ -67,7 +67,14 @@ struct FieldF {
     const void* data;
     int nx, ny, nz, pow2;
     float scale;
+    // modulation grid (modulated fields only)
+    const float* mod;
+    int mnx, mny, mnz, mpow2;
+    float mq;                // vector-grid spacing / modulation-grid spacing
 };
+
+// Step-start frame on the modulation grid: base cell and fraction.
+struct MF { int bx, by, bz; F3 f0; };
 
 template <int L>
 __device__ __forceinline__ F3 corner_f(const FieldF& F, int node) {
@@ -93,9 +100,46 @@ __device__ __forceinline__ int floor_frac(float t, float& frac) {
     return i;
 }
 
-// Trilinear periodic lookup at (base cell b, fraction f0) + offset p (cells).
-template <int L>
-__device__ __forceinline__ F3 field_f(const FieldF& F, int bx, int by, int bz, F3 f0, F3 p) {
+// Wrap an index that is usually already in [0, n) (a base cell plus a small offset).
+__device__ __forceinline__ int wrap_near(int i, int n, int pow2) {
+    return ((unsigned)i < (unsigned)n) ? i : wrap(i, n, pow2);
+}
+
+// Modulation value at the local offset p (vector-grid cells): the same trilinear periodic
+// lookup on the scalar grid, with the offset converted to modulation cells.
+__device__ __forceinline__ float modulation_f(const FieldF& F, const MF& m, F3 p) {
+    float fx, fy, fz;
+    const int cx = floor_frac(fmaf(p.x, F.mq, m.f0.x), fx), cy = floor_frac(fmaf(p.y, F.mq, m.f0.y), fy),
+              cz = floor_frac(fmaf(p.z, F.mq, m.f0.z), fz);
+    const int ix = wrap_near(m.bx + cx, F.mnx, F.mpow2), iy = wrap_near(m.by + cy, F.mny, F.mpow2),
+              iz = wrap_near(m.bz + cz, F.mnz, F.mpow2);
+    const int ix1 = ix + 1 == F.mnx ? 0 : ix + 1, iy1 = iy + 1 == F.mny ? 0 : iy + 1,
+              iz1 = iz + 1 == F.mnz ? 0 : iz + 1;
+    const int r00 = (ix * F.mny + iy) * F.mnz, r01 = (ix * F.mny + iy1) * F.mnz;
+    const int r10 = (ix1 * F.mny + iy) * F.mnz, r11 = (ix1 * F.mny + iy1) * F.mnz;
+    const float* M = F.mod;
+    const float m0 = __ldg(M + r00 + iz), m1 = __ldg(M + r00 + iz1);
+    const float m2 = __ldg(M + r01 + iz), m3 = __ldg(M + r01 + iz1);
+    const float m4 = __ldg(M + r10 + iz), m5 = __ldg(M + r10 + iz1);
+    const float m6 = __ldg(M + r11 + iz), m7 = __ldg(M + r11 + iz1);
+    const float gx = 1.0f - fx, gy = 1.0f - fy, gz = 1.0f - fz;
+    const float w00 = gx * gy, w01 = gx * fy, w10 = fx * gy, w11 = fx * fy;
+    float v = (w00 * gz) * m0;
+    v = fmaf(w00 * fz, m1, v);
+    v = fmaf(w01 * gz, m2, v);
+    v = fmaf(w01 * fz, m3, v);
+    v = fmaf(w10 * gz, m4, v);
+    v = fmaf(w10 * fz, m5, v);
+    v = fmaf(w11 * gz, m6, v);
+    v = fmaf(w11 * fz, m7, v);
+    return v;
+}
+
+// Trilinear periodic lookup at (base cell b, fraction f0) + offset p (cells); with M, times
+// the modulation value there.
+template <int L, bool M>
+__device__ __forceinline__ F3 field_f(const FieldF& F, int bx, int by, int bz, F3 f0, const MF& mf,
+                                      F3 p) {
     float fx, fy, fz;
     const int cx = floor_frac(f0.x + p.x, fx), cy = floor_frac(f0.y + p.y, fy),
               cz = floor_frac(f0.z + p.z, fz);
@@ -121,16 +165,22 @@ __device__ __forceinline__ F3 field_f(const FieldF& F, int bx, int by, int bz, F
     w = w10 * fz; B.x = fmaf(w, g5.x, B.x); B.y = fmaf(w, g5.y, B.y); B.z = fmaf(w, g5.z, B.z);
     w = w11 * gz; B.x = fmaf(w, g6.x, B.x); B.y = fmaf(w, g6.y, B.y); B.z = fmaf(w, g6.z, B.z);
     w = w11 * fz; B.x = fmaf(w, g7.x, B.x); B.y = fmaf(w, g7.y, B.y); B.z = fmaf(w, g7.z, B.z);
-    if constexpr (L != LAYOUT_F32X4) { B.x *= F.scale; B.y *= F.scale; B.z *= F.scale; }
+    if constexpr (M) {
+        float m = modulation_f(F, mf, p);
+        if constexpr (L != LAYOUT_F32X4) m *= F.scale;
+        B.x *= m; B.y *= m; B.z *= m;
+    } else if constexpr (L != LAYOUT_F32X4) {
+        B.x *= F.scale; B.y *= F.scale; B.z *= F.scale;
+    }
     return B;
 }
 
 struct Y { F3 p, u; };   // local position offset (cells) and direction
 
-template <int L>
-__device__ __forceinline__ Y deriv_f(const FieldF& F, int bx, int by, int bz, F3 f0, float kappa,
-                                     const Y& y) {
-    const F3 B = field_f<L>(F, bx, by, bz, f0, y.p);
+template <int L, bool M>
+__device__ __forceinline__ Y deriv_f(const FieldF& F, int bx, int by, int bz, F3 f0, const MF& mf,
+                                     float kappa, const Y& y) {
+    const F3 B = field_f<L, M>(F, bx, by, bz, f0, mf, y.p);
     Y k;
     k.p = y.u;
     k.u.x = kappa * (y.u.y * B.z - y.u.z * B.y);
@@ -153,7 +203,7 @@ __device__ __forceinline__ bool fin3(F3 a) { return isfinite(a.x) && isfinite(a.
 #define CRP_MIXED_BOUNDS __launch_bounds__(256)
 #endif
 
-template <int L>
+template <int L, bool M>
 __global__ void CRP_MIXED_BOUNDS k_propagate_mixed(const PropArgs a) {
     const int lane = threadIdx.x & 31;
     Counters* C = a.ctr;
@@ -180,6 +230,7 @@ __global__ void CRP_MIXED_BOUNDS k_propagate_mixed(const PropArgs a) {
     bool new_step = true;
     int bx = 0, by = 0, bz = 0;
     F3 f0{0, 0, 0};
+    MF mf{0, 0, 0, {0, 0, 0}};
     float h = 0, h_first = 0, h_propc = 0, h_int = 0, h_dist = 0, rl = 0, rpd = 0, kappa = 0;
     int rejected = 0;
     long long att_step = 0;
@@ -220,6 +271,10 @@ __global__ void CRP_MIXED_BOUNDS k_propagate_mixed(const PropArgs a) {
             const FieldDev& G = a.fields[gid];
             F.data = G.data; F.nx = G.nx; F.ny = G.ny; F.nz = G.nz; F.pow2 = G.pow2;
             F.scale = (float)G.scale;
+            if constexpr (M) {
+                F.mod = G.mod; F.mnx = G.mnx; F.mny = G.mny; F.mnz = G.mnz; F.mpow2 = G.mpow2;
+                F.mq = (float)(G.spacing * G.m_inv_spacing);
+            }
             sp = G.spacing; inv_sp = G.inv_spacing; sp_f = (float)sp; csp_f = (float)(kC * sp);
             ox = G.ox; oy = G.oy; oz = G.oz;
             hmin_c = (float)(a.hmin * inv_sp);
@@ -286,11 +341,27 @@ __global__ void CRP_MIXED_BOUNDS k_propagate_mixed(const PropArgs a) {
                 df_floor(Rx, bx, f0.x);
                 df_floor(Ry, by, f0.y);
                 df_floor(Rz, bz, f0.z);
+                if constexpr (M) {
+                    // step-start position in modulation cells (FP64, once per step)
+                    const FieldDev& G = a.fields[gid];
+                    auto mcell = [&](DF r, double o, double mo, int n, int& b, float& f) {
+                        const double rm = (to_x(r, o) - mo) * G.m_inv_spacing;
+                        const double fl = floor(rm);
+                        const long long i = (long long)fl;
+                        long long w = i % n;
+                        if (w < 0) w += n;
+                        b = (int)w;
+                        f = (float)(rm - fl);
+                    };
+                    mcell(Rx, ox, G.mox, F.mnx, mf.bx, mf.f0.x);
+                    mcell(Ry, oy, G.moy, F.mny, mf.by, mf.f0.y);
+                    mcell(Rz, oz, G.moz, F.mnz, mf.bz, mf.f0.z);
+                }
                 new_step = false;
             }
             // ---- one Cash-Karp attempt in the local frame (FP32) ----
             const Y y0{{0.0f, 0.0f, 0.0f}, u};
-            const Y k1 = deriv_f<L>(F, bx, by, bz, f0, kappa, y0);
+            const Y k1 = deriv_f<L, M>(F, bx, by, bz, f0, mf, kappa, y0);
             Y t;
 #define STG(expr)                                                                              \
             t.p.x = h * (expr(p.x)); t.p.y = h * (expr(p.y)); t.p.z = h * (expr(p.z));         \
@@ -298,19 +369,19 @@ __global__ void CRP_MIXED_BOUNDS k_propagate_mixed(const PropArgs a) {
             t.u.z = fmaf(h, (expr(u.z)), u.z);
 #define S2(c) (A21 * k1.c)
             STG(S2)
-            const Y k2 = deriv_f<L>(F, bx, by, bz, f0, kappa, t);
+            const Y k2 = deriv_f<L, M>(F, bx, by, bz, f0, mf, kappa, t);
 #define S3(c) (A31 * k1.c + A32 * k2.c)
             STG(S3)
-            const Y k3 = deriv_f<L>(F, bx, by, bz, f0, kappa, t);
+            const Y k3 = deriv_f<L, M>(F, bx, by, bz, f0, mf, kappa, t);
 #define S4(c) (A41 * k1.c + A42 * k2.c + A43 * k3.c)
             STG(S4)
-            const Y k4 = deriv_f<L>(F, bx, by, bz, f0, kappa, t);
+            const Y k4 = deriv_f<L, M>(F, bx, by, bz, f0, mf, kappa, t);
 #define S5(c) (A51 * k1.c + A52 * k2.c + A53 * k3.c + A54 * k4.c)
             STG(S5)
-            const Y k5 = deriv_f<L>(F, bx, by, bz, f0, kappa, t);
+            const Y k5 = deriv_f<L, M>(F, bx, by, bz, f0, mf, kappa, t);
 #define S6(c) (A61 * k1.c + A62 * k2.c + A63 * k3.c + A64 * k4.c + A65 * k5.c)
             STG(S6)
-            const Y k6 = deriv_f<L>(F, bx, by, bz, f0, kappa, t);
+            const Y k6 = deriv_f<L, M>(F, bx, by, bz, f0, mf, kappa, t);
 #define SB(c) (B1 * k1.c + B3 * k3.c + B4 * k4.c + B6 * k6.c)
 #define SE(c) (E1 * k1.c + E3 * k3.c + E4 * k4.c + E5 * k5.c + E6 * k6.c)
             const F3 dp{h * SB(p.x), h * SB(p.y), h * SB(p.z)};
@@ -437,23 +508,30 @@ __global__ void CRP_MIXED_BOUNDS k_propagate_mixed(const PropArgs a) {
 
 }  // namespace
 
-int launch_propagate_mixed(const PropArgs& a, int layout, int grid, int block, void* stream) {
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+// Kernel for (layout, modulated): FP32 or BF16 vector grids.
+template <typename Fn>
+int with_mixed_kernel(int layout, int mod, Fn&& fn) {
     switch (layout) {
-    case LAYOUT_F32X4: k_propagate_mixed<LAYOUT_F32X4><<<grid, block, 0, st>>>(a); break;
-    case LAYOUT_BF16X4: k_propagate_mixed<LAYOUT_BF16X4><<<grid, block, 0, st>>>(a); break;
+    case LAYOUT_F32X4:
+        return mod ? fn(k_propagate_mixed<LAYOUT_F32X4, true>) : fn(k_propagate_mixed<LAYOUT_F32X4, false>);
+    case LAYOUT_BF16X4:
+        return mod ? fn(k_propagate_mixed<LAYOUT_BF16X4, true>) : fn(k_propagate_mixed<LAYOUT_BF16X4, false>);
     default: return (int)cudaErrorInvalidValue;
     }
-    return (int)cudaGetLastError();
 }
 
-int propagate_mixed_occupancy(int layout, int block, int* blocks_per_sm) {
-    cudaError_t e = cudaErrorInvalidValue;
-    if (layout == LAYOUT_F32X4)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_propagate_mixed<LAYOUT_F32X4>, block, 0);
-    else if (layout == LAYOUT_BF16X4)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_propagate_mixed<LAYOUT_BF16X4>, block, 0);
-    return (int)e;
+int launch_propagate_mixed(const PropArgs& a, int layout, int mod, int grid, int block, void* stream) {
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    return with_mixed_kernel(layout, mod, [&](void (*k)(const PropArgs)) {
+        k<<<grid, block, 0, st>>>(a);
+        return (int)cudaGetLastError();
+    });
+}
+
+int propagate_mixed_occupancy(int layout, int mod, int block, int* blocks_per_sm) {
+    return with_mixed_kernel(layout, mod, [&](void (*k)(const PropArgs)) {
+        return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, block, 0);
+    });
 }
 
 }  // namespace crp

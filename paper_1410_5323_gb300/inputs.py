@@ -154,6 +154,61 @@ def kolmogorov_grid_torch(n: int, lmin_cells: float, lmax_cells: float, brms_t: 
     return out
 
 
+# --------------------------------------------------------------------------------------
+# Modulation grid (Sec. 3.2 modulated grids; Sec. 4 scenario: density -> field strength)
+# --------------------------------------------------------------------------------------
+def _band_filter(k, n: int, lmin_cells: float, lmax_cells: float, slope: float):
+    """|k|^slope on the band n/lmax <= |k| <= n/lmin, zero elsewhere (and at k = 0)."""
+    safe = np.where(k > 0, k, 1.0)
+    return np.where((k >= n / lmax_cells) & (k <= n / lmin_cells), safe ** slope, 0.0)
+
+
+def density_field(n: int, lmin_cells: float, lmax_cells: float, sigma_ln: float,
+                  seed: int) -> np.ndarray:
+    """Log-normal matter density rho [n, n, n] (float64, mean 1), periodic.
+
+    A Gaussian random field G with power |k|^-2 on the band n/lmax <= |k| <= n/lmin (white
+    noise filtered by |k|^-1, real FFTs), scaled to unit variance; rho = exp(sigma G -
+    sigma^2/2), renormalised to mean 1. A synthetic stand-in for a constrained large-scale
+    structure simulation: voids to clusters over exp(+-3 sigma)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    white = rng.standard_normal((n, n, n))
+    F = np.fft.rfftn(white)
+    del white
+    k1 = np.fft.fftfreq(n, d=1.0 / n)
+    kz = np.fft.rfftfreq(n, d=1.0 / n)
+    k = np.sqrt(k1[:, None, None] ** 2 + k1[None, :, None] ** 2 + kz[None, None, :] ** 2)
+    F *= _band_filter(k, n, lmin_cells, lmax_cells, -1.0)
+    del k
+    G = np.fft.irfftn(F, s=(n, n, n))
+    del F
+    G /= G.std()
+    rho = np.exp(sigma_ln * G - 0.5 * sigma_ln * sigma_ln)
+    rho /= rho.mean()
+    return rho
+
+
+def modulation_from_density(rho, exponent: float = 2.0 / 3.0) -> np.ndarray:
+    """Field-strength modulation M = rho^exponent (flux freezing under isotropic
+    compression: B ~ rho^(2/3)), normalised to <M^2> = 1 so that the modulated field keeps
+    the vector grid's B_rms on average. float32 [n, n, n]."""
+    M = np.power(rho, exponent)
+    M /= math.sqrt(float(np.mean(M * M)))
+    return M.astype(np.float32)
+
+
+def density_positions(n_particles: int, rho: np.ndarray, spacing_m: float, seed: int,
+                      origin_m=(0.0, 0.0, 0.0)) -> np.ndarray:
+    """Source positions [n, 3] (m) distributed like the matter density: a cell drawn with
+    probability proportional to rho, then a uniform point inside it."""
+    rng = np.random.Generator(np.random.PCG64(seed + 7919))
+    cdf = np.cumsum(rho.ravel(), dtype=np.float64)
+    cells = np.searchsorted(cdf, rng.uniform(0.0, cdf[-1], n_particles), side="right")
+    cells = np.minimum(cells, rho.size - 1)
+    ijk = np.stack(np.unravel_index(cells, rho.shape), axis=1).astype(np.float64)
+    return np.asarray(origin_m) + (ijk + rng.uniform(0.0, 1.0, (n_particles, 3))) * spacing_m
+
+
 def quantize_bf16(B, scale: float | None = None):
     """BF16 storage with one FP32 scale: B ~= scale * stored. Returns (stored bfloat16 tensor,
     scale as a Python float that is exactly an FP32 value). Default scale: the rms of |B|."""
@@ -347,10 +402,18 @@ class Workload:
     n_grids: int = 1
     particle_seed: int = 1
     rng_seed: int = 1          # Philox key for interaction sampling
+    # modulation grid (modulated workloads only): n^3 cells of mod_spacing_m, density with
+    # log-normal width mod_sigma_ln on mod_lmin..mod_lmax cells, sources follow the density
+    mod_n: int = 0
+    mod_spacing_m: float = 0.0
+    mod_lmin_cells: float = 2.0
+    mod_lmax_cells: float = 0.0
+    mod_sigma_ln: float = 0.0
+    mod_seed: int = 2
 
 
 def workload(name: str) -> Workload:
-    """The five synthetic workloads (turbulent grid, injection, propagation limits)."""
+    """The synthetic workloads (turbulent grid, injection, propagation limits)."""
     common = dict(spacing_m=0.25 * MPC, lmin_cells=2.0, tol=1e-4, hmin_m=1.0 * KPC,
                   hmax_m=1.0 * MPC, grid_seed=1)
     if name == "fp64_64cube_1k_protons":
@@ -371,6 +434,16 @@ def workload(name: str) -> Workload:
                         dmax_m=100.0 * MPC, species=(("H", 1.0),),
                         energy=("loguniform", 1e17, 10 ** 20.5), interactions=False,
                         n_grids=64, **common)
+    if name == "modulated_440cube_300kpc_x_256cube_50kpc_1M_nuclei":
+        # Sec. 4 geometry: modulation 132 Mpc at 300 kpc; vector grid at 50 kpc with a 500 kpc
+        # coherence length (Kolmogorov on 100 kpc .. 2.5 Mpc: L_c ~ l_max / 5)
+        return Workload(name, 1_000_000, 256, spacing_m=50.0 * KPC, lmin_cells=2.0,
+                        lmax_cells=50.0, brms_t=1.0 * NANOGAUSS, grid_seed=1, tol=1e-4,
+                        hmin_m=1.0 * KPC, hmax_m=1.0 * MPC, dmax_m=100.0 * MPC,
+                        species=(("H", 0.4), ("He", 0.3), ("N", 0.2), ("Fe", 0.1)),
+                        energy=("power", 1e18, 10 ** 20.5, 2.0), interactions=True,
+                        mod_n=440, mod_spacing_m=300.0 * KPC, mod_lmin_cells=2.0,
+                        mod_lmax_cells=110.0, mod_sigma_ln=1.0)
     if name == "adjoint_128cube_4k_protons":
         return Workload(name, 4096, 128, lmax_cells=32.0, brms_t=1.0 * NANOGAUSS,
                         dmax_m=1e6 * MPC, species=(("H", 1.0),), energy=("fixed", 10 ** 19.5),

@@ -15,10 +15,14 @@ def by_uid(d):
 
 def run_gpu(grids, parts, tables, tol, hmin, hmax, dmax, seed=1, capacity=None, max_steps=0,
             spacing=0.25 * I.MPC, form=0, calls=1, dtype=None, scale=1.0, origin=(0.0, 0.0, 0.0),
-            block_size=0, cadence=0):
+            block_size=0, cadence=0, mods=None, mod_spacing=1.0, mod_origin=(0.0, 0.0, 0.0)):
+    """mods: None, or one modulation grid per vector grid (modulated fields)."""
     import paper_1410_5323_gb300 as crp
 
     fields = [crp.Field(g, spacing, origin, scale=scale, dtype=dtype) for g in grids]
+    if mods is not None:
+        for f, m in zip(fields, mods):
+            f.modulate(m, mod_spacing, mod_origin)
     tabs = crp.Tables(tables) if tables is not None else None
     sim = crp.Simulation(fields, tabs, seed=seed, capacity=capacity or len(parts))
     sim.inject(parts)
@@ -30,8 +34,12 @@ def run_gpu(grids, parts, tables, tol, hmin, hmax, dmax, seed=1, capacity=None, 
 
 
 def run_oracle(grids, parts, tables, tol, hmin, hmax, dmax, seed=1, capacity=None, max_steps=0,
-               spacing=0.25 * I.MPC, dtype=None, scale=1.0, origin=(0.0, 0.0, 0.0), calls=1):
-    fields = [O.OracleField(g, spacing, origin, scale=scale, dtype=dtype) for g in grids]
+               spacing=0.25 * I.MPC, dtype=None, scale=1.0, origin=(0.0, 0.0, 0.0), calls=1,
+               mods=None, mod_spacing=1.0, mod_origin=(0.0, 0.0, 0.0)):
+    mods = mods if mods is not None else [None] * len(grids)
+    fields = [O.OracleField(g, spacing, origin, scale=scale, dtype=dtype, modulation=m,
+                            mod_spacing=mod_spacing, mod_origin=mod_origin)
+              for g, m in zip(grids, mods)]
     ot = O.OracleTables(tables) if tables is not None else None
     st = O.OracleState(capacity or len(parts))
     O.inject(st, parts, seed, ot)

@@ -50,6 +50,14 @@ def test_null_and_range_arguments_rejected_before_device_work(L):
     assert L.crp_field_create(g.ctypes.data, 9, 0, 2, 2, 2, 1.0, org, 1.0, C.byref(h)) == -1
     assert L.crp_field_create(g.ctypes.data, 2, 0, 2, 2, 2, 1.0, org, 0.0, C.byref(h)) == -1
     assert b"scale" in L.crp_last_error_detail()
+    m = np.ones((2, 2, 2), dtype=np.float32)
+    fake = C.c_void_p(8)         # never dereferenced: every check below fails first
+    assert L.crp_field_modulate(None, m.ctypes.data, 1, 0, 2, 2, 2, 1.0, org) == -1
+    assert L.crp_field_modulate(fake, None, 1, 0, 2, 2, 2, 1.0, org) == -1
+    assert L.crp_field_modulate(fake, m.ctypes.data, 0, 0, 2, 2, 2, 1.0, org) == -1     # F64
+    assert L.crp_field_modulate(fake, m.ctypes.data, 1, 0, 2, 0, 2, 1.0, org) == -1
+    assert L.crp_field_modulate(fake, m.ctypes.data, 1, 0, 2, 2, 2, 0.0, org) == -1
+    assert b"spacing" in L.crp_last_error_detail()
     assert L.crp_sim_create(None, 0, None, 1, 10, C.byref(h)) == -1
     assert L.crp_tables_create(1, 1, 1, 6.0, 25.0, None, None, None, None, C.byref(h)) == -1
     assert L.crp_propagate(None, None, 1e-4, 1.0, 2.0, 3.0, None) == -1
