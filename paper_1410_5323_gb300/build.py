@@ -40,7 +40,10 @@ def nvcc() -> str:
 
 def _compile(src: str, extra: list[str], verbose: bool) -> str:
     obj = os.path.join(OBJDIR, os.path.splitext(src)[0] + ".o")
-    cmd = [nvcc(), *ARCH, *COMMON, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+    # CRP_NVCC_EXTRA: extra nvcc flags, e.g. the register caps -DCRP_MIXED_MAXNREG=N and
+    # -DCRP_MIXED_MOD_MAXNREG=N of the precision-form kernels
+    user = os.environ.get("CRP_NVCC_EXTRA", "").split()
+    cmd = [nvcc(), *ARCH, *COMMON, *extra, *user, "-c", os.path.join(CSRC, src), "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -67,14 +67,19 @@ struct FieldF {
     const void* data;
     int nx, ny, nz, pow2;
     float scale;
-    // modulation grid (modulated fields only)
-    const float* mod;
-    int mnx, mny, mnz, mpow2;
-    float mq;                // vector-grid spacing / modulation-grid spacing
 };
 
-// Step-start frame on the modulation grid: base cell and fraction.
-struct MF { int bx, by, bz; F3 f0; };
+// Modulated fields: the step-start frame on the modulation grid. The 3x3x3 modulation nodes
+// around the step-start cell, on the side the particle is heading (per axis the start cell and
+// the next one along sign(u)), are loaded once per step into this lane's column of shared
+// memory; a stage whose cell lies in that block reads its 8 corners from there, any other
+// stage gathers them from the grid. Registers hold only the fraction, the ratio of spacings
+// and the block's low corner per axis (0 or -1 cells, packed in lo).
+struct MF { F3 f0; float q; int lo; };
+
+constexpr int kModNodes = 27;            // cached node values per lane
+constexpr int kModSlots = kModNodes + 3; // + the step-start cell (wrapped) per axis
+
 
 template <int L>
 __device__ __forceinline__ F3 corner_f(const FieldF& F, int node) {
@@ -105,23 +110,12 @@ __device__ __forceinline__ int wrap_near(int i, int n, int pow2) {
     return ((unsigned)i < (unsigned)n) ? i : wrap(i, n, pow2);
 }
 
-// Modulation value at the local offset p (vector-grid cells): the same trilinear periodic
-// lookup on the scalar grid, with the offset converted to modulation cells.
-__device__ __forceinline__ float modulation_f(const FieldF& F, const MF& m, F3 p) {
-    float fx, fy, fz;
-    const int cx = floor_frac(fmaf(p.x, F.mq, m.f0.x), fx), cy = floor_frac(fmaf(p.y, F.mq, m.f0.y), fy),
-              cz = floor_frac(fmaf(p.z, F.mq, m.f0.z), fz);
-    const int ix = wrap_near(m.bx + cx, F.mnx, F.mpow2), iy = wrap_near(m.by + cy, F.mny, F.mpow2),
-              iz = wrap_near(m.bz + cz, F.mnz, F.mpow2);
-    const int ix1 = ix + 1 == F.mnx ? 0 : ix + 1, iy1 = iy + 1 == F.mny ? 0 : iy + 1,
-              iz1 = iz + 1 == F.mnz ? 0 : iz + 1;
-    const int r00 = (ix * F.mny + iy) * F.mnz, r01 = (ix * F.mny + iy1) * F.mnz;
-    const int r10 = (ix1 * F.mny + iy) * F.mnz, r11 = (ix1 * F.mny + iy1) * F.mnz;
-    const float* M = F.mod;
-    const float m0 = __ldg(M + r00 + iz), m1 = __ldg(M + r00 + iz1);
-    const float m2 = __ldg(M + r01 + iz), m3 = __ldg(M + r01 + iz1);
-    const float m4 = __ldg(M + r10 + iz), m5 = __ldg(M + r10 + iz1);
-    const float m6 = __ldg(M + r11 + iz), m7 = __ldg(M + r11 + iz1);
+// Shared-memory slot k of this lane (column-major by lane: a warp's accesses hit 32 banks).
+__device__ __forceinline__ float& mslot(float* sm, int k) { return sm[k * blockDim.x + threadIdx.x]; }
+
+// Trilinear weights and the corner sum, in the same order for the cached and gathered paths.
+__device__ __forceinline__ float trilerp(float fx, float fy, float fz, float m0, float m1, float m2,
+                                         float m3, float m4, float m5, float m6, float m7) {
     const float gx = 1.0f - fx, gy = 1.0f - fy, gz = 1.0f - fz;
     const float w00 = gx * gy, w01 = gx * fy, w10 = fx * gy, w11 = fx * fy;
     float v = (w00 * gz) * m0;
@@ -135,10 +129,74 @@ __device__ __forceinline__ float modulation_f(const FieldF& F, const MF& m, F3 p
     return v;
 }
 
+// Step start: the wrapped node indices of the cached block along one axis.
+__device__ __forceinline__ void mod_axis_nodes(int b, int lo, int n, int pow2, int (&idx)[3]) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) idx[j] = wrap_near(b + lo + j, n, pow2);
+}
+
+// Step start: fill this lane's cached block from the modulation grid.
+__device__ __forceinline__ void mod_fill(float* sm, const FieldDev& G, int bx, int by, int bz, int lo) {
+    int ix[3], iy[3], iz[3];
+    mod_axis_nodes(bx, -(lo & 1), G.mnx, G.mpow2, ix);
+    mod_axis_nodes(by, -((lo >> 1) & 1), G.mny, G.mpow2, iy);
+    mod_axis_nodes(bz, -((lo >> 2) & 1), G.mnz, G.mpow2, iz);
+    const float* M = G.mod;
+    float v[kModNodes];
+#pragma unroll
+    for (int jx = 0; jx < 3; ++jx)
+#pragma unroll
+        for (int jy = 0; jy < 3; ++jy) {
+            const int row = (ix[jx] * G.mny + iy[jy]) * G.mnz;
+#pragma unroll
+            for (int jz = 0; jz < 3; ++jz) v[(jx * 3 + jy) * 3 + jz] = __ldg(M + row + iz[jz]);
+        }
+#pragma unroll
+    for (int k = 0; k < kModNodes; ++k) mslot(sm, k) = v[k];
+    mslot(sm, kModNodes + 0) = __int_as_float(bx);
+    mslot(sm, kModNodes + 1) = __int_as_float(by);
+    mslot(sm, kModNodes + 2) = __int_as_float(bz);
+}
+
+// Modulation value at the local offset p (vector-grid cells): the same trilinear periodic
+// lookup on the scalar grid, with the offset converted to modulation cells.
+__device__ __forceinline__ float modulation_f(const FieldDev* fields, int gid, float* sm, const MF& m, F3 p) {
+    float fx, fy, fz;
+    const int cx = floor_frac(fmaf(p.x, m.q, m.f0.x), fx), cy = floor_frac(fmaf(p.y, m.q, m.f0.y), fy),
+              cz = floor_frac(fmaf(p.z, m.q, m.f0.z), fz);
+    // cell relative to the cached block's low corner: 0 or 1 when inside it
+    const int jx = cx + (m.lo & 1), jy = cy + ((m.lo >> 1) & 1), jz = cz + ((m.lo >> 2) & 1);
+    float m0, m1, m2, m3, m4, m5, m6, m7;
+    if (((unsigned)jx | (unsigned)jy | (unsigned)jz) <= 1u) {
+        const int k = (jx * 3 + jy) * 3 + jz;
+        m0 = mslot(sm, k);      m1 = mslot(sm, k + 1);
+        m2 = mslot(sm, k + 3);  m3 = mslot(sm, k + 4);
+        m4 = mslot(sm, k + 9);  m5 = mslot(sm, k + 10);
+        m6 = mslot(sm, k + 12); m7 = mslot(sm, k + 13);
+    } else {
+        const FieldDev& G = fields[gid];
+        const int n_x = G.mnx, n_y = G.mny, n_z = G.mnz, pw = G.mpow2;
+        const int ix = wrap_near(__float_as_int(mslot(sm, kModNodes + 0)) + cx, n_x, pw);
+        const int iy = wrap_near(__float_as_int(mslot(sm, kModNodes + 1)) + cy, n_y, pw);
+        const int iz = wrap_near(__float_as_int(mslot(sm, kModNodes + 2)) + cz, n_z, pw);
+        const int ix1 = ix + 1 == n_x ? 0 : ix + 1, iy1 = iy + 1 == n_y ? 0 : iy + 1,
+                  iz1 = iz + 1 == n_z ? 0 : iz + 1;
+        const int r00 = (ix * n_y + iy) * n_z, r01 = (ix * n_y + iy1) * n_z;
+        const int r10 = (ix1 * n_y + iy) * n_z, r11 = (ix1 * n_y + iy1) * n_z;
+        const float* M = G.mod;
+        m0 = __ldg(M + r00 + iz); m1 = __ldg(M + r00 + iz1);
+        m2 = __ldg(M + r01 + iz); m3 = __ldg(M + r01 + iz1);
+        m4 = __ldg(M + r10 + iz); m5 = __ldg(M + r10 + iz1);
+        m6 = __ldg(M + r11 + iz); m7 = __ldg(M + r11 + iz1);
+    }
+    return trilerp(fx, fy, fz, m0, m1, m2, m3, m4, m5, m6, m7);
+}
+
 // Trilinear periodic lookup at (base cell b, fraction f0) + offset p (cells); with M, times
 // the modulation value there.
 template <int L, bool M>
-__device__ __forceinline__ F3 field_f(const FieldF& F, int bx, int by, int bz, F3 f0, const MF& mf,
+__device__ __forceinline__ F3 field_f(const FieldF& F, int bx, int by, int bz, F3 f0,
+                                      const FieldDev* fields, int gid, float* sm, const MF& mf,
                                       F3 p) {
     float fx, fy, fz;
     const int cx = floor_frac(f0.x + p.x, fx), cy = floor_frac(f0.y + p.y, fy),
@@ -166,7 +224,7 @@ __device__ __forceinline__ F3 field_f(const FieldF& F, int bx, int by, int bz, F
     w = w11 * gz; B.x = fmaf(w, g6.x, B.x); B.y = fmaf(w, g6.y, B.y); B.z = fmaf(w, g6.z, B.z);
     w = w11 * fz; B.x = fmaf(w, g7.x, B.x); B.y = fmaf(w, g7.y, B.y); B.z = fmaf(w, g7.z, B.z);
     if constexpr (M) {
-        float m = modulation_f(F, mf, p);
+        float m = modulation_f(fields, gid, sm, mf, p);
         if constexpr (L != LAYOUT_F32X4) m *= F.scale;
         B.x *= m; B.y *= m; B.z *= m;
     } else if constexpr (L != LAYOUT_F32X4) {
@@ -178,9 +236,10 @@ __device__ __forceinline__ F3 field_f(const FieldF& F, int bx, int by, int bz, F
 struct Y { F3 p, u; };   // local position offset (cells) and direction
 
 template <int L, bool M>
-__device__ __forceinline__ Y deriv_f(const FieldF& F, int bx, int by, int bz, F3 f0, const MF& mf,
+__device__ __forceinline__ Y deriv_f(const FieldF& F, int bx, int by, int bz, F3 f0,
+                                     const FieldDev* fields, int gid, float* sm, const MF& mf,
                                      float kappa, const Y& y) {
-    const F3 B = field_f<L, M>(F, bx, by, bz, f0, mf, y.p);
+    const F3 B = field_f<L, M>(F, bx, by, bz, f0, fields, gid, sm, mf, y.p);
     Y k;
     k.p = y.u;
     k.u.x = kappa * (y.u.y * B.z - y.u.z * B.y);
@@ -196,15 +255,8 @@ __device__ __forceinline__ float powf_pos(float r2, float p) { return exp2f(p * 
 
 __device__ __forceinline__ bool fin3(F3 a) { return isfinite(a.x) && isfinite(a.y) && isfinite(a.z); }
 
-// Register cap (more resident warps to hide gather latency); a build-time tuning knob.
-#ifdef CRP_MIXED_MAXNREG
-#define CRP_MIXED_BOUNDS __maxnreg__(CRP_MIXED_MAXNREG)
-#else
-#define CRP_MIXED_BOUNDS __launch_bounds__(256)
-#endif
-
 template <int L, bool M>
-__global__ void CRP_MIXED_BOUNDS k_propagate_mixed(const PropArgs a) {
+__device__ __forceinline__ void propagate_mixed_body(const PropArgs& a, float* sm) {
     const int lane = threadIdx.x & 31;
     Counters* C = a.ctr;
     const unsigned long long n_work = *(volatile unsigned long long*)&C->count[a.list];
@@ -230,7 +282,7 @@ __global__ void CRP_MIXED_BOUNDS k_propagate_mixed(const PropArgs a) {
     bool new_step = true;
     int bx = 0, by = 0, bz = 0;
     F3 f0{0, 0, 0};
-    MF mf{0, 0, 0, {0, 0, 0}};
+    MF mf{{0, 0, 0}, 1.0f, 0};
     float h = 0, h_first = 0, h_propc = 0, h_int = 0, h_dist = 0, rl = 0, rpd = 0, kappa = 0;
     int rejected = 0;
     long long att_step = 0;
@@ -271,10 +323,7 @@ __global__ void CRP_MIXED_BOUNDS k_propagate_mixed(const PropArgs a) {
             const FieldDev& G = a.fields[gid];
             F.data = G.data; F.nx = G.nx; F.ny = G.ny; F.nz = G.nz; F.pow2 = G.pow2;
             F.scale = (float)G.scale;
-            if constexpr (M) {
-                F.mod = G.mod; F.mnx = G.mnx; F.mny = G.mny; F.mnz = G.mnz; F.mpow2 = G.mpow2;
-                F.mq = (float)(G.spacing * G.m_inv_spacing);
-            }
+            if constexpr (M) mf.q = (float)(G.spacing * G.m_inv_spacing);
             sp = G.spacing; inv_sp = G.inv_spacing; sp_f = (float)sp; csp_f = (float)(kC * sp);
             ox = G.ox; oy = G.oy; oz = G.oz;
             hmin_c = (float)(a.hmin * inv_sp);
@@ -342,7 +391,8 @@ __global__ void CRP_MIXED_BOUNDS k_propagate_mixed(const PropArgs a) {
                 df_floor(Ry, by, f0.y);
                 df_floor(Rz, bz, f0.z);
                 if constexpr (M) {
-                    // step-start position in modulation cells (FP64, once per step)
+                    // step-start cell on the modulation grid (FP64, once per step), then this
+                    // lane's cached block of modulation nodes
                     const FieldDev& G = a.fields[gid];
                     auto mcell = [&](DF r, double o, double mo, int n, int& b, float& f) {
                         const double rm = (to_x(r, o) - mo) * G.m_inv_spacing;
@@ -353,15 +403,18 @@ __global__ void CRP_MIXED_BOUNDS k_propagate_mixed(const PropArgs a) {
                         b = (int)w;
                         f = (float)(rm - fl);
                     };
-                    mcell(Rx, ox, G.mox, F.mnx, mf.bx, mf.f0.x);
-                    mcell(Ry, oy, G.moy, F.mny, mf.by, mf.f0.y);
-                    mcell(Rz, oz, G.moz, F.mnz, mf.bz, mf.f0.z);
+                    int mbx, mby, mbz;
+                    mcell(Rx, ox, G.mox, G.mnx, mbx, mf.f0.x);
+                    mcell(Ry, oy, G.moy, G.mny, mby, mf.f0.y);
+                    mcell(Rz, oz, G.moz, G.mnz, mbz, mf.f0.z);
+                    mf.lo = (u.x < 0.0f ? 1 : 0) | (u.y < 0.0f ? 2 : 0) | (u.z < 0.0f ? 4 : 0);
+                    mod_fill(sm, G, mbx, mby, mbz, mf.lo);
                 }
                 new_step = false;
             }
             // ---- one Cash-Karp attempt in the local frame (FP32) ----
             const Y y0{{0.0f, 0.0f, 0.0f}, u};
-            const Y k1 = deriv_f<L, M>(F, bx, by, bz, f0, mf, kappa, y0);
+            const Y k1 = deriv_f<L, M>(F, bx, by, bz, f0, a.fields, gid, sm, mf, kappa, y0);
             Y t;
 #define STG(expr)                                                                              \
             t.p.x = h * (expr(p.x)); t.p.y = h * (expr(p.y)); t.p.z = h * (expr(p.z));         \
@@ -369,19 +422,19 @@ __global__ void CRP_MIXED_BOUNDS k_propagate_mixed(const PropArgs a) {
             t.u.z = fmaf(h, (expr(u.z)), u.z);
 #define S2(c) (A21 * k1.c)
             STG(S2)
-            const Y k2 = deriv_f<L, M>(F, bx, by, bz, f0, mf, kappa, t);
+            const Y k2 = deriv_f<L, M>(F, bx, by, bz, f0, a.fields, gid, sm, mf, kappa, t);
 #define S3(c) (A31 * k1.c + A32 * k2.c)
             STG(S3)
-            const Y k3 = deriv_f<L, M>(F, bx, by, bz, f0, mf, kappa, t);
+            const Y k3 = deriv_f<L, M>(F, bx, by, bz, f0, a.fields, gid, sm, mf, kappa, t);
 #define S4(c) (A41 * k1.c + A42 * k2.c + A43 * k3.c)
             STG(S4)
-            const Y k4 = deriv_f<L, M>(F, bx, by, bz, f0, mf, kappa, t);
+            const Y k4 = deriv_f<L, M>(F, bx, by, bz, f0, a.fields, gid, sm, mf, kappa, t);
 #define S5(c) (A51 * k1.c + A52 * k2.c + A53 * k3.c + A54 * k4.c)
             STG(S5)
-            const Y k5 = deriv_f<L, M>(F, bx, by, bz, f0, mf, kappa, t);
+            const Y k5 = deriv_f<L, M>(F, bx, by, bz, f0, a.fields, gid, sm, mf, kappa, t);
 #define S6(c) (A61 * k1.c + A62 * k2.c + A63 * k3.c + A64 * k4.c + A65 * k5.c)
             STG(S6)
-            const Y k6 = deriv_f<L, M>(F, bx, by, bz, f0, mf, kappa, t);
+            const Y k6 = deriv_f<L, M>(F, bx, by, bz, f0, a.fields, gid, sm, mf, kappa, t);
 #define SB(c) (B1 * k1.c + B3 * k3.c + B4 * k4.c + B6 * k6.c)
 #define SE(c) (E1 * k1.c + E3 * k3.c + E4 * k4.c + E5 * k5.c + E6 * k6.c)
             const F3 dp{h * SB(p.x), h * SB(p.y), h * SB(p.z)};
@@ -506,6 +559,30 @@ __global__ void CRP_MIXED_BOUNDS k_propagate_mixed(const PropArgs a) {
     }
 }
 
+// Register caps (more resident warps to hide gather latency); build-time tuning knobs.
+#ifdef CRP_MIXED_MAXNREG
+#define CRP_MIXED_BOUNDS __maxnreg__(CRP_MIXED_MAXNREG)
+#else
+#define CRP_MIXED_BOUNDS __launch_bounds__(256)
+#endif
+#ifdef CRP_MIXED_MOD_MAXNREG
+#define CRP_MIXED_MOD_BOUNDS __maxnreg__(CRP_MIXED_MOD_MAXNREG)
+#else
+#define CRP_MIXED_MOD_BOUNDS __launch_bounds__(256)
+#endif
+
+template <int L>
+__global__ void CRP_MIXED_BOUNDS k_propagate_mixed(const PropArgs a) {
+    propagate_mixed_body<L, false>(a, nullptr);
+}
+
+// Modulated fields; dynamic shared memory: kModSlots floats per thread.
+template <int L>
+__global__ void CRP_MIXED_MOD_BOUNDS k_propagate_mixed_mod(const PropArgs a) {
+    extern __shared__ float mod_sm[];
+    propagate_mixed_body<L, true>(a, mod_sm);
+}
+
 }  // namespace
 
 // Kernel for (layout, modulated): FP32 or BF16 vector grids.
@@ -513,24 +590,28 @@ template <typename Fn>
 int with_mixed_kernel(int layout, int mod, Fn&& fn) {
     switch (layout) {
     case LAYOUT_F32X4:
-        return mod ? fn(k_propagate_mixed<LAYOUT_F32X4, true>) : fn(k_propagate_mixed<LAYOUT_F32X4, false>);
+        return mod ? fn(k_propagate_mixed_mod<LAYOUT_F32X4>) : fn(k_propagate_mixed<LAYOUT_F32X4>);
     case LAYOUT_BF16X4:
-        return mod ? fn(k_propagate_mixed<LAYOUT_BF16X4, true>) : fn(k_propagate_mixed<LAYOUT_BF16X4, false>);
+        return mod ? fn(k_propagate_mixed_mod<LAYOUT_BF16X4>) : fn(k_propagate_mixed<LAYOUT_BF16X4>);
     default: return (int)cudaErrorInvalidValue;
     }
 }
 
+size_t mixed_smem(int mod, int block) { return mod ? (size_t)kModSlots * sizeof(float) * block : 0; }
+
 int launch_propagate_mixed(const PropArgs& a, int layout, int mod, int grid, int block, void* stream) {
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const size_t shm = mixed_smem(mod, block);
     return with_mixed_kernel(layout, mod, [&](void (*k)(const PropArgs)) {
-        k<<<grid, block, 0, st>>>(a);
+        k<<<grid, block, shm, st>>>(a);
         return (int)cudaGetLastError();
     });
 }
 
 int propagate_mixed_occupancy(int layout, int mod, int block, int* blocks_per_sm) {
+    const size_t shm = mixed_smem(mod, block);
     return with_mixed_kernel(layout, mod, [&](void (*k)(const PropArgs)) {
-        return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, block, 0);
+        return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, block, shm);
     });
 }
 
