@@ -51,7 +51,11 @@ class Tables(C.Structure):
 class Params(C.Structure):
     _fields_ = [("tol", C.c_double), ("hmin", C.c_double), ("hmax", C.c_double),
                 ("dmax", C.c_double), ("seed", C.c_uint64), ("max_steps", C.c_int64),
-                ("n_threads", C.c_int32), ("pad_", C.c_int32)]
+                ("n_threads", C.c_int32), ("boundary", C.c_int32),
+                ("box_origin", C.c_double * 3), ("box_size", C.c_double * 3)]
+
+
+BOUNDARY_NONE, BOUNDARY_REFLECT = 0, 1
 
 
 _DBL = ["x", "y", "z", "ux", "uy", "uz", "E", "s", "hprop", "tau", "u0x", "u0y", "u0z"]
@@ -187,12 +191,16 @@ def inject(state: OracleState, particles, seed: int, tables: OracleTables | None
 
 
 def propagate(state: OracleState, fields, tables: OracleTables | None, tol: float, hmin: float,
-              hmax: float, dmax: float, seed: int = 1, max_steps: int = 0, n_threads: int = 0):
-    """Returns (rc, stats dict)."""
+              hmax: float, dmax: float, seed: int = 1, max_steps: int = 0, n_threads: int = 0,
+              box=None):
+    """Returns (rc, stats dict). box: None, or (origin[3], size[3]) of a reflective box."""
     if n_threads <= 0:
         n_threads = os.cpu_count() or 1
     arr = (Field * len(fields))(*[f.c for f in fields])
-    prm = Params(tol, hmin, hmax, dmax, seed, max_steps, n_threads, 0)
+    org, size = box if box is not None else ((0.0, 0.0, 0.0), (0.0, 0.0, 0.0))
+    prm = Params(tol, hmin, hmax, dmax, seed, max_steps, n_threads,
+                 BOUNDARY_REFLECT if box is not None else BOUNDARY_NONE,
+                 (C.c_double * 3)(*org), (C.c_double * 3)(*size))
     stats = np.zeros(4, dtype=np.int64)
     rc = lib().orc_propagate(C.byref(state.c), arr, len(fields),
                              C.byref(tables.c) if tables else None, C.byref(prm), _ptr(stats))

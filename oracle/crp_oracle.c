@@ -361,8 +361,11 @@ int orc_inject(orc_state* st, int64_t first, int64_t count, uint64_t seed, const
     if (!st || first < 0 || count < 0 || first + count > st->capacity) return ORC_ERR_INVALID_ARG;
     for (int64_t i = first; i < first + count; ++i) {
         if (st->uid[i] < 0 || st->uid[i] >= ((int64_t)1 << 32)) return ORC_ERR_INVALID_ARG;
-        if (st->A[i] < 1 || st->Z[i] < 0 || st->Z[i] > st->A[i]) return ORC_ERR_INVALID_ARG;
-        if (t && (st->Z[i] > t->z_max || st->A[i] - st->Z[i] > t->n_max)) return ORC_ERR_INVALID_ARG;
+        /* Z < 0: an antinucleus, for backward tracking (Sec. 3.3 galactic propagation:
+         * cosmic rays propagated backwards from Earth); only without interaction tables */
+        if (st->A[i] < 1 || st->Z[i] > st->A[i] || st->Z[i] < -st->A[i]) return ORC_ERR_INVALID_ARG;
+        if (t && (st->Z[i] < 0 || st->Z[i] > t->z_max || st->A[i] - st->Z[i] > t->n_max))
+            return ORC_ERR_INVALID_ARG;
         st->s[i] = 0.0;
         st->hprop[i] = INFINITY;
         st->tau[i] = -orc_log(orc_uniform(seed, (uint64_t)st->uid[i], 0u, 0u));
@@ -393,6 +396,38 @@ typedef struct {
 } orc_job;
 
 static double clamp(double v, double lo, double hi) { return fmin(fmax(v, lo), hi); }
+
+/* Reflective boundary (Sec. 4: reflective boundary conditions make a finite volume stand
+ * for sources at much larger distances). Along each axis the box is [o, o + L]. A position
+ * outside it is folded back by mirror reflection at the faces: with t = (x - o) * (1/L) and
+ * k = floor(t), the fractional part r = t - k gives x' = o + r L for even k and
+ * x' = (o + L) - r L for odd k, and an odd k reverses the direction component. Returns 1 if
+ * the component was reversed. Positions inside the box (faces included) are unchanged. */
+static int reflect_axis(double* x, double o, double L)
+{
+    double hi = o + L;
+    if (!(*x < o || *x > hi)) return 0;
+    double t = (*x - o) * (1.0 / L);
+    double k = floor(t);
+    double r = t - k;
+    int odd = fmod(k, 2.0) != 0.0;
+    *x = odd ? hi - r * L : o + r * L;
+    return odd;
+}
+
+/* Reflect position and direction after an accepted step; the initial direction u0 takes
+ * the same sign flips, so that the deflection angle (u vs u0) is measured in the mirrored
+ * frame in which the particle keeps moving. */
+static void reflect_state(const orc_params* p, double y[6], orc_state* st, int64_t i)
+{
+    double* u0[3] = {st->u0x, st->u0y, st->u0z};
+    for (int a = 0; a < 3; ++a) {
+        if (reflect_axis(&y[a], p->box_origin[a], p->box_size[a])) {
+            y[3 + a] = -y[3 + a];
+            u0[a][i] = -u0[a][i];
+        }
+    }
+}
 
 static void propagate_one(orc_job* job, int64_t i)
 {
@@ -465,6 +500,7 @@ static void propagate_one(orc_job* job, int64_t i)
         n_att += att_step;
         att_total += att_step;
         for (int c = 0; c < 6; ++c) y[c] = y5[c];
+        if (p->boundary == ORC_BOUNDARY_REFLECT) reflect_state(p, y, st, i);
         int done = (h == h_dist);
         s = done ? p->dmax : s + h;
         n_steps += 1;
@@ -553,6 +589,11 @@ int orc_propagate(orc_state* st, const orc_field* fields, int32_t n_fields, cons
     if (!st || !fields || n_fields < 1 || !p) return ORC_ERR_INVALID_ARG;
     if (!(p->tol > 0.0) || !(p->hmin > 0.0) || !(p->hmax >= p->hmin) || !(p->dmax > 0.0))
         return ORC_ERR_INVALID_ARG;
+    if (p->boundary != ORC_BOUNDARY_NONE && p->boundary != ORC_BOUNDARY_REFLECT) return ORC_ERR_INVALID_ARG;
+    if (p->boundary == ORC_BOUNDARY_REFLECT)
+        for (int a = 0; a < 3; ++a)
+            if (!(p->box_size[a] > 0.0) || !isfinite(p->box_size[a]) || !isfinite(p->box_origin[a]))
+                return ORC_ERR_INVALID_ARG;
     for (int64_t i = 0; i < st->n; ++i)
         if (st->grid_id[i] < 0 || st->grid_id[i] >= n_fields) return ORC_ERR_INVALID_ARG;
     orc_job job;

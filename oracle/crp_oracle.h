@@ -76,8 +76,12 @@ typedef struct {
     uint64_t seed;       /* Philox key */
     int64_t max_steps;   /* accepted steps per particle per call; <= 0: no limit */
     int32_t n_threads;   /* <= 0: one */
-    int32_t pad_;
+    int32_t boundary;    /* ORC_BOUNDARY_NONE or ORC_BOUNDARY_REFLECT */
+    double box_origin[3];/* reflective box [origin, origin + size] per axis, m */
+    double box_size[3];
 } orc_params;
+
+enum { ORC_BOUNDARY_NONE = 0, ORC_BOUNDARY_REFLECT = 1 };
 
 /* Particle state, structure of arrays, `capacity` slots; slots [0, n) are in use. */
 typedef struct {
