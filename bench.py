@@ -250,7 +250,8 @@ def cpu_baseline(w, grids, tables, parts, sample: int, form_desc: str):
     threads = os.cpu_count() or 1
     t0 = time.perf_counter()
     rc, stats = O.propagate(st, [g.oracle_field(O, w.spacing_m) for g in grids], ot, w.tol,
-                            w.hmin_m, w.hmax_m, w.dmax_m, seed=w.rng_seed, n_threads=threads)
+                            w.hmin_m, w.hmax_m, w.dmax_m, seed=w.rng_seed, n_threads=threads,
+                            box=I.workload_box(w))
     dt = time.perf_counter() - t0
     return ({"value": stats["accepted"] / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
              "sample": f"{len(sub)} primaries of the same batch (+{stats['secondaries']} "
@@ -334,7 +335,7 @@ def run_reference(args):
         t0 = time.perf_counter()
         rc, stats = O.propagate(st, [g.oracle_field(O, w.spacing_m) for g in grids], ot, w.tol,
                                 w.hmin_m, w.hmax_m, w.dmax_m, seed=w.rng_seed,
-                                n_threads=os.cpu_count() or 1)
+                                n_threads=os.cpu_count() or 1, box=I.workload_box(w))
         dt = time.perf_counter() - t0
         if it >= args.warmup:
             times.append(dt)
@@ -378,6 +379,9 @@ def run_own(args):
     fields = [g.field(crp, w.spacing_m) for g in grids]
     tabs = crp.Tables(tables) if tables is not None else None
     sim = crp.Simulation(fields, tabs, seed=w.rng_seed, capacity=cap)
+    box = I.workload_box(w)
+    if box is not None:
+        sim.set_boundary(box)
     slice_steps = args.slice_steps if args.slice_steps >= 0 else (16000 if w.n_grids > 1 else 0)
     grid_bytes = sum(int(np.prod(f.shape)) for f in fields) * (8 if w.grid_n >= 512 else 16)
     grid_bytes += sum(int(g.mod.size) * 4 for g in grids if g.mod is not None)
@@ -539,6 +543,7 @@ def run_own(args):
                    "order": order,
                    "slice_steps": slice_steps,
                    "form": args.form, "dmax_mpc": w.dmax_m / I.MPC, "tol": w.tol,
+                   "boundary": "reflective box of the modulation volume" if box is not None else "none",
                    "l2": f"inputs larger than L2 (grids {grid_bytes / 1e6:.0f} MB in device layout, "
                          f"particle state {cap * 170 / 1e9:.2f} GB) and a 256 MB flush before every step",
                    "parallelism": f"dp{ws} (independent particle batches per GPU)"},

@@ -149,10 +149,24 @@ int crp_sim_destroy(crp_sim* sim);
  * allocations, fields, tables and seed; uids continue from 0 again. Synchronises. */
 int crp_sim_reset(crp_sim* sim);
 
+/* Reflective boundary (Sec. 4: reflective boundary conditions let a finite volume stand for
+ * sources at much larger distances). With CRP_BOUNDARY_REFLECT, after every accepted step a
+ * position outside the box [origin_m, origin_m + size_m] (per axis, faces included in the
+ * box) is folded back by mirror reflection: t = (x - o) * (1/L), k = floor(t), r = t - k,
+ * x' = o + r L for even k, (o + L) - r L for odd k; an odd k reverses that component of the
+ * direction and of the initial direction u0 (deflection angles stay in the mirrored frame).
+ * Secondaries inherit the folded state. Applies to later crp_propagate / crp_propagate_loop
+ * calls of this simulation; CRP_BOUNDARY_NONE (origin/size ignored, may be NULL) removes it.
+ * Errors: INVALID_ARG (NULL sim, unknown kind, a size <= 0 or not finite, origin not finite). */
+#define CRP_BOUNDARY_NONE 0
+#define CRP_BOUNDARY_REFLECT 1
+int crp_sim_set_boundary(crp_sim* sim, int32_t kind, const double origin_m[3], const double size_m[3]);
+
 /* ---- source injection (Sec. 4: sources emit isotropically; positions/directions/
  * energies come from the caller) ----------------------------------------------------------
- * Appends n particles after the ones already present. Each needs A >= 1, 0 <= Z <= A,
- * a species inside the tables (if any), uid < 2^32 (uid == NULL: uids continue the
+ * Appends n particles after the ones already present. Each needs A >= 1, -A <= Z <= A
+ * (Z < 0: an antinucleus, for backward tracking from the observer, Sec. 3.3; only in a
+ * simulation without tables), a species inside the tables (if any), uid < 2^32 (uid == NULL: uids continue the
  * count of primaries injected so far), 0 <= grid_id < n_fields (grid_id == NULL: 0).
  * The library initialises s = 0, no step proposal, the first optical depth
  * tau = -ln U(uid, 0, tag 0) (Philox), u0 = u, counters 0, status active.

@@ -18,6 +18,7 @@ FORM_FP64, FORM_MIXED = 0, 1
 ORDER_DEFAULT, ORDER_SLOT, ORDER_COST, ORDER_GRID = 0, 1, 2, 3
 PICKUP_DEFAULT, PICKUP_OFF, PICKUP_ON = 0, 1, 2
 STATUS_ACTIVE, STATUS_DONE, STATUS_NAN, STATUS_RANGE = 0, 1, 2, 3
+BOUNDARY_NONE, BOUNDARY_REFLECT = 0, 1
 
 # column name -> (id, numpy dtype)
 COLUMNS = {
@@ -83,6 +84,7 @@ def lib() -> C.CDLL:
             "crp_sim_reserve": ([p, i64], C.c_int),
             "crp_sim_destroy": ([p], C.c_int),
             "crp_sim_reset": ([p], C.c_int),
+            "crp_sim_set_boundary": ([p, i32, p, p], C.c_int),
             "crp_source_inject": ([p, p, i64, p], C.c_int),
             "crp_propagate": ([p, p, d, d, d, d, p], C.c_int),
             "crp_propagate_loop": ([p, p, d, d, d, d, i32, p], C.c_int),
@@ -277,6 +279,16 @@ class Simulation:
 
     def reset(self) -> None:
         _check(lib().crp_sim_reset(self._h), "crp_sim_reset")
+
+    def set_boundary(self, box=None) -> None:
+        """Reflective box (paper Sec. 4): ``box`` = (origin[3], size[3]) in metres, or None
+        for no boundary."""
+        if box is None:
+            _check(lib().crp_sim_set_boundary(self._h, BOUNDARY_NONE, None, None), "crp_sim_set_boundary")
+            return
+        org = (C.c_double * 3)(*[float(v) for v in box[0]])
+        size = (C.c_double * 3)(*[float(v) for v in box[1]])
+        _check(lib().crp_sim_set_boundary(self._h, BOUNDARY_REFLECT, org, size), "crp_sim_set_boundary")
 
     def reserve(self, capacity: int) -> None:
         _check(lib().crp_sim_reserve(self._h, int(capacity)), "crp_sim_reserve")

@@ -114,9 +114,9 @@ __global__ void k_inject_init(SimState S, long long first, long long n, int uid_
         if (!gid_given) S.grid_id[i] = 0;
         const int A = S.A[i], Z = S.Z[i];
         const long long uid = S.uid[i];
-        bool ok = A >= 1 && Z >= 0 && Z <= A && uid >= 0 && uid < (1ll << 32) &&
+        bool ok = A >= 1 && Z >= -A && Z <= A && uid >= 0 && uid < (1ll << 32) &&
                   S.grid_id[i] >= 0 && S.grid_id[i] < n_fields;
-        if (has_tables && (Z > z_max || A - Z > n_max)) ok = false;
+        if (has_tables && (Z < 0 || Z > z_max || A - Z > n_max)) ok = false;
         S.s[i] = 0.0;
         S.hprop[i] = INF;
         S.tau[i] = -crp_log(uniform01(seed, (unsigned long long)uid, 0u, 0u));
@@ -368,6 +368,8 @@ struct crp_sim {
     FieldDev* d_fields64 = nullptr;     // FP64 copies, for the FP64 form
     int layout = LAYOUT_F32X4;
     int mod = 0;                        // 1: every field carries a modulation grid
+    int boundary = CRP_BOUNDARY_NONE;   // crp_sim_set_boundary
+    double box_origin[3] = {0, 0, 0}, box_size[3] = {0, 0, 0};
     const crp_tables* tables = nullptr;
     unsigned long long seed = 0;
     long long capacity = 0;
@@ -659,6 +661,25 @@ int crp_sim_create(const crp_field* const* fields, int32_t n_fields, const crp_t
     return CRP_OK;
 }
 
+int crp_sim_set_boundary(crp_sim* s, int32_t kind, const double origin_m[3], const double size_m[3]) {
+    if (!s) return fail(CRP_ERR_INVALID_ARG, "sim is NULL");
+    if (kind == CRP_BOUNDARY_NONE) {
+        s->boundary = CRP_BOUNDARY_NONE;
+        return CRP_OK;
+    }
+    if (kind != CRP_BOUNDARY_REFLECT) return fail(CRP_ERR_INVALID_ARG, "unknown boundary kind");
+    if (!origin_m || !size_m) return fail(CRP_ERR_INVALID_ARG, "origin or size is NULL");
+    for (int c = 0; c < 3; ++c)
+        if (!std::isfinite(origin_m[c]) || !(size_m[c] > 0.0) || !std::isfinite(size_m[c]))
+            return fail(CRP_ERR_INVALID_ARG, "box origin must be finite, sizes finite and > 0");
+    s->boundary = kind;
+    for (int c = 0; c < 3; ++c) {
+        s->box_origin[c] = origin_m[c];
+        s->box_size[c] = size_m[c];
+    }
+    return CRP_OK;
+}
+
 int crp_sim_destroy(crp_sim* s) {
     if (!s) return fail(CRP_ERR_INVALID_ARG, "sim is NULL");
     if (s->last) cudaStreamSynchronize(s->last);
@@ -739,9 +760,9 @@ int crp_source_inject(crp_sim* s, const crp_particles* p, int64_t n, void* strea
     if (!p->is_device) {   // host columns: validate before touching the device
         for (long long i = 0; i < n; ++i) {
             const int A = p->A[i], Z = p->Z[i];
-            if (A < 1 || Z < 0 || Z > A) return fail(CRP_ERR_INVALID_ARG, "particle with invalid A/Z");
-            if (tab && (Z > tab->z_max || A - Z > tab->n_max))
-                return fail(CRP_ERR_INVALID_ARG, "species outside the interaction tables");
+            if (A < 1 || Z < -A || Z > A) return fail(CRP_ERR_INVALID_ARG, "particle with invalid A/Z");
+            if (tab && (Z < 0 || Z > tab->z_max || A - Z > tab->n_max))
+                return fail(CRP_ERR_INVALID_ARG, "species outside the interaction tables (antinuclei take none)");
             const long long uid = p->uid ? p->uid[i] : (long long)(h.n_primaries + i);
             if (uid < 0 || uid >= (1ll << 32)) return fail(CRP_ERR_INVALID_ARG, "uid outside [0, 2^32)");
             if (p->grid_id && (p->grid_id[i] < 0 || p->grid_id[i] >= n_fields))
@@ -879,6 +900,13 @@ int make_plan(crp_sim* s, const crp_params* prm, double tol, double hmin, double
     a.lists[1] = s->lists[1];
     a.done_list = s->done_list;
     a.ctr = s->ctr;
+    a.boundary = s->boundary == CRP_BOUNDARY_REFLECT ? 1 : 0;
+    for (int c = 0; c < 3; ++c) {
+        a.box_lo[c] = s->box_origin[c];
+        a.box_hi[c] = s->box_origin[c] + s->box_size[c];
+        a.box_len[c] = s->box_size[c];
+        a.box_inv[c] = s->boundary == CRP_BOUNDARY_REFLECT ? 1.0 / s->box_size[c] : 0.0;
+    }
     return CRP_OK;
 }
 

@@ -200,6 +200,18 @@ __device__ __forceinline__ double clampd(double v, double lo, double hi) {
     return fmin(fmax(v, lo), hi);
 }
 
+// Mirror fold of one coordinate into [lo, hi] (hi = lo + L, inv = 1/L): returns true when
+// the number of reflections is odd (the direction component reverses).
+__device__ __forceinline__ bool reflect_axis(double& x, double lo, double hi, double L, double inv) {
+    if (!(x < lo || x > hi)) return false;
+    const double t = (x - lo) * inv;
+    const double k = floor(t);
+    const double r = t - k;
+    const bool odd = fmod(k, 2.0) != 0.0;
+    x = odd ? hi - r * L : lo + r * L;
+    return odd;
+}
+
 __device__ __forceinline__ bool finite6(const Y6& y) {
     return isfinite(y.x) && isfinite(y.y) && isfinite(y.z) && isfinite(y.ux) &&
            isfinite(y.uy) && isfinite(y.uz);

@@ -93,6 +93,10 @@ struct PropArgs {
     int32_t* lists[2];
     int32_t* done_list;
     Counters* ctr;
+    // reflective box (boundary = 1): per axis origin, origin + size, size, 1/size
+    int32_t boundary;
+    int32_t pad_;
+    double box_lo[3], box_hi[3], box_len[3], box_inv[3];
 };
 
 // Launchers (defined in the kernel translation units).

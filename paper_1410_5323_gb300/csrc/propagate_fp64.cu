@@ -137,6 +137,17 @@ __global__ void __launch_bounds__(256) k_propagate_fp64(const PropArgs a) {
             n_att += att_step;
             att_tot += att_step;
             y = y5;
+            if (a.boundary) {   // reflective box: fold the position, flip u (and u0) per odd axis
+                if (reflect_axis(y.x, a.box_lo[0], a.box_hi[0], a.box_len[0], a.box_inv[0])) {
+                    y.ux = -y.ux; S.u0x[slot] = -S.u0x[slot];
+                }
+                if (reflect_axis(y.y, a.box_lo[1], a.box_hi[1], a.box_len[1], a.box_inv[1])) {
+                    y.uy = -y.uy; S.u0y[slot] = -S.u0y[slot];
+                }
+                if (reflect_axis(y.z, a.box_lo[2], a.box_hi[2], a.box_len[2], a.box_inv[2])) {
+                    y.uz = -y.uz; S.u0z[slot] = -S.u0z[slot];
+                }
+            }
             const bool done = (h == h_dist);
             s = done ? a.dmax : s + h;
             n_steps += 1;

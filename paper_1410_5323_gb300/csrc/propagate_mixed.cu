@@ -488,6 +488,23 @@ __device__ __forceinline__ void propagate_mixed_body(const PropArgs& a, float* s
             Ry = df_add(Ry, dp.y);
             Rz = df_add(Rz, dp.z);
             u = un;
+            if (a.boundary) {   // reflective box, evaluated on the FP64 position
+                auto fold = [&](DF& R, double o, int ax, float& uc, double* u0col) {
+                    double xd = to_x(R, o);
+                    const double lo = a.box_lo[ax], hi = a.box_hi[ax];
+                    if (!(xd < lo || xd > hi)) return;
+                    const double t = (xd - lo) * a.box_inv[ax];
+                    const double k = floor(t);
+                    const double r = t - k;
+                    const bool odd = fmod(k, 2.0) != 0.0;
+                    xd = odd ? hi - r * a.box_len[ax] : lo + r * a.box_len[ax];
+                    R = from_x(xd, o);
+                    if (odd) { uc = -uc; u0col[slot] = -u0col[slot]; }
+                };
+                fold(Rx, ox, 0, u.x, S.u0x);
+                fold(Ry, oy, 1, u.y, S.u0y);
+                fold(Rz, oz, 2, u.z, S.u0z);
+            }
             bool done = (h == h_dist);
             s_c = s_c + (double)h;
             if (s_c >= dmax_c) done = true;

@@ -410,6 +410,15 @@ class Workload:
     mod_lmax_cells: float = 0.0
     mod_sigma_ln: float = 0.0
     mod_seed: int = 2
+    reflect: bool = False      # reflective box = the modulation grid's volume
+
+
+def workload_box(w: Workload):
+    """(origin[3], size[3]) of the workload's reflective box in metres, or None."""
+    if not w.reflect:
+        return None
+    L = w.mod_n * w.mod_spacing_m
+    return (0.0, 0.0, 0.0), (L, L, L)
 
 
 def workload(name: str) -> Workload:
@@ -443,7 +452,7 @@ def workload(name: str) -> Workload:
                         species=(("H", 0.4), ("He", 0.3), ("N", 0.2), ("Fe", 0.1)),
                         energy=("power", 1e18, 10 ** 20.5, 2.0), interactions=True,
                         mod_n=440, mod_spacing_m=300.0 * KPC, mod_lmin_cells=2.0,
-                        mod_lmax_cells=110.0, mod_sigma_ln=1.0)
+                        mod_lmax_cells=110.0, mod_sigma_ln=1.0, reflect=True)
     if name == "adjoint_128cube_4k_protons":
         return Workload(name, 4096, 128, lmax_cells=32.0, brms_t=1.0 * NANOGAUSS,
                         dmax_m=1e6 * MPC, species=(("H", 1.0),), energy=("fixed", 10 ** 19.5),

@@ -15,7 +15,8 @@ def by_uid(d):
 
 def run_gpu(grids, parts, tables, tol, hmin, hmax, dmax, seed=1, capacity=None, max_steps=0,
             spacing=0.25 * I.MPC, form=0, calls=1, dtype=None, scale=1.0, origin=(0.0, 0.0, 0.0),
-            block_size=0, cadence=0, mods=None, mod_spacing=1.0, mod_origin=(0.0, 0.0, 0.0)):
+            block_size=0, cadence=0, mods=None, mod_spacing=1.0, mod_origin=(0.0, 0.0, 0.0),
+            box=None):
     """mods: None, or one modulation grid per vector grid (modulated fields)."""
     import paper_1410_5323_gb300 as crp
 
@@ -25,6 +26,8 @@ def run_gpu(grids, parts, tables, tol, hmin, hmax, dmax, seed=1, capacity=None, 
             f.modulate(m, mod_spacing, mod_origin)
     tabs = crp.Tables(tables) if tables is not None else None
     sim = crp.Simulation(fields, tabs, seed=seed, capacity=capacity or len(parts))
+    if box is not None:
+        sim.set_boundary(box)
     sim.inject(parts)
     for _ in range(calls):
         sim.propagate(tol, hmin, hmax, dmax, form=form, max_steps=max_steps, block_size=block_size,
@@ -35,7 +38,7 @@ def run_gpu(grids, parts, tables, tol, hmin, hmax, dmax, seed=1, capacity=None, 
 
 def run_oracle(grids, parts, tables, tol, hmin, hmax, dmax, seed=1, capacity=None, max_steps=0,
                spacing=0.25 * I.MPC, dtype=None, scale=1.0, origin=(0.0, 0.0, 0.0), calls=1,
-               mods=None, mod_spacing=1.0, mod_origin=(0.0, 0.0, 0.0)):
+               mods=None, mod_spacing=1.0, mod_origin=(0.0, 0.0, 0.0), box=None):
     mods = mods if mods is not None else [None] * len(grids)
     fields = [O.OracleField(g, spacing, origin, scale=scale, dtype=dtype, modulation=m,
                             mod_spacing=mod_spacing, mod_origin=mod_origin)
@@ -45,7 +48,8 @@ def run_oracle(grids, parts, tables, tol, hmin, hmax, dmax, seed=1, capacity=Non
     O.inject(st, parts, seed, ot)
     rc = 0
     for _ in range(calls):
-        rc, _ = O.propagate(st, fields, ot, tol, hmin, hmax, dmax, seed=seed, max_steps=max_steps)
+        rc, _ = O.propagate(st, fields, ot, tol, hmin, hmax, dmax, seed=seed, max_steps=max_steps,
+                            box=box)
     return st, rc
 
 

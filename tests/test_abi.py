@@ -58,6 +58,11 @@ def test_null_and_range_arguments_rejected_before_device_work(L):
     assert L.crp_field_modulate(fake, m.ctypes.data, 1, 0, 2, 0, 2, 1.0, org) == -1
     assert L.crp_field_modulate(fake, m.ctypes.data, 1, 0, 2, 2, 2, 0.0, org) == -1
     assert b"spacing" in L.crp_last_error_detail()
+    sz = (C.c_double * 3)(1.0, 0.0, 1.0)
+    assert L.crp_sim_set_boundary(None, 1, org, sz) == -1
+    assert L.crp_sim_set_boundary(fake, 7, org, sz) == -1                    # unknown kind
+    assert L.crp_sim_set_boundary(fake, 1, org, sz) == -1                    # a size of 0
+    assert L.crp_sim_set_boundary(fake, 1, None, sz) == -1
     assert L.crp_sim_create(None, 0, None, 1, 10, C.byref(h)) == -1
     assert L.crp_tables_create(1, 1, 1, 6.0, 25.0, None, None, None, None, C.byref(h)) == -1
     assert L.crp_propagate(None, None, 1e-4, 1.0, 2.0, 3.0, None) == -1

@@ -172,13 +172,14 @@ def _full_size():
 
 
 def test_full_size_modulated_workload_sampled_bit_identical(oracle_lib):
-    """The whole 10^6-nuclei batch through the 440^3 x 256^3 modulated field in the launch
-    configuration the benchmark times (FP64 form); 128 primaries spread over the batch, with
-    every secondary they produced, bit for bit against the oracle run on them alone."""
+    """The whole 10^6-nuclei batch through the 440^3 x 256^3 modulated field, reflective box of
+    the modulation volume, in the launch configuration the benchmark times (FP64 form); 128
+    primaries spread over the batch, with every secondary they produced, bit for bit against
+    the oracle run on them alone."""
     w, g, m, p = _full_size()
     t = I.synthetic_tables()
     cap = int(len(p) + np.sum(p.A.astype(np.int64) - 1))
-    kw = dict(spacing=w.spacing_m, mods=[m], mod_spacing=w.mod_spacing_m)
+    kw = dict(spacing=w.spacing_m, mods=[m], mod_spacing=w.mod_spacing_m, box=I.workload_box(w))
     sim, rc = run_gpu([g], p, t, w.tol, w.hmin_m, w.hmax_m, w.dmax_m, seed=w.rng_seed, capacity=cap, **kw)
     assert rc == 0
     gs = sim.state()
