@@ -311,3 +311,73 @@ def adjoint(field: OracleField, kappa: float, y0, h, lamT, grid_bar: np.ndarray 
     _sigs().orc_adjoint(C.byref(field.c), kappa, _ptr(y), _ptr(hh), len(hh), _ptr(lam), gp, _ptr(yb),
                         C.byref(kb))
     return yb, kb.value
+
+
+# ---- sources (Sec. 4, Eq. 1) and arrival binning -----------------------------------------
+MAX_SPECIES = 8
+
+
+class Spectrum(C.Structure):
+    _fields_ = [("n_species", C.c_int32), ("A", C.c_int32 * MAX_SPECIES),
+                ("Z", C.c_int32 * MAX_SPECIES), ("pad_", C.c_int32),
+                ("x", C.c_double * MAX_SPECIES), ("alpha", C.c_double), ("rcut_v", C.c_double),
+                ("e_min_ev", C.c_double), ("e_max_ev", C.c_double)]
+
+
+def spectrum(species, alpha: float, rcut_v: float, e_min_ev: float, e_max_ev: float) -> Spectrum:
+    """species: [(A, Z, x), ...]."""
+    sp = Spectrum()
+    sp.n_species = len(species)
+    for i, (a, z, x) in enumerate(species):
+        sp.A[i], sp.Z[i], sp.x[i] = int(a), int(z), float(x)
+    sp.alpha, sp.rcut_v, sp.e_min_ev, sp.e_max_ev = float(alpha), float(rcut_v), float(e_min_ev), float(e_max_ev)
+    return sp
+
+
+def _src_sigs():
+    L = lib()
+    if not getattr(L, "_src_sigs", False):
+        p, d, i32, i64, u64 = C.c_void_p, C.c_double, C.c_int32, C.c_int64, C.c_uint64
+        L.orc_source_sample.argtypes = [p, u64, u64, i64, p, p, p, p, p, p]
+        L.orc_source_sample.restype = i64
+        L.orc_atan2.argtypes = [d, d]
+        L.orc_atan2.restype = d
+        L.orc_healpix_ring.argtypes = [i32, d, d, d]
+        L.orc_healpix_ring.restype = i64
+        L.orc_arrival_map.argtypes = [p, i32, d, p]
+        L.orc_arrival_map.restype = C.c_int
+        L._src_sigs = True
+    return L
+
+
+def source_sample(sp: Spectrum, seed: int, uid_base: int, n: int):
+    """(A, Z, E, u [n, 3], n_failed) drawn from Eq. 1 with isotropic directions."""
+    A = np.zeros(n, np.int32)
+    Z = np.zeros(n, np.int32)
+    E = np.zeros(n)
+    u = np.zeros((3, n))
+    failed = _src_sigs().orc_source_sample(C.byref(sp), seed, uid_base, n, _ptr(A), _ptr(Z), _ptr(E),
+                                           _ptr(u[0]), _ptr(u[1]), _ptr(u[2]))
+    if failed < 0:
+        raise ValueError("invalid spectrum")
+    return A, Z, E, np.ascontiguousarray(u.T), int(failed)
+
+
+def atan2(y: float, x: float) -> float:
+    return _src_sigs().orc_atan2(y, x)
+
+
+def healpix_ring(nside: int, u) -> np.ndarray:
+    """Pixel index of each direction row of u [n, 3] (plain loop over the rows)."""
+    L = _src_sigs()
+    u = np.atleast_2d(np.asarray(u, dtype=np.float64))
+    return np.array([L.orc_healpix_ring(nside, float(a), float(b), float(c)) for a, b, c in u],
+                    dtype=np.int64)
+
+
+def arrival_map(state: OracleState, nside: int, e_min_ev: float) -> np.ndarray:
+    m = np.zeros(12 * nside * nside, dtype=np.uint64)
+    rc = _src_sigs().orc_arrival_map(C.byref(state.c), nside, e_min_ev, _ptr(m))
+    if rc != OK:
+        raise ValueError(f"orc_arrival_map failed: {rc}")
+    return m

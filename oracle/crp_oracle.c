@@ -821,3 +821,223 @@ void orc_adjoint(const orc_field* f, double kappa, const double y0[6], const dou
     for (int c = 0; c < 6; ++c) y0_bar[c] = lam[c];
     free(ys);
 }
+
+/* ---- source spectrum (Sec. 4, Eq. 1) ---------------------------------------------------
+ * dN_i/dE ~ x_i A_i^(alpha - 1) E^-alpha exp(-E / (Z_i R_cut)) on [E_min, E_max]. Sampled by
+ * rejection from the cutoff-free joint law: species i with probability proportional to
+ * w_i = x_i A_i^(alpha-1), E from E^-alpha by its inverse CDF, the pair kept with probability
+ * exp(-E / (Z_i R_cut)); a rejected pair is redrawn whole, so the kept pairs follow Eq. 1
+ * jointly. Random numbers: Philox counter (uid, k, tag 2) gives (U1, U2) for draw k,
+ * (uid, k, tag 3) gives U3. Directions are isotropic by Marsaglia (1972): v1, v2 uniform in
+ * (-1, 1) from counter (uid, k, tag 4), kept if s = v1^2 + v2^2 < 1, then
+ * u = (2 v1 sqrt(1 - s), 2 v2 sqrt(1 - s), 1 - 2 s). */
+static double uniform_words(uint32_t hi, uint32_t lo)
+{
+    uint64_t m = ((uint64_t)hi << 20) | (uint64_t)(lo >> 12);
+    return ((double)m + 0.5) * 0x1p-52;
+}
+
+static void philox_words(uint64_t seed, uint64_t uid, uint32_t k, uint32_t tag, uint32_t w[4])
+{
+    uint32_t ctr[4] = {(uint32_t)uid, (uint32_t)(uid >> 32), k, tag};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    orc_philox4x32_10(ctr, key, w);
+}
+
+int orc_spectrum_check(const orc_spectrum* sp)
+{
+    if (!sp || sp->n_species < 1 || sp->n_species > ORC_MAX_SPECIES) return ORC_ERR_INVALID_ARG;
+    if (!(sp->e_min_ev > 0.0) || !(sp->e_max_ev > sp->e_min_ev) || !isfinite(sp->e_max_ev))
+        return ORC_ERR_INVALID_ARG;
+    if (!(sp->rcut_v > 0.0) || !isfinite(sp->alpha)) return ORC_ERR_INVALID_ARG;
+    double total = 0.0;
+    for (int i = 0; i < sp->n_species; ++i) {
+        if (sp->A[i] < 1 || sp->Z[i] < 1 || sp->Z[i] > sp->A[i] || !(sp->x[i] >= 0.0)) return ORC_ERR_INVALID_ARG;
+        total += sp->x[i];
+    }
+    return total > 0.0 ? ORC_OK : ORC_ERR_INVALID_ARG;
+}
+
+int64_t orc_source_sample(const orc_spectrum* sp, uint64_t seed, uint64_t uid_base, int64_t n,
+                          int32_t* A, int32_t* Z, double* E, double* ux, double* uy, double* uz)
+{
+    if (orc_spectrum_check(sp) != ORC_OK || n < 0) return -1;
+    /* cumulative species weights w_i = x_i A_i^(alpha-1) */
+    double cum[ORC_MAX_SPECIES];
+    double acc = 0.0;
+    for (int i = 0; i < sp->n_species; ++i) {
+        double w = sp->x[i] * orc_exp((sp->alpha - 1.0) * orc_log((double)sp->A[i]));
+        acc = acc + w;
+        cum[i] = acc;
+    }
+    double W = acc;
+    /* inverse CDF of E^-alpha: E = (lo + U (hi - lo))^(1/g), g = 1 - alpha, lo/hi = E_min/max^g;
+     * alpha == 1: E = E_min exp(U ln(E_max/E_min)) */
+    double g = 1.0 - sp->alpha;
+    double lo = 0.0, hi = 0.0, lr = 0.0;
+    if (g != 0.0) {
+        lo = orc_exp(g * orc_log(sp->e_min_ev));
+        hi = orc_exp(g * orc_log(sp->e_max_ev));
+    } else {
+        lr = orc_log(sp->e_max_ev / sp->e_min_ev);
+    }
+    int64_t failed = 0;
+    for (int64_t p = 0; p < n; ++p) {
+        uint64_t uid = uid_base + (uint64_t)p;
+        int32_t a = 0, z = 0;
+        double e = 0.0;
+        for (uint32_t k = 0; k < ORC_SOURCE_DRAWS; ++k) {
+            uint32_t w[4], v[4];
+            philox_words(seed, uid, k, 2u, w);
+            double u1 = uniform_words(w[0], w[1]);
+            double u2 = uniform_words(w[2], w[3]);
+            int s = sp->n_species - 1;
+            double target = u1 * W;
+            for (int i = 0; i < sp->n_species; ++i)
+                if (target < cum[i]) { s = i; break; }
+            double en = g != 0.0 ? orc_exp(orc_log(lo + u2 * (hi - lo)) / g)
+                                 : sp->e_min_ev * orc_exp(u2 * lr);
+            philox_words(seed, uid, k, 3u, v);
+            double u3 = uniform_words(v[0], v[1]);
+            if (u3 < orc_exp(-en / ((double)sp->Z[s] * sp->rcut_v))) {
+                a = sp->A[s];
+                z = sp->Z[s];
+                e = en;
+                break;
+            }
+        }
+        double d[3] = {0.0, 0.0, 0.0};
+        int have_dir = 0;
+        for (uint32_t k = 0; k < ORC_SOURCE_DRAWS; ++k) {
+            uint32_t w[4];
+            philox_words(seed, uid, k, 4u, w);
+            double v1 = 2.0 * uniform_words(w[0], w[1]) - 1.0;
+            double v2 = 2.0 * uniform_words(w[2], w[3]) - 1.0;
+            double s = v1 * v1 + v2 * v2;
+            if (s < 1.0) {
+                double r = 2.0 * sqrt(1.0 - s);
+                d[0] = v1 * r;
+                d[1] = v2 * r;
+                d[2] = 1.0 - 2.0 * s;
+                have_dir = 1;
+                break;
+            }
+        }
+        if (a == 0 || !have_dir) {
+            failed += 1;
+            a = 0;
+            z = 0;
+        }
+        A[p] = a; Z[p] = z; E[p] = e;
+        ux[p] = d[0]; uy[p] = d[1]; uz[p] = d[2];
+    }
+    return failed;
+}
+
+/* ---- arrival binning (Sec. 4, Fig. 4: HEALPix maps of arrival directions) ------------- */
+static const double PI_D = 3.141592653589793;
+static const double HALF_PI_D = 1.5707963267948966;
+static const double QUARTER_PI_D = 0.7853981633974483;
+
+/* atan2 by one stated algorithm (so that both implementations bin identically): reduce to
+ * a = min(|x|,|y|) / max(|x|,|y|) in [0, 1]; for a > tan(pi/8) use atan a = pi/4 + atan b,
+ * b = (a - 1)/(a + 1); then atan b = 2 atan c with c = b / (1 + sqrt(1 + b^2)), |c| <= 0.2;
+ * atan c by its Taylor series through c^27/27 (Horner in c^2); undo the octant reduction. */
+double orc_atan2(double y, double x)
+{
+    if (x != x || y != y) return NAN;
+    double ax = fabs(x), ay = fabs(y);
+    if (ax == 0.0 && ay == 0.0) return 0.0;
+    int swap = ay > ax;
+    double a = swap ? ax / ay : ay / ax;
+    double base = 0.0;
+    double b = a;
+    if (a > 0.41421356237309503) {
+        b = (a - 1.0) / (a + 1.0);
+        base = QUARTER_PI_D;
+    }
+    double c = b / (1.0 + sqrt(1.0 + b * b));
+    double s = c * c;
+    double p = -1.0 / 27.0;
+    p = p * s + 1.0 / 25.0;
+    p = p * s - 1.0 / 23.0;
+    p = p * s + 1.0 / 21.0;
+    p = p * s - 1.0 / 19.0;
+    p = p * s + 1.0 / 17.0;
+    p = p * s - 1.0 / 15.0;
+    p = p * s + 1.0 / 13.0;
+    p = p * s - 1.0 / 11.0;
+    p = p * s + 1.0 / 9.0;
+    p = p * s - 1.0 / 7.0;
+    p = p * s + 1.0 / 5.0;
+    p = p * s - 1.0 / 3.0;
+    p = p * s + 1.0;
+    double r = base + 2.0 * (c * p);
+    if (swap) r = HALF_PI_D - r;
+    if (x < 0.0) r = PI_D - r;
+    if (y < 0.0) r = -r;
+    return r;
+}
+
+/* HEALPix RING-scheme pixel of direction (x, y, z) (not necessarily unit) for resolution
+ * nside (Gorski et al. 2005, ApJ 622, 759, Sec. 4): 12 nside^2 equal-area pixels on rings
+ * 1 .. 4 nside - 1 from the north pole, numbered ring by ring and eastwards in phi.
+ * With z = cos(theta) and t = phi / (pi/2) in [0, 4):
+ *  |z| <= 2/3 (equatorial belt): pixel edges are the lines where
+ *      A = nside (t - 3z/4 + 1/2) and B = nside (t + 3z/4 + 1/2) are integers; with
+ *      jp = floor(A), jm = floor(B) the ring is i = 2 nside - (jm - jp) and the pixel in the
+ *      ring j = (jp + jm + 1 - nside - s)/2 mod 4 nside, s = (i - nside + 1) mod 2 (rings with
+ *      s = 0 have a pixel centred on phi = 0, the others are offset by half a pixel);
+ *      index = 2 nside (nside - 1) + 4 nside (i - nside) + j.
+ *  |z| > 2/3 (polar caps): with the equal-area radius sigma = nside sqrt(3 (1 - |z|)) and
+ *      tp = t - floor(t), the ring counted from the pole is i = floor(tp sigma) +
+ *      floor((1 - tp) sigma) + 1 (at most nside), its 4 i pixels split phi evenly:
+ *      j = floor(t i); index = 2 i (i - 1) + j (north) or 12 nside^2 - 2 i (i + 1) + j (south).
+ * Returns -1 for a zero or non-finite direction. */
+int64_t orc_healpix_ring(int32_t nside, double x, double y, double z)
+{
+    double r = sqrt(x * x + y * y + z * z);
+    if (!(r > 0.0) || !isfinite(r) || nside < 1) return -1;
+    double zz = z / r;
+    double phi = orc_atan2(y, x);
+    if (phi < 0.0) phi = phi + 2.0 * PI_D;
+    double t = phi / HALF_PI_D;
+    if (t >= 4.0) t = t - 4.0;
+    int64_t ns = nside;
+    double dn = (double)nside;
+    double az = fabs(zz);
+    if (az <= 2.0 / 3.0) {
+        double sg = 0.75 * zz;
+        int64_t jp = (int64_t)floor(dn * (t - sg + 0.5));
+        int64_t jm = (int64_t)floor(dn * (t + sg + 0.5));
+        int64_t i = 2 * ns - (jm - jp);
+        if (i < ns) i = ns;
+        if (i > 3 * ns) i = 3 * ns;
+        int64_t s = (i - ns + 1) & 1;
+        int64_t j = (jp + jm + 1 - ns - s) / 2;
+        int64_t m = 4 * ns;
+        j = ((j % m) + m) % m;
+        return 2 * ns * (ns - 1) + m * (i - ns) + j;
+    }
+    double tp = t - floor(t);
+    double sigma = dn * sqrt(3.0 * (1.0 - az));
+    int64_t i = (int64_t)floor(tp * sigma) + (int64_t)floor((1.0 - tp) * sigma) + 1;
+    if (i > ns) i = ns;
+    int64_t j = (int64_t)floor(t * (double)i);
+    if (j >= 4 * i) j = 4 * i - 1;
+    if (zz > 0.0) return 2 * i * (i - 1) + j;
+    return 12 * ns * ns - 2 * i * (i + 1) + j;
+}
+
+/* Arrival map: every finished particle (status DONE) with E > e_min adds one count to the
+ * pixel of its arrival direction, the direction it arrives from: -u. */
+int orc_arrival_map(const orc_state* st, int32_t nside, double e_min_ev, uint64_t* map)
+{
+    if (!st || !map || nside < 1) return ORC_ERR_INVALID_ARG;
+    for (int64_t i = 0; i < st->n; ++i) {
+        if (st->status[i] != ORC_DONE || !(st->E[i] > e_min_ev)) continue;
+        int64_t pix = orc_healpix_ring(nside, -st->ux[i], -st->uy[i], -st->uz[i]);
+        if (pix >= 0) map[pix] += 1;
+    }
+    return ORC_OK;
+}

@@ -92,6 +92,19 @@ typedef struct {
     int64_t n;
 } orc_state;
 
+/* Source spectrum of Sec. 4, Eq. 1 (species i: mass A_i, charge Z_i, abundance x_i). */
+#define ORC_MAX_SPECIES 8
+#define ORC_SOURCE_DRAWS 64     /* draws per particle before a sample counts as failed */
+typedef struct {
+    int32_t n_species;
+    int32_t A[ORC_MAX_SPECIES], Z[ORC_MAX_SPECIES];
+    int32_t pad_;
+    double x[ORC_MAX_SPECIES];
+    double alpha;        /* spectral index */
+    double rcut_v;       /* cutoff rigidity, V (E cutoff Z_i * rcut_v in eV) */
+    double e_min_ev, e_max_ev;
+} orc_spectrum;
+
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 double orc_uniform(uint64_t seed, uint64_t uid, uint32_t k, uint32_t tag);
 double orc_exp(double x);
@@ -117,7 +130,16 @@ void orc_adjoint(const orc_field* f, double kappa, const double y0[6], const dou
                  int32_t n_steps, const double lamT[6], double* grid_bar, double y0_bar[6],
                  double* kappa_bar);
 
+/* Sources (Sec. 4, Eq. 1) and arrival binning (HEALPix RING scheme). */
+int orc_spectrum_check(const orc_spectrum* sp);
+int64_t orc_source_sample(const orc_spectrum* sp, uint64_t seed, uint64_t uid_base, int64_t n,
+                          int32_t* A, int32_t* Z, double* E, double* ux, double* uy, double* uz);
+double orc_atan2(double y, double x);
+int64_t orc_healpix_ring(int32_t nside, double x, double y, double z);
+int orc_arrival_map(const orc_state* st, int32_t nside, double e_min_ev, uint64_t* map);
+
 #ifdef __cplusplus
 }
 #endif
+
 #endif
