@@ -150,8 +150,12 @@ def build_inputs(w: I.Workload, n: int, rank: int):
         return [GridInput(grid=g) for g in grids], tables, parts
     grid = I.kolmogorov_grid(w.grid_n, w.spacing_m, w.lmin_cells, w.lmax_cells, w.brms_t,
                              w.grid_seed).astype(np.float32)
-    parts = I.make_particles(n, w.particle_seed + 7919 * rank, w.species, w.energy,
-                             uid_offset=rank * n)
+    if w.spectrum is not None:     # species, energies, directions are drawn on the device
+        parts = I.make_particles(n, w.particle_seed + 7919 * rank, (("H", 1.0),), ("fixed", 1e19),
+                                 uid_offset=rank * n)
+    else:
+        parts = I.make_particles(n, w.particle_seed + 7919 * rank, w.species, w.energy,
+                                 uid_offset=rank * n)
     if w.mod_n:             # modulated field; sources follow the matter density
         rho = I.density_field(w.mod_n, w.mod_lmin_cells, w.mod_lmax_cells, w.mod_sigma_ln, w.mod_seed)
         mod = I.modulation_from_density(rho)
@@ -168,6 +172,27 @@ def oracle_sample_index(w: I.Workload, n_total: int, sample: int) -> np.ndarray:
         k = max(1, min(per_grid, sample // w.n_grids))
         return (np.arange(w.n_grids)[:, None] * per_grid + np.arange(k)[None, :]).ravel()
     return np.arange(min(sample, n_total))
+
+
+def oracle_sources(w: I.Workload, parts, lo: int, count: int, seed: int):
+    """For Eq. 1 workloads: primaries lo .. lo+count-1 as the device draws them (the oracle's
+    sampler, same Philox counters), at the batch's positions; else the batch's own."""
+    sub = parts.take(np.arange(lo, lo + count))
+    if w.spectrum is None:
+        return sub
+    import oracle as O
+
+    species, alpha, rcut, emin, emax = w.spectrum
+    A, Z, E, u, _ = O.source_sample(O.spectrum(species, alpha, rcut, emin, emax), seed,
+                                    int(parts.uid[lo]), count)
+    sub.A[:], sub.Z[:], sub.E[:], sub.u[:] = A, Z, E, u
+    return sub
+
+
+def capacity_hint(w: I.Workload, parts) -> int:
+    if w.spectrum is not None:       # every primary may be Fe-56: room for 55 nucleons each
+        return int(len(parts) * max(a for a, _, _ in w.spectrum[0]))
+    return capacity_for(parts)
 
 
 def aggregate(dist, total_ms: float, accepted: float, attempted: float, device):
@@ -242,7 +267,8 @@ def cpu_baseline(w, grids, tables, parts, sample: int, form_desc: str):
     """The oracle, as it stands, on a bounded sample of the same workload."""
     import oracle as O
 
-    sub = parts.take(oracle_sample_index(w, len(parts), sample))
+    idx = oracle_sample_index(w, len(parts), sample)
+    sub = oracle_sources(w, parts, 0, len(idx), w.rng_seed) if w.spectrum is not None else parts.take(idx)
     cap = capacity_for(sub)
     st = O.OracleState(cap)
     ot = O.OracleTables(tables) if tables is not None else None
@@ -327,8 +353,11 @@ def run_reference(args):
     times, steps_acc = [], []
     for it in range(args.warmup + args.steps):
         lo = (it * per_step) % max(1, len(parts) - per_step)
-        sub = parts.take(np.arange(lo, lo + per_step) if w.n_grids == 1 else
-                         np.random.default_rng(it).choice(len(parts), per_step, replace=False))
+        if w.spectrum is not None:
+            sub = oracle_sources(w, parts, lo, per_step, w.rng_seed)
+        else:
+            sub = parts.take(np.arange(lo, lo + per_step) if w.n_grids == 1 else
+                             np.random.default_rng(it).choice(len(parts), per_step, replace=False))
         st = O.OracleState(capacity_for(sub))
         ot = O.OracleTables(tables) if tables is not None else None
         O.inject(st, sub, w.rng_seed, ot)
@@ -374,11 +403,13 @@ def run_own(args):
     n = args.n_particles or w.n_particles
     grids, tables, parts = build_inputs(w, n, rank)
     n = len(parts)
-    cap = capacity_for(parts)
+    cap = capacity_hint(w, parts)
 
     fields = [g.field(crp, w.spacing_m) for g in grids]
     tabs = crp.Tables(tables) if tables is not None else None
-    sim = crp.Simulation(fields, tabs, seed=w.rng_seed, capacity=cap)
+    # device-drawn sources: each rank its own Philox key (uids restart at 0 on every rank)
+    seed = w.rng_seed + (1000003 * rank if w.spectrum is not None else 0)
+    sim = crp.Simulation(fields, tabs, seed=seed, capacity=cap)
     box = I.workload_box(w)
     if box is not None:
         sim.set_boundary(box)
@@ -393,6 +424,20 @@ def run_own(args):
                 u=(d(parts.u[:, 0]), d(parts.u[:, 1]), d(parts.u[:, 2])),
                 E=d(parts.E), A=d(parts.A), Z=d(parts.Z), uid=d(parts.uid), grid_id=d(parts.grid_id))
     form_id = {"fp64": crp.FORM_FP64, "mixed": crp.FORM_MIXED}
+    spec = crp.Spectrum.of(*w.spectrum) if w.spectrum is not None else None
+    amap = (torch.zeros(12 * w.arrival_nside ** 2, dtype=torch.int64, device=dev)
+            if w.arrival_nside else None)
+
+    def add_sources(c):
+        if spec is not None:
+            sim.sample_sources(spec, c["x"], stream=stream)
+        else:
+            sim.inject(**c, stream=stream)
+
+    def bin_arrivals():
+        if amap is not None:
+            amap.zero_()
+            sim.arrival_map(w.arrival_nside, w.arrival_emin_ev, out=amap, stream=stream)
 
     def run_propagate(prm):
         if slice_steps > 0:
@@ -414,10 +459,11 @@ def run_own(args):
         p0 = torch.cuda.Event(enable_timing=True)
         p1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        sim.inject(**cols, stream=stream)
+        add_sources(cols)
         p0.record(stream)
         run_propagate(prm)
         p1.record(stream)
+        bin_arrivals()
         e1.record(stream)
         rc = sim.sync(0.0, raise_on_error=False)
         c = sim.counts()
@@ -485,21 +531,31 @@ def run_own(args):
                      u=(pin(parts.u[:, 0]), pin(parts.u[:, 1]), pin(parts.u[:, 2])),
                      E=pin(parts.E), A=pin(parts.A), Z=pin(parts.Z), uid=pin(parts.uid),
                      grid_id=pin(parts.grid_id))
+        if spec is not None:         # only positions go up; the arrival map comes back
+            hcols = {"x": hcols["x"]}
         h2d = sum(int(t.numel() * t.element_size()) for v in hcols.values()
                   for t in (v if isinstance(v, tuple) else (v,)))
-        out = sim.observe_buffers(cap, pinned=True)
+        out = sim.observe_buffers(cap, pinned=True) if amap is None else None
+        hmap = torch.empty_like(amap, device="cpu").pin_memory() if amap is not None else None
         e2e_times, e2e_steps, d2h = [], 0, 0
         for _ in range(args.steps):          # the device path is already warm
             sim.reset()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            sim.inject(**hcols, stream=stream)
+            add_sources(hcols)
             run_propagate(prm)
-            sim.sync(0.0, raise_on_error=False)
-            rec = sim.observe(out=out)
+            if amap is not None:
+                bin_arrivals()
+                hmap.copy_(amap, non_blocking=True)
+                sim.sync(0.0, raise_on_error=False)
+                torch.cuda.synchronize()
+                d2h = int(hmap.numel() * hmap.element_size())
+            else:
+                sim.sync(0.0, raise_on_error=False)
+                rec = sim.observe(out=out)
+                d2h = sim.observe_bytes(len(rec["uid"]))
             e2e_times.append(time.perf_counter() - t0)
             e2e_steps += sim.counts()["accepted"]
-            d2h = sim.observe_bytes(len(rec["uid"]))
         e2e = {"value": e2e_steps / sum(e2e_times), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
@@ -529,7 +585,8 @@ def run_own(args):
     # the graph loop adds an init kernel per step and a condition kernel per slice.
     slices = main["launches"] / 2
     per_slice = 1 + (1 if order == 1 else 3) + 4 + (1 if slice_steps > 0 else 0)
-    gpu_launches = int(2 * args.steps + slices * per_slice + (args.steps if slice_steps > 0 else 0))
+    per_step = 2 + (1 if spec is not None else 0) + (1 if amap is not None else 0)
+    gpu_launches = int(per_step * args.steps + slices * per_slice + (args.steps if slice_steps > 0 else 0))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
@@ -544,6 +601,11 @@ def run_own(args):
                    "slice_steps": slice_steps,
                    "form": args.form, "dmax_mpc": w.dmax_m / I.MPC, "tol": w.tol,
                    "boundary": "reflective box of the modulation volume" if box is not None else "none",
+                   "sources": ("Eq. 1 drawn on the device: H, He-4, N-14, Fe-56, x = 1, 0.5, 0.3, 0.1, "
+                               "alpha 1.8, R_cut 10^19.8 V, 1e18-1e21 eV, density-weighted positions")
+                   if spec is not None else "given columns",
+                   "arrival_map": (f"HEALPix RING nside {w.arrival_nside}, E > 10^18.7 eV, every step"
+                                   if amap is not None else None),
                    "l2": f"inputs larger than L2 (grids {grid_bytes / 1e6:.0f} MB in device layout, "
                          f"particle state {cap * 170 / 1e9:.2f} GB) and a 256 MB flush before every step",
                    "parallelism": f"dp{ws} (independent particle batches per GPU)"},
@@ -551,6 +613,7 @@ def run_own(args):
         "attempted_steps_per_step": attempted_all / args.steps,
         "reject_frac": 1.0 - accepted_all / max(attempted_all, 1.0),
         "secondaries_per_step": secondaries / args.steps,
+        "arrival_events_per_step": int(amap.sum()) if amap is not None else None,
         "sync_codes": sorted(set(rcs)),
         "roofline": roofline,
         "forms": forms,

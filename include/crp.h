@@ -294,6 +294,48 @@ int crp_adjoint_backward(crp_adjoint* adj, const double* uT_bar, double* grid_ba
 /* Recorded step sizes, [n_steps][n] (host or device). */
 int crp_adjoint_read_steps(crp_adjoint* adj, double* h, int32_t is_device);
 
+/* ---- sources with the Sec. 4 spectrum (Eq. 1) ---------------------------------------------
+ * dN_i/dE ~ x_i A_i^(alpha-1) E^-alpha exp(-E / (Z_i rcut_v)) on [e_min_ev, e_max_ev] for
+ * species i = (A_i, Z_i, x_i), i < n_species <= CRP_MAX_SPECIES (Sec. 4 uses alpha = 1.8,
+ * rcut_v = 10^19.8 V and H, He-4, N-14, Fe-56 with x = 1, 0.5, 0.3, 0.1). */
+#define CRP_MAX_SPECIES 8
+typedef struct {
+    int32_t n_species;
+    int32_t A[CRP_MAX_SPECIES], Z[CRP_MAX_SPECIES];   /* 1 <= Z <= A */
+    int32_t pad_;
+    double x[CRP_MAX_SPECIES];                        /* relative abundances, >= 0, not all 0 */
+    double alpha;                                     /* spectral index */
+    double rcut_v;                                    /* cutoff rigidity, V */
+    double e_min_ev, e_max_ev;                        /* 0 < e_min < e_max */
+} crp_spectrum;
+
+/* Appends n primaries at the given positions (x, y, z: n metres each; grid_id: n values or
+ * NULL for 0; host or device memory per is_device) whose species, energy and direction the
+ * library draws on the device: species i with weight x_i A_i^(alpha-1) and E from E^-alpha
+ * by its inverse CDF, the pair kept with probability exp(-E / (Z_i rcut_v)) and redrawn whole
+ * otherwise (so the kept pairs follow Eq. 1 jointly), the direction isotropic by Marsaglia's
+ * method. Random numbers: Philox4x32-10 keyed by the simulation seed, counter (uid, draw k,
+ * tag) with tag 2 for (species, energy), 3 for the acceptance, 4 for the direction; uids
+ * continue the count of primaries; powers and exponentials by the library's exp/log. A
+ * particle whose CRP_SOURCE_DRAWS draws were all rejected is stopped at injection and
+ * reported by crp_sync as INVALID_ARG. Then as crp_source_inject (s = 0, u0 = u, ...).
+ * Errors: INVALID_ARG (NULL sim, spec or position column, n < 0, capacity exceeded, invalid
+ * spectrum, a species outside the tables); CUDA. */
+#define CRP_SOURCE_DRAWS 64
+int crp_source_sample(crp_sim* sim, const crp_spectrum* spec, const double* x, const double* y,
+                      const double* z, const int32_t* grid_id, int32_t is_device, int64_t n,
+                      void* stream);
+
+/* ---- arrival maps (Sec. 4, Fig. 4) -------------------------------------------------------
+ * HEALPix RING-scheme pixel (Gorski et al. 2005) of each direction u[k] = (x, y, z) (device,
+ * [n][3], not necessarily unit) for 1 <= nside <= 8192; pix: n int64 (device), -1 for a zero
+ * or non-finite direction. phi comes from the library's atan2 (octant reduction, tan(pi/8)
+ * split, half-angle step, Taylor series through c^27), so that maps are reproducible. */
+int crp_healpix_ring(int32_t nside, const double* u, int64_t n, int64_t* pix, void* stream);
+/* Adds to map (device, 12 nside^2 uint64, the caller zeroes it) one count per finished
+ * particle (status DONE) with E > e_min_ev in the pixel of its arrival direction -u. */
+int crp_arrival_map(crp_sim* sim, int32_t nside, double e_min_ev, uint64_t* map, void* stream);
+
 /* ---- propagation that allocates nothing -------------------------------------------------
  * This entry point has no counterpart in the paper; it exists for callers that must not
  * have this library allocate device memory. Some host programs own every byte of GPU

@@ -9,9 +9,12 @@ fallback, and using the binding without the built library raises.
 from __future__ import annotations
 
 from .api import (  # noqa: F401
+    BOUNDARY_NONE,
+    BOUNDARY_REFLECT,
     COLUMNS,
     FORM_FP64,
     FORM_MIXED,
+    MAX_SPECIES,
     STATUS_ACTIVE,
     STATUS_DONE,
     STATUS_NAN,
@@ -19,6 +22,8 @@ from .api import (  # noqa: F401
     CrpError,
     Field,
     Simulation,
+    Spectrum,
     Tables,
+    healpix_ring,
     lib,
 )

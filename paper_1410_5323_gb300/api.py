@@ -45,6 +45,41 @@ class _Particles(C.Structure):
                                           "grid_id")] + [("is_device", C.c_int32), ("pad_", C.c_int32)]
 
 
+MAX_SPECIES = 8
+
+
+class Spectrum(C.Structure):
+    """Source spectrum of paper Sec. 4, Eq. 1 (crp_spectrum)."""
+    _fields_ = [("n_species", C.c_int32), ("A", C.c_int32 * MAX_SPECIES),
+                ("Z", C.c_int32 * MAX_SPECIES), ("pad_", C.c_int32),
+                ("x", C.c_double * MAX_SPECIES), ("alpha", C.c_double), ("rcut_v", C.c_double),
+                ("e_min_ev", C.c_double), ("e_max_ev", C.c_double)]
+
+    @classmethod
+    def of(cls, species, alpha: float, rcut_v: float, e_min_ev: float, e_max_ev: float) -> "Spectrum":
+        """species: [(A, Z, x), ...]."""
+        sp = cls()
+        sp.n_species = len(species)
+        for i, (a, z, x) in enumerate(species):
+            sp.A[i], sp.Z[i], sp.x[i] = int(a), int(z), float(x)
+        sp.alpha, sp.rcut_v = float(alpha), float(rcut_v)
+        sp.e_min_ev, sp.e_max_ev = float(e_min_ev), float(e_max_ev)
+        return sp
+
+
+def healpix_ring(nside: int, u, stream=None):
+    """HEALPix RING pixel of each row of u ([n, 3] torch tensor on the GPU, float64)."""
+    import torch
+
+    u = u.contiguous()
+    if not u.is_cuda or u.dtype != torch.float64:
+        raise TypeError("u must be a float64 CUDA tensor")
+    pix = torch.empty(u.shape[0], dtype=torch.int64, device=u.device)
+    _check(lib().crp_healpix_ring(int(nside), u.data_ptr(), int(u.shape[0]), pix.data_ptr(),
+                                  _stream_ptr(stream)), "crp_healpix_ring")
+    return pix
+
+
 class _Params(C.Structure):
     _fields_ = [("form", C.c_int32), ("block_size", C.c_int32), ("blocks_per_sm", C.c_int32),
                 ("cadence", C.c_int32), ("max_steps", C.c_int64), ("order", C.c_int32),
@@ -85,6 +120,9 @@ def lib() -> C.CDLL:
             "crp_sim_destroy": ([p], C.c_int),
             "crp_sim_reset": ([p], C.c_int),
             "crp_sim_set_boundary": ([p, i32, p, p], C.c_int),
+            "crp_source_sample": ([p, p, p, p, p, p, i32, i64, p], C.c_int),
+            "crp_healpix_ring": ([i32, p, i64, p, p], C.c_int),
+            "crp_arrival_map": ([p, i32, d, p, p], C.c_int),
             "crp_source_inject": ([p, p, i64, p], C.c_int),
             "crp_propagate": ([p, p, d, d, d, d, p], C.c_int),
             "crp_propagate_loop": ([p, p, d, d, d, d, i32, p], C.c_int),
@@ -252,6 +290,39 @@ class Simulation:
         ps = _Particles(*[b[0] for b in bufs], devs.pop(), 0)
         _check(lib().crp_source_inject(self._h, C.byref(ps), n, _stream_ptr(stream)),
                "crp_source_inject")
+
+    def sample_sources(self, spectrum: "Spectrum", x, grid_id=None, stream=None) -> None:
+        """Append len(x) primaries at positions x ([n, 3] or a 3-tuple of columns, numpy or
+        torch) with species, energy and direction drawn on the device from ``spectrum``."""
+        if isinstance(x, (tuple, list)):
+            cols = list(x)
+        elif _is_torch(x):
+            cols = [x[:, 0].contiguous(), x[:, 1].contiguous(), x[:, 2].contiguous()]
+        else:
+            x = np.asarray(x, dtype=np.float64)
+            cols = [np.ascontiguousarray(x[:, c]) for c in range(3)]
+        if grid_id is not None and not _is_torch(grid_id):
+            grid_id = np.asarray(grid_id, dtype=np.int32)
+        bufs = [_buf(c) for c in cols + [grid_id]]
+        devs = {b[1] for b in bufs if b[0] is not None}
+        if len(devs) != 1:
+            raise ValueError("columns must all be host or all be device buffers")
+        n = int(cols[0].shape[0])
+        _check(lib().crp_source_sample(self._h, C.byref(spectrum), bufs[0][0], bufs[1][0], bufs[2][0],
+                                       bufs[3][0], devs.pop(), n, _stream_ptr(stream)),
+               "crp_source_sample")
+
+    def arrival_map(self, nside: int, e_min_ev: float, out=None, stream=None):
+        """Counts of finished particles above e_min_ev per HEALPix RING pixel of -u (paper
+        Sec. 4, Fig. 4), accumulated into ``out`` (a zeroed uint64-sized int64 CUDA tensor of
+        12 nside^2) or a new one."""
+        import torch
+
+        if out is None:
+            out = torch.zeros(12 * nside * nside, dtype=torch.int64, device="cuda")
+        _check(lib().crp_arrival_map(self._h, int(nside), float(e_min_ev), out.data_ptr(),
+                                     _stream_ptr(stream)), "crp_arrival_map")
+        return out
 
     def propagate(self, tolerance: float, min_step_m: float, max_step_m: float,
                   max_distance_m: float, form: int = FORM_FP64, max_steps: int = 0,

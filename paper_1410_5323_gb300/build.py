@@ -28,6 +28,7 @@ SOURCES = [
     ("propagate_fp64.cu", ["--fmad=false"]),
     ("propagate_mixed.cu", []),
     ("adjoint.cu", ["--fmad=false"]),
+    ("sources.cu", ["--fmad=false"]),
 ]
 
 

@@ -792,6 +792,84 @@ int crp_source_inject(crp_sim* s, const crp_particles* p, int64_t n, void* strea
     return CRP_OK;
 }
 
+int crp_source_sample(crp_sim* s, const crp_spectrum* sp, const double* x, const double* y,
+                      const double* z, const int32_t* grid_id, int32_t is_device, int64_t n,
+                      void* stream) {
+    if (!s || !sp) return fail(CRP_ERR_INVALID_ARG, "sim or spectrum is NULL");
+    if (n < 0) return fail(CRP_ERR_INVALID_ARG, "n < 0");
+    if (n == 0) return CRP_OK;
+    if (!x || !y || !z) return fail(CRP_ERR_INVALID_ARG, "NULL position column");
+    if (sp->n_species < 1 || sp->n_species > CRP_MAX_SPECIES)
+        return fail(CRP_ERR_INVALID_ARG, "n_species outside [1, CRP_MAX_SPECIES]");
+    if (!(sp->e_min_ev > 0.0) || !(sp->e_max_ev > sp->e_min_ev) || !std::isfinite(sp->e_max_ev) ||
+        !(sp->rcut_v > 0.0) || !std::isfinite(sp->alpha))
+        return fail(CRP_ERR_INVALID_ARG, "need 0 < e_min < e_max, rcut > 0, finite alpha");
+    double total = 0.0;
+    for (int i = 0; i < sp->n_species; ++i) {
+        if (sp->A[i] < 1 || sp->Z[i] < 1 || sp->Z[i] > sp->A[i] || !(sp->x[i] >= 0.0) || !std::isfinite(sp->x[i]))
+            return fail(CRP_ERR_INVALID_ARG, "species need 1 <= Z <= A and abundance >= 0");
+        total += sp->x[i];
+    }
+    if (!(total > 0.0)) return fail(CRP_ERR_INVALID_ARG, "abundances are all zero");
+    const TablesDev* tab = s->tables ? &s->tables->dev : nullptr;
+    for (int i = 0; i < sp->n_species; ++i)
+        if (tab && (sp->Z[i] > tab->z_max || sp->A[i] - sp->Z[i] > tab->n_max))
+            return fail(CRP_ERR_INVALID_ARG, "species outside the interaction tables");
+    Counters h;
+    int rc = read_counters(s, &h);
+    if (rc) return rc;
+    if ((long long)h.n_used + n > s->capacity)
+        return fail(CRP_ERR_INVALID_ARG, "injection exceeds the simulation capacity");
+    if (h.n_primaries + (unsigned long long)n > (1ull << 32))
+        return fail(CRP_ERR_INVALID_ARG, "uids would exceed 2^32");
+    const int n_fields = (int)s->host_fields.size();
+    if (!is_device && grid_id)
+        for (long long i = 0; i < n; ++i)
+            if (grid_id[i] < 0 || grid_id[i] >= n_fields) return fail(CRP_ERR_INVALID_ARG, "grid_id out of range");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const cudaMemcpyKind kind = is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const long long f = (long long)h.n_used;
+    struct { const void* src; int col; } cp[] = {
+        {x, CRP_COL_X}, {y, CRP_COL_Y}, {z, CRP_COL_Z}, {grid_id, CRP_COL_GRID_ID}};
+    for (auto& c : cp) {
+        if (!c.src) continue;
+        char* dst = (char*)*col_ptr(s->st, c.col) + f * kCols[c.col].size;
+        CRP_CUDA(cudaMemcpyAsync(dst, c.src, (size_t)n * kCols[c.col].size, kind, st));
+    }
+    int e = launch_source_sample(s->st, f, n, h.n_primaries, *sp, s->seed, grid_for(n, 128, 8192), st);
+    if (e) return cuda_fail((cudaError_t)e, "source sampling kernel");
+    const int block = 256;
+    k_inject_init<<<grid_for(n, block, 4096), block, 0, st>>>(
+        s->st, f, n, 1, grid_id ? 1 : 0, h.n_primaries, n_fields, tab ? 1 : 0,
+        tab ? tab->z_max : 0, tab ? tab->n_max : 0, s->seed, s->done_list, s->ctr);
+    CRP_CUDA(cudaGetLastError());
+    k_set_used<<<1, 1, 0, st>>>(s->ctr, h.n_used + n, h.n_primaries + n);
+    CRP_CUDA(cudaGetLastError());
+    s->last = st;
+    return CRP_OK;
+}
+
+int crp_healpix_ring(int32_t nside, const double* u, int64_t n, int64_t* pix, void* stream) {
+    if (nside < 1 || nside > 8192) return fail(CRP_ERR_INVALID_ARG, "nside outside [1, 8192]");
+    if (n < 0) return fail(CRP_ERR_INVALID_ARG, "n < 0");
+    if (n == 0) return CRP_OK;
+    if (!u || !pix) return fail(CRP_ERR_INVALID_ARG, "NULL direction or pixel buffer");
+    int e = launch_healpix(nside, u, n, (long long*)pix, grid_for(n, 256, 8192), stream);
+    if (e) return cuda_fail((cudaError_t)e, "healpix kernel");
+    return CRP_OK;
+}
+
+int crp_arrival_map(crp_sim* s, int32_t nside, double e_min_ev, uint64_t* map, void* stream) {
+    if (!s || !map) return fail(CRP_ERR_INVALID_ARG, "sim or map is NULL");
+    if (nside < 1 || nside > 8192) return fail(CRP_ERR_INVALID_ARG, "nside outside [1, 8192]");
+    if (e_min_ev != e_min_ev) return fail(CRP_ERR_INVALID_ARG, "e_min is NaN");
+    const int grid = (s->sms > 0 ? s->sms : 1) * 4;
+    int e = launch_arrival_map(s->st, s->ctr, nside, e_min_ev, (unsigned long long*)map, grid, stream);
+    if (e) return cuda_fail((cudaError_t)e, "arrival map kernel");
+    s->last = reinterpret_cast<cudaStream_t>(stream);
+    return CRP_OK;
+}
+
 }  // extern "C"
 
 namespace {

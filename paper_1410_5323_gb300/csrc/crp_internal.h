@@ -3,6 +3,8 @@
 #pragma once
 #include <cstdint>
 
+#include "crp.h"
+
 namespace crp {
 
 // Grid layouts in device memory: one 4-wide vector per node, node index
@@ -100,6 +102,13 @@ struct PropArgs {
 };
 
 // Launchers (defined in the kernel translation units).
+// Sources and arrival maps (sources.cu).
+int launch_source_sample(const SimState& S, long long first, long long n, unsigned long long uid_base,
+                         const crp_spectrum& sp, unsigned long long seed, int grid, void* stream);
+int launch_healpix(int nside, const double* u, long long n, long long* pix, int grid, void* stream);
+int launch_arrival_map(const SimState& S, const Counters* C, int nside, double e_min,
+                       unsigned long long* map, int grid, void* stream);
+
 // `mod`: 1 for simulations whose fields carry a modulation grid.
 int launch_propagate_fp64(const PropArgs& a, int layout, int mod, int grid, int block, void* stream);
 int propagate_fp64_occupancy(int layout, int mod, int block, int* blocks_per_sm);

@@ -411,6 +411,14 @@ class Workload:
     mod_sigma_ln: float = 0.0
     mod_seed: int = 2
     reflect: bool = False      # reflective box = the modulation grid's volume
+    # sources drawn on the device from Eq. 1: ((A, Z, x), ...), alpha, R_cut (V), E range (eV)
+    spectrum: tuple | None = None
+    arrival_nside: int = 0     # arrival map resolution (0: none) and its energy threshold
+    arrival_emin_ev: float = 0.0
+
+
+EQ1_SPECIES = ((1, 1, 1.0), (4, 2, 0.5), (14, 7, 0.3), (56, 26, 0.1))   # Sec. 4: H, He, N, Fe
+EQ1_SPECTRUM = (EQ1_SPECIES, 1.8, 10 ** 19.8, 1e18, 1e21)
 
 
 def workload_box(w: Workload):
@@ -453,6 +461,18 @@ def workload(name: str) -> Workload:
                         energy=("power", 1e18, 10 ** 20.5, 2.0), interactions=True,
                         mod_n=440, mod_spacing_m=300.0 * KPC, mod_lmin_cells=2.0,
                         mod_lmax_cells=110.0, mod_sigma_ln=1.0, reflect=True)
+    if name == "sec4_eq1_440cube_x_256cube_1M_nuclei":
+        # the full Sec. 4 scenario: modulated field and reflective box as above, sources at
+        # density-weighted positions drawn from Eq. 1 on the device, arrival map (HEALPix
+        # nside 64) of events above 10^18.7 eV
+        w = workload("modulated_440cube_300kpc_x_256cube_50kpc_1M_nuclei")
+        w.name = name
+        w.spectrum = EQ1_SPECTRUM
+        w.species = tuple((str(a), x) for a, _, x in EQ1_SPECIES)   # informational
+        w.energy = ("eq1",)
+        w.arrival_nside = 64
+        w.arrival_emin_ev = 10 ** 18.7
+        return w
     if name == "adjoint_128cube_4k_protons":
         return Workload(name, 4096, 128, lmax_cells=32.0, brms_t=1.0 * NANOGAUSS,
                         dmax_m=1e6 * MPC, species=(("H", 1.0),), energy=("fixed", 10 ** 19.5),

@@ -63,6 +63,19 @@ def test_null_and_range_arguments_rejected_before_device_work(L):
     assert L.crp_sim_set_boundary(fake, 7, org, sz) == -1                    # unknown kind
     assert L.crp_sim_set_boundary(fake, 1, org, sz) == -1                    # a size of 0
     assert L.crp_sim_set_boundary(fake, 1, None, sz) == -1
+    import paper_1410_5323_gb300 as crp
+    sp = crp.Spectrum.of([(4, 2, 1.0)], 1.8, 1e19, 1e18, 1e21)
+    xs = np.zeros(4)
+    assert L.crp_source_sample(None, C.byref(sp), xs.ctypes.data, xs.ctypes.data, xs.ctypes.data, None, 0, 4, None) == -1
+    bad = crp.Spectrum.of([(4, 5, 1.0)], 1.8, 1e19, 1e18, 1e21)       # Z > A
+    assert L.crp_source_sample(fake, C.byref(bad), xs.ctypes.data, xs.ctypes.data, xs.ctypes.data, None, 0, 4, None) == -1
+    bad = crp.Spectrum.of([(4, 2, 1.0)], 1.8, 1e19, 1e21, 1e18)       # e_min > e_max
+    assert L.crp_source_sample(fake, C.byref(bad), xs.ctypes.data, xs.ctypes.data, xs.ctypes.data, None, 0, 4, None) == -1
+    assert L.crp_source_sample(fake, C.byref(sp), None, xs.ctypes.data, xs.ctypes.data, None, 0, 4, None) == -1
+    assert L.crp_healpix_ring(0, xs.ctypes.data, 1, xs.ctypes.data, None) == -1       # nside 0
+    assert L.crp_healpix_ring(8, None, 1, xs.ctypes.data, None) == -1
+    assert L.crp_arrival_map(fake, 9000, 1e18, xs.ctypes.data, None) == -1             # nside too large
+    assert L.crp_arrival_map(None, 8, 1e18, xs.ctypes.data, None) == -1
     assert L.crp_sim_create(None, 0, None, 1, 10, C.byref(h)) == -1
     assert L.crp_tables_create(1, 1, 1, 6.0, 25.0, None, None, None, None, C.byref(h)) == -1
     assert L.crp_propagate(None, None, 1e-4, 1.0, 2.0, 3.0, None) == -1
