@@ -381,3 +381,41 @@ def arrival_map(state: OracleState, nside: int, e_min_ev: float) -> np.ndarray:
     if rc != OK:
         raise ValueError(f"orc_arrival_map failed: {rc}")
     return m
+
+
+# ---- lenses (Sec. 3.3) ---------------------------------------------------------------------
+def _lens_sigs():
+    L = lib()
+    if not getattr(L, "_lens_sigs", False):
+        p, d, i32 = C.c_void_p, C.c_double, C.c_int32
+        L.orc_lens_apply.argtypes = [i32, i32, p, p, p, p, i32, p]
+        L.orc_lens_apply.restype = C.c_int
+        L.orc_lens_bin.argtypes = [p, i32, i32, p, d, p]
+        L.orc_lens_bin.restype = C.c_int
+        L._lens_sigs = True
+    return L
+
+
+def lens_apply(n_pix: int, row_ptr, col, val, x) -> np.ndarray:
+    """y [n_pix, n_maps] = sum_m M_m x[m]; row_ptr [n_mat, n_pix + 1] (global offsets into col
+    and val), x [n_mat, n_pix, n_maps] float64."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    c = np.ascontiguousarray(col, dtype=np.int32)
+    v = np.ascontiguousarray(val, dtype=np.float32)
+    xx = np.ascontiguousarray(x, dtype=np.float64)
+    n_mat, _, n_maps = xx.shape
+    y = np.zeros((n_pix, n_maps))
+    rc = _lens_sigs().orc_lens_apply(n_pix, n_mat, _ptr(rp), _ptr(c) if c.size else None,
+                                     _ptr(v) if v.size else None, _ptr(xx), n_maps, _ptr(y))
+    if rc != OK:
+        raise ValueError(f"orc_lens_apply failed: {rc}")
+    return y
+
+
+def lens_bin(state: OracleState, nside: int, edges, e_min_ev: float) -> np.ndarray:
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    x = np.zeros((len(e) - 1, 12 * nside * nside))
+    rc = _lens_sigs().orc_lens_bin(C.byref(state.c), nside, len(e) - 1, _ptr(e), e_min_ev, _ptr(x))
+    if rc != OK:
+        raise ValueError(f"orc_lens_bin failed: {rc}")
+    return x

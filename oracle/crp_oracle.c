@@ -1041,3 +1041,51 @@ int orc_arrival_map(const orc_state* st, int32_t nside, double e_min_ev, uint64_
     }
     return ORC_OK;
 }
+
+/* ---- lenses (Sec. 3.3: per-rigidity sparse matrices that transform directions at the
+ * galactic border into arrival directions at Earth, applied to whole distributions by
+ * matrix-vector products) --------------------------------------------------------------
+ * n_mat matrices of n_pix x n_pix in CSR form over shared arrays: matrix m, row p holds the
+ * entries k in [row_ptr[m (n_pix + 1) + p], row_ptr[m (n_pix + 1) + p + 1]) with column
+ * col[k] and value val[k] (single precision, as the lenses are stored). The observed maps are
+ * y[p][b] = sum over m, then over k of row p of matrix m, of val[k] x[m][col[k]][b], for the
+ * n_maps maps b of every rigidity bin m, summed in double precision. */
+int orc_lens_apply(int32_t n_pix, int32_t n_mat, const int64_t* row_ptr, const int32_t* col,
+                   const float* val, const double* x, int32_t n_maps, double* y)
+{
+    if (n_pix < 1 || n_mat < 1 || n_maps < 1 || !row_ptr || !x || !y) return ORC_ERR_INVALID_ARG;
+    for (int64_t p = 0; p < n_pix; ++p) {
+        for (int32_t b = 0; b < n_maps; ++b) {
+            double acc = 0.0;
+            for (int32_t m = 0; m < n_mat; ++m) {
+                const int64_t* rp = row_ptr + (int64_t)m * (n_pix + 1);
+                const double* xm = x + (int64_t)m * n_pix * n_maps;
+                for (int64_t k = rp[p]; k < rp[p + 1]; ++k)
+                    acc = acc + (double)val[k] * xm[(int64_t)col[k] * n_maps + b];
+            }
+            y[p * n_maps + b] = acc;
+        }
+    }
+    return ORC_OK;
+}
+
+/* Rigidity-binned arrival maps at the galactic border, the input of a lens: every finished
+ * charged particle (status DONE, Z > 0) with E > e_min and rigidity R = E/Z (V) in
+ * [edges[m], edges[m+1]) adds one count to x[m][pixel of -u] (HEALPix RING, nside). */
+int orc_lens_bin(const orc_state* st, int32_t nside, int32_t n_mat, const double* edges,
+                 double e_min_ev, double* x)
+{
+    if (!st || !edges || !x || nside < 1 || n_mat < 1) return ORC_ERR_INVALID_ARG;
+    int64_t n_pix = 12 * (int64_t)nside * nside;
+    for (int64_t i = 0; i < st->n; ++i) {
+        if (st->status[i] != ORC_DONE || st->Z[i] <= 0 || !(st->E[i] > e_min_ev)) continue;
+        double R = st->E[i] / (double)st->Z[i];
+        int32_t m = -1;
+        for (int32_t q = 0; q < n_mat; ++q)
+            if (edges[q] <= R && R < edges[q + 1]) { m = q; break; }
+        if (m < 0) continue;
+        int64_t pix = orc_healpix_ring(nside, -st->ux[i], -st->uy[i], -st->uz[i]);
+        if (pix >= 0) x[(int64_t)m * n_pix + pix] += 1.0;
+    }
+    return ORC_OK;
+}

@@ -138,6 +138,12 @@ double orc_atan2(double y, double x);
 int64_t orc_healpix_ring(int32_t nside, double x, double y, double z);
 int orc_arrival_map(const orc_state* st, int32_t nside, double e_min_ev, uint64_t* map);
 
+/* Lenses (Sec. 3.3): per-rigidity sparse matrices applied to arrival distributions. */
+int orc_lens_apply(int32_t n_pix, int32_t n_mat, const int64_t* row_ptr, const int32_t* col,
+                   const float* val, const double* x, int32_t n_maps, double* y);
+int orc_lens_bin(const orc_state* st, int32_t nside, int32_t n_mat, const double* edges,
+                 double e_min_ev, double* x);
+
 #ifdef __cplusplus
 }
 #endif

@@ -502,3 +502,80 @@ def batched_particles(w: Workload, n_per_grid: int, n_grids: int | None = None, 
     n = n_per_grid * n_grids
     gid = np.repeat(np.arange(n_grids, dtype=np.int32), n_per_grid)
     return make_particles(n, seed, w.species, w.energy, grid_ids=gid)
+
+
+# --------------------------------------------------------------------------------------
+# Synthetic lenses (Sec. 3.3: per-rigidity transfer matrices over HEALPix pixels)
+# --------------------------------------------------------------------------------------
+def healpix_centres(nside: int) -> np.ndarray:
+    """Unit vectors [12 nside^2, 3] of the HEALPix RING pixel centres (Gorski et al. 2005):
+    cap rings i < nside at z = 1 - i^2/(3 nside^2), phi = pi/(2i) (j + 1/2); belt rings at
+    z = 4/3 - 2i/(3 nside), phi = pi/(2 nside) (j + s/2), s = (i - nside + 1) mod 2."""
+    zs, ph = [], []
+    for i in range(1, nside):
+        j = np.arange(4 * i)
+        zs.append(np.full(4 * i, 1.0 - i * i / (3.0 * nside * nside)))
+        ph.append(math.pi / (2 * i) * (j + 0.5))
+    for i in range(nside, 3 * nside + 1):
+        j = np.arange(4 * nside)
+        zs.append(np.full(4 * nside, 4.0 / 3.0 - 2.0 * i / (3.0 * nside)))
+        ph.append(math.pi / (2 * nside) * (j + ((i - nside + 1) % 2) / 2.0))
+    for i in range(nside - 1, 0, -1):
+        j = np.arange(4 * i)
+        zs.append(np.full(4 * i, -(1.0 - i * i / (3.0 * nside * nside))))
+        ph.append(math.pi / (2 * i) * (j + 0.5))
+    z = np.concatenate(zs)
+    phi = np.concatenate(ph)
+    s = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    return np.stack([s * np.cos(phi), s * np.sin(phi), z], axis=1)
+
+
+def lens_edges(n_mat: int, r_min_v: float = 10 ** 18.5, r_max_v: float = 10 ** 21.0) -> np.ndarray:
+    """Rigidity bin edges (V), log-spaced."""
+    return np.logspace(math.log10(r_min_v), math.log10(r_max_v), n_mat + 1)
+
+
+def synthetic_lens(nside: int, edges, seed: int = 1, k: int = 32):
+    """A synthetic lens standing in for galactic-field lenses built by backtracking: for each
+    rigidity bin (centre R) and border pixel s, the arrival directions are spread around the
+    border direction rotated by delta(R) = 30 deg (10^19 V / R) (capped at 90 deg) about a
+    fixed random axis, with a Gaussian profile of width sigma(R) = max(0.5 deg,
+    3 deg (10^19 V / R)); the k pixels nearest to that centre carry the column, weights
+    normalised to a transmission 1 - 0.3 exp(-R / 10^19 V). Returns (row_ptr [n_mat, n_pix+1]
+    int64 with offsets into col/val, col int32, val float32) in CSR form, rows = arrival pixels."""
+    from scipy.spatial import cKDTree
+
+    rng = np.random.Generator(np.random.PCG64(seed))
+    c = healpix_centres(nside)
+    n_pix = len(c)
+    tree = cKDTree(c)
+    axis = rng.standard_normal(3)
+    axis /= np.linalg.norm(axis)
+    edges = np.asarray(edges, dtype=np.float64)
+    row_ptr = np.zeros((len(edges) - 1, n_pix + 1), dtype=np.int64)
+    cols, vals = [], []
+    offset = 0
+    for m in range(len(edges) - 1):
+        R = math.sqrt(edges[m] * edges[m + 1])
+        delta = math.radians(min(90.0, 30.0 * 1e19 / R))
+        sigma = math.radians(max(0.5, 3.0 * 1e19 / R))
+        # Rodrigues rotation of every centre about `axis` by delta
+        cd, sd = math.cos(delta), math.sin(delta)
+        rot = c * cd + np.cross(axis, c) * sd + np.outer(c @ axis, axis) * (1 - cd)
+        d, idx = tree.query(rot, k=k)                  # chord distances, [n_pix, k]
+        ang = 2.0 * np.arcsin(np.minimum(1.0, d / 2.0))
+        w = np.exp(-0.5 * (ang / sigma) ** 2)
+        w *= (1.0 - 0.3 * math.exp(-R / 1e19)) / w.sum(axis=1, keepdims=True)
+        # CSR with rows = arrival pixel (idx), columns = border pixel s
+        rows = idx.ravel()
+        colsm = np.repeat(np.arange(n_pix, dtype=np.int64), k)
+        order = np.lexsort((colsm, rows))
+        rows, colsm, wv = rows[order], colsm[order], w.ravel()[order]
+        counts = np.bincount(rows, minlength=n_pix)
+        row_ptr[m, 1:] = offset + np.cumsum(counts)
+        row_ptr[m, 0] = offset
+        cols.append(colsm.astype(np.int32))
+        vals.append(wv.astype(np.float32))
+        offset += len(rows)
+    return row_ptr, np.concatenate(cols), np.concatenate(vals)
+
