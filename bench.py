@@ -50,6 +50,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2.070e9 * 2 / 1e12   # FFMA lanes x 2
 MIXED_FP64_OPS_PER_ATTEMPT = 14
 MIXED_FP64_OPS_PER_ACCEPTED = 5
 MIXED_FP32_FLOP_PER_ATTEMPT = 612
+# DRAM bytes (read + write) of one lens launch by ncu, keyed by the number of maps (None until
+# measured on the current kernels).
+LENS_DRAM_BYTES: dict = {}
 # Modulated fields add one scalar trilinear lookup per field evaluation: FP64 form 6 x
 # (axes 12, weights 12, 8 products, 7 sums, 3 products m*B) = 252 per attempt; mixed form
 # 6 x 38 FP32 flops per attempt and, per accepted step, the step-start modulation cell in
@@ -85,6 +88,7 @@ def parse():
     ap.add_argument("--block-size", type=int, default=0)
     ap.add_argument("--cadence", type=int, default=0)
     ap.add_argument("--order", type=int, default=0, help="work-list order (CRP_ORDER_*); 0: default")
+    ap.add_argument("--n-maps", type=int, default=1, help="lens workload: maps per rigidity bin")
     ap.add_argument("--slice-steps", type=int, default=-1,
                     help="> 0: graph loop of slices of this many steps; 0: one call; -1: workload default")
     return ap.parse_args()
@@ -682,10 +686,113 @@ def run_adjoint(args):
     return 0
 
 
+def run_lens(args):
+    """Lens workload (Sec. 3.3): a synthetic nside-64 lens of 24 rigidity bins (32 entries per
+    column) applied to rigidity-binned arrival maps. value = stored entries applied per second
+    (entries x maps / device time), one fused launch over all bins per step; roofline against
+    HBM with the algorithmic bytes of a launch."""
+    import torch
+
+    import paper_1410_5323_gb300 as crp
+
+    ws, rank, _ = dist_env()
+    nside, n_mat, k = 64, 24, 32
+    n_pix = 12 * nside * nside
+    n_maps = args.n_maps
+    rp, col, val = I.synthetic_lens(nside, I.lens_edges(n_mat), seed=1, k=k)
+    nnz = int(col.size)
+    lens = crp.Lens(n_pix, rp, col, val)
+    dev = torch.device("cuda")
+    xh = np.random.default_rng(1 + rank).poisson(3.0, (n_mat, n_pix, n_maps)).astype(np.float64)
+    x = torch.from_numpy(xh if n_maps > 1 else xh[:, :, 0]).to(dev).contiguous()
+    y = torch.empty((n_pix, n_maps) if n_maps > 1 else (n_pix,), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        flush.zero_()
+        lens.apply(x, out=y, stream=stream)
+    clocks = ClockSampler(0 if ws == 1 else int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.synchronize()
+    clocks.start()
+    ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lens.apply(x, out=y, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    clk = clocks.stop()
+    t = sum(ms) * 1e-3
+    value = nnz * n_maps * args.steps / t
+    algo = nnz * 8 + n_mat * (n_pix + 1) * 8 + n_mat * n_pix * n_maps * 8 + n_pix * n_maps * 8
+    ach = algo * args.steps / t / 1e9
+    peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    # the launch is bound by the slower of streaming the lens (HBM) and one FP64 FMA per entry
+    # and map (GB300's FP64 pipe: 2 lanes/clk/SM); the bound reported is the one that binds
+    t_hbm = algo / (peak * 1e9)
+    t_fp64 = nnz * n_maps / (FP64_OPS_PEAK_T * 1e12)
+    hbm = {"achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "algorithmic_bytes": algo,
+           "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    kern = "k_lens_apply_vec (one map) / k_lens_apply_maps (several), one launch per step"
+    if t_fp64 >= t_hbm:
+        fl = 2.0 * nnz * n_maps * args.steps / t / 1e12
+        roof = {"bound": "alu", "achieved": fl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": fl / FP64_PEAK_TFLOPS, "traffic": LENS_DRAM_BYTES.get(n_maps), "kernel": kern,
+                "flop_per_entry_and_map": 2,
+                "peak_source": "derived: 152 SM x 2 FP64 lanes/clk x 2070 MHz, FMA=2 (of derived)", "hbm": hbm}
+    else:
+        roof = dict(bound="hbm", traffic=LENS_DRAM_BYTES.get(n_maps), kernel=kern, **hbm)
+    # end to end through the binding: maps up from pinned host memory, observed maps back
+    xp = torch.from_numpy(xh if n_maps > 1 else np.ascontiguousarray(xh[:, :, 0])).pin_memory()
+    yp = torch.empty(tuple(y.shape), dtype=torch.float64).pin_memory()
+    xd = torch.empty_like(x)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        xd.copy_(xp, non_blocking=True)
+        lens.apply(xd, out=y, stream=stream)
+        yp.copy_(y, non_blocking=True)
+        torch.cuda.synchronize()
+    te = time.perf_counter() - t0
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle as O
+
+        t1 = time.perf_counter()
+        O.lens_apply(n_pix, rp, col, val, xh[:, :, :1])
+        dt = time.perf_counter() - t1
+        cpu = {"value": nnz / dt, "unit": "entries/s", "cores": 1, "kind": "oracle",
+               "sample": f"the whole lens ({nnz} entries), one map, in {dt:.2f} s (FP64 oracle, one thread)"}
+    line = {
+        "metric": "lens entries applied/s (stored matrix entries x maps / device time, Sec. 3.3 lens)",
+        "value": value, "unit": "entries/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": sum(ms) / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 values, f64 products and sums", "data": "synthetic",
+        "config": {"workload": "lens_nside64_24bins", "n_pix": n_pix, "rigidity_bins": n_mat,
+                   "entries": nnz, "entries_per_column": k, "maps": n_maps,
+                   "lens_bytes": int(nnz * 8 + rp.nbytes),
+                   "l2": "lens (302 MB) larger than L2 and a 256 MB flush before every step",
+                   "parallelism": f"dp{ws} (independent lenses per GPU)"},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": nnz * n_maps * args.steps / te, "unit": "entries/s",
+                "h2d_bytes_per_step": int(xp.numel() * 8), "d2h_bytes_per_step": int(yp.numel() * 8)},
+        "gpu_launches": args.steps,
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.workload.startswith("adjoint"):
         return run_adjoint(args)
+    if args.workload.startswith("lens"):
+        return run_lens(args)
     w = workload_for(args)
     if args.form is None:
         both = w.name.startswith("fp64") or w.mod_n > 0

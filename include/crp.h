@@ -336,6 +336,36 @@ int crp_healpix_ring(int32_t nside, const double* u, int64_t n, int64_t* pix, vo
  * particle (status DONE) with E > e_min_ev in the pixel of its arrival direction -u. */
 int crp_arrival_map(crp_sim* sim, int32_t nside, double e_min_ev, uint64_t* map, void* stream);
 
+/* ---- lenses (Sec. 3.3) ----------------------------------------------------------------------
+ * A lens is a set of n_mat sparse matrices, one per rigidity bin, that map cosmic-ray
+ * directions at the galactic border (columns) to arrival directions at Earth (rows), both
+ * binned into n_pix pixels (12 nside^2 for HEALPix RING maps). CSR over shared arrays:
+ * matrix m, row p holds entries k in [row_ptr[m (n_pix + 1) + p], row_ptr[m (n_pix + 1) + p + 1])
+ * with column col[k] in [0, n_pix) and value val[k] (single precision, as lenses are
+ * stored). The matrices are stored one after the other: row_ptr starts at 0, is
+ * nondecreasing inside each matrix, and each matrix starts where the previous one ends;
+ * nnz = the last offset. edges: n_mat + 1 strictly increasing positive rigidities in V, the
+ * bin limits used by crp_lens_bin (NULL: no binning). All host pointers, copied to the device.
+ * Errors: INVALID_ARG (sizes < 1, NULL arrays, offsets or columns out of range, bad edges);
+ * OOM; CUDA. */
+typedef struct crp_lens crp_lens;
+int crp_lens_create(int32_t n_pix, int32_t n_mat, const int64_t* row_ptr, const int32_t* col,
+                    const float* val, const double* edges, crp_lens** out);
+int crp_lens_destroy(crp_lens* lens);
+/* Observed maps through the lens: y[p][b] = sum over m of (M_m x_m)[p][b] in FP64, each
+ * entry added with one rounding (fused multiply-add), for n_maps maps at once. x: device,
+ * [n_mat][n_pix][n_maps] FP64 (map b of rigidity bin m at the galactic border); y: device,
+ * [n_pix][n_maps] FP64, overwritten. For several maps each row sums its entries in stored
+ * order (matrix 0's row first); for one map the lanes that share a row add partial sums in an
+ * unspecified order. */
+int crp_lens_apply(const crp_lens* lens, const double* x, double* y, int32_t n_maps, void* stream);
+/* The lens input from a simulation: adds to x (device, [n_mat][12 nside^2] FP64; the caller
+ * zeroes it; needs n_pix = 12 nside^2) one count per finished particle with Z > 0 and
+ * E > e_min_ev, in rigidity bin m (edges[m] <= E/Z < edges[m+1]; outside all bins: none) and
+ * the HEALPix RING pixel of -u. */
+int crp_lens_bin(const crp_lens* lens, crp_sim* sim, int32_t nside, double e_min_ev, double* x,
+                 void* stream);
+
 /* ---- propagation that allocates nothing -------------------------------------------------
  * This entry point has no counterpart in the paper; it exists for callers that must not
  * have this library allocate device memory. Some host programs own every byte of GPU

@@ -1049,7 +1049,8 @@ int orc_arrival_map(const orc_state* st, int32_t nside, double e_min_ev, uint64_
  * entries k in [row_ptr[m (n_pix + 1) + p], row_ptr[m (n_pix + 1) + p + 1]) with column
  * col[k] and value val[k] (single precision, as the lenses are stored). The observed maps are
  * y[p][b] = sum over m, then over k of row p of matrix m, of val[k] x[m][col[k]][b], for the
- * n_maps maps b of every rigidity bin m, summed in double precision. */
+ * n_maps maps b of every rigidity bin m, summed in double precision with one rounding per
+ * entry (acc = fma(val, x, acc)). */
 int orc_lens_apply(int32_t n_pix, int32_t n_mat, const int64_t* row_ptr, const int32_t* col,
                    const float* val, const double* x, int32_t n_maps, double* y)
 {
@@ -1061,7 +1062,7 @@ int orc_lens_apply(int32_t n_pix, int32_t n_mat, const int64_t* row_ptr, const i
                 const int64_t* rp = row_ptr + (int64_t)m * (n_pix + 1);
                 const double* xm = x + (int64_t)m * n_pix * n_maps;
                 for (int64_t k = rp[p]; k < rp[p + 1]; ++k)
-                    acc = acc + (double)val[k] * xm[(int64_t)col[k] * n_maps + b];
+                    acc = fma((double)val[k], xm[(int64_t)col[k] * n_maps + b], acc);
             }
             y[p * n_maps + b] = acc;
         }

@@ -21,6 +21,7 @@ from .api import (  # noqa: F401
     STATUS_RANGE,
     CrpError,
     Field,
+    Lens,
     Simulation,
     Spectrum,
     Tables,

@@ -80,6 +80,58 @@ def healpix_ring(nside: int, u, stream=None):
     return pix
 
 
+class Lens:
+    """Per-rigidity sparse lens matrices (paper Sec. 3.3), CSR over shared arrays:
+    row_ptr [n_mat, n_pix + 1] int64 (offsets into col/val, matrices one after another),
+    col int32, val float32; edges: n_mat + 1 rigidities (V) of the bins, or None."""
+
+    def __init__(self, n_pix: int, row_ptr, col, val, edges=None):
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        c = np.ascontiguousarray(col, dtype=np.int32)
+        v = np.ascontiguousarray(val, dtype=np.float32)
+        e = None if edges is None else np.ascontiguousarray(edges, dtype=np.float64)
+        self.n_mat = int(rp.shape[0])
+        self.n_pix = int(n_pix)
+        self.nnz = int(c.size)
+        h = C.c_void_p()
+        _check(lib().crp_lens_create(self.n_pix, self.n_mat, rp.ctypes.data,
+                                     c.ctypes.data if c.size else None, v.ctypes.data if v.size else None,
+                                     None if e is None else e.ctypes.data, C.byref(h)), "crp_lens_create")
+        self._h = h
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.crp_lens_destroy(self._h)
+            self._h = None
+
+    def apply(self, x, out=None, stream=None):
+        """x: float64 CUDA tensor [n_mat, n_pix] or [n_mat, n_pix, n_maps]; returns
+        y = sum_m M_m x_m as [n_pix] or [n_pix, n_maps]."""
+        import torch
+
+        x = x.contiguous()
+        if not x.is_cuda or x.dtype != torch.float64:
+            raise TypeError("x must be a float64 CUDA tensor")
+        n_maps = 1 if x.dim() == 2 else int(x.shape[2])
+        if out is None:
+            out = torch.empty((self.n_pix,) if x.dim() == 2 else (self.n_pix, n_maps),
+                              dtype=torch.float64, device=x.device)
+        _check(lib().crp_lens_apply(self._h, x.data_ptr(), out.data_ptr(), n_maps, _stream_ptr(stream)),
+               "crp_lens_apply")
+        return out
+
+    def bin(self, sim: "Simulation", nside: int, e_min_ev: float, out=None, stream=None):
+        """Rigidity-binned arrival maps of a simulation: [n_mat, 12 nside^2] float64, added to
+        ``out`` (zeroed if created here)."""
+        import torch
+
+        if out is None:
+            out = torch.zeros((self.n_mat, self.n_pix), dtype=torch.float64, device="cuda")
+        _check(lib().crp_lens_bin(self._h, sim._h, int(nside), float(e_min_ev), out.data_ptr(),
+                                  _stream_ptr(stream)), "crp_lens_bin")
+        return out
+
+
 class _Params(C.Structure):
     _fields_ = [("form", C.c_int32), ("block_size", C.c_int32), ("blocks_per_sm", C.c_int32),
                 ("cadence", C.c_int32), ("max_steps", C.c_int64), ("order", C.c_int32),
@@ -123,6 +175,10 @@ def lib() -> C.CDLL:
             "crp_source_sample": ([p, p, p, p, p, p, i32, i64, p], C.c_int),
             "crp_healpix_ring": ([i32, p, i64, p, p], C.c_int),
             "crp_arrival_map": ([p, i32, d, p, p], C.c_int),
+            "crp_lens_create": ([i32, i32, p, p, p, p, p], C.c_int),
+            "crp_lens_destroy": ([p], C.c_int),
+            "crp_lens_apply": ([p, p, p, i32, p], C.c_int),
+            "crp_lens_bin": ([p, p, i32, d, p, p], C.c_int),
             "crp_source_inject": ([p, p, i64, p], C.c_int),
             "crp_propagate": ([p, p, d, d, d, d, p], C.c_int),
             "crp_propagate_loop": ([p, p, d, d, d, d, i32, p], C.c_int),

@@ -29,6 +29,7 @@ SOURCES = [
     ("propagate_mixed.cu", []),
     ("adjoint.cu", ["--fmad=false"]),
     ("sources.cu", ["--fmad=false"]),
+    ("lens.cu", ["--fmad=false"]),
 ]
 
 

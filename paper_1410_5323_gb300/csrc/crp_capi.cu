@@ -872,6 +872,136 @@ int crp_arrival_map(crp_sim* s, int32_t nside, double e_min_ev, uint64_t* map, v
 
 }  // extern "C"
 
+struct crp_lens {
+    int n_pix = 0, n_mat = 0, group = 32;
+    long long nnz = 0;
+    void* mem = nullptr;                 // [row_ptr | col | val | edges]
+    const long long* rp = nullptr;      // row starts (multiples of 4) of the merged rows
+    const int* rl = nullptr;            // row lengths
+    const int* col = nullptr;
+    const float* val = nullptr;
+    const double* edges = nullptr;
+};
+
+extern "C" {
+
+int crp_lens_create(int32_t n_pix, int32_t n_mat, const int64_t* row_ptr, const int32_t* col,
+                    const float* val, const double* edges, crp_lens** out) {
+    if (!out) return fail(CRP_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_pix < 1 || n_mat < 1) return fail(CRP_ERR_INVALID_ARG, "n_pix and n_mat must be >= 1");
+    if (!row_ptr) return fail(CRP_ERR_INVALID_ARG, "row_ptr is NULL");
+    const long long rows = (long long)n_mat * (n_pix + 1);
+    if (row_ptr[0] != 0) return fail(CRP_ERR_INVALID_ARG, "row_ptr must start at 0");
+    for (long long m = 0; m < n_mat; ++m) {
+        const int64_t* r = row_ptr + m * (n_pix + 1);
+        if (m > 0 && r[0] != row_ptr[m * (n_pix + 1) - 1])
+            return fail(CRP_ERR_INVALID_ARG, "each matrix must start where the previous one ends");
+        for (long long q = 0; q < n_pix; ++q)
+            if (r[q + 1] < r[q]) return fail(CRP_ERR_INVALID_ARG, "row_ptr decreases");
+    }
+    const long long nnz = row_ptr[rows - 1];
+    if (nnz > 0 && (!col || !val)) return fail(CRP_ERR_INVALID_ARG, "col or val is NULL");
+    if ((long long)n_mat * n_pix >= (1ll << 31)) return fail(CRP_ERR_INVALID_ARG, "n_mat * n_pix above 2^31");
+    for (long long k = 0; k < nnz; ++k)
+        if (col[k] < 0 || col[k] >= n_pix) return fail(CRP_ERR_INVALID_ARG, "column out of range");
+    if (edges)
+        for (int m = 0; m <= n_mat; ++m)
+            if (!(edges[m] > 0.0) || !std::isfinite(edges[m]) || (m > 0 && !(edges[m] > edges[m - 1])))
+                return fail(CRP_ERR_INVALID_ARG, "edges must be positive, finite, strictly increasing");
+    // row-merged form: row p = the row-p segments of matrices 0 .. n_mat-1 in order, columns
+    // offset by m n_pix into the stacked maps; each row starts on a 4-entry boundary (16-byte
+    // vector loads), rl holds its length, and the padding (column 0, value 0) is never summed
+    std::vector<long long> mrs((size_t)n_pix + 1, 0);
+    std::vector<int> mrl((size_t)n_pix, 0);
+    for (long long q = 0; q < n_pix; ++q) {
+        long long len = 0;
+        for (long long m = 0; m < n_mat; ++m) {
+            const int64_t* r = row_ptr + m * (n_pix + 1);
+            len += r[q + 1] - r[q];
+        }
+        if (len >= (1ll << 31)) return fail(CRP_ERR_INVALID_ARG, "a merged row above 2^31 entries");
+        mrl[q] = (int)len;
+        mrs[q + 1] = mrs[q] + (len + 3) / 4 * 4;
+    }
+    const long long padded = mrs[n_pix];
+    std::vector<int> mcol((size_t)padded, 0);
+    std::vector<float> mval((size_t)padded, 0.0f);
+    for (long long q = 0; q < n_pix; ++q) {
+        long long o = mrs[q];
+        for (long long m = 0; m < n_mat; ++m) {
+            const int64_t* r = row_ptr + m * (n_pix + 1);
+            for (long long k = r[q]; k < r[q + 1]; ++k, ++o) {
+                mcol[o] = (int)(m * n_pix + col[k]);
+                mval[o] = val[k];
+            }
+        }
+    }
+    const size_t b_rp = (size_t)(n_pix + 1) * 8, b_rl = (size_t)n_pix * 4;
+    const size_t b_col = (size_t)padded * 4, b_val = (size_t)padded * 4;
+    const size_t b_e = edges ? (size_t)(n_mat + 1) * 8 : 0;
+    auto up = [](size_t v) { return (v + 255) / 256 * 256; };
+    crp_lens* L = new crp_lens();
+    cudaError_t e = cudaMalloc(&L->mem, up(b_rp) + up(b_rl) + up(b_col) + up(b_val) + up(b_e) + 256);
+    if (e != cudaSuccess) { delete L; return cuda_fail(e, "cudaMalloc(lens)"); }
+    char* base = (char*)L->mem;
+    size_t off = 0;
+    L->rp = (const long long*)(base + off); off += up(b_rp);
+    L->rl = (const int*)(base + off); off += up(b_rl);
+    L->col = (const int*)(base + off); off += up(b_col);
+    L->val = (const float*)(base + off); off += up(b_val);
+    L->edges = edges ? (const double*)(base + off) : nullptr;
+    struct { const void* src; const void* dst; size_t n; } cp[] = {
+        {mrs.data(), L->rp, b_rp}, {mrl.data(), L->rl, b_rl}, {mcol.data(), L->col, b_col},
+        {mval.data(), L->val, b_val}, {edges, L->edges, b_e}};
+    for (auto& c : cp) {
+        if (!c.n) continue;
+        e = cudaMemcpy(const_cast<void*>(c.dst), c.src, c.n, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { cudaFree(L->mem); delete L; return cuda_fail(e, "cudaMemcpy(lens)"); }
+    }
+    L->n_pix = n_pix;
+    L->n_mat = n_mat;
+    L->nnz = nnz;
+    // lanes per row for one map: the mean merged row length in 4-entry vectors, rounded up to
+    // a power of two in [4, 32]
+    const double mean = (double)padded / 4.0 / (double)n_pix;
+    int g = 4;
+    while (g < 32 && g < mean) g *= 2;
+    L->group = g;
+    *out = L;
+    return CRP_OK;
+}
+
+int crp_lens_destroy(crp_lens* L) {
+    if (!L) return fail(CRP_ERR_INVALID_ARG, "lens is NULL");
+    if (L->mem) cudaFree(L->mem);
+    delete L;
+    return CRP_OK;
+}
+
+int crp_lens_apply(const crp_lens* L, const double* x, double* y, int32_t n_maps, void* stream) {
+    if (!L || !x || !y) return fail(CRP_ERR_INVALID_ARG, "lens, x or y is NULL");
+    if (n_maps < 1) return fail(CRP_ERR_INVALID_ARG, "n_maps must be >= 1");
+    int e = launch_lens_apply(L->n_pix, n_maps, L->group, L->rp, L->rl, L->col, L->val, x, y, device_sms(), stream);
+    if (e) return cuda_fail((cudaError_t)e, "lens kernel");
+    return CRP_OK;
+}
+
+int crp_lens_bin(const crp_lens* L, crp_sim* s, int32_t nside, double e_min_ev, double* x, void* stream) {
+    if (!L || !s || !x) return fail(CRP_ERR_INVALID_ARG, "lens, sim or x is NULL");
+    if (!L->edges) return fail(CRP_ERR_INVALID_ARG, "lens has no rigidity edges");
+    if (nside < 1 || nside > 8192 || 12ll * nside * nside != L->n_pix)
+        return fail(CRP_ERR_INVALID_ARG, "lens n_pix must be 12 nside^2");
+    if (e_min_ev != e_min_ev) return fail(CRP_ERR_INVALID_ARG, "e_min is NaN");
+    const int grid = (s->sms > 0 ? s->sms : 1) * 4;
+    int e = launch_lens_bin(s->st, s->ctr, nside, L->n_mat, L->edges, e_min_ev, x, grid, stream);
+    if (e) return cuda_fail((cudaError_t)e, "lens binning kernel");
+    s->last = reinterpret_cast<cudaStream_t>(stream);
+    return CRP_OK;
+}
+
+}  // extern "C"
+
 namespace {
 
 // FP64 descriptor of a field: the field itself for FP64 grids, else an FP64 copy of the

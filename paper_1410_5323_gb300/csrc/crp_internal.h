@@ -109,6 +109,12 @@ int launch_healpix(int nside, const double* u, long long n, long long* pix, int 
 int launch_arrival_map(const SimState& S, const Counters* C, int nside, double e_min,
                        unsigned long long* map, int grid, void* stream);
 
+// Lenses (lens.cu).
+int launch_lens_apply(int n_pix, int n_maps, int group, const long long* rs, const int* rl, const int* col,
+                      const float* val, const double* x, double* y, int sms, void* stream);
+int launch_lens_bin(const SimState& S, const Counters* C, int nside, int n_mat, const double* edges, double e_min,
+                    double* x, int grid, void* stream);
+
 // `mod`: 1 for simulations whose fields carry a modulation grid.
 int launch_propagate_fp64(const PropArgs& a, int layout, int mod, int grid, int block, void* stream);
 int propagate_fp64_occupancy(int layout, int mod, int block, int* blocks_per_sm);

@@ -76,6 +76,19 @@ def test_null_and_range_arguments_rejected_before_device_work(L):
     assert L.crp_healpix_ring(8, None, 1, xs.ctypes.data, None) == -1
     assert L.crp_arrival_map(fake, 9000, 1e18, xs.ctypes.data, None) == -1             # nside too large
     assert L.crp_arrival_map(None, 8, 1e18, xs.ctypes.data, None) == -1
+    rp = np.array([0, 1, 1], np.int64)
+    cl = np.array([0], np.int32)
+    vl = np.ones(1, np.float32)
+    assert L.crp_lens_create(0, 1, rp.ctypes.data, cl.ctypes.data, vl.ctypes.data, None, C.byref(h)) == -1
+    assert L.crp_lens_create(2, 1, None, cl.ctypes.data, vl.ctypes.data, None, C.byref(h)) == -1
+    bad_rp = np.array([1, 1, 1], np.int64)                                   # does not start at 0
+    assert L.crp_lens_create(2, 1, bad_rp.ctypes.data, cl.ctypes.data, vl.ctypes.data, None, C.byref(h)) == -1
+    bad_cl = np.array([2], np.int32)                                         # column out of range
+    assert L.crp_lens_create(2, 1, rp.ctypes.data, bad_cl.ctypes.data, vl.ctypes.data, None, C.byref(h)) == -1
+    ed = np.array([2.0, 1.0])                                                # edges decrease
+    assert L.crp_lens_create(2, 1, rp.ctypes.data, cl.ctypes.data, vl.ctypes.data, ed.ctypes.data, C.byref(h)) == -1
+    assert L.crp_lens_apply(None, xs.ctypes.data, xs.ctypes.data, 1, None) == -1
+    assert L.crp_lens_destroy(None) == -1
     assert L.crp_sim_create(None, 0, None, 1, 10, C.byref(h)) == -1
     assert L.crp_tables_create(1, 1, 1, 6.0, 25.0, None, None, None, None, C.byref(h)) == -1
     assert L.crp_propagate(None, None, 1e-4, 1.0, 2.0, 3.0, None) == -1
