@@ -687,8 +687,8 @@ def run_adjoint(args):
 
 
 def run_lens(args):
-    """Lens workload (Sec. 3.3): a synthetic nside-64 lens of 24 rigidity bins (32 entries per
-    column) applied to rigidity-binned arrival maps. value = stored entries applied per second
+    """Lens workload (Sec. 3.3): a synthetic nside-64 lens of 24 rigidity bins (24 entries per
+    column, 9.4 MB per matrix) applied to rigidity-binned arrival maps. value = stored entries applied per second
     (entries x maps / device time), one fused launch over all bins per step; roofline against
     HBM with the algorithmic bytes of a launch."""
     import torch
@@ -696,7 +696,7 @@ def run_lens(args):
     import paper_1410_5323_gb300 as crp
 
     ws, rank, _ = dist_env()
-    nside, n_mat, k = 64, 24, 32
+    nside, n_mat, k = 64, 24, 24
     n_pix = 12 * nside * nside
     n_maps = args.n_maps
     rp, col, val = I.synthetic_lens(nside, I.lens_edges(n_mat), seed=1, k=k)
@@ -773,7 +773,7 @@ def run_lens(args):
         "config": {"workload": "lens_nside64_24bins", "n_pix": n_pix, "rigidity_bins": n_mat,
                    "entries": nnz, "entries_per_column": k, "maps": n_maps,
                    "lens_bytes": int(nnz * 8 + rp.nbytes),
-                   "l2": "lens (302 MB) larger than L2 and a 256 MB flush before every step",
+                   "l2": "lens (227 MB) larger than L2 and a 256 MB flush before every step",
                    "parallelism": f"dp{ws} (independent lenses per GPU)"},
         "roofline": roof,
         "cpu_baseline": cpu,

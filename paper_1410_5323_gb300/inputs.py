@@ -453,9 +453,9 @@ def workload(name: str) -> Workload:
                         n_grids=64, **common)
     if name == "modulated_440cube_300kpc_x_256cube_50kpc_1M_nuclei":
         # Sec. 4 geometry: modulation 132 Mpc at 300 kpc; vector grid at 50 kpc with a 500 kpc
-        # coherence length (Kolmogorov on 100 kpc .. 2.5 Mpc: L_c ~ l_max / 5)
+        # coherence length (Kolmogorov on 100 kpc .. 2.2 Mpc)
         return Workload(name, 1_000_000, 256, spacing_m=50.0 * KPC, lmin_cells=2.0,
-                        lmax_cells=50.0, brms_t=1.0 * NANOGAUSS, grid_seed=1, tol=1e-4,
+                        lmax_cells=44.0, brms_t=1.0 * NANOGAUSS, grid_seed=1, tol=1e-4,
                         hmin_m=1.0 * KPC, hmax_m=1.0 * MPC, dmax_m=100.0 * MPC,
                         species=(("H", 0.4), ("He", 0.3), ("N", 0.2), ("Fe", 0.1)),
                         energy=("power", 1e18, 10 ** 20.5, 2.0), interactions=True,
@@ -535,13 +535,14 @@ def lens_edges(n_mat: int, r_min_v: float = 10 ** 18.5, r_max_v: float = 10 ** 2
     return np.logspace(math.log10(r_min_v), math.log10(r_max_v), n_mat + 1)
 
 
-def synthetic_lens(nside: int, edges, seed: int = 1, k: int = 32):
+def synthetic_lens(nside: int, edges, seed: int = 1, k: int = 24):
     """A synthetic lens standing in for galactic-field lenses built by backtracking: for each
     rigidity bin (centre R) and border pixel s, the arrival directions are spread around the
     border direction rotated by delta(R) = 30 deg (10^19 V / R) (capped at 90 deg) about a
     fixed random axis, with a Gaussian profile of width sigma(R) = max(0.5 deg,
     3 deg (10^19 V / R)); the k pixels nearest to that centre carry the column, weights
-    normalised to a transmission 1 - 0.3 exp(-R / 10^19 V). Returns (row_ptr [n_mat, n_pix+1]
+    normalised to a transmission 1 - 0.3 exp(-R / 10^19 V). k = 24 keeps a nside-64 matrix at
+    9.4 MB, inside the "less than 10 MB per matrix" of Sec. 3.3. Returns (row_ptr [n_mat, n_pix+1]
     int64 with offsets into col/val, col int32, val float32) in CSR form, rows = arrival pixels."""
     from scipy.spatial import cKDTree
 

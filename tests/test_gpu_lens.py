@@ -118,12 +118,12 @@ def test_rigidity_binning_and_pipeline(oracle_lib):
 
 
 def test_full_size_lens_every_row(oracle_lib):
-    """nside 64 (49152 pixels), 24 rigidity bins, 32 entries per column: 37.7 M entries."""
+    """nside 64 (49152 pixels), 24 rigidity bins, 24 entries per column: 28.3 M entries."""
     import paper_1410_5323_gb300 as crp
 
     nside = 64
     n_pix = 12 * nside * nside
-    rp, col, val = I.synthetic_lens(nside, I.lens_edges(24), seed=1, k=32)
+    rp, col, val = I.synthetic_lens(nside, I.lens_edges(24), seed=1)
     lens = crp.Lens(n_pix, rp, col, val)
     x = np.random.default_rng(63).poisson(3.0, (24, n_pix)).astype(np.float64)
     y = _gpu(lens, x)
