@@ -186,7 +186,8 @@ static double grid_at(const orc_field* f, int64_t i, int64_t j, int64_t k, int c
 }
 
 /* Modulation (Sec. 3.2): the scalar grid interpolated trilinearly, periodic over its own
- * extent, corners summed in the order 000, ..., 111 with weight ((w_x * w_y) * w_z). */
+ * extent, corners summed in the order 000, ..., 111 with weight ((w_x * w_y) * w_z), each
+ * corner added with one rounding, m = fma(w, M_corner, m) from m = 0. */
 double orc_modulation_value(const orc_field* f, const double x[3])
 {
     double inv = 1.0 / f->mod_spacing;
@@ -213,14 +214,15 @@ double orc_modulation_value(const orc_field* f, const double x[3])
                 int64_t k = (idx[0][a] * f->mod_ny + idx[1][b]) * f->mod_nz + idx[2][c];
                 double v = f->mod_dtype == ORC_F64 ? ((const double*)f->mod_data)[k]
                                                    : (double)((const float*)f->mod_data)[k];
-                m = m + wt * v;
+                m = fma(wt, v, m);
             }
     return m;
 }
 
 /* Fractional index r = (x - origin) * (1/spacing); cell i0 = floor(r) wrapped modulo n;
  * weights (1 - f, f) with f = r - floor(r). B is the sum over the 8 cell corners, taken
- * in the order (a,b,c) = 000, 001, 010, ..., 111, of ((w_x,a * w_y,b) * w_z,c) * B_corner. */
+ * in the order (a,b,c) = 000, 001, 010, ..., 111, of ((w_x,a * w_y,b) * w_z,c) * B_corner,
+ * each corner added with one rounding: B = fma(w, B_corner, B) from B = 0. */
 void orc_field_value(const orc_field* f, const double x[3], double B[3])
 {
     double inv = 1.0 / f->spacing;
@@ -245,7 +247,7 @@ void orc_field_value(const orc_field* f, const double x[3], double B[3])
             for (int c = 0; c < 2; ++c) {
                 double wt = (w[0][a] * w[1][b]) * w[2][c];
                 for (int q = 0; q < 3; ++q)
-                    B[q] = B[q] + wt * grid_at(f, idx[0][a], idx[1][b], idx[2][c], q);
+                    B[q] = fma(wt, grid_at(f, idx[0][a], idx[1][b], idx[2][c], q), B[q]);
             }
     if (f->mod_data) {
         double m = orc_modulation_value(f, x);
@@ -254,7 +256,8 @@ void orc_field_value(const orc_field* f, const double x[3], double B[3])
 }
 
 /* ---- equation of motion (Sec. 2, 3D deflections) -------------------------------- */
-/* y = (x, u); f(y) = (u, kappa u x B(x)), kappa = Z c / E (1/(T m)). */
+/* y = (x, u); f(y) = (u, kappa u x B(x)), kappa = Z c / E (1/(T m)); each cross-product
+ * component a b - c d as kappa * fma(a, b, -(c d)). */
 void orc_deriv(const orc_field* f, double kappa, const double y[6], double k[6])
 {
     double B[3];
@@ -262,9 +265,9 @@ void orc_deriv(const orc_field* f, double kappa, const double y[6], double k[6])
     k[0] = y[3];
     k[1] = y[4];
     k[2] = y[5];
-    k[3] = kappa * (y[4] * B[2] - y[5] * B[1]);
-    k[4] = kappa * (y[5] * B[0] - y[3] * B[2]);
-    k[5] = kappa * (y[3] * B[1] - y[4] * B[0]);
+    k[3] = kappa * fma(y[4], B[2], -(y[5] * B[1]));
+    k[4] = kappa * fma(y[5], B[0], -(y[3] * B[2]));
+    k[5] = kappa * fma(y[3], B[1], -(y[4] * B[0]));
 }
 
 /* ---- Cash & Karp (1990) embedded Runge-Kutta 4(5) tableau --------------------------- */
@@ -283,7 +286,9 @@ static const double CK_E[6] = {-277.0 / 64512.0, 0.0, 6925.0 / 370944.0, -6925.0
                                -277.0 / 14336.0, 277.0 / 7084.0};
 
 /* One attempt of step h from y (k1 = f(y) given): stages y_i = y + h * sum_j a_ij k_j,
- * sums taken left to right; y5 = y + h * sum_i b_i k_i; err = h * sum_i (b_i - b*_i) k_i. */
+ * sums taken left to right; y5 = y + h * sum_i b_i k_i; err = h * sum_i (b_i - b*_i) k_i.
+ * Every term after the first of a sum, and the final y + h * sum, is added with one rounding
+ * (fused multiply-add); the first term and h * sum of err are plain products. */
 void orc_ck_attempt(const orc_field* f, double kappa, const double y[6], const double k1[6],
                     double h, double y5[6], double err[6])
 {
@@ -293,30 +298,31 @@ void orc_ck_attempt(const orc_field* f, double kappa, const double y[6], const d
         double yt[6];
         for (int c = 0; c < 6; ++c) {
             double acc = CK_A[i][0] * k[0][c];
-            for (int j = 1; j < i; ++j) acc = acc + CK_A[i][j] * k[j][c];
-            yt[c] = y[c] + h * acc;
+            for (int j = 1; j < i; ++j) acc = fma(CK_A[i][j], k[j][c], acc);
+            yt[c] = fma(h, acc, y[c]);
         }
         orc_deriv(f, kappa, yt, k[i]);
     }
     for (int c = 0; c < 6; ++c) {
         double acc = CK_B5[0] * k[0][c];
-        for (int j = 1; j < 6; ++j) acc = acc + CK_B5[j] * k[j][c];
-        y5[c] = y[c] + h * acc;
+        for (int j = 1; j < 6; ++j) acc = fma(CK_B5[j], k[j][c], acc);
+        y5[c] = fma(h, acc, y[c]);
     }
     for (int c = 0; c < 6; ++c) {
         double acc = CK_E[0] * k[0][c];
-        for (int j = 1; j < 6; ++j) acc = acc + CK_E[j] * k[j][c];
+        for (int j = 1; j < 6; ++j) acc = fma(CK_E[j], k[j][c], acc);
         err[c] = h * acc;
     }
 }
 
-/* Error ratio r = max(|dx|/h, |du|) / tol with Euclidean norms ((a0^2 + a1^2) + a2^2);
- * r = 0 for a zero-length step. Accept iff r <= 1. */
+/* Error ratio r = max(|dx|/h, |du|) / tol with Euclidean norms ((a0^2 + a1^2) + a2^2), each
+ * square after the first added with one rounding; r = 0 for a zero-length step. Accept iff
+ * r <= 1. */
 double orc_error_ratio(const double err[6], double h, double tol)
 {
     if (h == 0.0) return 0.0;
-    double ex = sqrt((err[0] * err[0] + err[1] * err[1]) + err[2] * err[2]) / h;
-    double eu = sqrt((err[3] * err[3] + err[4] * err[4]) + err[5] * err[5]);
+    double ex = sqrt(fma(err[2], err[2], fma(err[1], err[1], err[0] * err[0]))) / h;
+    double eu = sqrt(fma(err[5], err[5], fma(err[4], err[4], err[3] * err[3])));
     return fmax(ex, eu) / tol;
 }
 
@@ -793,10 +799,10 @@ void orc_adjoint(const orc_field* f, double kappa, const double y0[6], const dou
         for (int c = 0; c < 6; ++c) Y[0][c] = y[c];
         orc_deriv(f, kappa, Y[0], k[0]);
         for (int i = 1; i < 6; ++i) {
-            for (int c = 0; c < 6; ++c) {
+            for (int c = 0; c < 6; ++c) {           /* the forward stage sums (orc_ck_attempt) */
                 double acc = CK_A[i][0] * k[0][c];
-                for (int j = 1; j < i; ++j) acc = acc + CK_A[i][j] * k[j][c];
-                Y[i][c] = y[c] + hn * acc;
+                for (int j = 1; j < i; ++j) acc = fma(CK_A[i][j], k[j][c], acc);
+                Y[i][c] = fma(hn, acc, y[c]);
             }
             orc_deriv(f, kappa, Y[i], k[i]);
         }

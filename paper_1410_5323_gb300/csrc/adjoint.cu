@@ -180,6 +180,10 @@ __device__ __forceinline__ void axpy6(Y6& acc, double s, const Y6& v) {
     acc.x = acc.x + s * v.x; acc.y = acc.y + s * v.y; acc.z = acc.z + s * v.z;
     acc.ux = acc.ux + s * v.ux; acc.uy = acc.uy + s * v.uy; acc.uz = acc.uz + s * v.uz;
 }
+__device__ __forceinline__ void fmaxpy6(Y6& acc, double s, const Y6& v) {
+    acc.x = __fma_rn(s, v.x, acc.x); acc.y = __fma_rn(s, v.y, acc.y); acc.z = __fma_rn(s, v.z, acc.z);
+    acc.ux = __fma_rn(s, v.ux, acc.ux); acc.uy = __fma_rn(s, v.uy, acc.uy); acc.uz = __fma_rn(s, v.uz, acc.uz);
+}
 __device__ __forceinline__ Y6 scale6(double s, const Y6& v) {
     return {s * v.x, s * v.y, s * v.z, s * v.ux, s * v.uy, s * v.uz};
 }
@@ -205,11 +209,11 @@ __device__ void adjoint_step(const FieldDev& F, double kappa, const Y6& y, doubl
     Y[0] = y;
     k[0] = deriv<L>(F, kappa, y);
     for (int i = 1; i < 6; ++i) {
-        // acc = A[i][0] k1; acc = acc + A[i][j] k_j (j < i), as in the stage sums
+        // the forward stage sums: acc = A[i][0] k1, then fused A[i][j] k_j (j < i); y + h acc fused
         Y6 acc = scale6(cA[i][0], k[0]);
-        for (int j = 1; j < i; ++j) axpy6(acc, cA[i][j], k[j]);
-        Y[i] = {y.x + hn * acc.x, y.y + hn * acc.y, y.z + hn * acc.z,
-                y.ux + hn * acc.ux, y.uy + hn * acc.uy, y.uz + hn * acc.uz};
+        for (int j = 1; j < i; ++j) fmaxpy6(acc, cA[i][j], k[j]);
+        Y[i] = {__fma_rn(hn, acc.x, y.x), __fma_rn(hn, acc.y, y.y), __fma_rn(hn, acc.z, y.z),
+                __fma_rn(hn, acc.ux, y.ux), __fma_rn(hn, acc.uy, y.uy), __fma_rn(hn, acc.uz, y.uz)};
         k[i] = deriv<L>(F, kappa, Y[i]);
     }
     Y6 kb[6];

@@ -1,7 +1,8 @@
 // crp_fp64.cuh -- FP64 arithmetic of the method shared by the FP64 propagate kernel and the
 // adjoint kernels: periodic trilinear lookup, Lorentz force, Cash & Karp (1990) attempt,
 // error ratio. Translation units including it are compiled with --fmad=false so that every
-// formula is evaluated exactly as written, in the stated order.
+// formula is evaluated exactly as written, in the stated order; the fused multiply-adds of
+// the reading are explicit (__fma_rn).
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
@@ -67,7 +68,8 @@ __device__ __forceinline__ void axis(double x, double o, double inv, int n, int 
 }
 
 // Modulation value M(x): scalar periodic trilinear lookup on the modulation grid, corners
-// in the order 000, 001, ..., 111, weight ((w_x * w_y) * w_z).
+// in the order 000, 001, ..., 111, weight ((w_x * w_y) * w_z), each corner added with one
+// rounding (fused multiply-add from 0).
 __device__ __forceinline__ double modulation(const FieldDev& F, double x, double y, double z) {
     long long ix0, ix1, iy0, iy1, iz0, iz1;
     double wx0, wx1, wy0, wy1, wz0, wz1;
@@ -83,19 +85,20 @@ __device__ __forceinline__ double modulation(const FieldDev& F, double x, double
     const double m4 = (double)__ldg(M + r10 + iz0), m5 = (double)__ldg(M + r10 + iz1);
     const double m6 = (double)__ldg(M + r11 + iz0), m7 = (double)__ldg(M + r11 + iz1);
     const double w00 = wx0 * wy0, w01 = wx0 * wy1, w10 = wx1 * wy0, w11 = wx1 * wy1;
-    double m = (w00 * wz0) * m0;
-    m = m + (w00 * wz1) * m1;
-    m = m + (w01 * wz0) * m2;
-    m = m + (w01 * wz1) * m3;
-    m = m + (w10 * wz0) * m4;
-    m = m + (w10 * wz1) * m5;
-    m = m + (w11 * wz0) * m6;
-    m = m + (w11 * wz1) * m7;
+    double m = __fma_rn(w00 * wz0, m0, 0.0);
+    m = __fma_rn(w00 * wz1, m1, m);
+    m = __fma_rn(w01 * wz0, m2, m);
+    m = __fma_rn(w01 * wz1, m3, m);
+    m = __fma_rn(w10 * wz0, m4, m);
+    m = __fma_rn(w10 * wz1, m5, m);
+    m = __fma_rn(w11 * wz0, m6, m);
+    m = __fma_rn(w11 * wz1, m7, m);
     return m;
 }
 
 // Trilinear periodic lookup; corners summed in the order 000, 001, ..., 111 (x, y, z),
-// weight ((w_x * w_y) * w_z). With M, the result is scaled by the modulation value.
+// weight ((w_x * w_y) * w_z), each corner added with one rounding (fused multiply-add from
+// 0). With M, the result is scaled by the modulation value.
 // With H, every lookup also folds its cell index into *hh (the visited-cell sequence of a
 // trajectory; no effect on the arithmetic).
 template <int L, bool H = false, bool M = false>
@@ -117,14 +120,17 @@ __device__ __forceinline__ V3 field_b(const FieldDev& F, double x, double y, dou
     const double w00 = wx0 * wy0, w01 = wx0 * wy1, w10 = wx1 * wy0, w11 = wx1 * wy1;
     double t;
     V3 B;
-    t = w00 * wz0; B.x = t * g0.x;       B.y = t * g0.y;       B.z = t * g0.z;
-    t = w00 * wz1; B.x = B.x + t * g1.x; B.y = B.y + t * g1.y; B.z = B.z + t * g1.z;
-    t = w01 * wz0; B.x = B.x + t * g2.x; B.y = B.y + t * g2.y; B.z = B.z + t * g2.z;
-    t = w01 * wz1; B.x = B.x + t * g3.x; B.y = B.y + t * g3.y; B.z = B.z + t * g3.z;
-    t = w10 * wz0; B.x = B.x + t * g4.x; B.y = B.y + t * g4.y; B.z = B.z + t * g4.z;
-    t = w10 * wz1; B.x = B.x + t * g5.x; B.y = B.y + t * g5.y; B.z = B.z + t * g5.z;
-    t = w11 * wz0; B.x = B.x + t * g6.x; B.y = B.y + t * g6.y; B.z = B.z + t * g6.z;
-    t = w11 * wz1; B.x = B.x + t * g7.x; B.y = B.y + t * g7.y; B.z = B.z + t * g7.z;
+#define CRP_CORNER(g, acc0x, acc0y, acc0z)                                                    \
+    B.x = __fma_rn(t, g.x, acc0x); B.y = __fma_rn(t, g.y, acc0y); B.z = __fma_rn(t, g.z, acc0z)
+    t = w00 * wz0; CRP_CORNER(g0, 0.0, 0.0, 0.0);
+    t = w00 * wz1; CRP_CORNER(g1, B.x, B.y, B.z);
+    t = w01 * wz0; CRP_CORNER(g2, B.x, B.y, B.z);
+    t = w01 * wz1; CRP_CORNER(g3, B.x, B.y, B.z);
+    t = w10 * wz0; CRP_CORNER(g4, B.x, B.y, B.z);
+    t = w10 * wz1; CRP_CORNER(g5, B.x, B.y, B.z);
+    t = w11 * wz0; CRP_CORNER(g6, B.x, B.y, B.z);
+    t = w11 * wz1; CRP_CORNER(g7, B.x, B.y, B.z);
+#undef CRP_CORNER
     if constexpr (M) {
         const double m = modulation(F, x, y, z);
         B.x = m * B.x; B.y = m * B.y; B.z = m * B.z;
@@ -134,24 +140,27 @@ __device__ __forceinline__ V3 field_b(const FieldDev& F, double x, double y, dou
 
 struct Y6 { double x, y, z, ux, uy, uz; };
 
-// f(y) = (u, kappa u x B(x))
+// f(y) = (u, kappa u x B(x)); a cross-product component a b - c d as kappa fma(a, b, -(c d)).
 template <int L, bool H = false, bool M = false>
 __device__ __forceinline__ Y6 deriv(const FieldDev& F, double kappa, const Y6& y,
                                     unsigned long long* hh = nullptr) {
     const V3 B = field_b<L, H, M>(F, y.x, y.y, y.z, hh);
     Y6 k;
     k.x = y.ux; k.y = y.uy; k.z = y.uz;
-    k.ux = kappa * (y.uy * B.z - y.uz * B.y);
-    k.uy = kappa * (y.uz * B.x - y.ux * B.z);
-    k.uz = kappa * (y.ux * B.y - y.uy * B.x);
+    k.ux = kappa * __fma_rn(y.uy, B.z, -(y.uz * B.y));
+    k.uy = kappa * __fma_rn(y.uz, B.x, -(y.ux * B.z));
+    k.uz = kappa * __fma_rn(y.ux, B.y, -(y.uy * B.x));
     return k;
 }
 
+// dst = y + h * sum, the final addition fused; the sums chain fused multiply-adds left to
+// right from a plain first product (zero tableau entries, b2 = b5 = 0 and b2 - b*2 = 0, are
+// not summed).
 #define CRP_STAGE(dst, expr)                                                           \
     do {                                                                               \
-        dst.x = y.x + h * (expr(x));  dst.y = y.y + h * (expr(y));                      \
-        dst.z = y.z + h * (expr(z));  dst.ux = y.ux + h * (expr(ux));                   \
-        dst.uy = y.uy + h * (expr(uy)); dst.uz = y.uz + h * (expr(uz));                 \
+        dst.x = __fma_rn(h, expr(x), y.x);    dst.y = __fma_rn(h, expr(y), y.y);        \
+        dst.z = __fma_rn(h, expr(z), y.z);    dst.ux = __fma_rn(h, expr(ux), y.ux);     \
+        dst.uy = __fma_rn(h, expr(uy), y.uy); dst.uz = __fma_rn(h, expr(uz), y.uz);     \
     } while (0)
 
 // One Cash-Karp attempt of size h from y with k1 = f(y).
@@ -163,21 +172,21 @@ __device__ __forceinline__ void ck_attempt(const FieldDev& F, double kappa, cons
 #define S2(c) (A21 * k1.c)
     CRP_STAGE(t, S2);
     const Y6 k2 = deriv<L, H, M>(F, kappa, t, hh);
-#define S3(c) (A31 * k1.c + A32 * k2.c)
+#define S3(c) __fma_rn(A32, k2.c, A31 * k1.c)
     CRP_STAGE(t, S3);
     const Y6 k3 = deriv<L, H, M>(F, kappa, t, hh);
-#define S4(c) (A41 * k1.c + A42 * k2.c + A43 * k3.c)
+#define S4(c) __fma_rn(A43, k3.c, __fma_rn(A42, k2.c, A41 * k1.c))
     CRP_STAGE(t, S4);
     const Y6 k4 = deriv<L, H, M>(F, kappa, t, hh);
-#define S5(c) (A51 * k1.c + A52 * k2.c + A53 * k3.c + A54 * k4.c)
+#define S5(c) __fma_rn(A54, k4.c, __fma_rn(A53, k3.c, __fma_rn(A52, k2.c, A51 * k1.c)))
     CRP_STAGE(t, S5);
     const Y6 k5 = deriv<L, H, M>(F, kappa, t, hh);
-#define S6(c) (A61 * k1.c + A62 * k2.c + A63 * k3.c + A64 * k4.c + A65 * k5.c)
+#define S6(c) __fma_rn(A65, k5.c, __fma_rn(A64, k4.c, __fma_rn(A63, k3.c, __fma_rn(A62, k2.c, A61 * k1.c))))
     CRP_STAGE(t, S6);
     const Y6 k6 = deriv<L, H, M>(F, kappa, t, hh);
-#define SB(c) (B1 * k1.c + B3 * k3.c + B4 * k4.c + B6 * k6.c)
+#define SB(c) __fma_rn(B6, k6.c, __fma_rn(B4, k4.c, __fma_rn(B3, k3.c, B1 * k1.c)))
     CRP_STAGE(y5, SB);
-#define SE(c) (h * (E1 * k1.c + E3 * k3.c + E4 * k4.c + E5 * k5.c + E6 * k6.c))
+#define SE(c) (h * __fma_rn(E6, k6.c, __fma_rn(E5, k5.c, __fma_rn(E4, k4.c, __fma_rn(E3, k3.c, E1 * k1.c)))))
     err.x = SE(x); err.y = SE(y); err.z = SE(z);
     err.ux = SE(ux); err.uy = SE(uy); err.uz = SE(uz);
 #undef S2
@@ -191,8 +200,8 @@ __device__ __forceinline__ void ck_attempt(const FieldDev& F, double kappa, cons
 
 __device__ __forceinline__ double error_ratio(const Y6& e, double h, double tol) {
     if (h == 0.0) return 0.0;
-    const double ex = sqrt((e.x * e.x + e.y * e.y) + e.z * e.z) / h;
-    const double eu = sqrt((e.ux * e.ux + e.uy * e.uy) + e.uz * e.uz);
+    const double ex = sqrt(__fma_rn(e.z, e.z, __fma_rn(e.y, e.y, e.x * e.x))) / h;
+    const double eu = sqrt(__fma_rn(e.uz, e.uz, __fma_rn(e.uy, e.uy, e.ux * e.ux)));
     return fmax(ex, eu) / tol;
 }
 
