@@ -23,8 +23,17 @@ namespace {
 
 using namespace fp64;
 
+// Register cap, a build-time tuning knob (-DCRP_FP64_MAXNREG=N). Unset by default: capping
+// the 176-register kernel at 168 (12 instead of 8 warps per SM, no spills) measured 3 % slower,
+// since the FP64 pipe, not latency, bounds it.
+#ifdef CRP_FP64_MAXNREG
+#define CRP_FP64_BOUNDS __maxnreg__(CRP_FP64_MAXNREG)
+#else
+#define CRP_FP64_BOUNDS __launch_bounds__(256)
+#endif
+
 template <int L, bool M>
-__global__ void __launch_bounds__(256) k_propagate_fp64(const PropArgs a) {
+__global__ void CRP_FP64_BOUNDS k_propagate_fp64(const PropArgs a) {
     const int lane = threadIdx.x & 31;
     Counters* C = a.ctr;
     const unsigned long long n_work = *(volatile unsigned long long*)&C->count[a.list];
