@@ -50,9 +50,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2.070e9 * 2 / 1e12   # FFMA lanes x 2
 MIXED_FP64_OPS_PER_ATTEMPT = 14
 MIXED_FP64_OPS_PER_ACCEPTED = 5
 MIXED_FP32_FLOP_PER_ATTEMPT = 612
-# DRAM bytes (read + write) of one lens launch by ncu, keyed by the number of maps (None until
-# measured on the current kernels).
-LENS_DRAM_BYTES: dict = {}
+# DRAM bytes (read + write) of one lens launch measured by ncu on the current kernels, keyed by
+# the number of maps (profiles/k_lens_apply_nside64_24bins.md).
+LENS_DRAM_BYTES = {1: 2.406e8, 32: 5.531e8}
 # Modulated fields add one scalar trilinear lookup per field evaluation: FP64 form 6 x
 # (axes 12, weights 12, 8 products, 7 sums, 3 products m*B) = 252 per attempt; mixed form
 # 6 x 38 FP32 flops per attempt and, per accepted step, the step-start modulation cell in
@@ -63,9 +63,10 @@ MIXED_MOD_FP32_FLOP_PER_ATTEMPT = 228
 # DRAM bytes (read + write) per attempted step of the propagate kernels, measured by ncu at
 # reduced batch (both launches of one call; the summaries under profiles/ name the command);
 # traffic of a call = this x its attempts. Keyed by (workload, form).
-DRAM_BYTES_PER_ATTEMPT = {("fp64_256cube_1M_nuclei", "fp64"): 140.5,
-                          ("fp64_256cube_1M_nuclei", "mixed"): 92.7,
-                          ("modulated_440cube_300kpc_x_256cube_50kpc_1M_nuclei", "fp64"): 417.6}
+DRAM_BYTES_PER_ATTEMPT = {("fp64_256cube_1M_nuclei", "fp64"): 140.2,
+                          ("fp64_256cube_1M_nuclei", "mixed"): 89.6,
+                          ("modulated_440cube_300kpc_x_256cube_50kpc_1M_nuclei", "fp64"): 411.1,
+                          ("modulated_440cube_300kpc_x_256cube_50kpc_1M_nuclei", "mixed"): 775.1}
 
 
 def parse():
