@@ -285,6 +285,7 @@ def cpu_baseline(w, grids, tables, parts, sample: int, form_desc: str):
                             box=I.workload_box(w))
     dt = time.perf_counter() - t0
     return ({"value": stats["accepted"] / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+             "per_core": stats["accepted"] / dt / threads,
              "sample": f"{len(sub)} primaries of the same batch (+{stats['secondaries']} "
                        f"secondaries), full {w.dmax_m / I.MPC:.0f} Mpc, {stats['accepted']} "
                        f"accepted steps in {dt:.2f} s ({form_desc} oracle)",
