@@ -366,6 +366,17 @@ int crp_lens_apply(const crp_lens* lens, const double* x, double* y, int32_t n_m
 int crp_lens_bin(const crp_lens* lens, crp_sim* sim, int32_t nside, double e_min_ev, double* x,
                  void* stream);
 
+/* ---- diagnostics and fault injection (no counterpart in the paper) ----------------------
+ * crp_debug_fail_allocations(n): the library's next n device allocations fail as if the device
+ * were out of memory (every entry point that allocates then returns CRP_ERR_OOM and frees
+ * what it had taken); 0 disarms. For testing the error paths without exhausting a GPU.
+ * crp_selftest_wait(limit, preset, stream): runs the kernels' bounded wait (limit polls of
+ * 64 ns) on a device flag initialised to `preset`; a flag that is never set (preset < 0)
+ * makes the wait run out and the call return CRP_ERR_TIMEOUT, preset >= 0 returns CRP_OK.
+ * Synchronises `stream`; the context stays usable either way. */
+int crp_debug_fail_allocations(int32_t n);
+int crp_selftest_wait(int32_t limit, int32_t preset, void* stream);
+
 /* ---- propagation that allocates nothing -------------------------------------------------
  * This entry point has no counterpart in the paper; it exists for callers that must not
  * have this library allocate device memory. Some host programs own every byte of GPU

@@ -25,6 +25,8 @@ from .api import (  # noqa: F401
     Simulation,
     Spectrum,
     Tables,
+    debug_fail_allocations,
     healpix_ring,
     lib,
+    selftest_wait,
 )

@@ -80,6 +80,17 @@ def healpix_ring(nside: int, u, stream=None):
     return pix
 
 
+def debug_fail_allocations(n: int) -> None:
+    """Fault injection: the library's next n device allocations fail as out of memory."""
+    _check(lib().crp_debug_fail_allocations(int(n)), "crp_debug_fail_allocations")
+
+
+def selftest_wait(limit: int, preset: int = -1, stream=None) -> int:
+    """Runs the kernels' bounded wait on a flag preset to `preset`; returns the status code
+    (ERR_TIMEOUT when the flag is never set, OK otherwise) without raising."""
+    return int(lib().crp_selftest_wait(int(limit), int(preset), _stream_ptr(stream)))
+
+
 class Lens:
     """Per-rigidity sparse lens matrices (paper Sec. 3.3), CSR over shared arrays:
     row_ptr [n_mat, n_pix + 1] int64 (offsets into col/val, matrices one after another),
@@ -176,6 +187,8 @@ def lib() -> C.CDLL:
             "crp_healpix_ring": ([i32, p, i64, p, p], C.c_int),
             "crp_arrival_map": ([p, i32, d, p, p], C.c_int),
             "crp_lens_create": ([i32, i32, p, p, p, p, p], C.c_int),
+            "crp_debug_fail_allocations": ([i32], C.c_int),
+            "crp_selftest_wait": ([i32, i32, p], C.c_int),
             "crp_lens_destroy": ([p], C.c_int),
             "crp_lens_apply": ([p, p, p, i32, p], C.c_int),
             "crp_lens_bin": ([p, p, i32, d, p, p], C.c_int),

@@ -12,11 +12,15 @@
 #include <cstring>
 #include <string>
 #include <thread>
+#include <atomic>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "crp.h"
 #include "crp_internal.h"
 #include "crp_math.cuh"
+#include "crp_sched.cuh"
 
 static_assert(CRP_STATUS_ACTIVE == crp::CRP_STATUS_ACTIVE_, "status numbering");
 static_assert(CRP_STATUS_DONE == crp::CRP_STATUS_DONE_, "status numbering");
@@ -38,6 +42,28 @@ int cuda_fail(cudaError_t e, const char* where) {
     g_detail = std::string(where) + ": " + cudaGetErrorString(e);
     return (e == cudaErrorMemoryAllocation) ? CRP_ERR_OOM : CRP_ERR_CUDA;
 }
+
+// Device allocations of the library go through here. crp_debug_fail_allocations(n) makes
+// the next n of them fail as out of memory (fault injection for tests).
+std::atomic<int> g_fail_allocs{0};
+
+template <typename T>
+cudaError_t dev_malloc(T** p, size_t bytes) {
+    int n = g_fail_allocs.load();
+    while (n > 0) {
+        if (g_fail_allocs.compare_exchange_weak(n, n - 1)) {
+            *p = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
+    }
+    return cudaMalloc(reinterpret_cast<void**>(p), bytes);
+}
+
+// NVTX range over one library call (visible in Nsight timelines; no cost without a tool).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 #define CRP_CUDA(call)                                      \
     do {                                                    \
@@ -399,7 +425,7 @@ void free_state(SimState& S) {
 int alloc_state(SimState& S, long long cap) {
     for (int c = 0; c < CRP_N_COLS; ++c) {
         void** p = col_ptr(S, c);
-        cudaError_t e = cudaMalloc(p, (size_t)cap * kCols[c].size);
+        cudaError_t e = dev_malloc(p, (size_t)cap * kCols[c].size);
         if (e != cudaSuccess) {
             free_state(S);
             return cuda_fail(e, "cudaMalloc(state)");
@@ -446,6 +472,7 @@ const char* crp_last_error_detail(void) { return g_detail.c_str(); }
 int crp_field_create(const void* grid, int32_t dtype, int32_t is_device, int32_t nx, int32_t ny,
                      int32_t nz, double spacing_m, const double origin_m[3], float scale,
                      crp_field** out) {
+    NvtxRange nvtx_("crp_field_create");
     if (!out) return fail(CRP_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!grid || !origin_m) return fail(CRP_ERR_INVALID_ARG, "grid or origin is NULL");
@@ -472,13 +499,13 @@ int crp_field_create(const void* grid, int32_t dtype, int32_t is_device, int32_t
     const void* src = grid;
     void* staging = nullptr;
     if (!is_device) {
-        CRP_CUDA(cudaMalloc(&staging, in_bytes));
+        CRP_CUDA(dev_malloc(&staging, in_bytes));
         cudaError_t e = cudaMemcpy(staging, grid, in_bytes, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) { cudaFree(staging); return cuda_fail(e, "cudaMemcpy(grid)"); }
         src = staging;
     }
     crp_field* f = new crp_field();
-    cudaError_t e = cudaMalloc(&f->mem, (size_t)nodes * out_elem);
+    cudaError_t e = dev_malloc(&f->mem, (size_t)nodes * out_elem);
     if (e != cudaSuccess) {
         if (staging) cudaFree(staging);
         delete f;
@@ -516,6 +543,7 @@ int crp_field_create(const void* grid, int32_t dtype, int32_t is_device, int32_t
 
 int crp_field_modulate(crp_field* field, const void* mod, int32_t dtype, int32_t is_device,
                        int32_t nx, int32_t ny, int32_t nz, double spacing_m, const double origin_m[3]) {
+    NvtxRange nvtx_("crp_field_modulate");
     if (!field || !mod || !origin_m) return fail(CRP_ERR_INVALID_ARG, "field, modulation or origin is NULL");
     if (dtype != CRP_DTYPE_F32) return fail(CRP_ERR_INVALID_ARG, "modulation grids are FP32");
     if (nx < 1 || ny < 1 || nz < 1) return fail(CRP_ERR_INVALID_ARG, "grid sizes must be >= 1");
@@ -527,7 +555,7 @@ int crp_field_modulate(crp_field* field, const void* mod, int32_t dtype, int32_t
         if (!std::isfinite(origin_m[a])) return fail(CRP_ERR_INVALID_ARG, "origin not finite");
     if (field->modmem) return fail(CRP_ERR_INVALID_ARG, "field already modulated");
     void* m = nullptr;
-    CRP_CUDA(cudaMalloc(&m, (size_t)nodes * sizeof(float)));
+    CRP_CUDA(dev_malloc(&m, (size_t)nodes * sizeof(float)));
     cudaError_t e = cudaMemcpy(m, mod, (size_t)nodes * sizeof(float),
                                is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { cudaFree(m); return cuda_fail(e, "cudaMemcpy(modulation)"); }
@@ -554,6 +582,7 @@ int crp_field_destroy(crp_field* field) {
 int crp_tables_create(int32_t z_max, int32_t n_max, int32_t n_nodes, double x0, double inv_dx,
                       const double* log10_loss, const double* log10_pd, const uint8_t* has_loss,
                       const uint8_t* has_pd, crp_tables** out) {
+    NvtxRange nvtx_("crp_tables_create");
     if (!out) return fail(CRP_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!log10_loss || !log10_pd || !has_loss || !has_pd)
@@ -580,7 +609,7 @@ int crp_tables_create(int32_t z_max, int32_t n_max, int32_t n_nodes, double x0, 
         pf[i] = (float)log10_pd[i];
     }
     crp_tables* t = new crp_tables();
-    cudaError_t e = cudaMalloc(&t->mem, total);
+    cudaError_t e = dev_malloc(&t->mem, total);
     if (e != cudaSuccess) { delete t; return cuda_fail(e, "cudaMalloc(tables)"); }
     char* base = (char*)t->mem;
     e = cudaMemcpy(base, log10_loss, vb, cudaMemcpyHostToDevice);
@@ -613,6 +642,7 @@ int crp_tables_destroy(crp_tables* tables) {
 
 int crp_sim_create(const crp_field* const* fields, int32_t n_fields, const crp_tables* tables,
                    uint64_t seed, int64_t capacity, crp_sim** out) {
+    NvtxRange nvtx_("crp_sim_create");
     if (!out) return fail(CRP_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!fields || n_fields < 1) return fail(CRP_ERR_INVALID_ARG, "need at least one field");
@@ -642,16 +672,16 @@ int crp_sim_create(const crp_field* const* fields, int32_t n_fields, const crp_t
     }
     int rc = alloc_state(s->st, capacity);
     cudaError_t e = cudaSuccess;
-    if (rc == CRP_OK) e = cudaMalloc(&s->d_fields, sizeof(FieldDev) * n_fields);
+    if (rc == CRP_OK) e = dev_malloc(&s->d_fields, sizeof(FieldDev) * n_fields);
     if (rc == CRP_OK && e == cudaSuccess)
         e = cudaMemcpy(s->d_fields, s->host_fields.data(), sizeof(FieldDev) * n_fields, cudaMemcpyHostToDevice);
-    if (rc == CRP_OK && e == cudaSuccess) e = cudaMalloc(&s->lists[0], sizeof(int32_t) * capacity);
-    if (rc == CRP_OK && e == cudaSuccess) e = cudaMalloc(&s->lists[1], sizeof(int32_t) * capacity);
-    if (rc == CRP_OK && e == cudaSuccess) e = cudaMalloc(&s->done_list, sizeof(int32_t) * capacity);
-    if (rc == CRP_OK && e == cudaSuccess) e = cudaMalloc(&s->ctr, sizeof(Counters));
+    if (rc == CRP_OK && e == cudaSuccess) e = dev_malloc(&s->lists[0], sizeof(int32_t) * capacity);
+    if (rc == CRP_OK && e == cudaSuccess) e = dev_malloc(&s->lists[1], sizeof(int32_t) * capacity);
+    if (rc == CRP_OK && e == cudaSuccess) e = dev_malloc(&s->done_list, sizeof(int32_t) * capacity);
+    if (rc == CRP_OK && e == cudaSuccess) e = dev_malloc(&s->ctr, sizeof(Counters));
     if (rc == CRP_OK && e == cudaSuccess) e = cudaMemset(s->ctr, 0, sizeof(Counters));
     const size_t sort_bytes = 2 * (size_t)kBuckets * n_fields * sizeof(unsigned);
-    if (rc == CRP_OK && e == cudaSuccess) e = cudaMalloc(&s->sort_scratch, sort_bytes);
+    if (rc == CRP_OK && e == cudaSuccess) e = dev_malloc(&s->sort_scratch, sort_bytes);
     if (rc == CRP_OK && e == cudaSuccess) e = cudaMemset(s->sort_scratch, 0, sort_bytes);
     if (rc != CRP_OK || e != cudaSuccess) {
         crp_sim_destroy(s);
@@ -698,6 +728,7 @@ int crp_sim_destroy(crp_sim* s) {
 }
 
 int crp_sim_reset(crp_sim* s) {
+    NvtxRange nvtx_("crp_sim_reset");
     if (!s) return fail(CRP_ERR_INVALID_ARG, "sim is NULL");
     int rc = sync_stream(s);
     if (rc) return rc;
@@ -707,6 +738,7 @@ int crp_sim_reset(crp_sim* s) {
 }
 
 int crp_sim_reserve(crp_sim* s, int64_t capacity) {
+    NvtxRange nvtx_("crp_sim_reserve");
     if (!s) return fail(CRP_ERR_INVALID_ARG, "sim is NULL");
     if (capacity >= (1ll << 31)) return fail(CRP_ERR_INVALID_ARG, "capacity out of range");
     if (capacity <= s->capacity) return CRP_OK;
@@ -717,9 +749,9 @@ int crp_sim_reserve(crp_sim* s, int64_t capacity) {
     rc = alloc_state(ns, capacity);
     if (rc) return rc;
     int32_t *l0 = nullptr, *l1 = nullptr, *dl = nullptr;
-    cudaError_t e = cudaMalloc(&l0, sizeof(int32_t) * capacity);
-    if (e == cudaSuccess) e = cudaMalloc(&l1, sizeof(int32_t) * capacity);
-    if (e == cudaSuccess) e = cudaMalloc(&dl, sizeof(int32_t) * capacity);
+    cudaError_t e = dev_malloc(&l0, sizeof(int32_t) * capacity);
+    if (e == cudaSuccess) e = dev_malloc(&l1, sizeof(int32_t) * capacity);
+    if (e == cudaSuccess) e = dev_malloc(&dl, sizeof(int32_t) * capacity);
     for (int c = 0; c < CRP_N_COLS && e == cudaSuccess; ++c)
         e = cudaMemcpy(*col_ptr(ns, c), *col_ptr(s->st, c), (size_t)h.n_used * kCols[c].size,
                        cudaMemcpyDeviceToDevice);
@@ -745,6 +777,7 @@ int crp_sim_reserve(crp_sim* s, int64_t capacity) {
 }
 
 int crp_source_inject(crp_sim* s, const crp_particles* p, int64_t n, void* stream) {
+    NvtxRange nvtx_("crp_source_inject");
     if (!s || !p) return fail(CRP_ERR_INVALID_ARG, "sim or particles is NULL");
     if (n < 0) return fail(CRP_ERR_INVALID_ARG, "n < 0");
     if (n == 0) return CRP_OK;
@@ -795,6 +828,7 @@ int crp_source_inject(crp_sim* s, const crp_particles* p, int64_t n, void* strea
 int crp_source_sample(crp_sim* s, const crp_spectrum* sp, const double* x, const double* y,
                       const double* z, const int32_t* grid_id, int32_t is_device, int64_t n,
                       void* stream) {
+    NvtxRange nvtx_("crp_source_sample");
     if (!s || !sp) return fail(CRP_ERR_INVALID_ARG, "sim or spectrum is NULL");
     if (n < 0) return fail(CRP_ERR_INVALID_ARG, "n < 0");
     if (n == 0) return CRP_OK;
@@ -850,6 +884,7 @@ int crp_source_sample(crp_sim* s, const crp_spectrum* sp, const double* x, const
 }
 
 int crp_healpix_ring(int32_t nside, const double* u, int64_t n, int64_t* pix, void* stream) {
+    NvtxRange nvtx_("crp_healpix_ring");
     if (nside < 1 || nside > 8192) return fail(CRP_ERR_INVALID_ARG, "nside outside [1, 8192]");
     if (n < 0) return fail(CRP_ERR_INVALID_ARG, "n < 0");
     if (n == 0) return CRP_OK;
@@ -860,6 +895,7 @@ int crp_healpix_ring(int32_t nside, const double* u, int64_t n, int64_t* pix, vo
 }
 
 int crp_arrival_map(crp_sim* s, int32_t nside, double e_min_ev, uint64_t* map, void* stream) {
+    NvtxRange nvtx_("crp_arrival_map");
     if (!s || !map) return fail(CRP_ERR_INVALID_ARG, "sim or map is NULL");
     if (nside < 1 || nside > 8192) return fail(CRP_ERR_INVALID_ARG, "nside outside [1, 8192]");
     if (e_min_ev != e_min_ev) return fail(CRP_ERR_INVALID_ARG, "e_min is NaN");
@@ -871,6 +907,48 @@ int crp_arrival_map(crp_sim* s, int32_t nside, double e_min_ev, uint64_t* map, v
 }
 
 }  // extern "C"
+
+extern "C" {
+
+int crp_debug_fail_allocations(int32_t n) {
+    if (n < 0) return fail(CRP_ERR_INVALID_ARG, "n < 0");
+    g_fail_allocs.store(n);
+    return CRP_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Waits on a device flag with the scheduler's bounded wait; *status = 1 if the wait ran out.
+__global__ void k_selftest_wait(int32_t* flag, int limit, int* status) {
+    int32_t v = -1;
+    *status = bounded_acquire_wait(flag, limit, v) ? 0 : 1;
+}
+
+}  // namespace
+
+extern "C" int crp_selftest_wait(int32_t limit, int32_t preset, void* stream) {
+    NvtxRange nvtx_("crp_selftest_wait");
+    if (limit < 1) return fail(CRP_ERR_INVALID_ARG, "limit must be >= 1");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int32_t* flag = nullptr;
+    CRP_CUDA(dev_malloc(&flag, 2 * sizeof(int32_t)));
+    int* status = reinterpret_cast<int*>(flag + 1);
+    const int32_t init[2] = {preset, -1};
+    cudaError_t e = cudaMemcpyAsync(flag, init, sizeof init, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        k_selftest_wait<<<1, 1, 0, st>>>(flag, limit, status);
+        e = cudaGetLastError();
+    }
+    int h = -1;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, status, sizeof h, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(flag);
+    if (e != cudaSuccess) return cuda_fail(e, "crp_selftest_wait");
+    if (h == 1) return fail(CRP_ERR_TIMEOUT, "self-test wait limit reached (expected when the flag is never set)");
+    return CRP_OK;
+}
 
 struct crp_lens {
     int n_pix = 0, n_mat = 0, group = 32;
@@ -887,6 +965,7 @@ extern "C" {
 
 int crp_lens_create(int32_t n_pix, int32_t n_mat, const int64_t* row_ptr, const int32_t* col,
                     const float* val, const double* edges, crp_lens** out) {
+    NvtxRange nvtx_("crp_lens_create");
     if (!out) return fail(CRP_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (n_pix < 1 || n_mat < 1) return fail(CRP_ERR_INVALID_ARG, "n_pix and n_mat must be >= 1");
@@ -942,7 +1021,7 @@ int crp_lens_create(int32_t n_pix, int32_t n_mat, const int64_t* row_ptr, const 
     const size_t b_e = edges ? (size_t)(n_mat + 1) * 8 : 0;
     auto up = [](size_t v) { return (v + 255) / 256 * 256; };
     crp_lens* L = new crp_lens();
-    cudaError_t e = cudaMalloc(&L->mem, up(b_rp) + up(b_rl) + up(b_col) + up(b_val) + up(b_e) + 256);
+    cudaError_t e = dev_malloc(&L->mem, up(b_rp) + up(b_rl) + up(b_col) + up(b_val) + up(b_e) + 256);
     if (e != cudaSuccess) { delete L; return cuda_fail(e, "cudaMalloc(lens)"); }
     char* base = (char*)L->mem;
     size_t off = 0;
@@ -980,6 +1059,7 @@ int crp_lens_destroy(crp_lens* L) {
 }
 
 int crp_lens_apply(const crp_lens* L, const double* x, double* y, int32_t n_maps, void* stream) {
+    NvtxRange nvtx_("crp_lens_apply");
     if (!L || !x || !y) return fail(CRP_ERR_INVALID_ARG, "lens, x or y is NULL");
     if (n_maps < 1) return fail(CRP_ERR_INVALID_ARG, "n_maps must be >= 1");
     int e = launch_lens_apply(L->n_pix, n_maps, L->group, L->rp, L->rl, L->col, L->val, x, y, device_sms(), stream);
@@ -988,6 +1068,7 @@ int crp_lens_apply(const crp_lens* L, const double* x, double* y, int32_t n_maps
 }
 
 int crp_lens_bin(const crp_lens* L, crp_sim* s, int32_t nside, double e_min_ev, double* x, void* stream) {
+    NvtxRange nvtx_("crp_lens_bin");
     if (!L || !s || !x) return fail(CRP_ERR_INVALID_ARG, "lens, sim or x is NULL");
     if (!L->edges) return fail(CRP_ERR_INVALID_ARG, "lens has no rigidity edges");
     if (nside < 1 || nside > 8192 || 12ll * nside * nside != L->n_pix)
@@ -1010,7 +1091,7 @@ int field_fp64_desc(crp_field* f, FieldDev& out) {
     if (f->dev.layout == LAYOUT_F64X4) { out = f->dev; return CRP_OK; }
     if (!f->mem64) {
         void* m = nullptr;
-        CRP_CUDA(cudaMalloc(&m, (size_t)f->nodes * 32));
+        CRP_CUDA(dev_malloc(&m, (size_t)f->nodes * 32));
         k_widen<<<grid_for(f->nodes, 256, 65535), 256>>>(f->mem, f->dev.layout, f->dev.scale,
                                                          (double2*)m, f->nodes);
         cudaError_t e = cudaGetLastError();
@@ -1043,7 +1124,7 @@ int ensure_fp64_fields(crp_sim* s) {
         d64.push_back(F);
     }
     void* d = nullptr;
-    CRP_CUDA(cudaMalloc(&d, sizeof(FieldDev) * d64.size()));
+    CRP_CUDA(dev_malloc(&d, sizeof(FieldDev) * d64.size()));
     cudaError_t e = cudaMemcpy(d, d64.data(), sizeof(FieldDev) * d64.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { cudaFree(d); return cuda_fail(e, "cudaMemcpy(fields64)"); }
     s->d_fields64 = (FieldDev*)d;
@@ -1184,6 +1265,7 @@ extern "C" {
 
 int crp_propagate(crp_sim* s, const crp_params* prm, double tol, double hmin, double hmax,
                   double dmax, void* stream) {
+    NvtxRange nvtx_("crp_propagate");
     Plan P;
     int rc = make_plan(s, prm, tol, hmin, hmax, dmax, P);
     if (rc) return rc;
@@ -1196,6 +1278,7 @@ int crp_propagate(crp_sim* s, const crp_params* prm, double tol, double hmin, do
 
 int crp_propagate_loop(crp_sim* s, const crp_params* prm, double tol, double hmin, double hmax,
                        double dmax, int32_t max_slices, void* stream) {
+    NvtxRange nvtx_("crp_propagate_loop");
     Plan P;
     int rc = make_plan(s, prm, tol, hmin, hmax, dmax, P);
     if (rc) return rc;
@@ -1249,6 +1332,7 @@ int crp_propagate_loop(crp_sim* s, const crp_params* prm, double tol, double hmi
 }
 
 int crp_sync(crp_sim* s, double timeout_s) {
+    NvtxRange nvtx_("crp_sync");
     if (!s) return fail(CRP_ERR_INVALID_ARG, "sim is NULL");
     if (timeout_s > 0) {
         const auto t0 = std::chrono::steady_clock::now();
@@ -1296,6 +1380,7 @@ int crp_sim_counts(crp_sim* s, int64_t counts[8]) {
 
 int crp_read_state(crp_sim* s, int32_t column, void* dst, int32_t dst_is_device, int64_t first,
                    int64_t count) {
+    NvtxRange nvtx_("crp_read_state");
     if (!s || !dst) return fail(CRP_ERR_INVALID_ARG, "NULL argument");
     if (column < 0 || column >= CRP_N_COLS) return fail(CRP_ERR_INVALID_ARG, "unknown column");
     if (first < 0 || count < 0 || first + count > s->capacity)
@@ -1309,6 +1394,7 @@ int crp_read_state(crp_sim* s, int32_t column, void* dst, int32_t dst_is_device,
 }
 
 int crp_observe(crp_sim* s, const crp_observer* o, int64_t first, int64_t capacity, int64_t* n_out) {
+    NvtxRange nvtx_("crp_observe");
     if (!s || !o || !n_out) return fail(CRP_ERR_INVALID_ARG, "NULL argument");
     if (first < 0 || capacity < 0) return fail(CRP_ERR_INVALID_ARG, "negative range");
     *n_out = 0;
@@ -1325,7 +1411,7 @@ int crp_observe(crp_sim* s, const crp_observer* o, int64_t first, int64_t capaci
     if (!o->is_device) {   // gather on the device into one staging block, then copy out
         size_t off = 0;
         const size_t sz8 = (size_t)n * 8, sz4 = (size_t)n * 4;
-        CRP_CUDA(cudaMalloc(&tmp, 13 * sz8 + 4 * sz4 + 2 * sz8));
+        CRP_CUDA(dev_malloc(&tmp, 13 * sz8 + 4 * sz4 + 2 * sz8));
         char* b = (char*)tmp;
         auto take8 = [&](void* want) -> void* { if (!want) return nullptr; void* r = b + off; off += sz8; return r; };
         auto take4 = [&](void* want) -> void* { if (!want) return nullptr; void* r = b + off; off += sz4; return r; };
@@ -1385,6 +1471,7 @@ extern "C" int crp_propagate_noalloc(const void* grid, int32_t nx, int32_t ny, i
                                      const crp_state_columns* cols, int64_t n, uint64_t seed,
                                      double tol, double hmin, double hmax, double dmax,
                                      int64_t max_steps, void* stream) {
+    NvtxRange nvtx_("crp_propagate_noalloc");
     if (!grid || !origin_m || !cols) return fail(CRP_ERR_INVALID_ARG, "NULL argument");
     if (n < 0 || n > CRP_NOALLOC_MAX_PARTICLES)
         return fail(CRP_ERR_INVALID_ARG, "n outside [0, CRP_NOALLOC_MAX_PARTICLES]");
@@ -1505,6 +1592,7 @@ void adj_free(crp_adjoint* a) {
 extern "C" {
 
 int crp_adjoint_create(const crp_field* field, int64_t n, int32_t n_steps, int32_t K, crp_adjoint** out) {
+    NvtxRange nvtx_("crp_adjoint_create");
     if (!out) return fail(CRP_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!field || n < 1 || n_steps < 1 || K < 1) return fail(CRP_ERR_INVALID_ARG, "need field, n >= 1, n_steps >= 1, checkpoint_every >= 1");
@@ -1521,10 +1609,10 @@ int crp_adjoint_create(const crp_field* field, int64_t n, int32_t n_steps, int32
         {&a->y0_bar, 6 * (size_t)n}, {&a->kappa_bar, (size_t)n}, {&a->y0_tmp, 6 * (size_t)n},
         {&a->kappa_tmp, (size_t)n}, {&a->E_tmp, (size_t)n}};
     for (auto& q : al) {
-        cudaError_t e = cudaMalloc(q.p, q.count * sizeof(double));
+        cudaError_t e = dev_malloc(q.p, q.count * sizeof(double));
         if (e != cudaSuccess) { adj_free(a); delete a; return cuda_fail(e, "cudaMalloc(adjoint)"); }
     }
-    cudaError_t e = cudaMalloc(&a->Z, sizeof(int32_t) * n);
+    cudaError_t e = dev_malloc(&a->Z, sizeof(int32_t) * n);
     if (e != cudaSuccess) { adj_free(a); delete a; return cuda_fail(e, "cudaMalloc(adjoint Z)"); }
     FieldDev F;
     int rc = field_fp64_desc(a->field, F);
@@ -1543,6 +1631,7 @@ int crp_adjoint_destroy(crp_adjoint* a) {
 
 int crp_adjoint_forward(crp_adjoint* a, const double* x0, const double* p0, const int32_t* Z,
                         double tol, double hmin, double hmax, double* xT, double* uT, void* stream) {
+    NvtxRange nvtx_("crp_adjoint_forward");
     if (!a || !x0 || !p0 || !Z || !xT || !uT) return fail(CRP_ERR_INVALID_ARG, "NULL argument");
     if (!(tol > 0.0) || !(hmin > 0.0) || !(hmax >= hmin) || !std::isfinite(hmax))
         return fail(CRP_ERR_INVALID_ARG, "need tolerance > 0 and 0 < min_step <= max_step");
@@ -1561,6 +1650,7 @@ int crp_adjoint_forward(crp_adjoint* a, const double* x0, const double* p0, cons
 
 int crp_adjoint_replay(crp_adjoint* a, const crp_field* field, const double* p0, double* xT,
                        double* uT, uint64_t* cell_hash, void* stream) {
+    NvtxRange nvtx_("crp_adjoint_replay");
     if (!a || !xT || !uT) return fail(CRP_ERR_INVALID_ARG, "NULL argument");
     if (!a->recorded) return fail(CRP_ERR_INVALID_ARG, "no recorded forward pass");
     crp_field* f = field ? const_cast<crp_field*>(field) : a->field;
@@ -1587,6 +1677,7 @@ int crp_adjoint_replay(crp_adjoint* a, const crp_field* field, const double* p0,
 
 int crp_adjoint_backward(crp_adjoint* a, const double* uT_bar, double* grid_bar, double* p0_bar,
                          double* x0_bar, void* stream) {
+    NvtxRange nvtx_("crp_adjoint_backward");
     if (!a || !uT_bar || !grid_bar || !p0_bar) return fail(CRP_ERR_INVALID_ARG, "NULL argument");
     if (!a->recorded) return fail(CRP_ERR_INVALID_ARG, "no recorded forward pass");
     FieldDev F;

@@ -20,6 +20,18 @@ __device__ __forceinline__ unsigned long long ld_volatile(const unsigned long lo
     return *(volatile const unsigned long long*)p;
 }
 
+// Waits, at most `limit` times 64 ns, for a non-negative value to be published at p (acquire
+// loads). Returns false if it never appeared; the caller turns that into a status bit.
+__device__ __forceinline__ bool bounded_acquire_wait(int32_t* p, int limit, int32_t& v) {
+    cuda::atomic_ref<int32_t, cuda::thread_scope_device> e(*p);
+    for (int t = 0; t < limit; ++t) {
+        v = e.load(cuda::memory_order_acquire);
+        if (v >= 0) return true;
+        __nanosleep(64);
+    }
+    return false;
+}
+
 // Append slot q to the list the launch pushes into (secondaries).
 __device__ __forceinline__ void sched_push(const PropArgs& a, int32_t q) {
     const int L = 1 - a.list;
@@ -70,15 +82,13 @@ __device__ __forceinline__ int sched_pop(const PropArgs& a, bool idle, int lane,
         if (v < 0 || v >= a.capacity) { bits |= BIT_BOUNDS; return -1; }
         return v;
     }
-    cuda::atomic_ref<int32_t, cuda::thread_scope_device> e(a.lists[P][pos]);
-    for (int t = 0; t < kPublishWaitLimit; ++t) {
-        const int32_t v = e.load(cuda::memory_order_acquire);
-        if (v >= a.capacity) { bits |= BIT_BOUNDS; return -1; }
-        if (v >= 0) return v;
-        __nanosleep(64);
+    int32_t v = -1;
+    if (!bounded_acquire_wait(a.lists[P] + pos, kPublishWaitLimit, v)) {
+        bits |= BIT_TIMEOUT;   // the entry never appeared: reported by crp_sync
+        return -1;
     }
-    bits |= BIT_TIMEOUT;       // the entry never appeared: reported by crp_sync
-    return -1;
+    if (v >= a.capacity) { bits |= BIT_BOUNDS; return -1; }
+    return v;
 }
 
 }  // namespace crp

@@ -89,6 +89,9 @@ def test_null_and_range_arguments_rejected_before_device_work(L):
     assert L.crp_lens_create(2, 1, rp.ctypes.data, cl.ctypes.data, vl.ctypes.data, ed.ctypes.data, C.byref(h)) == -1
     assert L.crp_lens_apply(None, xs.ctypes.data, xs.ctypes.data, 1, None) == -1
     assert L.crp_lens_destroy(None) == -1
+    assert L.crp_debug_fail_allocations(-1) == -1
+    assert L.crp_debug_fail_allocations(0) == 0
+    assert L.crp_selftest_wait(0, -1, None) == -1                            # limit < 1
     assert L.crp_sim_create(None, 0, None, 1, 10, C.byref(h)) == -1
     assert L.crp_tables_create(1, 1, 1, 6.0, 25.0, None, None, None, None, C.byref(h)) == -1
     assert L.crp_propagate(None, None, 1e-4, 1.0, 2.0, 3.0, None) == -1
