@@ -180,7 +180,7 @@ def density_field(n: int, lmin_cells: float, lmax_cells: float, sigma_ln: float,
     k = np.sqrt(k1[:, None, None] ** 2 + k1[None, :, None] ** 2 + kz[None, None, :] ** 2)
     F *= _band_filter(k, n, lmin_cells, lmax_cells, -1.0)
     del k
-    G = np.fft.irfftn(F, s=(n, n, n))
+    G = np.fft.irfftn(F, s=(n, n, n), axes=(0, 1, 2))
     del F
     G /= G.std()
     rho = np.exp(sigma_ln * G - 0.5 * sigma_ln * sigma_ln)
