@@ -270,7 +270,10 @@ int crp_observe(crp_sim* sim, const crp_observer* out, int64_t first, int64_t ca
  * checkpoint. Initial momenta p0 are in eV/c: E = |p0|, u0 = p0/E, kappa = Z c / E.
  * All array arguments are device pointers; [n][3] arrays are row-major.
  * Memory owned by the handle: 8 B x n x (n_steps + 6 (n_steps / checkpoint_every + 1) +
- * 6 (checkpoint_every + 1) + 20). */
+ * 6 (checkpoint_every + 1) + 20), plus 8 B x 36 x n x n_steps for the stage states of every
+ * step when that fits in half of the device's free memory at creation (then the backward pass
+ * recomputes all checkpoint segments in parallel; otherwise one segment at a time; the
+ * results are the same). */
 typedef struct crp_adjoint crp_adjoint;
 int crp_adjoint_create(const crp_field* field, int64_t n, int32_t n_steps,
                        int32_t checkpoint_every, crp_adjoint** out);

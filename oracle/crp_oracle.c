@@ -739,7 +739,7 @@ static void lookup_full(const orc_field* f, const double x[3], orc_lookup* L)
                 L->node[c8] = (idx[0][a] * f->ny + idx[1][b]) * f->nz + idx[2][c];
                 for (int q = 0; q < 3; ++q) {
                     L->G[c8][q] = grid_at(f, idx[0][a], idx[1][b], idx[2][c], q);
-                    L->B[q] = L->B[q] + wt * L->G[c8][q];
+                    L->B[q] = fma(wt, L->G[c8][q], L->B[q]);     /* as orc_field_value */
                 }
             }
 }

@@ -3,8 +3,9 @@
 //
 // A forward pass with the adaptive Cash-Karp controller records the accepted step sizes
 // h_n and checkpoints y = (x, u) every K steps. The map y_{n+1} = y_n + h_n sum_i b_i k_i
-// is then differentiated exactly for fixed h_n: per segment of K steps the states are
-// recomputed from the checkpoint, and the steps are reversed stage by stage with the
+// is then differentiated exactly for fixed h_n: the states are recomputed from the
+// checkpoints (all segments in parallel into a stage-state buffer when the device has room,
+// else one segment at a time per particle), and the steps are reversed stage by stage with the
 // vector-Jacobian product of f(y) = (u, kappa u x B(x)), which also yields dL/dkappa and
 // scatters dL/dB into the grid gradient through the trilinear weights (FP64 atomics).
 // Compiled with --fmad=false; per-particle arithmetic follows the oracle's order.
@@ -139,9 +140,9 @@ __device__ __forceinline__ void lookup_full(const FieldDev& F, const Y6& Y, doub
                 node[c8] = (ix[a] * F.ny + iy[b]) * F.nz + iz[c];
                 const V3 g = corner<L>(F, node[c8]);
                 G[c8][0] = g.x; G[c8][1] = g.y; G[c8][2] = g.z;
-                B[0] = B[0] + wt * g.x;
-                B[1] = B[1] + wt * g.y;
-                B[2] = B[2] + wt * g.z;
+                B[0] = __fma_rn(wt, g.x, B[0]);      // as the forward lookup
+                B[1] = __fma_rn(wt, g.y, B[1]);
+                B[2] = __fma_rn(wt, g.z, B[2]);
             }
 }
 
@@ -201,21 +202,26 @@ __constant__ double cA[6][5] = {
     {1631.0 / 55296.0, 175.0 / 512.0, 575.0 / 13824.0, 44275.0 / 110592.0, 253.0 / 4096.0}};
 __constant__ double cB5[6] = {37.0 / 378.0, 0.0, 250.0 / 621.0, 125.0 / 594.0, 0.0, 512.0 / 1771.0};
 
-// One reverse step: lam = dL/dy_{m+1} in, dL/dy_m out; y = y_m.
+// The six stage states Y_0 = y_m, ..., Y_5 of step m (the forward stage sums: acc = A[i][0]
+// k1, then fused A[i][j] k_j for j < i; y + h acc fused).
 template <int L>
-__device__ void adjoint_step(const FieldDev& F, double kappa, const Y6& y, double hn, Y6& lam,
-                             double* __restrict__ grid_bar, double& kappa_bar) {
-    Y6 Y[6], k[6];
+__device__ __forceinline__ void stage_states(const FieldDev& F, double kappa, const Y6& y, double hn, Y6 (&Y)[6]) {
+    Y6 k[6];
     Y[0] = y;
     k[0] = deriv<L>(F, kappa, y);
     for (int i = 1; i < 6; ++i) {
-        // the forward stage sums: acc = A[i][0] k1, then fused A[i][j] k_j (j < i); y + h acc fused
         Y6 acc = scale6(cA[i][0], k[0]);
         for (int j = 1; j < i; ++j) fmaxpy6(acc, cA[i][j], k[j]);
         Y[i] = {__fma_rn(hn, acc.x, y.x), __fma_rn(hn, acc.y, y.y), __fma_rn(hn, acc.z, y.z),
                 __fma_rn(hn, acc.ux, y.ux), __fma_rn(hn, acc.uy, y.uy), __fma_rn(hn, acc.uz, y.uz)};
-        k[i] = deriv<L>(F, kappa, Y[i]);
+        if (i < 5) k[i] = deriv<L>(F, kappa, Y[i]);
     }
+}
+
+// One reverse step from the stage states: lam = dL/dy_{m+1} in, dL/dy_m out.
+template <int L>
+__device__ void reverse_step(const FieldDev& F, double kappa, const Y6 (&Y)[6], double hn, Y6& lam,
+                             double* __restrict__ grid_bar, double& kappa_bar) {
     Y6 kb[6];
     for (int i = 0; i < 6; ++i) kb[i] = scale6(hn * cB5[i], lam);
     Y6 yb = lam;
@@ -226,6 +232,59 @@ __device__ void adjoint_step(const FieldDev& F, double kappa, const Y6& y, doubl
         for (int j = 0; j < i; ++j) axpy6(kb[j], hn * cA[i][j], Yb);
     }
     lam = yb;
+}
+
+template <int L>
+__device__ __forceinline__ void adjoint_step(const FieldDev& F, double kappa, const Y6& y, double hn, Y6& lam,
+                                             double* __restrict__ grid_bar, double& kappa_bar) {
+    Y6 Y[6];
+    stage_states<L>(F, kappa, y, hn, Y);
+    reverse_step<L>(F, kappa, Y, hn, lam, grid_bar, kappa_bar);
+}
+
+// Stage states of every step, all segments at once: thread (particle i, segment sg)
+// recomputes its segment from the checkpoint and stores Y_0..Y_5 of each step at
+// stages[((m * 6 + s) * 6 + c) * n + i]. The reverse sweep then only reads them.
+template <int L>
+__global__ void k_adj_stages(FieldDev F, const double* __restrict__ kap, const double* __restrict__ h,
+                             const double* __restrict__ ck, double* __restrict__ stages, int n_steps,
+                             int K, long long n) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int n_seg = (n_steps + K - 1) / K;
+    if (t >= n * n_seg) return;
+    const long long i = t % n;
+    const int sg = (int)(t / n);
+    const double kappa = kap[i];
+    const int m0 = sg * K, m1 = min(m0 + K, n_steps);
+    Y6 y;
+    load6(ck + (long long)sg * 6 * n, n, i, y);
+    for (int m = m0; m < m1; ++m) {
+        const double hm = h[(long long)m * n + i];
+        Y6 Y[6];
+        stage_states<L>(F, kappa, y, hm, Y);
+        for (int q = 0; q < 6; ++q) store6(stages + (long long)(m * 6 + q) * 6 * n, n, i, Y[q]);
+        frozen_step<L>(F, kappa, y, hm);
+    }
+}
+
+// Reverse sweep over stored stage states, one thread per particle.
+template <int L>
+__global__ void k_adj_reverse(FieldDev F, const double* __restrict__ kap, const double* __restrict__ h,
+                              const double* __restrict__ stages, int n_steps, const double* __restrict__ uT_bar,
+                              double* __restrict__ grid_bar, double* __restrict__ y0_bar,
+                              double* __restrict__ kappa_bar_out, long long n) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double kappa = kap[i];
+    Y6 lam{0.0, 0.0, 0.0, uT_bar[3 * i], uT_bar[3 * i + 1], uT_bar[3 * i + 2]};
+    double kappa_bar = 0.0;
+    for (int m = n_steps - 1; m >= 0; --m) {
+        Y6 Y[6];
+        for (int q = 0; q < 6; ++q) load6(stages + (long long)(m * 6 + q) * 6 * n, n, i, Y[q]);
+        reverse_step<L>(F, kappa, Y, h[(long long)m * n + i], lam, grid_bar, kappa_bar);
+    }
+    store6(y0_bar, n, i, lam);
+    kappa_bar_out[i] = kappa_bar;
 }
 
 template <int L>
@@ -311,8 +370,18 @@ int adj_replay(const FieldDev& F, const double* y0, const double* kappa, const d
 }
 
 int adj_backward(const FieldDev& F, const double* kappa, const double* h, const double* ck,
-                 double* seg, int n_steps, int K, const double* uT_bar, double* grid_bar,
+                 double* seg, double* stages, int n_steps, int K, const double* uT_bar, double* grid_bar,
                  double* y0_bar, double* kappa_bar, long long n, void* stream) {
+    if (stages) {       // all segments recomputed at once, then the reverse sweep reads them
+        const long long threads = n * ((n_steps + K - 1) / K);
+        k_adj_stages<LAYOUT_F64X4><<<blocks(threads), 128, 0, (cudaStream_t)stream>>>(
+            F, kappa, h, ck, stages, n_steps, K, n);
+        const int e = (int)cudaGetLastError();
+        if (e) return e;
+        k_adj_reverse<LAYOUT_F64X4><<<blocks(n), 128, 0, (cudaStream_t)stream>>>(
+            F, kappa, h, stages, n_steps, uT_bar, grid_bar, y0_bar, kappa_bar, n);
+        return (int)cudaGetLastError();
+    }
     k_adj_backward<LAYOUT_F64X4><<<blocks(n), 128, 0, (cudaStream_t)stream>>>(
         F, kappa, h, ck, seg, n_steps, K, uT_bar, grid_bar, y0_bar, kappa_bar, n);
     return (int)cudaGetLastError();

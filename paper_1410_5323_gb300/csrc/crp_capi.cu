@@ -1573,6 +1573,7 @@ struct crp_adjoint {
     double *y0 = nullptr, *kappa = nullptr, *E = nullptr, *h = nullptr, *ck = nullptr;
     double *seg = nullptr, *y0_bar = nullptr, *kappa_bar = nullptr, *y0_tmp = nullptr;
     double *kappa_tmp = nullptr, *E_tmp = nullptr;
+    double* stages = nullptr;            // [n_steps][6 stages][6][n] stage states, if room
     int32_t* Z = nullptr;
     bool recorded = false;
 };
@@ -1581,7 +1582,7 @@ namespace {
 
 void adj_free(crp_adjoint* a) {
     double* ds[] = {a->y0, a->kappa, a->E, a->h, a->ck, a->seg, a->y0_bar, a->kappa_bar, a->y0_tmp,
-                    a->kappa_tmp, a->E_tmp};
+                    a->kappa_tmp, a->E_tmp, a->stages};
     for (double* p : ds)
         if (p) cudaFree(p);
     if (a->Z) cudaFree(a->Z);
@@ -1617,6 +1618,16 @@ int crp_adjoint_create(const crp_field* field, int64_t n, int32_t n_steps, int32
     FieldDev F;
     int rc = field_fp64_desc(a->field, F);
     if (rc) { adj_free(a); delete a; return rc; }
+    // stage states of all steps (36 doubles per step and particle) when they fit in half of
+    // the free memory: the reverse pass then recomputes every segment in parallel
+    size_t free_b = 0, total_b = 0;
+    const size_t st_bytes = (size_t)36 * sizeof(double) * (size_t)n_steps * (size_t)n;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && st_bytes <= free_b / 2) {
+        if (dev_malloc(&a->stages, st_bytes) != cudaSuccess) {
+            a->stages = nullptr;
+            cudaGetLastError();
+        }
+    }
     *out = a;
     return CRP_OK;
 }
@@ -1684,7 +1695,7 @@ int crp_adjoint_backward(crp_adjoint* a, const double* uT_bar, double* grid_bar,
     int rc = field_fp64_desc(a->field, F);
     if (rc) return rc;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    int e = adj_backward(F, a->kappa, a->h, a->ck, a->seg, a->n_steps, a->K, uT_bar, grid_bar,
+    int e = adj_backward(F, a->kappa, a->h, a->ck, a->seg, a->stages, a->n_steps, a->K, uT_bar, grid_bar,
                          a->y0_bar, a->kappa_bar, a->n, st);
     if (e) return cuda_fail((cudaError_t)e, "adjoint backward");
     e = adj_p0bar(a->y0, a->kappa, a->E, a->y0_bar, a->kappa_bar, p0_bar, x0_bar, a->n, st);

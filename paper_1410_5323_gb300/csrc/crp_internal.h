@@ -131,7 +131,7 @@ int adj_record(const FieldDev& F, const double* y0, const double* kappa, double 
 int adj_replay(const FieldDev& F, const double* y0, const double* kappa, const double* h, int n_steps,
                double* xT, double* uT, unsigned long long* cell_hash, long long n, void* stream);
 int adj_backward(const FieldDev& F, const double* kappa, const double* h, const double* ck,
-                 double* seg, int n_steps, int K, const double* uT_bar, double* grid_bar,
+                 double* seg, double* stages, int n_steps, int K, const double* uT_bar, double* grid_bar,
                  double* y0_bar, double* kappa_bar, long long n, void* stream);
 int adj_p0bar(const double* y0, const double* kappa, const double* E, const double* y0_bar,
               const double* kappa_bar, double* p0_bar, double* x0_bar, long long n, void* stream);
