@@ -682,7 +682,7 @@ def run_adjoint(args):
         "config": {"workload": w.name, "particles": n, "frozen_steps": n_steps, "checkpoint_every": K,
                    "grid": f"{w.grid_n}^3 f32 (read as its FP64 copy)"},
         "forward_ms": sum(fwd_ms) / args.steps, "backward_ms": sum(bwd_ms) / args.steps,
-        "gpu_launches": 2 + 2 * args.steps,
+        "gpu_launches": 5 * args.steps,     # init + record; stage recompute + reverse + p0 gradient
     }
     print(json.dumps(line), flush=True)
     return 0

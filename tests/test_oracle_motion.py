@@ -131,3 +131,22 @@ def test_error_ratio_definition(oracle_lib):
     err = np.array([3.0, 4.0, 0.0, 0.0, 0.0, 2e-3])
     assert oracle_lib.error_ratio(err, 1000.0, 1e-4) == pytest.approx(max(5.0 / 1000.0, 2e-3) / 1e-4, rel=1e-15)
     assert oracle_lib.error_ratio(np.zeros(6), 0.0, 1e-4) == 0.0
+
+
+def test_fixed_step_global_error_is_fifth_order(oracle_lib):
+    """Steps forced to a fixed h (h_min = h_max = h: every attempt is accepted) over one full
+    gyration: the error of the returned position against the closed-form circle falls as h^5
+    (fitted slope 5 +- 0.3), the global order of the propagated 5th-order solution."""
+    rg = gyro_radius(E19, 1, B0)
+    dmax = 2 * math.pi * rg
+    hs, errs = [], []
+    for n_steps in (20, 40, 80, 160):
+        h = dmax / n_steps
+        st, rc, _ = run(particles([1, 0, 0], E19), uniform_grid([0, 0, B0]), I.MPC, dmax, tol=1.0,
+                        hmin=h, hmax=h)
+        assert rc == 0 and st.status[0] == O.DONE
+        assert abs(int(st.n_steps[0]) - n_steps) <= 1
+        hs.append(h)
+        errs.append(math.hypot(math.hypot(st.x[0], st.y[0]), st.z[0]))
+    slope = np.polyfit(np.log(hs), np.log(errs), 1)[0]
+    assert abs(slope - 5.0) < 0.3, (slope, errs)
