@@ -345,6 +345,58 @@ def mixed_error_statement(w, mixed_state, oracle_state):
             "note": "per-particle angles are chaotic beyond ~15 Mpc (1-ulp floor); see DESIGN.md"}
 
 
+def angle_deg(a, b):
+    c = np.cross(a, b)
+    return np.degrees(np.arctan2(np.linalg.norm(c, axis=1), np.sum(a * b, axis=1)))
+
+
+def precision_error_by_distance(crp, w, grids, tables, parts, sample: int,
+                                distances_mpc=(1.0, 2.0, 5.0, 10.0, 20.0)):
+    """Arrival-direction error of the precision form against the FP64 form on the GPU, per
+    primary, at several distances, next to the chaos floor (the FP64 form against itself with
+    u0 moved by one ulp in x). Each distance is a fresh run of the first `sample` primaries."""
+    sub = parts.take(np.arange(min(sample, len(parts))))
+    bumped = sub.take(np.arange(len(sub)))
+    bumped.u[:, 0] = np.nextafter(bumped.u[:, 0], 2.0)
+    fields = [g.field(crp, w.spacing_m) for g in grids]
+    tabs = crp.Tables(tables) if tables is not None else None
+    box = I.workload_box(w)
+    out = {"sample_primaries": len(sub), "distances_mpc": list(distances_mpc), "median_deg": [], "p95_deg": [],
+           "max_deg": [], "chaos_floor_median_deg": [], "chaos_floor_p95_deg": []}
+
+    def final_u(p, form, dmax):
+        sim = crp.Simulation(fields, tabs, seed=w.rng_seed, capacity=capacity_for(p))
+        if box is not None:
+            sim.set_boundary(box)
+        if w.spectrum is not None:
+            sim.sample_sources(crp.Spectrum.of(*w.spectrum), p.x)
+        else:
+            sim.inject(p)
+        sim.propagate(w.tol, w.hmin_m, w.hmax_m, dmax, form=form)
+        sim.sync(timeout_s=600.0, raise_on_error=False)
+        d = sim.state()
+        prim = d["uid"] < 2 ** 32
+        order = np.argsort(d["uid"][prim])
+        return np.stack([d["ux"], d["uy"], d["uz"]], 1)[prim][order]
+
+    for dist in distances_mpc:
+        ref = final_u(sub, crp.FORM_FP64, dist * I.MPC)
+        mix = final_u(sub, crp.FORM_MIXED, dist * I.MPC)
+        floor_ = final_u(bumped, crp.FORM_FP64, dist * I.MPC) if w.spectrum is None else ref
+        e = angle_deg(ref, mix)
+        f = angle_deg(ref, floor_)
+        out["median_deg"].append(float(np.median(e)))
+        out["p95_deg"].append(float(np.quantile(e, 0.95)))
+        out["max_deg"].append(float(e.max()))
+        out["chaos_floor_median_deg"].append(float(np.median(f)))
+        out["chaos_floor_p95_deg"].append(float(np.quantile(f, 0.95)))
+    ok = [d for d, p95 in zip(distances_mpc, out["p95_deg"]) if p95 <= 0.1]
+    out["p95_within_0p1deg_up_to_mpc"] = max(ok) if ok else None
+    if w.spectrum is not None:
+        out["note"] = "sources drawn on the device: the chaos floor is not measured for this workload"
+    return out
+
+
 # ---------------------------------------------------------------------------------------
 def run_reference(args):
     ws, rank, _ = dist_env()
@@ -584,7 +636,9 @@ def run_own(args):
                                                        calls=args.steps, workload=w.name,
                                                        modulated=modulated)},
                  "mixed_over_fp64": (other["value"] / value) if other_form == "mixed" else (value / other["value"]),
-                 "mixed_error_vs_fp64_oracle": forms_err}
+                 "mixed_error_vs_fp64_oracle": forms_err,
+                 "mixed_error_vs_fp64_by_distance": (precision_error_by_distance(crp, w, grids, tables, parts, 16384)
+                                                     if rank == 0 and w.n_grids == 1 and w.grid_n < 512 else None)}
 
     # our kernels in the timed region: per step inject init + slot count; per propagate slice
     # prepare + work-list build (1 kernel, or 3 for the ordered builds) + 2 x (propagate + swap);
