@@ -6,7 +6,9 @@
 //   * lengths in grid-cell units; Cash-Karp stages in FP32 in a local frame: offsets from
 //     the step-start cell, so stage positions stay O(1) and FP32 keeps ~1e-7 of a cell;
 //   * the position itself is a double-float (hi + lo FP32 pair, TwoSum) in cell units,
-//     which resolves 1 kpc steps at 500 Mpc without any FP64 instruction;
+//     which resolves 1 kpc steps at 500 Mpc without any FP64 instruction; the direction
+//     is a double-float as well (its per-step increment is added with TwoSum), so rounding
+//     does not accumulate in it over thousands of steps;
 //   * the step-error norm and the accept/reject decision stay FP64: the six FP32 error
 //     components are widened and their squared norms compared against tol^2 in FP64
 //     (|dx|/h is computed as |sum_i e_i u_i|, so no division by h is needed);
@@ -269,6 +271,7 @@ __device__ __forceinline__ void propagate_mixed_body(const PropArgs& a, float* s
     // particle state (cell units)
     DF Rx{0, 0}, Ry{0, 0}, Rz{0, 0};
     F3 u{0, 0, 0};
+    F3 ul{0, 0, 0};                    // low parts of the direction (double-float, like R)
     double E = 0, s_c = 0;
     float hprop = 0, tau = 0;
     int A = 0, Z = 0, n_int = 0, gid = 0;
@@ -297,7 +300,8 @@ __device__ __forceinline__ void propagate_mixed_body(const PropArgs& a, float* s
     };
     auto store = [&](int status, bool exact_end) {
         S.x[slot] = to_x(Rx, ox); S.y[slot] = to_x(Ry, oy); S.z[slot] = to_x(Rz, oz);
-        S.ux[slot] = u.x; S.uy[slot] = u.y; S.uz[slot] = u.z;
+        S.ux[slot] = (double)u.x + (double)ul.x; S.uy[slot] = (double)u.y + (double)ul.y;
+        S.uz[slot] = (double)u.z + (double)ul.z;
         S.E[slot] = E;
         S.s[slot] = exact_end ? a.dmax : s_c * sp;
         S.hprop[slot] = (double)hprop * sp;
@@ -330,7 +334,11 @@ __device__ __forceinline__ void propagate_mixed_body(const PropArgs& a, float* s
             hmax_c = (float)(a.hmax * inv_sp);
             dmax_c = a.dmax * inv_sp;
             Rx = from_x(__ldcg(&S.x[slot]), ox); Ry = from_x(__ldcg(&S.y[slot]), oy); Rz = from_x(__ldcg(&S.z[slot]), oz);
-            u = {(float)__ldcg(&S.ux[slot]), (float)__ldcg(&S.uy[slot]), (float)__ldcg(&S.uz[slot])};
+            {
+                const double dx = __ldcg(&S.ux[slot]), dy = __ldcg(&S.uy[slot]), dz = __ldcg(&S.uz[slot]);
+                u = {(float)dx, (float)dy, (float)dz};
+                ul = {(float)(dx - (double)u.x), (float)(dy - (double)u.y), (float)(dz - (double)u.z)};
+            }
             E = __ldcg(&S.E[slot]);
             s_c = __ldcg(&S.s[slot]) * inv_sp;
             hprop = (float)(__ldcg(&S.hprop[slot]) * inv_sp);
@@ -438,7 +446,7 @@ __device__ __forceinline__ void propagate_mixed_body(const PropArgs& a, float* s
 #define SB(c) (B1 * k1.c + B3 * k3.c + B4 * k4.c + B6 * k6.c)
 #define SE(c) (E1 * k1.c + E3 * k3.c + E4 * k4.c + E5 * k5.c + E6 * k6.c)
             const F3 dp{h * SB(p.x), h * SB(p.y), h * SB(p.z)};
-            const F3 un{fmaf(h, SB(u.x), u.x), fmaf(h, SB(u.y), u.y), fmaf(h, SB(u.z), u.z)};
+            const F3 du{h * SB(u.x), h * SB(u.y), h * SB(u.z)};       // direction increment
             const F3 ex{SE(p.x), SE(p.y), SE(p.z)};                  // |dx| / h
             const F3 eu{h * SE(u.x), h * SE(u.y), h * SE(u.z)};      // |du|
 #undef STG
@@ -464,7 +472,7 @@ __device__ __forceinline__ void propagate_mixed_body(const PropArgs& a, float* s
                 rejected = 1;
                 continue;
             }
-            if (!(fin3(dp) && fin3(un))) {
+            if (!(fin3(dp) && fin3(du))) {
                 n_att += att_step;
                 att_tot += att_step;
                 bits |= BIT_NAN;
@@ -487,9 +495,14 @@ __device__ __forceinline__ void propagate_mixed_body(const PropArgs& a, float* s
             Rx = df_add(Rx, dp.x);
             Ry = df_add(Ry, dp.y);
             Rz = df_add(Rz, dp.z);
-            u = un;
+            {   // direction as a double-float: the increment is added with TwoSum
+                const DF nx = df_add(DF{u.x, ul.x}, du.x), ny = df_add(DF{u.y, ul.y}, du.y),
+                         nz = df_add(DF{u.z, ul.z}, du.z);
+                u = {nx.hi, ny.hi, nz.hi};
+                ul = {nx.lo, ny.lo, nz.lo};
+            }
             if (a.boundary) {   // reflective box, evaluated on the FP64 position
-                auto fold = [&](DF& R, double o, int ax, float& uc, double* u0col) {
+                auto fold = [&](DF& R, double o, int ax, float& uc, float& ucl, double* u0col) {
                     double xd = to_x(R, o);
                     const double lo = a.box_lo[ax], hi = a.box_hi[ax];
                     if (!(xd < lo || xd > hi)) return;
@@ -499,11 +512,11 @@ __device__ __forceinline__ void propagate_mixed_body(const PropArgs& a, float* s
                     const bool odd = fmod(k, 2.0) != 0.0;
                     xd = odd ? hi - r * a.box_len[ax] : lo + r * a.box_len[ax];
                     R = from_x(xd, o);
-                    if (odd) { uc = -uc; u0col[slot] = -u0col[slot]; }
+                    if (odd) { uc = -uc; ucl = -ucl; u0col[slot] = -u0col[slot]; }
                 };
-                fold(Rx, ox, 0, u.x, S.u0x);
-                fold(Ry, oy, 1, u.y, S.u0y);
-                fold(Rz, oz, 2, u.z, S.u0z);
+                fold(Rx, ox, 0, u.x, ul.x, S.u0x);
+                fold(Ry, oy, 1, u.y, ul.y, S.u0y);
+                fold(Rz, oz, 2, u.z, ul.z, S.u0z);
             }
             bool done = (h == h_dist);
             s_c = s_c + (double)h;
@@ -526,7 +539,8 @@ __device__ __forceinline__ void propagate_mixed_body(const PropArgs& a, float* s
                     const long long qs = (long long)q;
                     const unsigned long long uid2 = (1ull << 32) + uid * 64ull + kk;
                     S.x[qs] = to_x(Rx, ox); S.y[qs] = to_x(Ry, oy); S.z[qs] = to_x(Rz, oz);
-                    S.ux[qs] = u.x; S.uy[qs] = u.y; S.uz[qs] = u.z;
+                    S.ux[qs] = (double)u.x + (double)ul.x; S.uy[qs] = (double)u.y + (double)ul.y;
+                    S.uz[qs] = (double)u.z + (double)ul.z;
                     S.E[qs] = E_sec;
                     S.s[qs] = done ? a.dmax : s_c * sp;
                     S.hprop[qs] = __longlong_as_double(0x7ff0000000000000LL);
