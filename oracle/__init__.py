@@ -89,8 +89,15 @@ def lib():
         L.orc_modulation_value.restype = d
         L.orc_deriv.argtypes = [p, d, p, p]
         L.orc_ck_attempt.argtypes = [p, d, p, p, d, p, p]
-        L.orc_error_ratio.argtypes = [p, d, d]
-        L.orc_error_ratio.restype = d
+        L.orc_error_sums.argtypes = [p, p, p]
+        L.orc_error_accept.argtypes = [d, d, d, d]
+        L.orc_error_accept.restype = C.c_int
+        L.orc_ctrl_log2.argtypes = [d]
+        L.orc_ctrl_log2.restype = C.c_float
+        L.orc_ctrl_log2r.argtypes = [d, d, d, d]
+        L.orc_ctrl_log2r.restype = C.c_float
+        L.orc_ctrl_factor.argtypes = [C.c_float, C.c_float, C.c_float, C.c_float]
+        L.orc_ctrl_factor.restype = C.c_float
         L.orc_rates.argtypes = [p, i32, i32, d, p, p]
         L.orc_rates.restype = C.c_int
         L.orc_inject.argtypes = [p, i64, i64, u64, p]
@@ -237,9 +244,28 @@ def ck_attempt(field: OracleField, kappa: float, y, h: float):
     return y5, err
 
 
-def error_ratio(err, h: float, tol: float) -> float:
+def error_sums(err):
+    """(|dx|^2, |du|^2) of an error vector (dx, du)."""
     e = np.ascontiguousarray(err, dtype=np.float64)
-    return lib().orc_error_ratio(_ptr(e), h, tol)
+    out = np.zeros(2)
+    lib().orc_error_sums(_ptr(e), _ptr(out), _ptr(out[1:]))
+    return float(out[0]), float(out[1])
+
+
+def error_accept(sx: float, su: float, h: float, tol: float) -> bool:
+    return bool(lib().orc_error_accept(sx, su, h, tol))
+
+
+def ctrl_log2(v: float) -> float:
+    return float(lib().orc_ctrl_log2(v))
+
+
+def ctrl_log2r(sx: float, su: float, h: float, tol: float) -> float:
+    return float(lib().orc_ctrl_log2r(sx, su, h, tol))
+
+
+def ctrl_factor(log2r: float, p: float, lo: float, hi: float) -> float:
+    return float(lib().orc_ctrl_factor(log2r, p, lo, hi))
 
 
 def rates(tables: OracleTables, A: int, Z: int, E: float):

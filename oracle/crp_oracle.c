@@ -315,15 +315,86 @@ void orc_ck_attempt(const orc_field* f, double kappa, const double y[6], const d
     }
 }
 
-/* Error ratio r = max(|dx|/h, |du|) / tol with Euclidean norms ((a0^2 + a1^2) + a2^2), each
- * square after the first added with one rounding; r = 0 for a zero-length step. Accept iff
- * r <= 1. */
-double orc_error_ratio(const double err[6], double h, double tol)
+/* Error of one attempt (Sec. 3.1: a step is kept when its estimated error is within the
+ * requested accuracy), r = max(|dx|/h, |du|) / tol with Euclidean norms. The norms stay
+ * squared: sx = |dx|^2 and su = |du|^2, each ((a0^2 + a1^2) + a2^2) with every square after
+ * the first added with one rounding. */
+void orc_error_sums(const double err[6], double* sx, double* su)
 {
-    if (h == 0.0) return 0.0;
-    double ex = sqrt(fma(err[2], err[2], fma(err[1], err[1], err[0] * err[0]))) / h;
-    double eu = sqrt(fma(err[5], err[5], fma(err[4], err[4], err[3] * err[3])));
-    return fmax(ex, eu) / tol;
+    *sx = fma(err[2], err[2], fma(err[1], err[1], err[0] * err[0]));
+    *su = fma(err[5], err[5], fma(err[4], err[4], err[3] * err[3]));
+}
+
+/* r <= 1 compared as squares in FP64: sx <= (h tol)^2 and su <= tol^2, each product
+ * rounded once; a zero-length step is always accepted (r = 0). A NaN sum rejects. */
+int orc_error_accept(double sx, double su, double h, double tol)
+{
+    if (h == 0.0) return 1;
+    double ht = h * tol;
+    return sx <= ht * ht && su <= tol * tol;
+}
+
+/* ---- step-size controller (a heuristic: only its inputs and outputs are FP64) ----------
+ * log2 of a non-negative double in FP32, from its bits: the unbiased exponent e plus log2 m
+ * of the top 23 significand bits (truncated) m in [1, 2), reduced to [sqrt(1/2), sqrt(2)),
+ * with ln m = 2 atanh s = 2 (s + s^3/3 + s^5/5 + s^7/7), s = (m - 1)/(m + 1) (truncation
+ * error below 3e-8). Zero and subnormal inputs give -inf (no error), infinity and NaN +inf
+ * (an infinite error). */
+float orc_ctrl_log2(double v)
+{
+    uint64_t b;
+    memcpy(&b, &v, sizeof b);
+    int ef = (int)((b >> 52) & 0x7FFu);
+    if (ef == 0x7FF) return INFINITY;
+    if (ef == 0) return -INFINITY;
+    int e = ef - 1023;
+    uint32_t mb = 0x3F800000u | (uint32_t)((b >> 29) & 0x7FFFFFu);
+    float m;
+    memcpy(&m, &mb, sizeof m);
+    if (m > 0x1.6a09e6p+0f) {        /* sqrt(2) */
+        m = m * 0.5f;
+        e = e + 1;
+    }
+    float s = (m - 1.0f) / (m + 1.0f);
+    float s2 = s * s;
+    float q = 0x1.24924ap-3f;        /* 1/7 */
+    q = q * s2 + 0x1.99999ap-3f;     /* 1/5 */
+    q = q * s2 + 0x1.555556p-2f;     /* 1/3 */
+    q = q * s2 + 1.0f;
+    float ln_m = (2.0f * s) * q;
+    return (float)e + ln_m * 0x1.715476p+0f;    /* 1/ln 2 */
+}
+
+/* log2 r = max(log2 sx / 2 - log2 h, log2 su / 2) - log2 tol, in FP32. */
+float orc_ctrl_log2r(double sx, double su, double h, double tol)
+{
+    float lx = 0.5f * (orc_ctrl_log2(sx) - 2.0f * orc_ctrl_log2(h));
+    float lu = 0.5f * orc_ctrl_log2(su);
+    return fmaxf(lx, lu) - orc_ctrl_log2(tol);
+}
+
+/* 0.95 r^p = 0.95 2^y with y = p log2 r clamped to [-8, 8] (beyond it every factor below is
+ * clamped anyway): 2^n exactly (n = floor y) times e^(f ln 2), f = y - n in [0, 1), by
+ * Taylor through the 8th power (truncation error below 1e-7); the result clamped to
+ * [lo, hi]. A NaN y counts as -8 (the smallest factor). */
+float orc_ctrl_factor(float log2r, float p, float lo, float hi)
+{
+    float y = fminf(fmaxf(p * log2r, -8.0f), 8.0f);
+    float n = floorf(y);
+    float x = (y - n) * 0x1.62e430p-1f;         /* ln 2 */
+    float q = 0x1.a01a02p-16f;                  /* 1/8! */
+    q = q * x + 0x1.a01a02p-13f;                /* 1/7! */
+    q = q * x + 0x1.6c16c2p-10f;                /* 1/6! */
+    q = q * x + 0x1.111112p-7f;                 /* 1/5! */
+    q = q * x + 0x1.555556p-5f;                 /* 1/4! */
+    q = q * x + 0x1.555556p-3f;                 /* 1/3! */
+    q = q * x + 0.5f;
+    q = q * x + 1.0f;
+    q = q * x + 1.0f;
+    uint32_t pb = (uint32_t)((int)n + 127) << 23;
+    float p2;
+    memcpy(&p2, &pb, sizeof p2);
+    return fminf(fmaxf(0.95f * (q * p2), lo), hi);
 }
 
 /* ---- tabulated rates (Sec. 2 interactions; synthetic tables) -----------------------
@@ -469,17 +540,17 @@ static void propagate_one(orc_job* job, int64_t i)
 
         /* propagation: Cash-Karp attempts until the FP64 error ratio is <= 1 */
         double kappa = (double)Z * C_LIGHT / E;
-        double k1[6], y5[6], err[6], r;
+        double k1[6], y5[6], err[6], sx, su;
         orc_deriv(fld, kappa, y, k1);
         int rejected = 0;
         int64_t att_step = 0;
         for (;;) {
             orc_ck_attempt(fld, kappa, y, k1, h, y5, err);
             att_step += 1;
-            r = orc_error_ratio(err, h, p->tol);
-            if (r <= 1.0 || h <= p->hmin) break;
-            double shrink = clamp(0.95 * orc_exp(-0.25 * orc_log(r)), 0.1, 1.0);
-            h = fmax(h * shrink, p->hmin);
+            orc_error_sums(err, &sx, &su);
+            if (orc_error_accept(sx, su, h, p->tol) || h <= p->hmin) break;
+            float shrink = orc_ctrl_factor(orc_ctrl_log2r(sx, su, h, p->tol), -0.25f, 0.1f, 1.0f);
+            h = fmax(h * (double)shrink, p->hmin);
             rejected = 1;
         }
         int finite = 1;
@@ -512,8 +583,9 @@ static void propagate_one(orc_job* job, int64_t i)
         n_steps += 1;
         acc_total += 1;
         taken += 1;
-        double grow = (r == 0.0) ? 5.0 : clamp(0.95 * orc_exp(-0.2 * orc_log(r)), 0.2, 5.0);
-        double hnext = h * grow;
+        float grow = (h == 0.0 || (sx == 0.0 && su == 0.0))
+                         ? 5.0f : orc_ctrl_factor(orc_ctrl_log2r(sx, su, h, p->tol), -0.2f, 0.2f, 5.0f);
+        double hnext = h * (double)grow;
         if (!rejected && h_first < h_prop) hnext = fmax(hnext, h_prop);
         hprop = clamp(hnext, p->hmin, p->hmax);
 
@@ -657,21 +729,22 @@ int orc_record_steps(const orc_field* f, double kappa, const double y0[6], doubl
     for (int32_t n = 0; n < n_steps; ++n) {
         double h_prop = fmin(fmax(hprop, hmin), hmax);
         double h = h_prop;
-        double k1[6], y5[6], err[6], r;
+        double k1[6], y5[6], err[6], sx, su;
         orc_deriv(f, kappa, y, k1);
         int rejected = 0;
         for (;;) {
             orc_ck_attempt(f, kappa, y, k1, h, y5, err);
-            r = orc_error_ratio(err, h, tol);
-            if (r <= 1.0 || h <= hmin) break;
-            double shrink = clamp(0.95 * orc_exp(-0.25 * orc_log(r)), 0.1, 1.0);
-            h = fmax(h * shrink, hmin);
+            orc_error_sums(err, &sx, &su);
+            if (orc_error_accept(sx, su, h, tol) || h <= hmin) break;
+            float shrink = orc_ctrl_factor(orc_ctrl_log2r(sx, su, h, tol), -0.25f, 0.1f, 1.0f);
+            h = fmax(h * (double)shrink, hmin);
             rejected = 1;
         }
         for (int c = 0; c < 6; ++c) y[c] = y5[c];
         h_out[n] = h;
-        double grow = (r == 0.0) ? 5.0 : clamp(0.95 * orc_exp(-0.2 * orc_log(r)), 0.2, 5.0);
-        double hnext = h * grow;
+        float grow = (h == 0.0 || (sx == 0.0 && su == 0.0))
+                         ? 5.0f : orc_ctrl_factor(orc_ctrl_log2r(sx, su, h, tol), -0.2f, 0.2f, 5.0f);
+        double hnext = h * (double)grow;
         if (!rejected && h < h_prop) hnext = fmax(hnext, h_prop);
         hprop = clamp(hnext, hmin, hmax);
     }

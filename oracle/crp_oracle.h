@@ -114,7 +114,11 @@ double orc_modulation_value(const orc_field* f, const double x[3]);
 void orc_deriv(const orc_field* f, double kappa, const double y[6], double k[6]);
 void orc_ck_attempt(const orc_field* f, double kappa, const double y[6], const double k1[6],
                     double h, double y5[6], double err[6]);
-double orc_error_ratio(const double err[6], double h, double tol);
+void orc_error_sums(const double err[6], double* sx, double* su);
+int orc_error_accept(double sx, double su, double h, double tol);
+float orc_ctrl_log2(double v);
+float orc_ctrl_log2r(double sx, double su, double h, double tol);
+float orc_ctrl_factor(float log2r, float p, float lo, float hi);
 int orc_rates(const orc_tables* t, int32_t A, int32_t Z, double E, double* r_loss, double* r_pd);
 int orc_inject(orc_state* st, int64_t first, int64_t count, uint64_t seed, const orc_tables* t);
 int orc_propagate(orc_state* st, const orc_field* fields, int32_t n_fields, const orc_tables* t,

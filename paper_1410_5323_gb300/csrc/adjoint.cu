@@ -57,6 +57,8 @@ __global__ void k_adj_record(FieldDev F, const double* __restrict__ y0, const do
     Y6 y;
     load6(y0, n, i, y);
     const double kappa = kap[i];
+    const double tol2 = tol * tol;
+    const float lg_tol = ctrl_log2(tol);
     double hprop = __longlong_as_double(0x7ff0000000000000LL);
     for (int m = 0; m < n_steps; ++m) {
         if (m % K == 0) store6(ck + (long long)(m / K) * 6 * n, n, i, y);
@@ -64,20 +66,21 @@ __global__ void k_adj_record(FieldDev F, const double* __restrict__ y0, const do
         double h = h_prop;
         const Y6 k1 = deriv<L>(F, kappa, y);
         Y6 y5, err;
-        double r;
+        double sx, su;
         int rejected = 0;
         for (;;) {
             ck_attempt<L>(F, kappa, y, k1, h, y5, err);
-            r = error_ratio(err, h, tol);
-            if (r <= 1.0 || h <= hmin) break;
-            const double shrink = clampd(0.95 * crp_exp(-0.25 * crp_log(r)), 0.1, 1.0);
-            h = fmax(h * shrink, hmin);
+            error_sums(err, sx, su);
+            if (error_accept(sx, su, h, tol, tol2) || h <= hmin) break;
+            const float shrink = ctrl_factor(ctrl_log2r(sx, su, h, lg_tol), -0.25f, 0.1f, 1.0f);
+            h = fmax(h * widen_normal(shrink), hmin);
             rejected = 1;
         }
         y = y5;
         h_out[(long long)m * n + i] = h;
-        const double grow = (r == 0.0) ? 5.0 : clampd(0.95 * crp_exp(-0.2 * crp_log(r)), 0.2, 5.0);
-        double hnext = h * grow;
+        const float grow = (h == 0.0 || (sx == 0.0 && su == 0.0))
+                               ? 5.0f : ctrl_factor(ctrl_log2r(sx, su, h, lg_tol), -0.2f, 0.2f, 5.0f);
+        double hnext = h * widen_normal(grow);
         if (!rejected && h < h_prop) hnext = fmax(hnext, h_prop);
         hprop = clampd(hnext, hmin, hmax);
     }

@@ -51,13 +51,56 @@ __device__ __forceinline__ V3 corner(const FieldDev& F, long long node) {
     return g;
 }
 
+// floor(r) as an integer and as a double, from the bits of r with integer instructions only
+// (GB300 rounds and converts FP64 values on its FP64 pipe, which the lookups' arithmetic
+// already saturates). Exact for |r| < 2^63, where it equals floor() and its conversion;
+// beyond that, and for infinities and NaN, i = 0 and fl = r (any index is wrapped into the
+// grid afterwards).
+__device__ __forceinline__ void floor_split(double r, long long& i, double& fl) {
+    constexpr long long kSign = (long long)0x8000000000000000ull;
+    constexpr long long kMant = 0xFFFFFFFFFFFFFll;
+    const long long b = __double_as_longlong(r);
+    const int ef = (int)((b >> 52) & 0x7FF);
+    const bool neg = b < 0;
+    const long long mag = b & ~kSign;
+    if (ef < 1023) {                                   // |r| < 1: floor is 0, -0 or -1
+        const bool m1 = neg && mag != 0;
+        i = m1 ? -1 : 0;
+        fl = __longlong_as_double(m1 ? (long long)0xBFF0000000000000ull : (b & kSign));
+    } else if (ef < 1075) {                            // 1 <= |r| < 2^52: fb fraction bits
+        const int fb = 1075 - ef;
+        const long long fm = (1ll << fb) - 1;
+        const long long n = ((mag & kMant) | (kMant + 1)) >> fb;       // |trunc r|
+        if (!neg) {
+            i = n;
+            fl = __longlong_as_double(b & ~fm);
+        } else if ((mag & fm) == 0) {
+            i = -n;
+            fl = r;
+        } else {                                       // floor = -(n + 1), n + 1 <= 2^52
+            const long long k = n + 1;
+            const int p = 63 - __clzll(k);
+            i = -k;
+            fl = __longlong_as_double(kSign | ((long long)(1023 + p) << 52) | ((k << (52 - p)) & kMant));
+        }
+    } else if (ef < 1086) {                            // 2^52 <= |r| < 2^63: integral
+        const long long n = ((mag & kMant) | (kMant + 1)) << (ef - 1075);
+        i = neg ? -n : n;
+        fl = r;
+    } else {
+        i = 0;
+        fl = r;
+    }
+}
+
 // One axis of the periodic lookup: r = (x - o)*(1/spacing), i0 = floor(r) mod n, weights.
 __device__ __forceinline__ void axis(double x, double o, double inv, int n, int pow2,
                                      long long& i0, long long& i1, double& w0, double& w1) {
     const double r = (x - o) * inv;
-    const double fl = floor(r);
+    long long i;
+    double fl;
+    floor_split(r, i, fl);
     const double fr = r - fl;
-    const long long i = (long long)fl;
     long long a;
     if (pow2) a = i & (long long)(n - 1);
     else { a = i % n; if (a < 0) a += n; }
@@ -198,11 +241,79 @@ __device__ __forceinline__ void ck_attempt(const FieldDev& F, double kappa, cons
 #undef SE
 }
 
-__device__ __forceinline__ double error_ratio(const Y6& e, double h, double tol) {
-    if (h == 0.0) return 0.0;
-    const double ex = sqrt(__fma_rn(e.z, e.z, __fma_rn(e.y, e.y, e.x * e.x))) / h;
-    const double eu = sqrt(__fma_rn(e.uz, e.uz, __fma_rn(e.uy, e.uy, e.ux * e.ux)));
-    return fmax(ex, eu) / tol;
+// Error of an attempt, kept squared: sx = |dx|^2, su = |du|^2, each ((a0^2 + a1^2) + a2^2).
+// Accept iff the step has zero length or sx <= (h tol)^2 and su <= tol^2 (r <= 1 for
+// r = max(|dx|/h, |du|)/tol, compared as squares; a NaN sum rejects).
+__device__ __forceinline__ void error_sums(const Y6& e, double& sx, double& su) {
+    sx = __fma_rn(e.z, e.z, __fma_rn(e.y, e.y, e.x * e.x));
+    su = __fma_rn(e.uz, e.uz, __fma_rn(e.uy, e.uy, e.ux * e.ux));
+}
+
+__device__ __forceinline__ bool error_accept(double sx, double su, double h, double tol, double tol2) {
+    if (h == 0.0) return true;
+    const double ht = h * tol;
+    return sx <= ht * ht && su <= tol2;
+}
+
+// Step-size controller. The factor is a heuristic, so only its inputs (the FP64 error sums)
+// and its application (h times the factor, in FP64) are FP64; the factor itself is FP32 on
+// the FP32 pipe. ctrl_log2: log2 of a non-negative double from its bits -- exponent plus
+// log2 of the top 23 significand bits m in [1, 2) (truncated), m reduced to
+// [sqrt(1/2), sqrt(2)), ln m = 2 atanh s through s^7, s = (m - 1)/(m + 1); -inf for zero
+// and subnormals, +inf for infinity and NaN.
+__device__ __forceinline__ float ctrl_log2(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int ef = (int)((b >> 52) & 0x7FFu);
+    if (ef == 0x7FF) return __int_as_float(0x7f800000);
+    if (ef == 0) return __int_as_float((int)0xff800000u);
+    int e = ef - 1023;
+    float m = __uint_as_float(0x3F800000u | (unsigned)((b >> 29) & 0x7FFFFFu));
+    if (m > 0x1.6a09e6p+0f) {
+        m = __fmul_rn(m, 0.5f);
+        e += 1;
+    }
+    const float s = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
+    const float s2 = __fmul_rn(s, s);
+    float q = 0x1.24924ap-3f;                                  // 1/7
+    q = __fadd_rn(__fmul_rn(q, s2), 0x1.99999ap-3f);           // 1/5
+    q = __fadd_rn(__fmul_rn(q, s2), 0x1.555556p-2f);           // 1/3
+    q = __fadd_rn(__fmul_rn(q, s2), 1.0f);
+    const float ln_m = __fmul_rn(__fmul_rn(2.0f, s), q);
+    return __fadd_rn((float)e, __fmul_rn(ln_m, 0x1.715476p+0f));   // 1/ln 2
+}
+
+// log2 r = max(log2 sx / 2 - log2 h, log2 su / 2) - log2 tol.
+__device__ __forceinline__ float ctrl_log2r(double sx, double su, double h, float lg_tol) {
+    const float lx = __fmul_rn(0.5f, __fsub_rn(ctrl_log2(sx), __fmul_rn(2.0f, ctrl_log2(h))));
+    const float lu = __fmul_rn(0.5f, ctrl_log2(su));
+    return __fsub_rn(fmaxf(lx, lu), lg_tol);
+}
+
+// 0.95 r^p clamped to [lo, hi]: y = p log2 r clamped to [-8, 8] (a NaN y counts as -8),
+// 2^floor(y) exactly times e^(f ln 2) (f the fractional part) by Taylor through x^8/8!.
+__device__ __forceinline__ float ctrl_factor(float log2r, float p, float lo, float hi) {
+    const float y = fminf(fmaxf(__fmul_rn(p, log2r), -8.0f), 8.0f);
+    const float n = floorf(y);
+    const float x = __fmul_rn(__fsub_rn(y, n), 0x1.62e430p-1f);   // ln 2
+    float q = 0x1.a01a02p-16f;                                 // 1/8!
+    q = __fadd_rn(__fmul_rn(q, x), 0x1.a01a02p-13f);           // 1/7!
+    q = __fadd_rn(__fmul_rn(q, x), 0x1.6c16c2p-10f);           // 1/6!
+    q = __fadd_rn(__fmul_rn(q, x), 0x1.111112p-7f);            // 1/5!
+    q = __fadd_rn(__fmul_rn(q, x), 0x1.555556p-5f);            // 1/4!
+    q = __fadd_rn(__fmul_rn(q, x), 0x1.555556p-3f);            // 1/3!
+    q = __fadd_rn(__fmul_rn(q, x), 0.5f);
+    q = __fadd_rn(__fmul_rn(q, x), 1.0f);
+    q = __fadd_rn(__fmul_rn(q, x), 1.0f);
+    const float p2 = __int_as_float(((int)n + 127) << 23);
+    return fminf(fmaxf(__fmul_rn(0.95f, __fmul_rn(q, p2)), lo), hi);
+}
+
+// Exact widening of a normal float (the clamped factors) to double with integer
+// instructions (the hardware conversion issues on the FP64 pipe).
+__device__ __forceinline__ double widen_normal(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned hi = (u & 0x80000000u) | ((((u >> 23) & 0xFFu) + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
+    return __hiloint2double((int)hi, (int)(u << 29));
 }
 
 __device__ __forceinline__ double clampd(double v, double lo, double hi) {

@@ -47,7 +47,9 @@ __global__ void CRP_FP64_BOUNDS k_propagate_fp64(const PropArgs a) {
     unsigned long long uid = 0;
     long long n_steps = 0, n_att = 0, taken = 0;
     bool new_step = true;
-    double h = 0, h_first = 0, h_propc = 0, h_int = 0, h_dist = 0, rl = 0, rpd = 0;
+    double h = 0, h_first = 0, h_propc = 0, h_int = 0, h_dist = 0, rl = 0, rpd = 0, kappa = 0;
+    const double tol2 = a.tol * a.tol;
+    const float lg_tol = ctrl_log2(a.tol);
     int rejected = 0;
     long long att_step = 0;
     unsigned long long acc_tot = 0, att_tot = 0, sec_tot = 0;
@@ -108,20 +110,21 @@ __global__ void CRP_FP64_BOUNDS k_propagate_fp64(const PropArgs a) {
                 if (h_int < h) h = h_int;
                 if (h_dist < h) h = h_dist;
                 h_first = h;
+                kappa = (double)Z * kC / E;   // E and Z are constant within a step
                 rejected = 0;
                 att_step = 0;
                 new_step = false;
             }
             // ---- propagation: one Cash-Karp attempt ----
-            const double kappa = (double)Z * kC / E;
             const Y6 k1 = deriv<L, false, M>(F, kappa, y);
             Y6 y5, err;
             ck_attempt<L, false, M>(F, kappa, y, k1, h, y5, err);
             att_step += 1;
-            const double r = error_ratio(err, h, a.tol);
-            if (!(r <= 1.0 || h <= a.hmin)) {
-                const double shrink = clampd(0.95 * crp_exp(-0.25 * crp_log(r)), 0.1, 1.0);
-                h = fmax(h * shrink, a.hmin);
+            double sx, su;
+            error_sums(err, sx, su);
+            if (!(error_accept(sx, su, h, a.tol, tol2) || h <= a.hmin)) {
+                const float shrink = ctrl_factor(ctrl_log2r(sx, su, h, lg_tol), -0.25f, 0.1f, 1.0f);
+                h = fmax(h * widen_normal(shrink), a.hmin);
                 rejected = 1;
                 continue;
             }
@@ -162,8 +165,9 @@ __global__ void CRP_FP64_BOUNDS k_propagate_fp64(const PropArgs a) {
             n_steps += 1;
             acc_tot += 1;
             taken += 1;
-            const double grow = (r == 0.0) ? 5.0 : clampd(0.95 * crp_exp(-0.2 * crp_log(r)), 0.2, 5.0);
-            double hnext = h * grow;
+            const float grow = (h == 0.0 || (sx == 0.0 && su == 0.0))
+                                   ? 5.0f : ctrl_factor(ctrl_log2r(sx, su, h, lg_tol), -0.2f, 0.2f, 5.0f);
+            double hnext = h * widen_normal(grow);
             if (!rejected && h_first < h_propc) hnext = fmax(hnext, h_propc);
             hprop = clampd(hnext, a.hmin, a.hmax);
             // ---- continuous loss at gamma0 ----

@@ -126,11 +126,10 @@ def test_fifth_order_solution_local_error_h6(oracle_lib):
     assert abs(slope - 6.0) < 0.3
 
 
-def test_error_ratio_definition(oracle_lib):
-    """r = max(|dx|/h, |du|)/tol, Euclidean norms; zero-length step gives r = 0."""
-    err = np.array([3.0, 4.0, 0.0, 0.0, 0.0, 2e-3])
-    assert oracle_lib.error_ratio(err, 1000.0, 1e-4) == pytest.approx(max(5.0 / 1000.0, 2e-3) / 1e-4, rel=1e-15)
-    assert oracle_lib.error_ratio(np.zeros(6), 0.0, 1e-4) == 0.0
+def test_error_sums_definition(oracle_lib):
+    """sx = |dx|^2, su = |du|^2 (Euclidean norms, kept squared)."""
+    assert oracle_lib.error_sums([3.0, 4.0, 0.0, 0.0, 0.0, 2e-3]) == (25.0, 2e-3 * 2e-3)
+    assert oracle_lib.error_sums([0.0, 0.0, 12.0, 1.0, 2.0, 2.0]) == (144.0, 9.0)
 
 
 def test_fixed_step_global_error_is_fifth_order(oracle_lib):
