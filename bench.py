@@ -34,13 +34,14 @@ UNIT = "steps/s"
 
 # Algorithmic FP64 work of the method (counted from its formulas; each +,-,*,/,sqrt,max one
 # flop, each elementary function one flop):
-#   per attempt: 6 field evaluations x (lookup 69 + Lorentz 12) = 486, stage sums 210,
-#   5th-order update 54, error estimate 60, squared error norms 10 + (h tol)^2 2,
-#   h x step factor and its clamp 2 (the factor itself is FP32 work)  -> 824
-#   per accepted step: kappa = Z c / E -> 2; with tables: bids, gamma0, 2 table
-#   interpolations, loss, tau -> 30 more
-FLOP_PER_ATTEMPT = 824
-FLOP_PER_ACCEPTED = 2
+#   per attempt: 5 field evaluations (stages 2-6) x (lookup 69 + Lorentz 12) = 405, stage
+#   sums 210, 5th-order update 54, error estimate 60, squared error norms 10 + (h tol)^2 2,
+#   h x step factor and its clamp 2 (the factor itself is FP32 work)  -> 743
+#   per accepted step: the next step's first field evaluation 81 (rejected attempts reuse
+#   it), kappa = Z c / E 2 -> 83; with tables: bids, gamma0, 2 table interpolations, loss,
+#   tau -> 30 more
+FLOP_PER_ATTEMPT = 743
+FLOP_PER_ACCEPTED = 83
 FLOP_PER_ACCEPTED_TABLES = 30
 # FP64 pipe of one GB300: 2 FP64 lanes/clk/SM x 152 SMs x 2070 MHz = 6.29e11 ops/s,
 # 1.259e12 FLOP/s counting an FMA as two (the FP64 form issues no FMA: ceiling 0.5).
@@ -56,19 +57,21 @@ MIXED_FP32_FLOP_PER_ATTEMPT = 612
 # DRAM bytes (read + write) of one lens launch measured by ncu on the current kernels, keyed by
 # the number of maps (profiles/k_lens_apply_nside64_24bins.md).
 LENS_DRAM_BYTES = {1: 2.406e8, 32: 5.531e8}
-# Modulated fields add one scalar trilinear lookup per field evaluation: FP64 form 6 x
-# (axes 12, weights 12, 8 products, 7 sums, 3 products m*B) = 252 per attempt; mixed form
+# Modulated fields add one scalar trilinear lookup per field evaluation: FP64 form 42 each
+# (axes 12, weights 12, 8 products, 7 sums, 3 products m*B), 5 x 42 = 210 per attempt and 42
+# per accepted step; mixed form
 # 6 x 38 FP32 flops per attempt and, per accepted step, the step-start modulation cell in
 # FP64 (3 x (2 widenings, 3 add, 1 mul, floor, 2 conversions, 1 mul)) = 33 FP64 ops.
-MOD_FLOP_PER_ATTEMPT = 252
+MOD_FLOP_PER_ATTEMPT = 210
+MOD_FLOP_PER_ACCEPTED = 42
 MIXED_MOD_FP64_OPS_PER_ACCEPTED = 33
 MIXED_MOD_FP32_FLOP_PER_ATTEMPT = 228
 # DRAM bytes (read + write) per attempted step of the propagate kernels, measured by ncu at
 # reduced batch (both launches of one call; the summaries under profiles/ name the command);
 # traffic of a call = this x its attempts. Keyed by (workload, form).
-DRAM_BYTES_PER_ATTEMPT = {("fp64_256cube_1M_nuclei", "fp64"): 140.1,
+DRAM_BYTES_PER_ATTEMPT = {("fp64_256cube_1M_nuclei", "fp64"): 140.5,
                           ("fp64_256cube_1M_nuclei", "mixed"): 90.5,
-                          ("modulated_440cube_300kpc_x_256cube_50kpc_1M_nuclei", "fp64"): 411.1,
+                          ("modulated_440cube_300kpc_x_256cube_50kpc_1M_nuclei", "fp64"): 405.2,
                           ("modulated_440cube_300kpc_x_256cube_50kpc_1M_nuclei", "mixed"): 776.7}
 
 
@@ -307,7 +310,8 @@ def roofline_for(form, attempted, accepted, tables, prop_s, calls=1, workload=""
     """Roofline of the propagate kernel for one form, from the live CUDA-event time."""
     if form == "fp64":
         per_att = FLOP_PER_ATTEMPT + (MOD_FLOP_PER_ATTEMPT if modulated else 0)
-        flops = per_att * attempted + (FLOP_PER_ACCEPTED + (FLOP_PER_ACCEPTED_TABLES if tables else 0)) * accepted
+        per_acc = FLOP_PER_ACCEPTED + (MOD_FLOP_PER_ACCEPTED if modulated else 0) + (FLOP_PER_ACCEPTED_TABLES if tables else 0)
+        flops = per_att * attempted + per_acc * accepted
         ach = flops / prop_s / 1e12
         return {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / FP64_PEAK_TFLOPS, "traffic": traffic_for(workload, form, attempted, calls),

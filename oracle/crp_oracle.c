@@ -94,34 +94,37 @@ static const double LN10 = 0x1.26bb1bbb55516p+1;        /* ln 10 */
 static const double INV_LN10 = 0.4342944819032518;      /* 1/ln 10 */
 
 /* exp(x) = 2^n exp(r), x = n ln2 + r, |r| <= ln2/2; exp(r) by its Taylor series through
- * r^14/14! (truncation below 2^-60 on that interval), Horner order. */
+ * r^14/14! (truncation below 2^-60 on that interval), Horner order, each step one fused
+ * multiply-add; r = (x - n ln2_hi) - n ln2_lo with the products fused (n ln2_hi is exact). */
 double orc_exp(double x)
 {
     if (x != x) return x;
     if (x > 709.782712893384) return INFINITY;
     if (x < -745.1332191019412) return 0.0;
-    double n = floor(x * INV_LN2 + 0.5);
-    double r = (x - n * LN2_HI) - n * LN2_LO;
-    double p = 1.0 / 87178291200.0;         /* 1/14! */
-    p = p * r + 1.0 / 6227020800.0;          /* 1/13! */
-    p = p * r + 1.0 / 479001600.0;           /* 1/12! */
-    p = p * r + 1.0 / 39916800.0;            /* 1/11! */
-    p = p * r + 1.0 / 3628800.0;             /* 1/10! */
-    p = p * r + 1.0 / 362880.0;              /* 1/9!  */
-    p = p * r + 1.0 / 40320.0;               /* 1/8!  */
-    p = p * r + 1.0 / 5040.0;                /* 1/7!  */
-    p = p * r + 1.0 / 720.0;                 /* 1/6!  */
-    p = p * r + 1.0 / 120.0;                 /* 1/5!  */
-    p = p * r + 1.0 / 24.0;                  /* 1/4!  */
-    p = p * r + 1.0 / 6.0;                   /* 1/3!  */
-    p = p * r + 0.5;                         /* 1/2!  */
-    p = p * r + 1.0;                         /* 1/1!  */
-    p = p * r + 1.0;                         /* 1/0!  */
+    double n = floor(fma(x, INV_LN2, 0.5));
+    double r = fma(-n, LN2_LO, fma(-n, LN2_HI, x));
+    double p = 1.0 / 87178291200.0;          /* 1/14! */
+    p = fma(p, r, 1.0 / 6227020800.0);       /* 1/13! */
+    p = fma(p, r, 1.0 / 479001600.0);        /* 1/12! */
+    p = fma(p, r, 1.0 / 39916800.0);         /* 1/11! */
+    p = fma(p, r, 1.0 / 3628800.0);          /* 1/10! */
+    p = fma(p, r, 1.0 / 362880.0);           /* 1/9!  */
+    p = fma(p, r, 1.0 / 40320.0);            /* 1/8!  */
+    p = fma(p, r, 1.0 / 5040.0);             /* 1/7!  */
+    p = fma(p, r, 1.0 / 720.0);              /* 1/6!  */
+    p = fma(p, r, 1.0 / 120.0);              /* 1/5!  */
+    p = fma(p, r, 1.0 / 24.0);               /* 1/4!  */
+    p = fma(p, r, 1.0 / 6.0);                /* 1/3!  */
+    p = fma(p, r, 0.5);                      /* 1/2!  */
+    p = fma(p, r, 1.0);                      /* 1/1!  */
+    p = fma(p, r, 1.0);                      /* 1/0!  */
     return ldexp(p, (int)n);
 }
 
 /* log(x) = e ln2 + log(m), x = m 2^e with m in [sqrt(1/2), sqrt(2));
- * log(m) = 2 atanh(s), s = (m-1)/(m+1), |s| <= 0.1716, series through s^23/23. */
+ * log(m) = 2 atanh(s) = 2s + 2s t, s = (m-1)/(m+1), |s| <= 0.1716, t = s^2/3 + s^4/5 + ...
+ * through s^22/23 (Horner in s^2, fused), 2s + 2s t and e ln2_lo + log(m) fused, e ln2_hi
+ * exact. */
 double orc_log(double x)
 {
     if (x != x) return x;
@@ -137,20 +140,21 @@ double orc_log(double x)
     double s = (m - 1.0) / (m + 1.0);
     double s2 = s * s;
     double p = 1.0 / 23.0;
-    p = p * s2 + 1.0 / 21.0;
-    p = p * s2 + 1.0 / 19.0;
-    p = p * s2 + 1.0 / 17.0;
-    p = p * s2 + 1.0 / 15.0;
-    p = p * s2 + 1.0 / 13.0;
-    p = p * s2 + 1.0 / 11.0;
-    p = p * s2 + 1.0 / 9.0;
-    p = p * s2 + 1.0 / 7.0;
-    p = p * s2 + 1.0 / 5.0;
-    p = p * s2 + 1.0 / 3.0;
+    p = fma(p, s2, 1.0 / 21.0);
+    p = fma(p, s2, 1.0 / 19.0);
+    p = fma(p, s2, 1.0 / 17.0);
+    p = fma(p, s2, 1.0 / 15.0);
+    p = fma(p, s2, 1.0 / 13.0);
+    p = fma(p, s2, 1.0 / 11.0);
+    p = fma(p, s2, 1.0 / 9.0);
+    p = fma(p, s2, 1.0 / 7.0);
+    p = fma(p, s2, 1.0 / 5.0);
+    p = fma(p, s2, 1.0 / 3.0);
     double t = s2 * p;                       /* s^2/3 + s^4/5 + ... */
-    double log_m = 2.0 * s + 2.0 * s * t;
+    double s_2 = 2.0 * s;
+    double log_m = fma(s_2, t, s_2);
     double de = (double)e;
-    return de * LN2_HI + (de * LN2_LO + log_m);
+    return fma(de, LN2_HI, fma(de, LN2_LO, log_m));
 }
 
 /* ---- field lookup: trilinear interpolation on a periodic regular grid (Sec. 3.2) --- */
@@ -186,7 +190,7 @@ static double grid_at(const orc_field* f, int64_t i, int64_t j, int64_t k, int c
 }
 
 /* Modulation (Sec. 3.2): the scalar grid interpolated trilinearly, periodic over its own
- * extent, corners summed in the order 000, ..., 111 with weight ((w_x * w_y) * w_z), each
+ * extent (fractional index formed as for the field), corners summed in the order 000, ..., 111 with weight ((w_x * w_y) * w_z), each
  * corner added with one rounding, m = fma(w, M_corner, m) from m = 0. */
 double orc_modulation_value(const orc_field* f, const double x[3])
 {
@@ -195,7 +199,7 @@ double orc_modulation_value(const orc_field* f, const double x[3])
     int64_t idx[3][2];
     double w[3][2];
     for (int a = 0; a < 3; ++a) {
-        double r = (x[a] - f->mod_origin[a]) * inv;
+        double r = fma(x[a], inv, -(f->mod_origin[a] * inv));
         double fl = floor(r);
         double fr = r - fl;
         int64_t i = (int64_t)fl;
@@ -219,7 +223,8 @@ double orc_modulation_value(const orc_field* f, const double x[3])
     return m;
 }
 
-/* Fractional index r = (x - origin) * (1/spacing); cell i0 = floor(r) wrapped modulo n;
+/* Fractional index r = x (1/spacing) - origin (1/spacing), the product origin (1/spacing)
+ * rounded once and r in one fused multiply-add; cell i0 = floor(r) wrapped modulo n;
  * weights (1 - f, f) with f = r - floor(r). B is the sum over the 8 cell corners, taken
  * in the order (a,b,c) = 000, 001, 010, ..., 111, of ((w_x,a * w_y,b) * w_z,c) * B_corner,
  * each corner added with one rounding: B = fma(w, B_corner, B) from B = 0. */
@@ -230,7 +235,7 @@ void orc_field_value(const orc_field* f, const double x[3], double B[3])
     int64_t idx[3][2];
     double w[3][2];
     for (int a = 0; a < 3; ++a) {
-        double r = (x[a] - f->origin[a]) * inv;
+        double r = fma(x[a], inv, -(f->origin[a] * inv));
         double fl = floor(r);
         double fr = r - fl;
         int64_t i = (int64_t)fl;
@@ -786,7 +791,7 @@ static void lookup_full(const orc_field* f, const double x[3], orc_lookup* L)
     int64_t idx[3][2];
     double w[3][2], dwd[3][2];
     for (int a = 0; a < 3; ++a) {
-        double r = (x[a] - f->origin[a]) * inv;
+        double r = fma(x[a], inv, -(f->origin[a] * inv));
         double fl = floor(r);
         double fr = r - fl;
         int64_t i = (int64_t)fl;

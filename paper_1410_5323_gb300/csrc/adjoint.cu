@@ -123,9 +123,9 @@ __device__ __forceinline__ void lookup_full(const FieldDev& F, const Y6& Y, doub
                                             double dw[8][3], long long node[8], double G[8][3]) {
     long long ix[2], iy[2], iz[2];
     double wx[2], wy[2], wz[2];
-    axis(Y.x, F.ox, F.inv_spacing, F.nx, F.pow2, ix[0], ix[1], wx[0], wx[1]);
-    axis(Y.y, F.oy, F.inv_spacing, F.ny, F.pow2, iy[0], iy[1], wy[0], wy[1]);
-    axis(Y.z, F.oz, F.inv_spacing, F.nz, F.pow2, iz[0], iz[1], wz[0], wz[1]);
+    axis(Y.x, F.oix, F.inv_spacing, F.nx, F.pow2, ix[0], ix[1], wx[0], wx[1]);
+    axis(Y.y, F.oiy, F.inv_spacing, F.ny, F.pow2, iy[0], iy[1], wy[0], wy[1]);
+    axis(Y.z, F.oiz, F.inv_spacing, F.nz, F.pow2, iz[0], iz[1], wz[0], wz[1]);
     const double dd[2] = {-F.inv_spacing, F.inv_spacing};
     B[0] = 0.0; B[1] = 0.0; B[2] = 0.0;
     int c8 = 0;

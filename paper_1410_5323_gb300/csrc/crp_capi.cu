@@ -535,6 +535,7 @@ int crp_field_create(const void* grid, int32_t dtype, int32_t is_device, int32_t
     d.inv_spacing = 1.0 / spacing_m;
     d.spacing = spacing_m;
     d.ox = origin_m[0]; d.oy = origin_m[1]; d.oz = origin_m[2];
+    d.oix = d.ox * d.inv_spacing; d.oiy = d.oy * d.inv_spacing; d.oiz = d.oz * d.inv_spacing;
     d.scale = (dtype == CRP_DTYPE_BF16 || dtype == CRP_DTYPE_F16) ? (double)scale : 1.0;
     d.mod = nullptr;
     *out = f;
@@ -567,6 +568,7 @@ int crp_field_modulate(crp_field* field, const void* mod, int32_t dtype, int32_t
     d.m_inv_spacing = 1.0 / spacing_m;
     d.m_spacing = spacing_m;
     d.mox = origin_m[0]; d.moy = origin_m[1]; d.moz = origin_m[2];
+    d.moix = d.mox * d.m_inv_spacing; d.moiy = d.moy * d.m_inv_spacing; d.moiz = d.moz * d.m_inv_spacing;
     return CRP_OK;
 }
 
@@ -1121,6 +1123,7 @@ int ensure_fp64_fields(crp_sim* s) {
         F.mod = H.mod; F.mnx = H.mnx; F.mny = H.mny; F.mnz = H.mnz; F.mpow2 = H.mpow2;
         F.m_inv_spacing = H.m_inv_spacing; F.m_spacing = H.m_spacing;
         F.mox = H.mox; F.moy = H.moy; F.moz = H.moz;
+        F.moix = H.moix; F.moiy = H.moiy; F.moiz = H.moiz;
         d64.push_back(F);
     }
     void* d = nullptr;
@@ -1518,6 +1521,7 @@ extern "C" int crp_propagate_noalloc(const void* grid, int32_t nx, int32_t ny, i
     f.inv_spacing = 1.0 / spacing_m;
     f.spacing = spacing_m;
     f.ox = origin_m[0]; f.oy = origin_m[1]; f.oz = origin_m[2];
+    f.oix = f.ox * f.inv_spacing; f.oiy = f.oy * f.inv_spacing; f.oiz = f.oz * f.inv_spacing;
     f.scale = 1.0;
     SimState S{c.x, c.y, c.z, c.ux, c.uy, c.uz, c.E, c.s, c.hprop, c.tau, c.u0x, c.u0y, c.u0z,
                c.A, c.Z, c.n_int, c.status, c.grid_id, c.uid, c.n_steps, c.n_att};

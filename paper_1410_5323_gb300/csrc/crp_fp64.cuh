@@ -93,10 +93,11 @@ __device__ __forceinline__ void floor_split(double r, long long& i, double& fl) 
     }
 }
 
-// One axis of the periodic lookup: r = (x - o)*(1/spacing), i0 = floor(r) mod n, weights.
-__device__ __forceinline__ void axis(double x, double o, double inv, int n, int pow2,
+// One axis of the periodic lookup: r = x (1/spacing) - o (1/spacing) with one rounding (oi is
+// the product o (1/spacing), rounded once), i0 = floor(r) mod n, weights (1 - f, f).
+__device__ __forceinline__ void axis(double x, double oi, double inv, int n, int pow2,
                                      long long& i0, long long& i1, double& w0, double& w1) {
-    const double r = (x - o) * inv;
+    const double r = __fma_rn(x, inv, -oi);
     long long i;
     double fl;
     floor_split(r, i, fl);
@@ -116,9 +117,9 @@ __device__ __forceinline__ void axis(double x, double o, double inv, int n, int 
 __device__ __forceinline__ double modulation(const FieldDev& F, double x, double y, double z) {
     long long ix0, ix1, iy0, iy1, iz0, iz1;
     double wx0, wx1, wy0, wy1, wz0, wz1;
-    axis(x, F.mox, F.m_inv_spacing, F.mnx, F.mpow2, ix0, ix1, wx0, wx1);
-    axis(y, F.moy, F.m_inv_spacing, F.mny, F.mpow2, iy0, iy1, wy0, wy1);
-    axis(z, F.moz, F.m_inv_spacing, F.mnz, F.mpow2, iz0, iz1, wz0, wz1);
+    axis(x, F.moix, F.m_inv_spacing, F.mnx, F.mpow2, ix0, ix1, wx0, wx1);
+    axis(y, F.moiy, F.m_inv_spacing, F.mny, F.mpow2, iy0, iy1, wy0, wy1);
+    axis(z, F.moiz, F.m_inv_spacing, F.mnz, F.mpow2, iz0, iz1, wz0, wz1);
     const long long ny = F.mny, nz = F.mnz;
     const float* M = F.mod;
     const long long r00 = (ix0 * ny + iy0) * nz, r01 = (ix0 * ny + iy1) * nz;
@@ -149,9 +150,9 @@ __device__ __forceinline__ V3 field_b(const FieldDev& F, double x, double y, dou
                                       unsigned long long* hh = nullptr) {
     long long ix0, ix1, iy0, iy1, iz0, iz1;
     double wx0, wx1, wy0, wy1, wz0, wz1;
-    axis(x, F.ox, F.inv_spacing, F.nx, F.pow2, ix0, ix1, wx0, wx1);
-    axis(y, F.oy, F.inv_spacing, F.ny, F.pow2, iy0, iy1, wy0, wy1);
-    axis(z, F.oz, F.inv_spacing, F.nz, F.pow2, iz0, iz1, wz0, wz1);
+    axis(x, F.oix, F.inv_spacing, F.nx, F.pow2, ix0, ix1, wx0, wx1);
+    axis(y, F.oiy, F.inv_spacing, F.ny, F.pow2, iy0, iy1, wy0, wy1);
+    axis(z, F.oiz, F.inv_spacing, F.nz, F.pow2, iz0, iz1, wz0, wz1);
     const long long ny = F.ny, nz = F.nz;
     if constexpr (H) *hh = *hh * 0x9E3779B97F4A7C15ull + (unsigned long long)((ix0 * ny + iy0) * nz + iz0) + 1ull;
     const long long r00 = (ix0 * ny + iy0) * nz, r01 = (ix0 * ny + iy1) * nz;

@@ -20,6 +20,7 @@ struct FieldDev {
     double inv_spacing;      // 1/spacing, rounded once
     double spacing;
     double ox, oy, oz;
+    double oix, oiy, oiz;    // origin * (1/spacing), rounded once
     double scale;            // BF16/F16 multiplier (1 otherwise)
     // Modulation grid (Sec. 3.2 modulated grids): B(x) = M(x) b(x) with M a scalar FP32
     // periodic grid, node (i,j,k) at (i*mny + j)*mnz + k; nullptr when the field has none.
@@ -27,6 +28,7 @@ struct FieldDev {
     int32_t mnx, mny, mnz, mpow2;
     double m_inv_spacing, m_spacing;
     double mox, moy, moz;
+    double moix, moiy, moiz; // modulation origin * (1/spacing), rounded once
 };
 
 struct TablesDev {

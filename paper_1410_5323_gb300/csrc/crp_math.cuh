@@ -52,32 +52,35 @@ constexpr double kSqrtHalf = 0x1.6a09e667f3bcdp-1;
 constexpr double kLn10 = 0x1.26bb1bbb55516p+1;
 constexpr double kInvLn10 = 0.4342944819032518;
 
-// exp(x) = 2^n e^r, |r| <= ln2/2, e^r by Taylor through r^14/14! in Horner order.
+// exp(x) = 2^n e^r, |r| <= ln2/2, e^r by Taylor through r^14/14! in Horner order, every
+// step one fused multiply-add; r = (x - n ln2_hi) - n ln2_lo with fused products.
 __device__ __forceinline__ double crp_exp(double x) {
     if (x != x) return x;
     if (x > 709.782712893384) return __longlong_as_double(0x7ff0000000000000LL);
     if (x < -745.1332191019412) return 0.0;
-    const double n = floor(__dadd_rn(__dmul_rn(x, kInvLn2), 0.5));
-    const double r = __dsub_rn(__dsub_rn(x, __dmul_rn(n, kLn2Hi)), __dmul_rn(n, kLn2Lo));
+    const double n = floor(__fma_rn(x, kInvLn2, 0.5));
+    const double r = __fma_rn(-n, kLn2Lo, __fma_rn(-n, kLn2Hi, x));
     double p = 1.0 / 87178291200.0;
-    p = __dadd_rn(__dmul_rn(p, r), 1.0 / 6227020800.0);
-    p = __dadd_rn(__dmul_rn(p, r), 1.0 / 479001600.0);
-    p = __dadd_rn(__dmul_rn(p, r), 1.0 / 39916800.0);
-    p = __dadd_rn(__dmul_rn(p, r), 1.0 / 3628800.0);
-    p = __dadd_rn(__dmul_rn(p, r), 1.0 / 362880.0);
-    p = __dadd_rn(__dmul_rn(p, r), 1.0 / 40320.0);
-    p = __dadd_rn(__dmul_rn(p, r), 1.0 / 5040.0);
-    p = __dadd_rn(__dmul_rn(p, r), 1.0 / 720.0);
-    p = __dadd_rn(__dmul_rn(p, r), 1.0 / 120.0);
-    p = __dadd_rn(__dmul_rn(p, r), 1.0 / 24.0);
-    p = __dadd_rn(__dmul_rn(p, r), 1.0 / 6.0);
-    p = __dadd_rn(__dmul_rn(p, r), 0.5);
-    p = __dadd_rn(__dmul_rn(p, r), 1.0);
-    p = __dadd_rn(__dmul_rn(p, r), 1.0);
+    p = __fma_rn(p, r, 1.0 / 6227020800.0);
+    p = __fma_rn(p, r, 1.0 / 479001600.0);
+    p = __fma_rn(p, r, 1.0 / 39916800.0);
+    p = __fma_rn(p, r, 1.0 / 3628800.0);
+    p = __fma_rn(p, r, 1.0 / 362880.0);
+    p = __fma_rn(p, r, 1.0 / 40320.0);
+    p = __fma_rn(p, r, 1.0 / 5040.0);
+    p = __fma_rn(p, r, 1.0 / 720.0);
+    p = __fma_rn(p, r, 1.0 / 120.0);
+    p = __fma_rn(p, r, 1.0 / 24.0);
+    p = __fma_rn(p, r, 1.0 / 6.0);
+    p = __fma_rn(p, r, 0.5);
+    p = __fma_rn(p, r, 1.0);
+    p = __fma_rn(p, r, 1.0);
     return ldexp(p, (int)n);
 }
 
-// log(x) = e ln2 + 2 atanh(s), s = (m-1)/(m+1), m in [sqrt(1/2), sqrt(2)), through s^23/23.
+// log(x) = e ln2 + log m, m in [sqrt(1/2), sqrt(2)); log m = 2s + 2s t with s = (m-1)/(m+1)
+// and t = s^2/3 + ... + s^22/23 (fused Horner in s^2); e ln2_lo + log m and e ln2_hi + that
+// fused (e ln2_hi is exact).
 __device__ __forceinline__ double crp_log(double x) {
     if (x != x) return x;
     if (x < 0.0) return __longlong_as_double(0x7ff8000000000000LL);
@@ -89,20 +92,21 @@ __device__ __forceinline__ double crp_log(double x) {
     const double s = __ddiv_rn(__dsub_rn(m, 1.0), __dadd_rn(m, 1.0));
     const double s2 = __dmul_rn(s, s);
     double p = 1.0 / 23.0;
-    p = __dadd_rn(__dmul_rn(p, s2), 1.0 / 21.0);
-    p = __dadd_rn(__dmul_rn(p, s2), 1.0 / 19.0);
-    p = __dadd_rn(__dmul_rn(p, s2), 1.0 / 17.0);
-    p = __dadd_rn(__dmul_rn(p, s2), 1.0 / 15.0);
-    p = __dadd_rn(__dmul_rn(p, s2), 1.0 / 13.0);
-    p = __dadd_rn(__dmul_rn(p, s2), 1.0 / 11.0);
-    p = __dadd_rn(__dmul_rn(p, s2), 1.0 / 9.0);
-    p = __dadd_rn(__dmul_rn(p, s2), 1.0 / 7.0);
-    p = __dadd_rn(__dmul_rn(p, s2), 1.0 / 5.0);
-    p = __dadd_rn(__dmul_rn(p, s2), 1.0 / 3.0);
+    p = __fma_rn(p, s2, 1.0 / 21.0);
+    p = __fma_rn(p, s2, 1.0 / 19.0);
+    p = __fma_rn(p, s2, 1.0 / 17.0);
+    p = __fma_rn(p, s2, 1.0 / 15.0);
+    p = __fma_rn(p, s2, 1.0 / 13.0);
+    p = __fma_rn(p, s2, 1.0 / 11.0);
+    p = __fma_rn(p, s2, 1.0 / 9.0);
+    p = __fma_rn(p, s2, 1.0 / 7.0);
+    p = __fma_rn(p, s2, 1.0 / 5.0);
+    p = __fma_rn(p, s2, 1.0 / 3.0);
     const double t = __dmul_rn(s2, p);
-    const double log_m = __dadd_rn(__dmul_rn(2.0, s), __dmul_rn(__dmul_rn(2.0, s), t));
+    const double s_2 = __dmul_rn(2.0, s);
+    const double log_m = __fma_rn(s_2, t, s_2);
     const double de = (double)e;
-    return __dadd_rn(__dmul_rn(de, kLn2Hi), __dadd_rn(__dmul_rn(de, kLn2Lo), log_m));
+    return __fma_rn(de, kLn2Hi, __fma_rn(de, kLn2Lo, log_m));
 }
 
 // ---- tabulated rates at gamma0 = E/(A m_p c^2) ------------------------------------------

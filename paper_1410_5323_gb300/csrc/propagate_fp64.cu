@@ -42,6 +42,7 @@ __global__ void CRP_FP64_BOUNDS k_propagate_fp64(const PropArgs a) {
 
     int slot = -1;
     Y6 y{0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    Y6 k1{0.0, 0.0, 0.0, 0.0, 0.0, 0.0};   // derivative at the step start
     double E = 0, s = 0, hprop = 0, tau = 0;
     int A = 0, Z = 0, n_int = 0, gid = 0;
     unsigned long long uid = 0;
@@ -111,12 +112,12 @@ __global__ void CRP_FP64_BOUNDS k_propagate_fp64(const PropArgs a) {
                 if (h_dist < h) h = h_dist;
                 h_first = h;
                 kappa = (double)Z * kC / E;   // E and Z are constant within a step
+                k1 = deriv<L, false, M>(F, kappa, y);   // rejected attempts reuse k1
                 rejected = 0;
                 att_step = 0;
                 new_step = false;
             }
             // ---- propagation: one Cash-Karp attempt ----
-            const Y6 k1 = deriv<L, false, M>(F, kappa, y);
             Y6 y5, err;
             ck_attempt<L, false, M>(F, kappa, y, k1, h, y5, err);
             att_step += 1;
