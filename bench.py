@@ -70,9 +70,8 @@ MIXED_MOD_FP32_FLOP_PER_ATTEMPT = 228
 # reduced batch (both launches of one call; the summaries under profiles/ name the command);
 # traffic of a call = this x its attempts. Keyed by (workload, form).
 DRAM_BYTES_PER_ATTEMPT = {("fp64_256cube_1M_nuclei", "fp64"): 140.5,
-                          ("fp64_256cube_1M_nuclei", "mixed"): 90.5,
-                          ("modulated_440cube_300kpc_x_256cube_50kpc_1M_nuclei", "fp64"): 405.2,
-                          ("modulated_440cube_300kpc_x_256cube_50kpc_1M_nuclei", "mixed"): 776.7}
+                          ("fp64_256cube_1M_nuclei", "mixed"): 99.4,      # cell-major grid copy
+                          ("modulated_440cube_300kpc_x_256cube_50kpc_1M_nuclei", "fp64"): 405.2}
 
 
 def parse():
@@ -667,6 +666,9 @@ def run_own(args):
                    "order": order,
                    "slice_steps": slice_steps,
                    "form": args.form, "dmax_mpc": w.dmax_m / I.MPC, "tol": w.tol,
+                   "precision_form_grid_layout": (None if args.form != "mixed" and other is None else
+                                                  "cells (8 corners per cell, 256-bit loads)"
+                                                  if sim.grid_layout() == crp.GRID_CELLS else "nodes"),
                    "boundary": "reflective box of the modulation volume" if box is not None else "none",
                    "sources": ("Eq. 1 drawn on the device: H, He-4, N-14, Fe-56, x = 1, 0.5, 0.3, 0.1, "
                                "alpha 1.8, R_cut 10^19.8 V, 1e18-1e21 eV, density-weighted positions")

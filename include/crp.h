@@ -195,6 +195,24 @@ int crp_source_inject(crp_sim* sim, const crp_particles* particles, int64_t n, v
  * continuous loss; photo-disintegration when the interaction bid was the step; observer.
  * Asynchronous on `stream`. Errors: INVALID_ARG (tolerance <= 0, min_step_m <= 0,
  * max_step_m < min_step_m, max_distance_m <= 0, unknown form); CUDA (launch failure). */
+/* Grid layout read by the precision form (CRP_FORM_MIXED; the FP64 form always reads its
+ * FP64 node copy). NODES: one 4-wide vector per node (16 B FP32, 8 B BF16), 8 scattered
+ * corner reads per lookup. CELLS: a cell-major copy holding the 8 corners of every cell
+ * contiguously (FP32: 8 x 3 floats = 96 B; BF16: 8 x 4 halves = 64 B), periodic wrap
+ * included, read with 3 (FP32) or 2 (BF16) 32-byte loads per lookup; it takes 6x (FP32) or
+ * 8x (BF16) the node grid's device memory, is built on first use and freed with the field,
+ * and gives results identical to NODES (the same corner values in the same arithmetic).
+ * AUTO: CELLS when the copies of all the simulation's fields fit in free device memory with
+ * 4 GiB to spare, else NODES. CELLS when they do not fit: CRP_ERR_OOM. */
+#define CRP_GRID_AUTO 0
+#define CRP_GRID_NODES 1
+#define CRP_GRID_CELLS 2
+
+/* The layout the precision form reads under CRP_GRID_AUTO: CRP_GRID_CELLS once the
+ * simulation's cell-major copies are built (by a precision-form call that found room for
+ * them), else CRP_GRID_NODES. sim and layout non-NULL, else CRP_ERR_INVALID_ARG. */
+int crp_sim_grid_layout(const crp_sim* sim, int32_t* layout);
+
 typedef struct {
     int32_t form;            /* CRP_FORM_FP64 or CRP_FORM_MIXED */
     int32_t block_size;      /* threads per block, multiple of 32; 0: default */
@@ -203,6 +221,8 @@ typedef struct {
     int64_t max_steps;       /* accepted steps per particle per call; <= 0: no limit */
     int32_t order;           /* work-list order: CRP_ORDER_* (0: default = CRP_ORDER_COST) */
     int32_t pickup;          /* secondaries created in a launch: CRP_PICKUP_* (0: default = OFF) */
+    int32_t grid_layout;     /* precision form: CRP_GRID_* (0: default = AUTO) */
+    int32_t pad_;
 } crp_params;
 /* Scheduling choices (never change a particle's result, only when it runs). */
 #define CRP_ORDER_DEFAULT 0

@@ -14,6 +14,9 @@ from .api import (  # noqa: F401
     COLUMNS,
     FORM_FP64,
     FORM_MIXED,
+    GRID_AUTO,
+    GRID_CELLS,
+    GRID_NODES,
     MAX_SPECIES,
     STATUS_ACTIVE,
     STATUS_DONE,

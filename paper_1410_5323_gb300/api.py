@@ -15,6 +15,8 @@ ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_QUEUE_FULL = -1, -2, -3, -4
 ERR_TIMEOUT, ERR_NAN_STATE, ERR_TABLE_RANGE = -5, -6, -7
 DTYPE_F64, DTYPE_F32, DTYPE_BF16, DTYPE_F16 = 0, 1, 2, 3
 FORM_FP64, FORM_MIXED = 0, 1
+# grid layout read by the precision form (crp.h CRP_GRID_*)
+GRID_AUTO, GRID_NODES, GRID_CELLS = 0, 1, 2
 ORDER_DEFAULT, ORDER_SLOT, ORDER_COST, ORDER_GRID = 0, 1, 2, 3
 PICKUP_DEFAULT, PICKUP_OFF, PICKUP_ON = 0, 1, 2
 STATUS_ACTIVE, STATUS_DONE, STATUS_NAN, STATUS_RANGE = 0, 1, 2, 3
@@ -146,7 +148,7 @@ class Lens:
 class _Params(C.Structure):
     _fields_ = [("form", C.c_int32), ("block_size", C.c_int32), ("blocks_per_sm", C.c_int32),
                 ("cadence", C.c_int32), ("max_steps", C.c_int64), ("order", C.c_int32),
-                ("pickup", C.c_int32)]
+                ("pickup", C.c_int32), ("grid_layout", C.c_int32), ("pad_", C.c_int32)]
 
 
 _OBS_I64 = ("uid",)
@@ -396,17 +398,18 @@ class Simulation:
     def propagate(self, tolerance: float, min_step_m: float, max_step_m: float,
                   max_distance_m: float, form: int = FORM_FP64, max_steps: int = 0,
                   block_size: int = 0, blocks_per_sm: int = 0, cadence: int = 0,
-                  order: int = 0, pickup: int = 0, stream=None) -> None:
-        prm = _Params(form, block_size, blocks_per_sm, cadence, max_steps, order, pickup)
+                  order: int = 0, pickup: int = 0, grid_layout: int = GRID_AUTO, stream=None) -> None:
+        prm = _Params(form, block_size, blocks_per_sm, cadence, max_steps, order, pickup, grid_layout)
         _check(lib().crp_propagate(self._h, C.byref(prm), tolerance, min_step_m, max_step_m,
                                    max_distance_m, _stream_ptr(stream)), "crp_propagate")
 
     def propagate_loop(self, tolerance: float, min_step_m: float, max_step_m: float,
                        max_distance_m: float, max_steps: int, max_slices: int = 1 << 20,
                        form: int = FORM_FP64, block_size: int = 0, blocks_per_sm: int = 0,
-                       cadence: int = 0, order: int = 0, pickup: int = 0, stream=None) -> None:
+                       cadence: int = 0, order: int = 0, pickup: int = 0, grid_layout: int = GRID_AUTO,
+                       stream=None) -> None:
         """Slices of max_steps accepted steps until done, as one device-side graph loop."""
-        prm = _Params(form, block_size, blocks_per_sm, cadence, max_steps, order, pickup)
+        prm = _Params(form, block_size, blocks_per_sm, cadence, max_steps, order, pickup, grid_layout)
         _check(lib().crp_propagate_loop(self._h, C.byref(prm), tolerance, min_step_m, max_step_m,
                                         max_distance_m, int(max_slices), _stream_ptr(stream)),
                "crp_propagate_loop")
@@ -419,6 +422,12 @@ class Simulation:
 
     def reset(self) -> None:
         _check(lib().crp_sim_reset(self._h), "crp_sim_reset")
+
+    def grid_layout(self) -> int:
+        """GRID_CELLS once the precision form's cell-major copies are built, else GRID_NODES."""
+        v = C.c_int32(0)
+        _check(lib().crp_sim_grid_layout(self._h, C.byref(v)), "crp_sim_grid_layout")
+        return int(v.value)
 
     def set_boundary(self, box=None) -> None:
         """Reflective box (paper Sec. 4): ``box`` = (origin[3], size[3]) in metres, or None

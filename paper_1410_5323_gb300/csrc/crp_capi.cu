@@ -101,6 +101,29 @@ __global__ void k_layout<unsigned short, ushort4>(const unsigned short* __restri
         out[i] = make_ushort4(in[3 * i], in[3 * i + 1], in[3 * i + 2], 0);
 }
 
+// Cell-major copy of a 4-wide FP32 or BF16 node layout for the precision form: cell
+// (i, j, k) holds its corners (i+a, j+b, k+c) mod n in the order 4a + 2b + c; FP32 keeps 3
+// floats per corner (96 B per cell), BF16 the 4 halves of the node (64 B per cell).
+__global__ void k_cells(const void* __restrict__ in, int bf16, int nx, int ny, int nz, void* __restrict__ out) {
+    const long long n = (long long)nx * ny * nz;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(c / ((long long)ny * nz)), j = (int)((c / nz) % ny), k = (int)(c % nz);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int a = q >> 2, b = (q >> 1) & 1, d = q & 1;
+            const long long node = ((long long)((i + a) % nx) * ny + (j + b) % ny) * nz + (k + d) % nz;
+            if (bf16) {
+                static_cast<ushort4*>(out)[c * 8 + q] = static_cast<const ushort4*>(in)[node];
+            } else {
+                const float4 v = static_cast<const float4*>(in)[node];
+                float* o = static_cast<float*>(out) + c * 24 + 3 * q;
+                o[0] = v.x; o[1] = v.y; o[2] = v.z;
+            }
+        }
+    }
+}
+
 // Widen a 4-wide FP32 / BF16 / F16 node layout to FP64 pairs (x, y | z, 0), with the exact
 // per-corner expression the FP64 kernel would otherwise evaluate on every lookup.
 __global__ void k_widen(const void* __restrict__ in, int layout, double scale,
@@ -379,6 +402,7 @@ struct crp_field {
     long long nodes = 0;
     void* mem64 = nullptr;   // FP64 copy for the FP64 form (built on first use)
     FieldDev dev64{};
+    void* memc = nullptr;    // cell-major copy for the precision form (built on first use)
     void* modmem = nullptr;  // modulation grid, FP32 (crp_field_modulate)
 };
 
@@ -392,6 +416,7 @@ struct crp_sim {
     std::vector<crp_field*> handles;
     FieldDev* d_fields = nullptr;
     FieldDev* d_fields64 = nullptr;     // FP64 copies, for the FP64 form
+    FieldDev* d_fields_cells = nullptr; // cell-major copies, for the precision form
     int layout = LAYOUT_F32X4;
     int mod = 0;                        // 1: every field carries a modulation grid
     int boundary = CRP_BOUNDARY_NONE;   // crp_sim_set_boundary
@@ -576,6 +601,7 @@ int crp_field_destroy(crp_field* field) {
     if (!field) return fail(CRP_ERR_INVALID_ARG, "field is NULL");
     if (field->mem) cudaFree(field->mem);
     if (field->mem64) cudaFree(field->mem64);
+    if (field->memc) cudaFree(field->memc);
     if (field->modmem) cudaFree(field->modmem);
     delete field;
     return CRP_OK;
@@ -712,12 +738,19 @@ int crp_sim_set_boundary(crp_sim* s, int32_t kind, const double origin_m[3], con
     return CRP_OK;
 }
 
+int crp_sim_grid_layout(const crp_sim* s, int32_t* layout) {
+    if (!s || !layout) return fail(CRP_ERR_INVALID_ARG, "sim or layout is NULL");
+    *layout = s->d_fields_cells ? CRP_GRID_CELLS : CRP_GRID_NODES;
+    return CRP_OK;
+}
+
 int crp_sim_destroy(crp_sim* s) {
     if (!s) return fail(CRP_ERR_INVALID_ARG, "sim is NULL");
     if (s->last) cudaStreamSynchronize(s->last);
     free_state(s->st);
     if (s->d_fields) cudaFree(s->d_fields);
     if (s->d_fields64) cudaFree(s->d_fields64);
+    if (s->d_fields_cells) cudaFree(s->d_fields_cells);
     if (s->lists[0]) cudaFree(s->lists[0]);
     if (s->lists[1]) cudaFree(s->lists[1]);
     if (s->done_list) cudaFree(s->done_list);
@@ -1134,6 +1167,47 @@ int ensure_fp64_fields(crp_sim* s) {
     return CRP_OK;
 }
 
+// Cell-major copies (precision form): bytes they need beyond what is already built.
+long long cells_bytes_needed(const crp_sim* s) {
+    long long need = 0;
+    for (const crp_field* f : s->handles)
+        if (!f->memc) need += f->nodes * (f->dev.layout == LAYOUT_BF16X4 ? 64 : 96);
+    return need;
+}
+
+// Build (once per field) the cell-major copies and this simulation's descriptor array for
+// them (geometry and modulation as when the simulation was created).
+int ensure_cell_fields(crp_sim* s) {
+    if (s->d_fields_cells) return CRP_OK;
+    int rc = sync_stream(s);
+    if (rc) return rc;
+    std::vector<FieldDev> dc;
+    for (size_t i = 0; i < s->handles.size(); ++i) {
+        crp_field* f = s->handles[i];
+        const bool bf16 = f->dev.layout == LAYOUT_BF16X4;
+        if (!f->memc) {
+            void* m = nullptr;
+            CRP_CUDA(dev_malloc(&m, (size_t)f->nodes * (bf16 ? 64 : 96)));
+            k_cells<<<grid_for(f->nodes, 256, 65535), 256>>>(f->mem, bf16 ? 1 : 0, f->dev.nx, f->dev.ny,
+                                                              f->dev.nz, m);
+            cudaError_t e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+            if (e != cudaSuccess) { cudaFree(m); return cuda_fail(e, "cell-major copy"); }
+            f->memc = m;
+        }
+        FieldDev F = s->host_fields[i];
+        F.data = f->memc;
+        F.layout = bf16 ? LAYOUT_BF16_CELLS : LAYOUT_F32_CELLS;
+        dc.push_back(F);
+    }
+    void* d = nullptr;
+    CRP_CUDA(dev_malloc(&d, sizeof(FieldDev) * dc.size()));
+    cudaError_t e = cudaMemcpy(d, dc.data(), sizeof(FieldDev) * dc.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { cudaFree(d); return cuda_fail(e, "cudaMemcpy(fields cells)"); }
+    s->d_fields_cells = (FieldDev*)d;
+    return CRP_OK;
+}
+
 int make_plan(crp_sim* s, const crp_params* prm, double tol, double hmin, double hmax,
               double dmax, Plan& P) {
     if (!s || !prm) return fail(CRP_ERR_INVALID_ARG, "sim or params is NULL");
@@ -1160,6 +1234,27 @@ int make_plan(crp_sim* s, const crp_params* prm, double tol, double hmin, double
         if (rc) return rc;
         fields = s->d_fields64;
         layout = LAYOUT_F64X4;
+    }
+    if (prm->grid_layout != CRP_GRID_AUTO && prm->grid_layout != CRP_GRID_NODES &&
+        prm->grid_layout != CRP_GRID_CELLS)
+        return fail(CRP_ERR_INVALID_ARG, "unknown grid_layout");
+    if (mixed && prm->grid_layout != CRP_GRID_NODES) {
+        bool use = true;
+        if (!s->d_fields_cells) {
+            size_t free_b = 0, total_b = 0;
+            CRP_CUDA(cudaMemGetInfo(&free_b, &total_b));
+            const long long need = cells_bytes_needed(s);
+            const bool fits = (double)need + 4.0 * (1ll << 30) <= (double)free_b;
+            if (!fits && prm->grid_layout == CRP_GRID_CELLS)
+                return fail(CRP_ERR_OOM, "cell-major grid copies do not fit in free device memory");
+            use = fits;
+        }
+        if (use) {
+            int rc = ensure_cell_fields(s);
+            if (rc) return rc;
+            fields = s->d_fields_cells;
+            layout = layout == LAYOUT_BF16X4 ? LAYOUT_BF16_CELLS : LAYOUT_F32_CELLS;
+        }
     }
     int bps = prm->blocks_per_sm;
     if (bps <= 0) {

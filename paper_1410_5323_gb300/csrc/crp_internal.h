@@ -9,7 +9,11 @@ namespace crp {
 
 // Grid layouts in device memory: one 4-wide vector per node, node index
 // (i*ny + j)*nz + k, the 4th lane unused (padding keeps every corner one aligned load).
-enum Layout : int32_t { LAYOUT_F32X4 = 0, LAYOUT_F64X4 = 1, LAYOUT_BF16X4 = 2, LAYOUT_F16X4 = 3 };
+enum Layout : int32_t { LAYOUT_F32X4 = 0, LAYOUT_F64X4 = 1, LAYOUT_BF16X4 = 2, LAYOUT_F16X4 = 3,
+                        // cell-major copies for the precision form: the 8 corners of cell
+                        // (i, j, k) at cell index (i*ny + j)*nz + k, corner (a, b, c) at 4a + 2b + c;
+                        // FP32: 3 floats per corner (96 B per cell), BF16: 4 halves (64 B)
+                        LAYOUT_F32_CELLS = 4, LAYOUT_BF16_CELLS = 5 };
 
 struct FieldDev {
     const void* data;

@@ -95,6 +95,48 @@ __device__ __forceinline__ F3 corner_f(const FieldF& F, int node) {
     }
 }
 
+template <int L>
+constexpr bool kBF16 = (L == LAYOUT_BF16X4 || L == LAYOUT_BF16_CELLS);
+
+// 256-bit read-only loads: the cell-major layouts hold a cell's 8 corners in 96 B (FP32) or
+// 64 B (BF16), 32-byte aligned, so a lookup takes 3 or 2 loads instead of 8 scattered ones.
+__device__ __forceinline__ void ld8(const void* p, unsigned (&w)[8]) {
+    asm("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]),
+                   "=r"(w[7])
+                 : "l"(p));
+}
+
+// The 8 corners of a cell from a cell-major copy, in the order 000, 001, ..., 111 (the same
+// values corner_f reads from the node layout).
+template <int L>
+__device__ __forceinline__ void cell_corners(const FieldF& F, long long cell, F3& g0, F3& g1, F3& g2, F3& g3,
+                                             F3& g4, F3& g5, F3& g6, F3& g7) {
+    if constexpr (L == LAYOUT_F32_CELLS) {
+        const unsigned* q = static_cast<const unsigned*>(F.data) + cell * 24;
+        unsigned a[8], b[8], c[8];
+        ld8(q, a);
+        ld8(q + 8, b);
+        ld8(q + 16, c);
+        auto f = [](unsigned u) { return __uint_as_float(u); };
+        g0 = {f(a[0]), f(a[1]), f(a[2])}; g1 = {f(a[3]), f(a[4]), f(a[5])};
+        g2 = {f(a[6]), f(a[7]), f(b[0])}; g3 = {f(b[1]), f(b[2]), f(b[3])};
+        g4 = {f(b[4]), f(b[5]), f(b[6])}; g5 = {f(b[7]), f(c[0]), f(c[1])};
+        g6 = {f(c[2]), f(c[3]), f(c[4])}; g7 = {f(c[5]), f(c[6]), f(c[7])};
+    } else {
+        // BF16: per corner two words, (x | y << 16) and (z | pad << 16)
+        const unsigned* q = static_cast<const unsigned*>(F.data) + cell * 16;
+        unsigned a[8], b[8];
+        ld8(q, a);
+        ld8(q + 8, b);
+        auto c3 = [](unsigned w0, unsigned w1) {
+            return F3{__uint_as_float(w0 << 16), __uint_as_float(w0 & 0xFFFF0000u), __uint_as_float(w1 << 16)};
+        };
+        g0 = c3(a[0], a[1]); g1 = c3(a[2], a[3]); g2 = c3(a[4], a[5]); g3 = c3(a[6], a[7]);
+        g4 = c3(b[0], b[1]); g5 = c3(b[2], b[3]); g6 = c3(b[4], b[5]); g7 = c3(b[6], b[7]);
+    }
+}
+
 // floor(t) and t - floor(t) without conversion instructions, exact for |t| < 2^22:
 // adding 1.5 * 2^23 rounds t to an integer held in the low mantissa bits.
 __device__ __forceinline__ int floor_frac(float t, float& frac) {
@@ -205,14 +247,19 @@ __device__ __forceinline__ F3 field_f(const FieldF& F, int bx, int by, int bz, F
               cz = floor_frac(f0.z + p.z, fz);
     const int ix = wrap(bx + cx, F.nx, F.pow2), iy = wrap(by + cy, F.ny, F.pow2),
               iz = wrap(bz + cz, F.nz, F.pow2);
-    const int ix1 = ix + 1 == F.nx ? 0 : ix + 1, iy1 = iy + 1 == F.ny ? 0 : iy + 1,
-              iz1 = iz + 1 == F.nz ? 0 : iz + 1;
-    const int r00 = (ix * F.ny + iy) * F.nz, r01 = (ix * F.ny + iy1) * F.nz;
-    const int r10 = (ix1 * F.ny + iy) * F.nz, r11 = (ix1 * F.ny + iy1) * F.nz;
-    const F3 g0 = corner_f<L>(F, r00 + iz), g1 = corner_f<L>(F, r00 + iz1);
-    const F3 g2 = corner_f<L>(F, r01 + iz), g3 = corner_f<L>(F, r01 + iz1);
-    const F3 g4 = corner_f<L>(F, r10 + iz), g5 = corner_f<L>(F, r10 + iz1);
-    const F3 g6 = corner_f<L>(F, r11 + iz), g7 = corner_f<L>(F, r11 + iz1);
+    F3 g0, g1, g2, g3, g4, g5, g6, g7;
+    if constexpr (L == LAYOUT_F32X4 || L == LAYOUT_BF16X4) {
+        const int ix1 = ix + 1 == F.nx ? 0 : ix + 1, iy1 = iy + 1 == F.ny ? 0 : iy + 1,
+                  iz1 = iz + 1 == F.nz ? 0 : iz + 1;
+        const int r00 = (ix * F.ny + iy) * F.nz, r01 = (ix * F.ny + iy1) * F.nz;
+        const int r10 = (ix1 * F.ny + iy) * F.nz, r11 = (ix1 * F.ny + iy1) * F.nz;
+        g0 = corner_f<L>(F, r00 + iz); g1 = corner_f<L>(F, r00 + iz1);
+        g2 = corner_f<L>(F, r01 + iz); g3 = corner_f<L>(F, r01 + iz1);
+        g4 = corner_f<L>(F, r10 + iz); g5 = corner_f<L>(F, r10 + iz1);
+        g6 = corner_f<L>(F, r11 + iz); g7 = corner_f<L>(F, r11 + iz1);
+    } else {
+        cell_corners<L>(F, ((long long)ix * F.ny + iy) * F.nz + iz, g0, g1, g2, g3, g4, g5, g6, g7);
+    }
     const float gx = 1.0f - fx, gy = 1.0f - fy, gz = 1.0f - fz;
     const float w00 = gx * gy, w01 = gx * fy, w10 = fx * gy, w11 = fx * fy;
     float w;
@@ -227,9 +274,9 @@ __device__ __forceinline__ F3 field_f(const FieldF& F, int bx, int by, int bz, F
     w = w11 * fz; B.x = fmaf(w, g7.x, B.x); B.y = fmaf(w, g7.y, B.y); B.z = fmaf(w, g7.z, B.z);
     if constexpr (M) {
         float m = modulation_f(fields, gid, sm, mf, p);
-        if constexpr (L != LAYOUT_F32X4) m *= F.scale;
+        if constexpr (kBF16<L>) m *= F.scale;
         B.x *= m; B.y *= m; B.z *= m;
-    } else if constexpr (L != LAYOUT_F32X4) {
+    } else if constexpr (kBF16<L>) {
         B.x *= F.scale; B.y *= F.scale; B.z *= F.scale;
     }
     return B;
@@ -616,7 +663,7 @@ __global__ void CRP_MIXED_MOD_BOUNDS k_propagate_mixed_mod(const PropArgs a) {
 
 }  // namespace
 
-// Kernel for (layout, modulated): FP32 or BF16 vector grids.
+// Kernel for (layout, modulated): FP32 or BF16 vector grids, node- or cell-major.
 template <typename Fn>
 int with_mixed_kernel(int layout, int mod, Fn&& fn) {
     switch (layout) {
@@ -624,6 +671,10 @@ int with_mixed_kernel(int layout, int mod, Fn&& fn) {
         return mod ? fn(k_propagate_mixed_mod<LAYOUT_F32X4>) : fn(k_propagate_mixed<LAYOUT_F32X4>);
     case LAYOUT_BF16X4:
         return mod ? fn(k_propagate_mixed_mod<LAYOUT_BF16X4>) : fn(k_propagate_mixed<LAYOUT_BF16X4>);
+    case LAYOUT_F32_CELLS:
+        return mod ? fn(k_propagate_mixed_mod<LAYOUT_F32_CELLS>) : fn(k_propagate_mixed<LAYOUT_F32_CELLS>);
+    case LAYOUT_BF16_CELLS:
+        return mod ? fn(k_propagate_mixed_mod<LAYOUT_BF16_CELLS>) : fn(k_propagate_mixed<LAYOUT_BF16_CELLS>);
     default: return (int)cudaErrorInvalidValue;
     }
 }

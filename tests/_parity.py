@@ -16,7 +16,7 @@ def by_uid(d):
 def run_gpu(grids, parts, tables, tol, hmin, hmax, dmax, seed=1, capacity=None, max_steps=0,
             spacing=0.25 * I.MPC, form=0, calls=1, dtype=None, scale=1.0, origin=(0.0, 0.0, 0.0),
             block_size=0, cadence=0, mods=None, mod_spacing=1.0, mod_origin=(0.0, 0.0, 0.0),
-            box=None):
+            box=None, grid_layout=0):
     """mods: None, or one modulation grid per vector grid (modulated fields)."""
     import paper_1410_5323_gb300 as crp
 
@@ -31,7 +31,7 @@ def run_gpu(grids, parts, tables, tol, hmin, hmax, dmax, seed=1, capacity=None, 
     sim.inject(parts)
     for _ in range(calls):
         sim.propagate(tol, hmin, hmax, dmax, form=form, max_steps=max_steps, block_size=block_size,
-                      cadence=cadence)
+                      cadence=cadence, grid_layout=grid_layout)
     rc = sim.sync(timeout_s=600.0, raise_on_error=False)
     return sim, rc
 

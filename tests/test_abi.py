@@ -63,6 +63,9 @@ def test_null_and_range_arguments_rejected_before_device_work(L):
     assert L.crp_sim_set_boundary(fake, 7, org, sz) == -1                    # unknown kind
     assert L.crp_sim_set_boundary(fake, 1, org, sz) == -1                    # a size of 0
     assert L.crp_sim_set_boundary(fake, 1, None, sz) == -1
+    lay = C.c_int32(0)
+    assert L.crp_sim_grid_layout(None, C.byref(lay)) == -1
+    assert L.crp_sim_grid_layout(fake, None) == -1
     import paper_1410_5323_gb300 as crp
     sp = crp.Spectrum.of([(4, 2, 1.0)], 1.8, 1e19, 1e18, 1e21)
     xs = np.zeros(4)
