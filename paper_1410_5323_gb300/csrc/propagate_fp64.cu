@@ -9,7 +9,10 @@
 // second launch of this kernel processes.
 //
 // Compiled with --fmad=false: every FP64 expression is evaluated as written, in the same
-// order as the stated reading, so results are bit-identical to the FP64 oracle.
+// order as the stated reading, so results are bit-identical to the FP64 oracle. Work that
+// the reading leaves to the implementation stays off the FP64 pipe, which bounds this
+// kernel: the lookup's floors and indices are integer operations on the bits of the grid
+// coordinate, and the step-size factor is FP32 (from the bits of the FP64 error sums).
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 
@@ -24,8 +27,8 @@ namespace {
 using namespace fp64;
 
 // Register cap, a build-time tuning knob (-DCRP_FP64_MAXNREG=N). Unset by default: capping
-// the 176-register kernel at 168 (12 instead of 8 warps per SM, no spills) measured 3 % slower,
-// since the FP64 pipe, not latency, bounds it.
+// the 170-register kernel at 168 (12 instead of 8 warps per SM, no spills) measured 1.6 %
+// slower, since the FP64 pipe, not latency, bounds it.
 #ifdef CRP_FP64_MAXNREG
 #define CRP_FP64_BOUNDS __maxnreg__(CRP_FP64_MAXNREG)
 #else

@@ -14,7 +14,10 @@
 //     (|dx|/h is computed as |sum_i e_i u_i|, so no division by h is needed);
 //   * path length s stays FP64 so the observer lands exactly on the distance limit;
 //   * continuous loss and interaction rates in FP32 from FP32 copies of the tables; the
-//     Philox streams and the nucleon rule are the same integers as in the FP64 form.
+//     Philox streams and the nucleon rule are the same integers as in the FP64 form;
+//   * the vector grid is read from a cell-major copy when one is built (the 8 corners of a
+//     cell together, 3 or 2 256-bit loads per lookup instead of 8 scattered node reads: the
+//     lookups were bound by L1 requests), else from the node grid; both give the same bits.
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 

@@ -22,6 +22,8 @@ def _same(args, all_done=True, **kw):
     for layout in (crp.GRID_NODES, crp.GRID_CELLS, crp.GRID_AUTO):
         sim, rc = run_gpu(*args, form=MIXED, grid_layout=layout, **kw)
         assert rc == 0
+        # small grids: AUTO finds room for the copies
+        assert sim.grid_layout() == (crp.GRID_NODES if layout == crp.GRID_NODES else crp.GRID_CELLS)
         states.append(sim.state())
         del sim
     assert np.all(states[0]["status"] == O.DONE) or not all_done
