@@ -55,7 +55,7 @@ MIXED_FP64_OPS_PER_ATTEMPT = 14
 MIXED_FP64_OPS_PER_ACCEPTED = 5
 MIXED_FP32_FLOP_PER_ATTEMPT = 612
 # DRAM bytes (read + write) of one lens launch measured by ncu on the current kernels, keyed by
-# the number of maps (profiles/k_lens_apply_nside64_24bins.md).
+# the number of maps (the lens summary under profiles/ names the command).
 LENS_DRAM_BYTES = {1: 2.406e8, 32: 5.531e8}
 # Modulated fields add one scalar trilinear lookup per field evaluation: FP64 form 42 each
 # (axes 12, weights 12, 8 products, 7 sums, 3 products m*B), 5 x 42 = 210 per attempt and 42
@@ -348,7 +348,7 @@ def mixed_error_statement(w, mixed_state, oracle_state):
     ks_E = stats.ks_2samp(np.log10(mixed_state["E"][sel_m]), np.log10(oracle_state["E"][sel_o])).pvalue
     return {"sample_primaries": n_s, "distance_mpc": w.dmax_m / I.MPC,
             "ks_p_deflection": float(ks_defl), "ks_p_log_energy": float(ks_E),
-            "note": "per-particle angles are chaotic beyond ~15 Mpc (1-ulp floor); see DESIGN.md"}
+            "note": "per-particle angles are chaotic beyond ~15 Mpc (1-ulp floor): per-particle error by distance is in mixed_error_vs_fp64_by_distance"}
 
 
 def angle_deg(a, b):
