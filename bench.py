@@ -95,6 +95,7 @@ def parse():
     ap.add_argument("--cadence", type=int, default=0)
     ap.add_argument("--order", type=int, default=0, help="work-list order (CRP_ORDER_*); 0: default")
     ap.add_argument("--n-maps", type=int, default=1, help="lens workload: maps per rigidity bin")
+    ap.add_argument("--lens-group", type=int, default=0, help="lens workload: lanes per row for one map; 0: default")
     ap.add_argument("--slice-steps", type=int, default=-1,
                     help="> 0: graph loop of slices of this many steps; 0: one call; -1: workload default")
     return ap.parse_args()
@@ -767,6 +768,8 @@ def run_lens(args):
     rp, col, val = I.synthetic_lens(nside, I.lens_edges(n_mat), seed=1, k=k)
     nnz = int(col.size)
     lens = crp.Lens(n_pix, rp, col, val)
+    if args.lens_group:
+        lens.set_group(args.lens_group)
     dev = torch.device("cuda")
     xh = np.random.default_rng(1 + rank).poisson(3.0, (n_mat, n_pix, n_maps)).astype(np.float64)
     x = torch.from_numpy(xh if n_maps > 1 else xh[:, :, 0]).to(dev).contiguous()

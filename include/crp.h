@@ -375,6 +375,10 @@ typedef struct crp_lens crp_lens;
 int crp_lens_create(int32_t n_pix, int32_t n_mat, const int64_t* row_ptr, const int32_t* col,
                     const float* val, const double* edges, crp_lens** out);
 int crp_lens_destroy(crp_lens* lens);
+/* Lanes that share one row when a single map is applied: 4, 8, 16 or 32 (a tuning choice; the
+ * default is the mean merged row length in 4-entry vectors, rounded up to a power of two in
+ * [4, 32]). The sum stays within the same FP64 bound for any choice. Errors: INVALID_ARG. */
+int crp_lens_set_group(crp_lens* lens, int32_t lanes_per_row);
 /* Observed maps through the lens: y[p][b] = sum over m of (M_m x_m)[p][b] in FP64, each
  * entry added with one rounding (fused multiply-add), for n_maps maps at once. x: device,
  * [n_mat][n_pix][n_maps] FP64 (map b of rigidity bin m at the galactic border); y: device,

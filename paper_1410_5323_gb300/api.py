@@ -117,6 +117,10 @@ class Lens:
             _lib.crp_lens_destroy(self._h)
             self._h = None
 
+    def set_group(self, lanes_per_row: int) -> None:
+        """Lanes per row for one map (4, 8, 16 or 32)."""
+        _check(lib().crp_lens_set_group(self._h, int(lanes_per_row)), "crp_lens_set_group")
+
     def apply(self, x, out=None, stream=None):
         """x: float64 CUDA tensor [n_mat, n_pix] or [n_mat, n_pix, n_maps]; returns
         y = sum_m M_m x_m as [n_pix] or [n_pix, n_maps]."""

@@ -1086,6 +1086,13 @@ int crp_lens_create(int32_t n_pix, int32_t n_mat, const int64_t* row_ptr, const 
     return CRP_OK;
 }
 
+int crp_lens_set_group(crp_lens* L, int32_t g) {
+    if (!L) return fail(CRP_ERR_INVALID_ARG, "lens is NULL");
+    if (g != 4 && g != 8 && g != 16 && g != 32) return fail(CRP_ERR_INVALID_ARG, "lanes per row must be 4, 8, 16 or 32");
+    L->group = g;
+    return CRP_OK;
+}
+
 int crp_lens_destroy(crp_lens* L) {
     if (!L) return fail(CRP_ERR_INVALID_ARG, "lens is NULL");
     if (L->mem) cudaFree(L->mem);

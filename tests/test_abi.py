@@ -66,6 +66,8 @@ def test_null_and_range_arguments_rejected_before_device_work(L):
     lay = C.c_int32(0)
     assert L.crp_sim_grid_layout(None, C.byref(lay)) == -1
     assert L.crp_sim_grid_layout(fake, None) == -1
+    assert L.crp_lens_set_group(None, 16) == -1
+    assert L.crp_lens_set_group(fake, 12) == -1                               # not 4, 8, 16, 32
     import paper_1410_5323_gb300 as crp
     sp = crp.Spectrum.of([(4, 2, 1.0)], 1.8, 1e19, 1e18, 1e21)
     xs = np.zeros(4)

@@ -48,6 +48,22 @@ def test_one_map_within_bound_every_group_size(oracle_lib, k):
     assert np.all(np.abs(y - ref) <= _bound(n_pix, rp, col, val, x[:, :, None])[:, 0] + 1e-300)
 
 
+@pytest.mark.parametrize("g", [4, 8, 16, 32])
+def test_one_map_every_forced_group_size(oracle_lib, g):
+    """The same lens with each group size forced: within the same bound."""
+    import paper_1410_5323_gb300 as crp
+
+    nside = 8
+    n_pix = 12 * nside * nside
+    rp, col, val = I.synthetic_lens(nside, I.lens_edges(5), seed=9, k=20)
+    lens = crp.Lens(n_pix, rp, col, val)
+    lens.set_group(g)
+    x = np.random.default_rng(g).standard_normal((5, n_pix))
+    y = _gpu(lens, x)
+    ref = O.lens_apply(n_pix, rp, col, val, x[:, :, None])[:, 0]
+    assert np.all(np.abs(y - ref) <= _bound(n_pix, rp, col, val, x[:, :, None])[:, 0] + 1e-300)
+
+
 @pytest.mark.parametrize("n_maps", [2, 32, 45])
 def test_several_maps_bit_identical(oracle_lib, n_maps):
     import paper_1410_5323_gb300 as crp
