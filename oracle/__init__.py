@@ -85,6 +85,8 @@ def lib():
         L.orc_log.argtypes = [d]
         L.orc_log.restype = d
         L.orc_field_value.argtypes = [p, p, p]
+        L.orc_grid_value.argtypes = [p, i64, i64, i64, i32]
+        L.orc_grid_value.restype = d
         L.orc_modulation_value.argtypes = [p, p]
         L.orc_modulation_value.restype = d
         L.orc_deriv.argtypes = [p, d, p, p]
@@ -221,6 +223,19 @@ def field_value(field: OracleField, x) -> np.ndarray:
     B = np.zeros(3)
     lib().orc_field_value(C.byref(field.c), _ptr(xa), _ptr(B))
     return B
+
+
+def grid_values(field: OracleField) -> np.ndarray:
+    """Every stored node value as the oracle widens it, shape (nx, ny, nz, 3)."""
+    L = lib()
+    nx, ny, nz = field.c.nx, field.c.ny, field.c.nz
+    out = np.empty((nx, ny, nz, 3))
+    for i in range(nx):
+        for j in range(ny):
+            for k in range(nz):
+                for c in range(3):
+                    out[i, j, k, c] = L.orc_grid_value(C.byref(field.c), i, j, k, c)
+    return out
 
 
 def modulation_value(field: OracleField, x) -> float:

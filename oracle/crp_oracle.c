@@ -21,8 +21,9 @@
  *   - integrator: Cash & Karp (1990) embedded RK4(5), 5th-order solution propagated;
  *   - continuous energy loss and photo-disintegration with nucleon secondaries (Sec. 2),
  *     from tabulated rates, sampled with Philox4x32-10 (Salmon et al. 2011).
- * parity unpinned: full turbulent-field trajectories (the paper prints none); they are
- * held by closed-form sub-cases and invariants in the tests.
+ * Every function is pinned by a test that does not use this file's code (closed forms,
+ * library routines, brute force, every bit pattern of the F16 storage); full
+ * turbulent-field trajectories compose them and have no printed values in the paper.
  */
 #include "crp_oracle.h"
 
@@ -187,6 +188,13 @@ static double grid_at(const orc_field* f, int64_t i, int64_t j, int64_t k, int c
     case ORC_BF16: return bf16_to_double(((const uint16_t*)f->data)[idx]) * f->scale;
     default: return f16_to_double(((const uint16_t*)f->data)[idx]) * f->scale;
     }
+}
+
+/* Stored value of node (i, j, k), component c, widened to double (times the scale for
+ * BF16/F16 storage): the value every lookup of that node reads (Sec. 3.2 regular grids). */
+double orc_grid_value(const orc_field* f, int64_t i, int64_t j, int64_t k, int32_t c)
+{
+    return grid_at(f, i, j, k, c);
 }
 
 /* Modulation (Sec. 3.2): the scalar grid interpolated trilinearly, periodic over its own

@@ -110,6 +110,7 @@ double orc_uniform(uint64_t seed, uint64_t uid, uint32_t k, uint32_t tag);
 double orc_exp(double x);
 double orc_log(double x);
 void orc_field_value(const orc_field* f, const double x[3], double B[3]);
+double orc_grid_value(const orc_field* f, int64_t i, int64_t j, int64_t k, int32_t c);
 double orc_modulation_value(const orc_field* f, const double x[3]);
 void orc_deriv(const orc_field* f, double kappa, const double y[6], double k[6]);
 void orc_ck_attempt(const orc_field* f, double kappa, const double y[6], const double k1[6],

@@ -93,3 +93,25 @@ def test_storage_widening(oracle_lib, dtype):
         f = O.OracleField(bits, 1.0, scale=2e-13, dtype=O.BF16)
         assert np.allclose(oracle_lib.field_value(f, np.array([1.25, 2.75, 0.125])),
                            np.array([0.5, -0.25, 3.0]) * 2e-13, rtol=1e-15)
+
+
+@pytest.mark.parametrize("scale", [1.0, 2e-13, -3.5])
+def test_f16_widening_every_pattern(oracle_lib, scale):
+    """F16 storage (Sec. 3.2 grids; the F16 storage type is this project's reading): every
+    one of the 65 536 half-precision bit patterns -- normals, subnormals, +-0, +-inf, NaN --
+    widens to numpy's float16 value in float64, times the FP32 scale in FP64."""
+    bits = np.arange(65536, dtype=np.uint32).astype(np.uint16)
+    g = np.empty((16, 16, 256, 3), dtype=np.uint16)
+    g[..., 0] = bits.reshape(16, 16, 256)
+    g[..., 1] = np.roll(bits, 1).reshape(16, 16, 256)
+    g[..., 2] = np.roll(bits, 12345).reshape(16, 16, 256)
+    f = O.OracleField(g, 1.0, scale=scale, dtype=O.F16)
+    got = O.grid_values(f)
+    with np.errstate(invalid="ignore"):
+        want = g.view(np.float16).astype(np.float64) * np.float64(np.float32(scale))
+    nan = np.isnan(want)
+    assert nan.sum() == 3 * 2 * 1023                 # 1023 NaN payloads of either sign
+    assert np.array_equal(np.isnan(got), nan)
+    assert np.array_equal(got[~nan], want[~nan])
+    # signs of zero and infinity are kept
+    assert np.array_equal(np.signbit(got[~nan]), np.signbit(want[~nan]))
