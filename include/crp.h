@@ -423,14 +423,18 @@ int crp_selftest_wait(int32_t limit, int32_t preset, void* stream);
  * crp_propagate does, to max_distance_m or max_steps accepted steps (<= 0: no limit).
  * The field is `grid_f32x4`: a device pointer, 16-byte aligned, to nx*ny*nz float4 nodes
  * (x, y, z components, fourth lane ignored), node (i,j,k) at index (i*ny + j)*nz + k.
- * The call waits for the work on `stream` to finish and returns CRP_OK or the device
- * status as a code (CRP_ERR_NAN_STATE, CRP_ERR_INVALID_ARG for an invalid particle).
+ * The call synchronises `stream` (it waits for the work to finish), reads the device
+ * status word back and returns CRP_OK or that status as the code crp_sync would give:
+ * CRP_ERR_NAN_STATE (non-finite state), CRP_ERR_INVALID_ARG (an invalid particle),
+ * CRP_ERR_CUDA (a work-list entry out of range was skipped, e.g. when two calls overlap
+ * on the shared array; particles may then be left unpropagated), CRP_ERR_TIMEOUT,
+ * CRP_ERR_QUEUE_FULL, CRP_ERR_TABLE_RANGE (not reachable without interactions).
  *
  * Limits and sharing: n <= CRP_NOALLOC_MAX_PARTICLES, else CRP_ERR_INVALID_ARG and nothing
  * runs. The first call on a device looks up the static array's device address (once per
- * device, with that device current); make that first call before any stream capture.
- * Every call reuses the same array and clears what must start at zero, so calls that
- * overlap on the GPU (from several host threads or streams) race: serialise them.
+ * device, with that device current), so make that first call before any stream capture
+ * begins. Every call reuses the same array and clears what must start at zero, so calls
+ * that overlap on the GPU (from several host threads or streams) race: serialise them.
  * It never calls cudaMalloc, cudaFree or any allocating routine. */
 #define CRP_NOALLOC_MAX_PARTICLES 262144
 #define CRP_NOALLOC_SCRATCH_BYTES (512 + 3 * 4 * CRP_NOALLOC_MAX_PARTICLES)

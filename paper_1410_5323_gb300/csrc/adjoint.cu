@@ -345,6 +345,12 @@ __global__ void k_adj_p0bar(const double* __restrict__ y0, const double* __restr
 
 int blocks(long long n) { return (int)((n + 127) / 128); }
 
+// Kernels with one thread per chain run one warp per block: 4096 chains are then 128 blocks
+// spread over 128 SMs instead of 32 blocks of four warps on 32 SMs (each warp's sequential
+// chain is bound by its SM's FP64 pipe and lookup latency, not by occupancy).
+constexpr int kChainBlock = 32;
+int chain_blocks(long long n) { return (int)((n + kChainBlock - 1) / kChainBlock); }
+
 }  // namespace
 
 int adj_init(const double* x0, const double* p0, const int32_t* Z, double* y0, double* kappa,
@@ -356,7 +362,7 @@ int adj_init(const double* x0, const double* p0, const int32_t* Z, double* y0, d
 int adj_record(const FieldDev& F, const double* y0, const double* kappa, double tol, double hmin,
                double hmax, int n_steps, int K, double* h, double* ck, double* xT, double* uT,
                long long n, void* stream) {
-    k_adj_record<LAYOUT_F64X4><<<blocks(n), 128, 0, (cudaStream_t)stream>>>(
+    k_adj_record<LAYOUT_F64X4><<<chain_blocks(n), kChainBlock, 0, (cudaStream_t)stream>>>(
         F, y0, kappa, tol, hmin, hmax, n_steps, K, h, ck, xT, uT, n);
     return (int)cudaGetLastError();
 }
@@ -364,10 +370,10 @@ int adj_record(const FieldDev& F, const double* y0, const double* kappa, double 
 int adj_replay(const FieldDev& F, const double* y0, const double* kappa, const double* h, int n_steps,
                double* xT, double* uT, unsigned long long* cell_hash, long long n, void* stream) {
     if (cell_hash)
-        k_adj_replay<LAYOUT_F64X4, true><<<blocks(n), 128, 0, (cudaStream_t)stream>>>(
+        k_adj_replay<LAYOUT_F64X4, true><<<chain_blocks(n), kChainBlock, 0, (cudaStream_t)stream>>>(
             F, y0, kappa, h, n_steps, xT, uT, cell_hash, n);
     else
-        k_adj_replay<LAYOUT_F64X4, false><<<blocks(n), 128, 0, (cudaStream_t)stream>>>(
+        k_adj_replay<LAYOUT_F64X4, false><<<chain_blocks(n), kChainBlock, 0, (cudaStream_t)stream>>>(
             F, y0, kappa, h, n_steps, xT, uT, nullptr, n);
     return (int)cudaGetLastError();
 }
@@ -381,11 +387,11 @@ int adj_backward(const FieldDev& F, const double* kappa, const double* h, const 
             F, kappa, h, ck, stages, n_steps, K, n);
         const int e = (int)cudaGetLastError();
         if (e) return e;
-        k_adj_reverse<LAYOUT_F64X4><<<blocks(n), 128, 0, (cudaStream_t)stream>>>(
+        k_adj_reverse<LAYOUT_F64X4><<<chain_blocks(n), kChainBlock, 0, (cudaStream_t)stream>>>(
             F, kappa, h, stages, n_steps, uT_bar, grid_bar, y0_bar, kappa_bar, n);
         return (int)cudaGetLastError();
     }
-    k_adj_backward<LAYOUT_F64X4><<<blocks(n), 128, 0, (cudaStream_t)stream>>>(
+    k_adj_backward<LAYOUT_F64X4><<<chain_blocks(n), kChainBlock, 0, (cudaStream_t)stream>>>(
         F, kappa, h, ck, seg, n_steps, K, uT_bar, grid_bar, y0_bar, kappa_bar, n);
     return (int)cudaGetLastError();
 }

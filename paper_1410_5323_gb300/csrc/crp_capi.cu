@@ -1666,8 +1666,15 @@ extern "C" int crp_propagate_noalloc(const void* grid, int32_t nx, int32_t ny, i
     CRP_CUDA(cudaStreamSynchronize(st));
     unsigned bits = 0;
     CRP_CUDA(cudaMemcpy(&bits, &ctr->status_bits, sizeof bits, cudaMemcpyDeviceToHost));
+    // every device status bit is an error here, mapped to the codes crp_sync uses
+    if (bits & BIT_QUEUE_FULL) return fail(CRP_ERR_QUEUE_FULL, "secondary queue full");
     if (bits & BIT_NAN) return fail(CRP_ERR_NAN_STATE, "non-finite particle state");
+    if (bits & BIT_RANGE) return fail(CRP_ERR_TABLE_RANGE, "species outside tables");
     if (bits & BIT_INVALID) return fail(CRP_ERR_INVALID_ARG, "invalid particle");
+    if (bits & BIT_TIMEOUT) return fail(CRP_ERR_TIMEOUT, "a pushed secondary never appeared in its list");
+    if (bits & BIT_BOUNDS)
+        return fail(CRP_ERR_CUDA, "a work-list entry was out of range and skipped (overlapping calls?)");
+    if (bits) return fail(CRP_ERR_CUDA, "unknown device status bit");
     return CRP_OK;
 }
 

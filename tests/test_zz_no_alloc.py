@@ -72,13 +72,19 @@ def _noalloc(L, grid, parts, seed, dmax):
 
 def test_noalloc_matches_existing_entry_point_twice():
     L = _lib()
+    L.crp_debug_fail_allocations.argtypes = [C.c_int32]
     grid = I.kolmogorov_grid(16, 0.25 * I.MPC, 2, 8, 1e-13, 21).astype(np.float32)
     cases = [(I.make_particles(300, 31, species=(("H", .5), ("Fe", .5)),
                                energy=("power", 1e18, 1e20, 2.0)), 5, 20 * I.MPC),
              (I.make_particles(77, 32, energy=("loguniform", 1e17, 1e20)), 6, 12 * I.MPC)]
     for parts, seed, dmax in cases:          # two calls in a row share the static scratch
         ref = _reference(grid, parts, seed, dmax)
-        got = _noalloc(L, grid, parts, seed, dmax)
+        # every device allocation the library makes fails while armed: the call must not need one
+        assert L.crp_debug_fail_allocations(1 << 30) == 0
+        try:
+            got = _noalloc(L, grid, parts, seed, dmax)
+        finally:
+            L.crp_debug_fail_allocations(0)
         for k in ref:
             assert np.array_equal(ref[k], got[k]), k
         assert np.all(got["status"] == 1)
