@@ -28,6 +28,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_1410_5323_gb300 import inputs as I  # noqa: E402
+from paper_1410_5323_gb300 import shard  # noqa: E402
 
 METRIC = "particle RK-steps/s (accepted Cash-Karp steps summed over particles / propagate time)"
 UNIT = "steps/s"
@@ -158,11 +159,12 @@ def build_inputs(w: I.Workload, n: int, rank: int):
         parts = I.make_particles(n, w.particle_seed + 7919 * rank, w.species, w.energy,
                                  uid_offset=rank * n)
         return [GridInput(bf16=q, scale=scale)], tables, parts
-    if w.n_grids > 1:
-        grids, _ = I.batched_grids(w)
+    if w.n_grids > 1:           # realisations split by grid id over the ranks (one job)
+        ws = dist_env()[0]
+        ids = shard.grid_shard(w.n_grids, rank, ws)
+        grids, _ = I.batched_grids(w, ids=ids)
         per = max(1, n // w.n_grids)
-        parts = I.batched_particles(w, per, seed=w.particle_seed + 7919 * rank)
-        parts.uid[:] += rank * len(parts)
+        parts = shard.take_grid_shard(I.batched_particles(w, per, seed=w.particle_seed), ids)
         return [GridInput(grid=g) for g in grids], tables, parts
     grid = I.kolmogorov_grid(w.grid_n, w.spacing_m, w.lmin_cells, w.lmax_cells, w.brms_t,
                              w.grid_seed).astype(np.float32)
@@ -819,7 +821,7 @@ def run_own(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
+        "scaling": "strong" if w.n_grids > 1 else "weak", "vs_baseline": None,
         "dtype": "f64" if args.form == "fp64" else "f32 stages / f64 norm+path / double-float position",
         "data": "synthetic",
         "config": {"workload": w.name, "particles_per_gpu": n,
@@ -841,7 +843,9 @@ def run_own(args):
                    "l2": f"inputs larger than L2 (grids {grid_bytes / 1e6:.0f} MB in device layout, "
                          f"particle state {cap * 140 / 1e9:.2f} GB at 140 B per slot) and a 256 MB flush "
                          f"before every step",
-                   "parallelism": f"dp{ws} (independent particle batches per GPU)"},
+                   "parallelism": (f"dp{ws} (the {w.n_grids} realisations split by grid id: each GPU "
+                                   f"holds its own grids and their particles)" if w.n_grids > 1 else
+                                   f"dp{ws} (independent particle batches per GPU)")},
         "accepted_steps_per_step": accepted_all / args.steps,
         "attempted_steps_per_step": attempted_all / args.steps,
         "reject_frac": 1.0 - accepted_all / max(attempted_all, 1.0),
@@ -885,13 +889,24 @@ def run_adjoint(args):
     import paper_1410_5323_gb300 as crp
     from paper_1410_5323_gb300.adjoint import Adjoint, direction_loss, perturbed_targets
 
+    ws, rank, local = dist_env()
+    dist = None
+    if ws > 1 and not getattr(args, "leg", False):
+        import torch.distributed as dist
+
+        if not dist.is_initialized():
+            dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     w = workload_for(args)
-    n = args.n_particles or w.n_particles
+    n_all = args.n_particles or w.n_particles
     n_steps, K = 2000, 64
     g = I.kolmogorov_grid(w.grid_n, w.spacing_m, w.lmin_cells, w.lmax_cells, w.brms_t,
                           w.grid_seed).astype(np.float32)
-    p = I.make_particles(n, w.particle_seed, w.species, w.energy)
-    dev = torch.device("cuda")
+    # the job's chains split into blocks over the ranks; dL/dB is summed over them
+    lo, hi = shard.block_range(n_all, rank, ws)
+    p = I.make_particles(n_all, w.particle_seed, w.species, w.energy).take(np.arange(lo, hi))
+    n = len(p)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
     peaks = peaks_for(dev)
     field = crp.Field(torch.from_numpy(g).to(dev), w.spacing_m)
     adj = Adjoint(field, n, n_steps, K)
@@ -899,10 +914,12 @@ def run_adjoint(args):
     p0 = torch.from_numpy(p.u * p.E[:, None]).to(dev)
     Z = torch.from_numpy(p.Z).to(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    clocks = ClockSampler(0)
+    clocks = ClockSampler(local)
     fwd_ms, bwd_ms = [], []
     for it in range(args.warmup + args.steps):
         if it == args.warmup:
+            if dist is not None:
+                dist.barrier()
             torch.cuda.synchronize()
             clocks.start()
         flush.zero_()
@@ -915,15 +932,19 @@ def run_adjoint(args):
         direction_loss(u, t).backward()
         e1b.record()
         gb, pb, xb = adj.backward(u.grad, g.shape)
+        shard.allreduce_sum_(gb, dist)
         e2.record()
         torch.cuda.synchronize()
         if it >= args.warmup:
             fwd_ms.append(e0.elapsed_time(e1))
             bwd_ms.append(e1b.elapsed_time(e2))
+    if dist is not None:
+        dist.barrier()
     clk = clocks.stop()
     steps = n * n_steps
+    t_max, steps_all, _ = aggregate(dist, (sum(fwd_ms) + sum(bwd_ms)), float(steps * args.steps), 0.0, dev)
     t_s = (sum(fwd_ms) + sum(bwd_ms)) * 1e-3
-    value = steps * args.steps / t_s
+    value = steps_all / (t_max * 1e-3)
     h = adj.steps().cpu().numpy()
     # attempts of the recorded forward are not counted by the kernel: a step is one attempt
     # when no rejection happened, which the recorded sizes show (h equals the proposal).
@@ -976,7 +997,7 @@ def run_adjoint(args):
 
     # ---- error statement: reverse pass vs the oracle's, central differences ----
     err, cpu = None, None
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and ws == 1:
         _, uT = adj.forward(x0, p0, Z, w.tol, w.hmin_m, w.hmax_m)
         t = perturbed_targets(uT)
         un = torch.linalg.norm(uT, dim=1, keepdim=True)
@@ -1017,14 +1038,17 @@ def run_adjoint(args):
         cpu = {"value": len(pick) * n_steps / dt, "unit": "steps/s", "cores": 1, "kind": "oracle",
                "sample": f"{len(pick)} of the {n} chains: recorded forward + reverse pass over "
                          f"{n_steps} frozen steps in {dt:.2f} s (FP64 oracle, one thread)"}
+    if dist is not None and not getattr(args, "leg", False):
+        dist.destroy_process_group()
     return {
         "metric": "frozen particle-steps differentiated/s (recorded forward + checkpointed reverse pass)",
-        "value": value, "unit": "steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": t_s * 1e3 / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "particles": n, "frozen_steps": n_steps, "checkpoint_every": K,
-                   "grid": f"{w.grid_n}^3 f32 (read as its FP64 copy)",
-                   "l2": "256 MB flush before every step"},
+        "value": value, "unit": "steps/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "particles": n_all, "particles_per_gpu": n, "frozen_steps": n_steps,
+                   "checkpoint_every": K, "grid": f"{w.grid_n}^3 f32 (read as its FP64 copy)",
+                   "l2": "256 MB flush before every step",
+                   "parallelism": f"dp{ws} (chains split in blocks; dL/dB summed by one all-reduce per step)"},
         "forward_ms": sum(fwd_ms) / args.steps, "backward_ms": sum(bwd_ms) / args.steps,
         "roofline": roof, "e2e": e2e, "error_vs_fp64_oracle": err, "cpu_baseline": cpu,
         "gpu_launches": 5 * args.steps,     # init + record; stage recompute + reverse + p0 gradient
@@ -1224,7 +1248,9 @@ def main():
                                                                   "workloads; the adjoint's oracle timing is "
                                                                   "its cpu_baseline"}))
             return 0
-        print(json.dumps(run_adjoint(args)), flush=True)
+        line = run_adjoint(args)
+        if dist_env()[1] == 0:
+            print(json.dumps(line), flush=True)
         return 0
     w = workload_for(args)
     default_run = args.workload == "fp64_256cube_1M_nuclei" and not args.n_particles and not args.grid_n

@@ -486,14 +486,16 @@ def batched_brms(n_grids: int = 64, seed: int = 1, lo: float = 0.1, hi: float = 
     return np.exp(rng.uniform(math.log(lo), math.log(hi), n_grids)) * NANOGAUSS
 
 
-def batched_grids(w: Workload, n_grids: int | None = None, grid_n: int | None = None):
+def batched_grids(w: Workload, n_grids: int | None = None, grid_n: int | None = None, ids=None):
     """Field realisations of the batching workload: seeds 1..n, B_rms log-uniform in
-    [0.1, 10] nG, each an FP32 [n, n, n, 3] Kolmogorov grid."""
+    [0.1, 10] nG, each an FP32 [n, n, n, 3] Kolmogorov grid. With `ids`, only those
+    realisations (same seeds and B_rms as in the whole set)."""
     n_grids = n_grids or w.n_grids
     grid_n = grid_n or w.grid_n
     brms = batched_brms(n_grids)
+    ids = range(n_grids) if ids is None else [int(i) for i in ids]
     return [kolmogorov_grid(grid_n, w.spacing_m, w.lmin_cells, w.lmax_cells, float(brms[i]),
-                            i + 1).astype(np.float32) for i in range(n_grids)], brms
+                            i + 1).astype(np.float32) for i in ids], brms
 
 
 def batched_particles(w: Workload, n_per_grid: int, n_grids: int | None = None, seed: int = 1):
