@@ -153,9 +153,12 @@ def build_inputs(w: I.Workload, n: int, rank: int):
     """Field grids (list of GridInput), tables, particles of the workload (this rank's batch)."""
     tables = I.synthetic_tables() if w.interactions else None
     if w.grid_n >= 512:     # generated and quantised on the device (BF16 + one FP32 scale)
+        import torch
+
         B = I.kolmogorov_grid_torch(w.grid_n, w.lmin_cells, w.lmax_cells, w.brms_t, w.grid_seed)
         q, scale = I.quantize_bf16(B)
         del B
+        torch.cuda.empty_cache()       # the FFT's working memory goes back to the device
         parts = I.make_particles(n, w.particle_seed + 7919 * rank, w.species, w.energy,
                                  uid_offset=rank * n)
         return [GridInput(bf16=q, scale=scale)], tables, parts
@@ -1220,6 +1223,8 @@ def run_leg(args, workload: str, sample: int) -> dict:
 
     import torch
 
+    gc.collect()                       # the previous leg's grids and state are freed
+    torch.cuda.empty_cache()
     a = copy.copy(args)
     a.workload, a.leg = workload, True
     a.steps, a.warmup = args.forms_steps, args.forms_warmup
