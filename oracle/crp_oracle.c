@@ -386,13 +386,11 @@ float orc_ctrl_log2r(double sx, double su, double h, double tol)
     return fmaxf(lx, lu) - orc_ctrl_log2(tol);
 }
 
-/* 0.95 r^p = 0.95 2^y with y = p log2 r clamped to [-8, 8] (beyond it every factor below is
- * clamped anyway): 2^n exactly (n = floor y) times e^(f ln 2), f = y - n in [0, 1), by
- * Taylor through the 8th power (truncation error below 1e-7); the result clamped to
- * [lo, hi]. A NaN y counts as -8 (the smallest factor). */
-float orc_ctrl_factor(float log2r, float p, float lo, float hi)
+/* 2^y in FP32 for y in [-126, 126] (the caller clamps): 2^n exactly (n = floor y) times
+ * e^(f ln 2), f = y - n in [0, 1), by Taylor through the 8th power in Horner order (truncation
+ * error below 1e-7); the product q 2^n rounded once. */
+static float pow2_series(float y)
 {
-    float y = fminf(fmaxf(p * log2r, -8.0f), 8.0f);
     float n = floorf(y);
     float x = (y - n) * 0x1.62e430p-1f;         /* ln 2 */
     float q = 0x1.a01a02p-16f;                  /* 1/8! */
@@ -407,40 +405,69 @@ float orc_ctrl_factor(float log2r, float p, float lo, float hi)
     uint32_t pb = (uint32_t)((int)n + 127) << 23;
     float p2;
     memcpy(&p2, &pb, sizeof p2);
-    return fminf(fmaxf(0.95f * (q * p2), lo), hi);
+    return q * p2;
+}
+
+/* 0.95 r^p = 0.95 2^y with y = p log2 r clamped to [-8, 8] (beyond it every factor below is
+ * clamped anyway), the result clamped to [lo, hi]. A NaN y counts as -8 (the smallest
+ * factor). */
+float orc_ctrl_factor(float log2r, float p, float lo, float hi)
+{
+    float y = fminf(fmaxf(p * log2r, -8.0f), 8.0f);
+    return fminf(fmaxf(0.95f * pow2_series(y), lo), hi);
 }
 
 /* ---- tabulated rates (Sec. 2 interactions; synthetic tables) -----------------------
- * gamma0 = E / (A m_p c^2); x = log(gamma0) * (1/ln 10); t = (x - x0) * inv_dx clamped to
- * [0, n_nodes-1]; j = floor(t) (at most n_nodes-2); v = T_j + (t - j)(T_{j+1} - T_j);
- * rate = exp(v ln 10). Returns 0 or ORC_RANGE if the species is outside the table. */
-int orc_rates(const orc_tables* t, int32_t A, int32_t Z, double E, double* r_loss, double* r_pd)
+ * The rates are a heuristic input (tabulated, interpolated), so they are evaluated in FP32
+ * from the FP64 state, by the same bit-level log2 and power-of-two series as the step
+ * controller:
+ *   x = (log2 E - log2(A m_p c^2)) log10(2), each log2 from the bits (orc_ctrl_log2; the
+ *       product A m_p c^2 in FP64), i.e. x = log10 gamma0;
+ *   t = (x - x0) inv_dx clamped to [0, n_nodes-1]; j = floor(t) (at most n_nodes-2);
+ *   v = T_j + (t - j)(T_{j+1} - T_j) over the FP64 table entries rounded to FP32;
+ *   rate = 2^(v log2 10), the exponent clamped to [-126, 126] (pow2_series).
+ * Every operation is one FP32 rounding in the order written. Relative error of a rate
+ * against the exact interpolation: below 2^-23 (|v log2 10| + 4), 2e-5 for the tables'
+ * |v| < 40. Returns 0, or ORC_RANGE if the species is outside the table. */
+int orc_rates_f32(const orc_tables* t, int32_t A, int32_t Z, double E, float* r_loss, float* r_pd)
 {
-    *r_loss = 0.0;
-    *r_pd = 0.0;
+    *r_loss = 0.0f;
+    *r_pd = 0.0f;
     if (!t) return 0;
     int32_t N = A - Z;
     if (Z < 0 || N < 0 || Z > t->z_max || N > t->n_max) return ORC_RANGE;
     int64_t sp = (int64_t)Z * (t->n_max + 1) + N;
-    double gamma0 = E / ((double)A * MP_C2_EV);
-    double x = orc_log(gamma0) * INV_LN10;
-    double tt = (x - t->x0) * t->inv_dx;
-    double tmax = (double)(t->n_nodes - 1);
-    tt = fmin(fmax(tt, 0.0), tmax);
-    int64_t j = (int64_t)floor(tt);
+    float lg = orc_ctrl_log2(E) - orc_ctrl_log2((double)A * MP_C2_EV);
+    float x = lg * 0x1.344136p-2f;                       /* log10 2 */
+    float tt = (x - (float)t->x0) * (float)t->inv_dx;
+    float tmax = (float)(t->n_nodes - 1);
+    tt = fminf(fmaxf(tt, 0.0f), tmax);
+    int32_t j = (int32_t)floorf(tt);
     if (j > t->n_nodes - 2) j = t->n_nodes - 2;
-    double fr = tt - (double)j;
+    float fr = tt - (float)j;
     if (t->has_loss[sp]) {
         const double* T = t->log10_loss + sp * t->n_nodes;
-        double v = T[j] + fr * (T[j + 1] - T[j]);
-        *r_loss = orc_exp(v * LN10);
+        float a = (float)T[j], b = (float)T[j + 1];
+        float y = (a + fr * (b - a)) * 0x1.a934f0p+1f;   /* log2 10 */
+        *r_loss = pow2_series(fminf(fmaxf(y, -126.0f), 126.0f));
     }
     if (t->has_pd[sp]) {
         const double* T = t->log10_pd + sp * t->n_nodes;
-        double v = T[j] + fr * (T[j + 1] - T[j]);
-        *r_pd = orc_exp(v * LN10);
+        float a = (float)T[j], b = (float)T[j + 1];
+        float y = (a + fr * (b - a)) * 0x1.a934f0p+1f;
+        *r_pd = pow2_series(fminf(fmaxf(y, -126.0f), 126.0f));
     }
     return 0;
+}
+
+/* The FP32 rates widened (exactly) to FP64. */
+int orc_rates(const orc_tables* t, int32_t A, int32_t Z, double E, double* r_loss, double* r_pd)
+{
+    float rl = 0.0f, rp = 0.0f;
+    int rc = orc_rates_f32(t, A, Z, E, &rl, &rp);
+    *r_loss = (double)rl;
+    *r_pd = (double)rp;
+    return rc;
 }
 
 /* ---- source injection (Sec. 4: isotropic emission; sampled positions/directions are
@@ -534,16 +561,19 @@ static void propagate_one(orc_job* job, int64_t i)
     int64_t acc_total = 0, att_total = 0, taken = 0;
 
     while (status == ORC_ACTIVE && (p->max_steps <= 0 || taken < p->max_steps)) {
-        /* rates at the start of the step (gamma0) */
-        double rl = 0.0, rpd = 0.0;
-        if (orc_rates(tab, A, Z, E, &rl, &rpd) != 0) {
+        /* rates at the start of the step (gamma0), FP32 */
+        float rl_f = 0.0f, rpd_f = 0.0f;
+        if (orc_rates_f32(tab, A, Z, E, &rl_f, &rpd_f) != 0) {
             status = ORC_RANGE;
             break;
         }
-        /* bids (Sec. 3.1): propagation, continuous loss, interaction, distance; lowest wins */
+        double rl = (double)rl_f, rpd = (double)rpd_f;
+        /* bids (Sec. 3.1): propagation, continuous loss, interaction, distance; lowest wins.
+         * The loss and interaction bids are FP32 quotients (of heuristic inputs), widened:
+         * 0.1 / R_loss and max(tau, 0) / R_pd with tau rounded to FP32. */
         double h_prop = fmin(fmax(hprop, p->hmin), p->hmax);
-        double h_loss = rl > 0.0 ? 0.1 / rl : INFINITY;
-        double h_int = rpd > 0.0 ? fmax(tau, 0.0) / rpd : INFINITY;
+        double h_loss = rl_f > 0.0f ? (double)(0.1f / rl_f) : INFINITY;
+        double h_int = rpd_f > 0.0f ? (double)((float)fmax(tau, 0.0) / rpd_f) : INFINITY;
         double h_dist = p->dmax - s;
         double h = h_prop;
         if (h_loss < h) h = h_loss;

@@ -120,6 +120,7 @@ int orc_error_accept(double sx, double su, double h, double tol);
 float orc_ctrl_log2(double v);
 float orc_ctrl_log2r(double sx, double su, double h, double tol);
 float orc_ctrl_factor(float log2r, float p, float lo, float hi);
+int orc_rates_f32(const orc_tables* t, int32_t A, int32_t Z, double E, float* r_loss, float* r_pd);
 int orc_rates(const orc_tables* t, int32_t A, int32_t Z, double E, double* r_loss, double* r_pd);
 int orc_inject(orc_state* st, int64_t first, int64_t count, uint64_t seed, const orc_tables* t);
 int orc_propagate(orc_state* st, const orc_field* fields, int32_t n_fields, const orc_tables* t,

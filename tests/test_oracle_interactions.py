@@ -19,12 +19,29 @@ def _by_uid(st):
     return {k: v[order] for k, v in snap.items()}
 
 
+def _f32_rate_bound(rate, E=1e21, slope=3.0):
+    """Relative error bound of the FP32 rate evaluation (u = 2^-24 per rounding):
+    exponent y = v log2 10: two roundings of |y| -> ln2 u (2|y| + 2);
+    the FP32 table entries and interpolation: ln10 u 2|v|;
+    the coordinate x = log10 gamma0: log2 E and log2(A m_p c^2) (< 90 each), their difference
+    and the scaling, plus the 23-bit truncation of each argument (2 x 1.7e-7), times the
+    table's slope d log10 rate / d log10 gamma (<= 3 here), times ln10."""
+    u = 2.0 ** -24
+    y = abs(math.log2(rate))
+    v = abs(math.log10(rate))
+    lgE = abs(math.log2(E))
+    x_err = (u * (lgE + 90.0 + 90.0 + 4.0) + 2 * 1.72e-7) * math.log10(2.0)
+    return math.log(2.0) * u * (2 * y + 2) + math.log(10.0) * (u * 2 * v + slope * x_err)
+
+
 def test_table_interpolation_reproduces_closed_form(oracle_lib):
     """Breaks sit on nodes and log10 rates are linear in log10(gamma) between them, so the
-    log-linear interpolation equals the closed form to roundoff."""
+    log-linear interpolation equals the closed form; the FP32 evaluation stays within its
+    stated bound (a pure relative tolerance: the rates are ~1e-25 per metre)."""
     t = I.synthetic_tables()
     ot = O.OracleTables(t)
     rng = np.random.default_rng(11)
+    worst = 0.0
     for _ in range(2000):
         Z = int(rng.integers(1, 27))
         N = int(rng.integers(0, 31))
@@ -34,11 +51,32 @@ def test_table_interpolation_reproduces_closed_form(oracle_lib):
         rc, rl, rp = oracle_lib.rates(ot, A, Z, E)
         assert rc == 0
         xc = min(max(math.log10(E / (A * MP)), 6.0), 14.0)
-        assert rl == pytest.approx(float(I.loss_rate_closed_form(A, Z, xc)), rel=1e-12)
+        want = float(I.loss_rate_closed_form(A, Z, xc))
+        assert rl == pytest.approx(want, rel=_f32_rate_bound(want, E), abs=0.0)
+        worst = max(worst, abs(rl / want - 1.0))
         if A > 1:
-            assert rp == pytest.approx(float(I.pd_rate_closed_form(A, xc)), rel=1e-12)
+            want = float(I.pd_rate_closed_form(A, xc))
+            assert rp == pytest.approx(want, rel=_f32_rate_bound(want, E), abs=0.0)
         else:
             assert rp == 0.0
+        # the rates are FP32 values, widened exactly
+        assert float(np.float32(rl)) == rl and float(np.float32(rp)) == rp
+    assert 1e-8 < worst < 4e-5          # FP32 evaluation, not an FP64 one
+
+
+def test_rates_clamp_to_the_table_ends(oracle_lib):
+    """Below and above the tabulated Lorentz factors the end values hold (clamped
+    coordinate); E = 0 and E = inf clamp the same way."""
+    ot = O.OracleTables(I.synthetic_tables())
+    for A, Z in ((56, 26), (4, 2), (1, 1)):
+        lo = oracle_lib.rates(ot, A, Z, 10 ** 6 * A * MP)
+        hi = oracle_lib.rates(ot, A, Z, 10 ** 14 * A * MP)
+        assert oracle_lib.rates(ot, A, Z, 10 ** 3 * A * MP) == lo
+        assert oracle_lib.rates(ot, A, Z, 0.0) == lo
+        assert oracle_lib.rates(ot, A, Z, 10 ** 17 * A * MP) == hi
+        assert oracle_lib.rates(ot, A, Z, math.inf) == hi
+        want = float(I.loss_rate_closed_form(A, Z, 6.0))
+        assert lo[1] == pytest.approx(want, rel=_f32_rate_bound(want, slope=0.0), abs=0.0)
 
 
 def test_zero_rate_species_and_range(oracle_lib):
@@ -57,7 +95,10 @@ def test_continuous_loss_closed_form(oracle_lib):
     st, rc, _ = run(particles([1, 0, 0], 1e19), uniform_grid([0, 0, 0]), I.MPC, dmax, tables=t,
                     hmax=100 * I.MPC)
     assert rc == 0 and st.status[0] == O.DONE
-    assert st.E[0] == pytest.approx(1e19 * math.exp(-R * dmax), rel=1e-13)
+    # the rate the oracle evaluates (FP32, within its bound of R), then the exponential law
+    _, Rf, _ = oracle_lib.rates(O.OracleTables(t), 1, 1, 1e19)
+    assert Rf == pytest.approx(R, rel=_f32_rate_bound(R, 1e19, slope=0.0), abs=0.0)
+    assert st.E[0] == pytest.approx(1e19 * math.exp(-Rf * dmax), rel=1e-13, abs=0.0)
     assert st.n_steps[0] >= 20                                        # 0.1/R = 5 Mpc steps
     assert st.n_int[0] == 0
 
