@@ -91,8 +91,6 @@ static const double LN2_HI = 0x1.62e42feep-1;           /* ln 2 truncated to 32 
 static const double LN2_LO = 0x1.a39ef35793c76p-33;     /* ln 2 - LN2_HI */
 static const double INV_LN2 = 0x1.71547652b82fep+0;     /* 1/ln 2 */
 static const double SQRT_HALF = 0x1.6a09e667f3bcdp-1;   /* sqrt(1/2) */
-static const double LN10 = 0x1.26bb1bbb55516p+1;        /* ln 10 */
-static const double INV_LN10 = 0.4342944819032518;      /* 1/ln 10 */
 
 /* exp(x) = 2^n exp(r), x = n ln2 + r, |r| <= ln2/2; exp(r) by its Taylor series through
  * r^14/14! (truncation below 2^-60 on that interval), Horner order, each step one fused

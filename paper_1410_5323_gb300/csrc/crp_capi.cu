@@ -657,6 +657,7 @@ int crp_tables_create(int32_t z_max, int32_t n_max, int32_t n_nodes, double x0, 
     d.has_pd = (const uint8_t*)(flags + n_sp);
     d.z_max = z_max; d.n_max = n_max; d.n_nodes = n_nodes;
     d.x0 = x0; d.inv_dx = inv_dx;
+    d.x0_f = (float)x0; d.inv_dx_f = (float)inv_dx;
     *out = t;
     return CRP_OK;
 }

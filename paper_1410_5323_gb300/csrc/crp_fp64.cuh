@@ -8,6 +8,7 @@
 #include <cuda_fp16.h>
 
 #include "crp_internal.h"
+#include "crp_math.cuh"
 
 namespace crp {
 namespace fp64 {
@@ -290,10 +291,9 @@ __device__ __forceinline__ float ctrl_log2r(double sx, double su, double h, floa
     return __fsub_rn(fmaxf(lx, lu), lg_tol);
 }
 
-// 0.95 r^p clamped to [lo, hi]: y = p log2 r clamped to [-8, 8] (a NaN y counts as -8),
-// 2^floor(y) exactly times e^(f ln 2) (f the fractional part) by Taylor through x^8/8!.
-__device__ __forceinline__ float ctrl_factor(float log2r, float p, float lo, float hi) {
-    const float y = fminf(fmaxf(__fmul_rn(p, log2r), -8.0f), 8.0f);
+// 2^y in FP32 for y in [-126, 126] (the caller clamps): 2^floor(y) exactly times e^(f ln 2)
+// (f the fractional part) by Taylor through x^8/8! in Horner order, the product rounded once.
+__device__ __forceinline__ float pow2_series(float y) {
     const float n = floorf(y);
     const float x = __fmul_rn(__fsub_rn(y, n), 0x1.62e430p-1f);   // ln 2
     float q = 0x1.a01a02p-16f;                                 // 1/8!
@@ -306,7 +306,13 @@ __device__ __forceinline__ float ctrl_factor(float log2r, float p, float lo, flo
     q = __fadd_rn(__fmul_rn(q, x), 1.0f);
     q = __fadd_rn(__fmul_rn(q, x), 1.0f);
     const float p2 = __int_as_float(((int)n + 127) << 23);
-    return fminf(fmaxf(__fmul_rn(0.95f, __fmul_rn(q, p2)), lo), hi);
+    return __fmul_rn(q, p2);
+}
+
+// 0.95 r^p clamped to [lo, hi]: y = p log2 r clamped to [-8, 8] (a NaN y counts as -8).
+__device__ __forceinline__ float ctrl_factor(float log2r, float p, float lo, float hi) {
+    const float y = fminf(fmaxf(__fmul_rn(p, log2r), -8.0f), 8.0f);
+    return fminf(fmaxf(__fmul_rn(0.95f, pow2_series(y)), lo), hi);
 }
 
 // Exact widening of a normal float (the clamped factors) to double with integer
@@ -315,6 +321,48 @@ __device__ __forceinline__ double widen_normal(float f) {
     const unsigned u = __float_as_uint(f);
     const unsigned hi = (u & 0x80000000u) | ((((u >> 23) & 0xFFu) + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
     return __hiloint2double((int)hi, (int)(u << 29));
+}
+
+// Exact widening of any float: normals with integer instructions, zeros, subnormals,
+// infinities and NaN (rare here) by the conversion.
+__device__ __forceinline__ double widen_f32(float f) {
+    const unsigned e = (__float_as_uint(f) >> 23) & 0xFFu;
+    return (e == 0u || e == 0xFFu) ? (double)f : widen_normal(f);
+}
+
+// Tabulated loss and photo-disintegration rates at gamma0 = E / (A m_p c^2), in FP32 from the
+// FP64 state (the rates are a tabulated heuristic): x = (log2 E - log2(A m_p c^2)) log10 2 with
+// the bit-level log2 of the step controller (the product in FP64); t = (x - x0) inv_dx clamped
+// to [0, n - 1], j = floor t (at most n - 2), v = T_j + (t - j)(T_{j+1} - T_j) over the FP32
+// table copies; rate = 2^(v log2 10), the exponent clamped to [-126, 126] (normal results).
+// Returns false if the species lies outside the tables.
+__device__ __forceinline__ bool table_rates_f32(const TablesDev& t, int A, int Z, double E,
+                                                float& r_loss, float& r_pd) {
+    r_loss = 0.0f;
+    r_pd = 0.0f;
+    const int N = A - Z;
+    if (Z < 0 || N < 0 || Z > t.z_max || N > t.n_max) return false;
+    const long long sp = (long long)Z * (t.n_max + 1) + N;
+    const float lg = __fsub_rn(ctrl_log2(E), ctrl_log2(__dmul_rn((double)A, kMpC2)));
+    const float x = __fmul_rn(lg, 0x1.344136p-2f);                  // log10 2
+    float tt = __fmul_rn(__fsub_rn(x, t.x0_f), t.inv_dx_f);
+    tt = fminf(fmaxf(tt, 0.0f), (float)(t.n_nodes - 1));
+    int j = (int)floorf(tt);
+    if (j > t.n_nodes - 2) j = t.n_nodes - 2;
+    const float fr = __fsub_rn(tt, (float)j);
+    if (t.has_loss[sp]) {
+        const float* T = t.loss_f + sp * t.n_nodes;
+        const float a = __ldg(T + j), b = __ldg(T + j + 1);
+        const float y = __fmul_rn(__fadd_rn(a, __fmul_rn(fr, __fsub_rn(b, a))), 0x1.a934f0p+1f);  // log2 10
+        r_loss = pow2_series(fminf(fmaxf(y, -126.0f), 126.0f));
+    }
+    if (t.has_pd[sp]) {
+        const float* T = t.pd_f + sp * t.n_nodes;
+        const float a = __ldg(T + j), b = __ldg(T + j + 1);
+        const float y = __fmul_rn(__fadd_rn(a, __fmul_rn(fr, __fsub_rn(b, a))), 0x1.a934f0p+1f);
+        r_pd = pow2_series(fminf(fmaxf(y, -126.0f), 126.0f));
+    }
+    return true;
 }
 
 __device__ __forceinline__ double clampd(double v, double lo, double hi) {

@@ -44,6 +44,7 @@ struct TablesDev {
     const uint8_t* has_pd;
     int32_t z_max, n_max, n_nodes, pad_;
     double x0, inv_dx;
+    float x0_f, inv_dx_f;    // the same rounded to FP32 (FP32 rate evaluation)
 };
 
 struct SimState {            // structure of arrays, `capacity` slots

@@ -49,8 +49,6 @@ constexpr double kLn2Hi = 0x1.62e42feep-1;
 constexpr double kLn2Lo = 0x1.a39ef35793c76p-33;
 constexpr double kInvLn2 = 0x1.71547652b82fep+0;
 constexpr double kSqrtHalf = 0x1.6a09e667f3bcdp-1;
-constexpr double kLn10 = 0x1.26bb1bbb55516p+1;
-constexpr double kInvLn10 = 0.4342944819032518;
 
 // exp(x) = 2^n e^r, |r| <= ln2/2, e^r by Taylor through r^14/14! in Horner order, every
 // step one fused multiply-add; r = (x - n ln2_hi) - n ln2_lo with fused products.
@@ -107,35 +105,6 @@ __device__ __forceinline__ double crp_log(double x) {
     const double log_m = __fma_rn(s_2, t, s_2);
     const double de = (double)e;
     return __fma_rn(de, kLn2Hi, __fma_rn(de, kLn2Lo, log_m));
-}
-
-// ---- tabulated rates at gamma0 = E/(A m_p c^2) ------------------------------------------
-// Returns false if the species lies outside the tables.
-__device__ __forceinline__ bool table_rates(const TablesDev& t, int A, int Z, double E,
-                                            double& r_loss, double& r_pd) {
-    r_loss = 0.0;
-    r_pd = 0.0;
-    const int N = A - Z;
-    if (Z < 0 || N < 0 || Z > t.z_max || N > t.n_max) return false;
-    const long long sp = (long long)Z * (t.n_max + 1) + N;
-    const double gamma0 = __ddiv_rn(E, __dmul_rn((double)A, kMpC2));
-    const double x = __dmul_rn(crp_log(gamma0), kInvLn10);
-    double tt = __dmul_rn(__dsub_rn(x, t.x0), t.inv_dx);
-    tt = fmin(fmax(tt, 0.0), (double)(t.n_nodes - 1));
-    long long j = (long long)floor(tt);
-    if (j > t.n_nodes - 2) j = t.n_nodes - 2;
-    const double fr = __dsub_rn(tt, (double)j);
-    if (t.has_loss[sp]) {
-        const double* T = t.loss + sp * t.n_nodes;
-        const double a = __ldg(T + j), b = __ldg(T + j + 1);
-        r_loss = crp_exp(__dmul_rn(__dadd_rn(a, __dmul_rn(fr, __dsub_rn(b, a))), kLn10));
-    }
-    if (t.has_pd[sp]) {
-        const double* T = t.pd + sp * t.n_nodes;
-        const double a = __ldg(T + j), b = __ldg(T + j + 1);
-        r_pd = crp_exp(__dmul_rn(__dadd_rn(a, __dmul_rn(fr, __dsub_rn(b, a))), kLn10));
-    }
-    return true;
 }
 
 }  // namespace crp

@@ -95,19 +95,18 @@ __global__ void CRP_FP64_BOUNDS k_propagate_fp64(const PropArgs a) {
             const FieldDev& F = a.fields[gid];
             // ---- bids (Sec. 3.1): lowest of propagation, loss, interaction, distance ----
             if (new_step) {
-                if (a.has_tables) {
-                    if (!table_rates(a.tab, A, Z, E, rl, rpd)) {
-                        bits |= BIT_RANGE;
-                        store(CRP_STATUS_RANGE_);
-                        continue;
-                    }
-                } else {
-                    rl = 0.0;
-                    rpd = 0.0;
+                float rl_f = 0.0f, rpd_f = 0.0f;
+                if (a.has_tables && !table_rates_f32(a.tab, A, Z, E, rl_f, rpd_f)) {
+                    bits |= BIT_RANGE;
+                    store(CRP_STATUS_RANGE_);
+                    continue;
                 }
+                // FP32 rates (normal or zero) widened; loss and interaction bids as FP32 quotients
+                rl = rl_f > 0.0f ? widen_normal(rl_f) : 0.0;
+                rpd = rpd_f > 0.0f ? widen_normal(rpd_f) : 0.0;
                 h_propc = clampd(hprop, a.hmin, a.hmax);
-                const double h_loss = rl > 0.0 ? 0.1 / rl : INF;
-                h_int = rpd > 0.0 ? fmax(tau, 0.0) / rpd : INF;
+                const double h_loss = rl_f > 0.0f ? widen_f32(__fdiv_rn(0.1f, rl_f)) : INF;
+                h_int = rpd_f > 0.0f ? widen_f32(__fdiv_rn(__double2float_rn(fmax(tau, 0.0)), rpd_f)) : INF;
                 h_dist = a.dmax - s;
                 h = h_propc;
                 if (h_loss < h) h = h_loss;
