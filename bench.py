@@ -39,11 +39,12 @@ UNIT = "steps/s"
 #   sums 210, 5th-order update 54, error estimate 60, squared error norms 10 + (h tol)^2 2,
 #   h x step factor and its clamp 2 (the factor itself is FP32 work)  -> 743
 #   per accepted step: the next step's first field evaluation 81 (rejected attempts reuse
-#   it), kappa = Z c / E 2 -> 83; with tables: bids, gamma0, 2 table interpolations, loss,
-#   tau -> 30 more
+#   it), kappa = Z c / E 2 -> 83; with tables (the rates themselves are FP32 work, below):
+#   distance bid 1, max(tau, 0) 1, three bid comparisons 3, loss h R, exp, E x 3, tau - h R 2
+#   -> 10 more
 FLOP_PER_ATTEMPT = 743
 FLOP_PER_ACCEPTED = 83
-FLOP_PER_ACCEPTED_TABLES = 30
+FLOP_PER_ACCEPTED_TABLES = 10
 # FP64 pipe of one GB300: 2 FP64 lanes/clk/SM x 152 SMs x 2070 MHz = 6.29e11 ops/s,
 # 1.259e12 FLOP/s counting an FMA as two (the FP64 form issues no FMA: ceiling 0.5).
 FP64_PEAK_TFLOPS = 152 * 2 * 2.070e9 * 2 / 1e12
@@ -89,6 +90,7 @@ def parse():
     ap.add_argument("--workload", default="fp64_256cube_1M_nuclei")
     ap.add_argument("--n-particles", type=int, default=0, help="override batch size (testing)")
     ap.add_argument("--grid-n", type=int, default=0, help="override grid size (profiling)")
+    ap.add_argument("--bf16", action="store_true", help="store the grid as BF16 + scale (profiling)")
     ap.add_argument("--cpu-sample", type=int, default=16384, help="primaries in the oracle sample")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -113,6 +115,9 @@ def workload_for(args) -> I.Workload:
     if args.grid_n:
         w.grid_n = args.grid_n
         w.name = f"{w.name} (grid {args.grid_n}^3)"
+    if args.bf16:
+        w.bf16 = True
+        w.name = f"{w.name} (bf16 grid)"
     return w
 
 
@@ -152,7 +157,7 @@ class GridInput:
 def build_inputs(w: I.Workload, n: int, rank: int):
     """Field grids (list of GridInput), tables, particles of the workload (this rank's batch)."""
     tables = I.synthetic_tables() if w.interactions else None
-    if w.grid_n >= 512:     # generated and quantised on the device (BF16 + one FP32 scale)
+    if w.bf16:              # generated and quantised on the device (BF16 + one FP32 scale)
         import torch
 
         B = I.kolmogorov_grid_torch(w.grid_n, w.lmin_cells, w.lmax_cells, w.brms_t, w.grid_seed)
@@ -325,8 +330,11 @@ def traffic_for(workload, form, attempted, calls):
 LOOKUP_BYTES = {"f64": 8 * 3 * 8, "f32": 8 * 3 * 4, "bf16": 8 * 3 * 2}
 MOD_LOOKUP_BYTES = 8 * 4
 # FP32 work of the FP64 form: the step-size factor per attempt (log2 of three FP64 values
-# from their bits, 3 x 14, their combination 6, the clamped power 26).
+# from their bits, 3 x 14, their combination 6, the clamped power 26); with tables, per
+# accepted step the rates (two bit-level log2 28, coordinate 8, two interpolated powers of
+# two 2 x 27) and the two bid quotients 2.
 FP64_FORM_FP32_FLOP_PER_ATTEMPT = 74
+FP64_FORM_FP32_FLOP_PER_ACCEPTED_TABLES = 92
 L2_BYTES = 126 * 1024 * 1024
 
 
@@ -375,7 +383,8 @@ def roofline_terms(form, attempted, accepted, tables, prop_s, modulated=False, g
         per_acc = (FLOP_PER_ACCEPTED + (MOD_FLOP_PER_ACCEPTED if modulated else 0)
                    + (FLOP_PER_ACCEPTED_TABLES if tables else 0))
         f64 = per_att * attempted + per_acc * accepted
-        f32 = FP64_FORM_FP32_FLOP_PER_ATTEMPT * attempted
+        f32 = FP64_FORM_FP32_FLOP_PER_ATTEMPT * attempted + (FP64_FORM_FP32_FLOP_PER_ACCEPTED_TABLES * accepted
+                                                              if tables else 0)
         t64 = {"achieved": f64 / prop_s / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                "flop_per_attempt": per_att, "flop_per_accepted": per_acc,
                "peak_source": "derived: 152 SM x 2 FP64 lanes/clk x 2070 MHz, FMA=2 (of derived)"}
@@ -623,7 +632,7 @@ def run_own(args):
     grids, tables, parts = build_inputs(w, n, rank)
     n = len(parts)
     cap = capacity_hint(w, parts)
-    bf16 = w.grid_n >= 512
+    bf16 = w.bf16
 
     fields = [g.field(crp, w.spacing_m) for g in grids]
     tabs = crp.Tables(tables) if tables is not None else None

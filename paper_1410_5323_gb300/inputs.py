@@ -415,6 +415,7 @@ class Workload:
     spectrum: tuple | None = None
     arrival_nside: int = 0     # arrival map resolution (0: none) and its energy threshold
     arrival_emin_ev: float = 0.0
+    bf16: bool = False         # grid generated on the device (torch FFT) and stored as BF16 + scale
 
 
 EQ1_SPECIES = ((1, 1, 1.0), (4, 2, 0.5), (14, 7, 0.3), (56, 26, 0.1))   # Sec. 4: H, He, N, Fe
@@ -445,7 +446,7 @@ def workload(name: str) -> Workload:
     if name == "mixed_1024cube_10M_pFe":
         return Workload(name, 10_000_000, 1024, lmax_cells=256.0, brms_t=0.5 * NANOGAUSS,
                         dmax_m=500.0 * MPC, species=(("H", 0.5), ("Fe", 0.5)),
-                        energy=("power", 1e18, 10 ** 20.5, 2.0), interactions=False, **common)
+                        energy=("power", 1e18, 10 ** 20.5, 2.0), interactions=False, bf16=True, **common)
     if name == "batched_64x128cube_12.8M_protons":
         return Workload(name, 64 * 200_000, 128, lmax_cells=32.0, brms_t=1.0 * NANOGAUSS,
                         dmax_m=100.0 * MPC, species=(("H", 1.0),),
