@@ -811,13 +811,12 @@ void orc_frozen_forward(const orc_field* f, double kappa, const double y0[6], co
     for (int c = 0; c < 6; ++c) yT[c] = y[c];
 }
 
-/* Trilinear lookup with the corner weights, their x-derivatives and the grid indices. */
+/* Trilinear lookup with the corner weights, the grid indices and the field's Jacobian. */
 typedef struct {
     double B[3];
     double w[8];            /* corner weights, corner order 000, 001, ..., 111 */
-    double dw[8][3];        /* d w / d x_a */
+    double J[3][3];         /* J[q][a] = d B_q / d x_a */
     int64_t node[8];
-    double G[8][3];
 } orc_lookup;
 
 static void lookup_full(const orc_field* f, const double x[3], orc_lookup* L)
@@ -841,26 +840,33 @@ static void lookup_full(const orc_field* f, const double x[3], orc_lookup* L)
         dwd[a][1] = inv;
     }
     L->B[0] = 0.0; L->B[1] = 0.0; L->B[2] = 0.0;
+    for (int q = 0; q < 3; ++q)
+        for (int a = 0; a < 3; ++a) L->J[q][a] = 0.0;
     int c8 = 0;
     for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b)
             for (int c = 0; c < 2; ++c, ++c8) {
                 double wt = (w[0][a] * w[1][b]) * w[2][c];
+                double dw[3];
+                dw[0] = (dwd[0][a] * w[1][b]) * w[2][c];
+                dw[1] = (w[0][a] * dwd[1][b]) * w[2][c];
+                dw[2] = (w[0][a] * w[1][b]) * dwd[2][c];
                 L->w[c8] = wt;
-                L->dw[c8][0] = (dwd[0][a] * w[1][b]) * w[2][c];
-                L->dw[c8][1] = (w[0][a] * dwd[1][b]) * w[2][c];
-                L->dw[c8][2] = (w[0][a] * w[1][b]) * dwd[2][c];
                 L->node[c8] = (idx[0][a] * f->ny + idx[1][b]) * f->nz + idx[2][c];
                 for (int q = 0; q < 3; ++q) {
-                    L->G[c8][q] = grid_at(f, idx[0][a], idx[1][b], idx[2][c], q);
-                    L->B[q] = fma(wt, L->G[c8][q], L->B[q]);     /* as orc_field_value */
+                    double G = grid_at(f, idx[0][a], idx[1][b], idx[2][c], q);
+                    L->B[q] = fma(wt, G, L->B[q]);     /* as orc_field_value */
+                    for (int d = 0; d < 3; ++d) L->J[q][d] = fma(dw[d], G, L->J[q][d]);
                 }
             }
 }
 
 /* Vector-Jacobian product of f(Y) = (u, kappa u x B(x)) with kbar = (abar, bbar):
  *   Bbar = kappa (bbar x u);  kappa_bar += bbar . (u x B);
- *   Ybar_u = abar + kappa (B x bbar);  Ybar_x[a] = sum_c dw_c/dx_a (G_c . Bbar);
+ *   Ybar_u = abar + kappa (B x bbar);
+ *   Ybar_x[a] = sum_q J[q][a] Bbar[q], with the field's Jacobian at Y,
+ *   J[q][a] = d B_q / d x_a = sum_c (d w_c / d x_a) G_c[q] summed over the corners 000..111
+ *   with one rounding per corner (fused multiply-add from 0);
  *   grid_bar[c] += w_c Bbar. */
 static void vjp_f(const orc_field* f, double kappa, const double Y[6], const double kb[6],
                   double Yb[6], double* grid_bar, double* kappa_bar)
@@ -880,10 +886,8 @@ static void vjp_f(const orc_field* f, double kappa, const double Y[6], const dou
     Yb[3] = kb[0] + kappa * (L.B[1] * bb[2] - L.B[2] * bb[1]);
     Yb[4] = kb[1] + kappa * (L.B[2] * bb[0] - L.B[0] * bb[2]);
     Yb[5] = kb[2] + kappa * (L.B[0] * bb[1] - L.B[1] * bb[0]);
-    Yb[0] = 0.0; Yb[1] = 0.0; Yb[2] = 0.0;
+    for (int a = 0; a < 3; ++a) Yb[a] = (L.J[0][a] * Bb[0] + L.J[1][a] * Bb[1]) + L.J[2][a] * Bb[2];
     for (int c = 0; c < 8; ++c) {
-        double gB = (L.G[c][0] * Bb[0] + L.G[c][1] * Bb[1]) + L.G[c][2] * Bb[2];
-        for (int a = 0; a < 3; ++a) Yb[a] = Yb[a] + L.dw[c][a] * gB;
         if (grid_bar)
             for (int q = 0; q < 3; ++q)
                 grid_bar[L.node[c] * 3 + q] = grid_bar[L.node[c] * 3 + q] + L.w[c] * Bb[q];
