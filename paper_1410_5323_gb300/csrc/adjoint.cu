@@ -116,18 +116,29 @@ __global__ void k_adj_replay(FieldDev F, const double* __restrict__ y0, const do
     if (H) cell_hash[i] = hh;
 }
 
-// Full lookup: B, corner weights, their x-derivatives, nodes and corner values; corner order
-// 000, 001, ..., 111; dw_c/dx_a = (d w_a) * w_b * w_c with d(1 - f) = -1/spacing, d f = 1/spacing.
+// What the reverse sweep needs of one lookup: B, the corner weights and nodes, and the field's
+// Jacobian J[q][a] = dB_q/dx_a = sum_c (dw_c/dx_a) G_c[q] (corners 000, 001, ..., 111, one
+// rounding per corner; dw_c/dx_a = (d w_a) * w_b * w_c with d(1 - f) = -1/spacing,
+// d f = 1/spacing). B is formed exactly as the forward lookup forms it.
+struct Look {
+    double B[3], w[8], J[3][3];
+    long long node[8];
+};
+
 template <int L>
-__device__ __forceinline__ void lookup_full(const FieldDev& F, const Y6& Y, double B[3], double w[8],
-                                            double dw[8][3], long long node[8], double G[8][3]) {
+__device__ __forceinline__ void lookup_jac(const FieldDev& F, double x, double y, double z, Look& o) {
     long long ix[2], iy[2], iz[2];
     double wx[2], wy[2], wz[2];
-    axis(Y.x, F.oix, F.inv_spacing, F.nx, F.pow2, ix[0], ix[1], wx[0], wx[1]);
-    axis(Y.y, F.oiy, F.inv_spacing, F.ny, F.pow2, iy[0], iy[1], wy[0], wy[1]);
-    axis(Y.z, F.oiz, F.inv_spacing, F.nz, F.pow2, iz[0], iz[1], wz[0], wz[1]);
+    axis(x, F.oix, F.inv_spacing, F.nx, F.pow2, ix[0], ix[1], wx[0], wx[1]);
+    axis(y, F.oiy, F.inv_spacing, F.ny, F.pow2, iy[0], iy[1], wy[0], wy[1]);
+    axis(z, F.oiz, F.inv_spacing, F.nz, F.pow2, iz[0], iz[1], wz[0], wz[1]);
     const double dd[2] = {-F.inv_spacing, F.inv_spacing};
-    B[0] = 0.0; B[1] = 0.0; B[2] = 0.0;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        o.B[q] = 0.0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) o.J[q][d] = 0.0;
+    }
     int c8 = 0;
 #pragma unroll
     for (int a = 0; a < 2; ++a)
@@ -135,49 +146,59 @@ __device__ __forceinline__ void lookup_full(const FieldDev& F, const Y6& Y, doub
         for (int b = 0; b < 2; ++b)
 #pragma unroll
             for (int c = 0; c < 2; ++c, ++c8) {
-                const double wt = (wx[a] * wy[b]) * wz[c];
-                w[c8] = wt;
-                dw[c8][0] = (dd[a] * wy[b]) * wz[c];
-                dw[c8][1] = (wx[a] * dd[b]) * wz[c];
-                dw[c8][2] = (wx[a] * wy[b]) * dd[c];
-                node[c8] = (ix[a] * F.ny + iy[b]) * F.nz + iz[c];
-                const V3 g = corner<L>(F, node[c8]);
-                G[c8][0] = g.x; G[c8][1] = g.y; G[c8][2] = g.z;
-                B[0] = __fma_rn(wt, g.x, B[0]);      // as the forward lookup
-                B[1] = __fma_rn(wt, g.y, B[1]);
-                B[2] = __fma_rn(wt, g.z, B[2]);
+                const double wab = wx[a] * wy[b];
+                const double wt = wab * wz[c];
+                const double dw[3] = {(dd[a] * wy[b]) * wz[c], (wx[a] * dd[b]) * wz[c], wab * dd[c]};
+                o.w[c8] = wt;
+                o.node[c8] = (ix[a] * F.ny + iy[b]) * F.nz + iz[c];
+                const V3 g = corner<L>(F, o.node[c8]);
+                const double G[3] = {g.x, g.y, g.z};
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    o.B[q] = __fma_rn(wt, G[q], o.B[q]);      // as the forward lookup
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) o.J[q][d] = __fma_rn(dw[d], G[q], o.J[q][d]);
+                }
             }
 }
 
-// Vector-Jacobian product of f at stage state Y with cotangent kb (see the file comment).
-template <int L>
-__device__ __forceinline__ void vjp_f(const FieldDev& F, double kappa, const Y6& Y, const Y6& kb,
-                                      Y6& Yb, double* __restrict__ grid_bar, double& kappa_bar) {
-    double B[3], w[8], dw[8][3], G[8][3];
-    long long node[8];
-    lookup_full<L>(F, Y, B, w, dw, node, G);
-    const double Bb0 = kappa * (kb.uy * Y.uz - kb.uz * Y.uy);
-    const double Bb1 = kappa * (kb.uz * Y.ux - kb.ux * Y.uz);
-    const double Bb2 = kappa * (kb.ux * Y.uy - kb.uy * Y.ux);
-    const double uxB0 = Y.uy * B[2] - Y.uz * B[1];
-    const double uxB1 = Y.uz * B[0] - Y.ux * B[2];
-    const double uxB2 = Y.ux * B[1] - Y.uy * B[0];
+// Vector-Jacobian product of f(Y) = (u, kappa u x B(x)) with cotangent kb = (abar, bbar), from
+// the stage's direction u, field B, Jacobian J, corner weights w and nodes:
+//   Bbar = kappa (bbar x u); kappa_bar += bbar . (u x B); Ybar_u = abar + kappa (B x bbar);
+//   Ybar_x = J^T Bbar; grid_bar[node_c] += w_c Bbar (FP64 atomics).
+__device__ __forceinline__ void vjp_apply(double kappa, double ux, double uy, double uz, const double B[3],
+                                          const double J[3][3], const double w[8], const long long node[8],
+                                          const Y6& kb, Y6& Yb, double* __restrict__ grid_bar,
+                                          double& kappa_bar) {
+    const double Bb0 = kappa * (kb.uy * uz - kb.uz * uy);
+    const double Bb1 = kappa * (kb.uz * ux - kb.ux * uz);
+    const double Bb2 = kappa * (kb.ux * uy - kb.uy * ux);
+    const double uxB0 = uy * B[2] - uz * B[1];
+    const double uxB1 = uz * B[0] - ux * B[2];
+    const double uxB2 = ux * B[1] - uy * B[0];
     kappa_bar = kappa_bar + ((kb.ux * uxB0 + kb.uy * uxB1) + kb.uz * uxB2);
     Yb.ux = kb.x + kappa * (B[1] * kb.uz - B[2] * kb.uy);
     Yb.uy = kb.y + kappa * (B[2] * kb.ux - B[0] * kb.uz);
     Yb.uz = kb.z + kappa * (B[0] * kb.uy - B[1] * kb.ux);
-    Yb.x = 0.0; Yb.y = 0.0; Yb.z = 0.0;
+    Yb.x = (J[0][0] * Bb0 + J[1][0] * Bb1) + J[2][0] * Bb2;
+    Yb.y = (J[0][1] * Bb0 + J[1][1] * Bb1) + J[2][1] * Bb2;
+    Yb.z = (J[0][2] * Bb0 + J[1][2] * Bb1) + J[2][2] * Bb2;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
-        const double gB = (G[c][0] * Bb0 + G[c][1] * Bb1) + G[c][2] * Bb2;
-        Yb.x = Yb.x + dw[c][0] * gB;
-        Yb.y = Yb.y + dw[c][1] * gB;
-        Yb.z = Yb.z + dw[c][2] * gB;
         double* gp = grid_bar + node[c] * 3;
         atomicAdd(gp + 0, w[c] * Bb0);
         atomicAdd(gp + 1, w[c] * Bb1);
         atomicAdd(gp + 2, w[c] * Bb2);
     }
+}
+
+// Vector-Jacobian product of f at stage state Y (lookup on the fly).
+template <int L>
+__device__ __forceinline__ void vjp_f(const FieldDev& F, double kappa, const Y6& Y, const Y6& kb,
+                                      Y6& Yb, double* __restrict__ grid_bar, double& kappa_bar) {
+    Look o;
+    lookup_jac<L>(F, Y.x, Y.y, Y.z, o);
+    vjp_apply(kappa, Y.ux, Y.uy, Y.uz, o.B, o.J, o.w, o.node, kb, Yb, grid_bar, kappa_bar);
 }
 
 __device__ __forceinline__ void axpy6(Y6& acc, double s, const Y6& v) {
@@ -204,6 +225,7 @@ __constant__ double cA[6][5] = {
     {-11.0 / 54.0, 5.0 / 2.0, -70.0 / 27.0, 35.0 / 27.0, 0.0},
     {1631.0 / 55296.0, 175.0 / 512.0, 575.0 / 13824.0, 44275.0 / 110592.0, 253.0 / 4096.0}};
 __constant__ double cB5[6] = {37.0 / 378.0, 0.0, 250.0 / 621.0, 125.0 / 594.0, 0.0, 512.0 / 1771.0};
+constexpr double cB5h[6] = {37.0 / 378.0, 0.0, 250.0 / 621.0, 125.0 / 594.0, 0.0, 512.0 / 1771.0};
 
 // The six stage states Y_0 = y_m, ..., Y_5 of step m (the forward stage sums: acc = A[i][0]
 // k1, then fused A[i][j] k_j for j < i; y + h acc fused).
@@ -245,13 +267,48 @@ __device__ __forceinline__ void adjoint_step(const FieldDev& F, double kappa, co
     reverse_step<L>(F, kappa, Y, hn, lam, grid_bar, kappa_bar);
 }
 
-// Stage states of every step, all segments at once: thread (particle i, segment sg)
-// recomputes its segment from the checkpoint and stores Y_0..Y_5 of each step at
-// stages[((m * 6 + s) * 6 + c) * n + i]. The reverse sweep then only reads them.
+// Stage records: for every step m and stage s of chain i, what the reverse sweep applies
+// (all of it a function of the stage state alone): the direction u, B, the Jacobian J and
+// the corner weights (kRecD doubles at rec_d[((m * 6 + s) * kRecD + k) * n + i]) and the
+// corner nodes (kRecN int32 at rec_n[((m * 6 + s) * kRecN + k) * n + i]).
+constexpr int kRecD = 3 + 3 + 9 + 8;
+constexpr int kRecN = 8;
+static_assert(kAdjRecordBytes == 6 * (kRecD * sizeof(double) + kRecN * sizeof(int32_t)), "record size");
+
+__device__ __forceinline__ void put_rec(double* __restrict__ rec_d, int32_t* __restrict__ rec_n, long long n,
+                                        long long i, int m, int st, const Y6& Y, const Look& o) {
+    double* d = rec_d + ((long long)(m * 6 + st) * kRecD) * n + i;
+    d[0 * n] = Y.ux; d[1 * n] = Y.uy; d[2 * n] = Y.uz;
+    d[3 * n] = o.B[0]; d[4 * n] = o.B[1]; d[5 * n] = o.B[2];
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) d[(6 + 3 * q + a) * n] = o.J[q][a];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) d[(15 + c) * n] = o.w[c];
+    int32_t* q = rec_n + ((long long)(m * 6 + st) * kRecN) * n + i;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) q[c * n] = (int32_t)o.node[c];
+}
+
+// f(Y) from its lookup, exactly as deriv() forms it.
+__device__ __forceinline__ Y6 deriv_from(double kappa, const Y6& y, const Look& o) {
+    Y6 k;
+    k.x = y.ux; k.y = y.uy; k.z = y.uz;
+    k.ux = kappa * __fma_rn(y.uy, o.B[2], -(y.uz * o.B[1]));
+    k.uy = kappa * __fma_rn(y.uz, o.B[0], -(y.ux * o.B[2]));
+    k.uz = kappa * __fma_rn(y.ux, o.B[1], -(y.uy * o.B[0]));
+    return k;
+}
+
+// Stage records of every step, all segments at once: thread (particle i, segment sg)
+// recomputes its segment from the checkpoint. Each step evaluates f at its six stage states
+// with the forward stage sums (as ck_attempt) and advances y by the 5th-order update, so the
+// states are the frozen forward's, bit for bit.
 template <int L>
-__global__ void k_adj_stages(FieldDev F, const double* __restrict__ kap, const double* __restrict__ h,
-                             const double* __restrict__ ck, double* __restrict__ stages, int n_steps,
-                             int K, long long n) {
+__global__ void k_adj_records(FieldDev F, const double* __restrict__ kap, const double* __restrict__ h,
+                              const double* __restrict__ ck, double* __restrict__ rec_d,
+                              int32_t* __restrict__ rec_n, int n_steps, int K, long long n) {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const int n_seg = (n_steps + K - 1) / K;
     if (t >= n * n_seg) return;
@@ -262,29 +319,124 @@ __global__ void k_adj_stages(FieldDev F, const double* __restrict__ kap, const d
     Y6 y;
     load6(ck + (long long)sg * 6 * n, n, i, y);
     for (int m = m0; m < m1; ++m) {
-        const double hm = h[(long long)m * n + i];
-        Y6 Y[6];
-        stage_states<L>(F, kappa, y, hm, Y);
-        for (int q = 0; q < 6; ++q) store6(stages + (long long)(m * 6 + q) * 6 * n, n, i, Y[q]);
-        frozen_step<L>(F, kappa, y, hm);
+        const double h_ = h[(long long)m * n + i];
+        Look o;
+        Y6 t_;
+        lookup_jac<L>(F, y.x, y.y, y.z, o);
+        put_rec(rec_d, rec_n, n, i, m, 0, y, o);
+        const Y6 k1 = deriv_from(kappa, y, o);
+#define ADJ_STAGE(dst, expr)                                                                \
+        do {                                                                                \
+            dst.x = __fma_rn(h_, expr(x), y.x);    dst.y = __fma_rn(h_, expr(y), y.y);      \
+            dst.z = __fma_rn(h_, expr(z), y.z);    dst.ux = __fma_rn(h_, expr(ux), y.ux);   \
+            dst.uy = __fma_rn(h_, expr(uy), y.uy); dst.uz = __fma_rn(h_, expr(uz), y.uz);   \
+        } while (0)
+#define R2(c) (A21 * k1.c)
+        ADJ_STAGE(t_, R2);
+        lookup_jac<L>(F, t_.x, t_.y, t_.z, o);
+        put_rec(rec_d, rec_n, n, i, m, 1, t_, o);
+        const Y6 k2 = deriv_from(kappa, t_, o);
+#define R3(c) __fma_rn(A32, k2.c, A31 * k1.c)
+        ADJ_STAGE(t_, R3);
+        lookup_jac<L>(F, t_.x, t_.y, t_.z, o);
+        put_rec(rec_d, rec_n, n, i, m, 2, t_, o);
+        const Y6 k3 = deriv_from(kappa, t_, o);
+#define R4(c) __fma_rn(A43, k3.c, __fma_rn(A42, k2.c, A41 * k1.c))
+        ADJ_STAGE(t_, R4);
+        lookup_jac<L>(F, t_.x, t_.y, t_.z, o);
+        put_rec(rec_d, rec_n, n, i, m, 3, t_, o);
+        const Y6 k4 = deriv_from(kappa, t_, o);
+#define R5(c) __fma_rn(A54, k4.c, __fma_rn(A53, k3.c, __fma_rn(A52, k2.c, A51 * k1.c)))
+        ADJ_STAGE(t_, R5);
+        lookup_jac<L>(F, t_.x, t_.y, t_.z, o);
+        put_rec(rec_d, rec_n, n, i, m, 4, t_, o);
+        const Y6 k5 = deriv_from(kappa, t_, o);
+#define R6(c) __fma_rn(A65, k5.c, __fma_rn(A64, k4.c, __fma_rn(A63, k3.c, __fma_rn(A62, k2.c, A61 * k1.c))))
+        ADJ_STAGE(t_, R6);
+        lookup_jac<L>(F, t_.x, t_.y, t_.z, o);
+        put_rec(rec_d, rec_n, n, i, m, 5, t_, o);
+        const Y6 k6 = deriv_from(kappa, t_, o);
+#define RB(c) __fma_rn(B6, k6.c, __fma_rn(B4, k4.c, __fma_rn(B3, k3.c, B1 * k1.c)))
+        Y6 y5;
+        ADJ_STAGE(y5, RB);
+        y = y5;
+#undef ADJ_STAGE
+#undef R2
+#undef R3
+#undef R4
+#undef R5
+#undef R6
+#undef RB
     }
 }
 
-// Reverse sweep over stored stage states, one thread per particle.
-template <int L>
-__global__ void k_adj_reverse(FieldDev F, const double* __restrict__ kap, const double* __restrict__ h,
-                              const double* __restrict__ stages, int n_steps, const double* __restrict__ uT_bar,
-                              double* __restrict__ grid_bar, double* __restrict__ y0_bar,
-                              double* __restrict__ kappa_bar_out, long long n) {
+// One stage of the reverse sweep from its record.
+__device__ __forceinline__ void vjp_rec(const double* __restrict__ rec_d, const int32_t* __restrict__ rec_n,
+                                        long long n, long long i, int m, int st, double kappa,
+                                        const Y6& kb, Y6& Yb, double* __restrict__ grid_bar,
+                                        double& kappa_bar) {
+    const double* d = rec_d + ((long long)(m * 6 + st) * kRecD) * n + i;
+    const int32_t* q = rec_n + ((long long)(m * 6 + st) * kRecN) * n + i;
+    const double B[3] = {__ldcs(d + 3 * n), __ldcs(d + 4 * n), __ldcs(d + 5 * n)};
+    double J[3][3], w[8];
+    long long node[8];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) J[a][b] = __ldcs(d + (6 + 3 * a + b) * n);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        w[c] = __ldcs(d + (15 + c) * n);
+        node[c] = __ldcs(q + c * n);
+    }
+    vjp_apply(kappa, __ldcs(d), __ldcs(d + n), __ldcs(d + 2 * n), B, J, w, node, kb, Yb, grid_bar, kappa_bar);
+}
+
+// L2 prefetch of one step's records (read by the next iteration of the reverse sweep).
+__device__ __forceinline__ void prefetch_step(const double* rec_d, const int32_t* rec_n, long long n,
+                                              long long i, int m) {
+    const double* d = rec_d + ((long long)m * 6 * kRecD) * n + i;
+    for (int k = 0; k < 6 * kRecD; ++k) asm volatile("prefetch.global.L2 [%0];" ::"l"(d + k * n));
+    const int32_t* q = rec_n + ((long long)m * 6 * kRecN) * n + i;
+    for (int k = 0; k < 6 * kRecN; ++k) asm volatile("prefetch.global.L2 [%0];" ::"l"(q + k * n));
+}
+
+// Reverse sweep over the stage records, one thread per particle: the adjoint of
+// y' = y + h sum_i b_i k_i and of the stage sums, stages in reverse (the oracle's order).
+__global__ void k_adj_reverse(const double* __restrict__ kap, const double* __restrict__ h,
+                              const double* __restrict__ rec_d, const int32_t* __restrict__ rec_n,
+                              int n_steps, const double* __restrict__ uT_bar, double* __restrict__ grid_bar,
+                              double* __restrict__ y0_bar, double* __restrict__ kappa_bar_out, long long n) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double kappa = kap[i];
     Y6 lam{0.0, 0.0, 0.0, uT_bar[3 * i], uT_bar[3 * i + 1], uT_bar[3 * i + 2]};
     double kappa_bar = 0.0;
     for (int m = n_steps - 1; m >= 0; --m) {
-        Y6 Y[6];
-        for (int q = 0; q < 6; ++q) load6(stages + (long long)(m * 6 + q) * 6 * n, n, i, Y[q]);
-        reverse_step<L>(F, kappa, Y, h[(long long)m * n + i], lam, grid_bar, kappa_bar);
+        if (m > 0) prefetch_step(rec_d, rec_n, n, i, m - 1);
+        const double hn = h[(long long)m * n + i];
+        Y6 kb0 = scale6(hn * cB5h[0], lam), kb1 = scale6(hn * cB5h[1], lam), kb2 = scale6(hn * cB5h[2], lam),
+           kb3 = scale6(hn * cB5h[3], lam), kb4 = scale6(hn * cB5h[4], lam), kb5 = scale6(hn * cB5h[5], lam);
+        Y6 yb = lam, Yb;
+        vjp_rec(rec_d, rec_n, n, i, m, 5, kappa, kb5, Yb, grid_bar, kappa_bar);
+        add6(yb, Yb);
+        axpy6(kb0, hn * A61, Yb); axpy6(kb1, hn * A62, Yb); axpy6(kb2, hn * A63, Yb);
+        axpy6(kb3, hn * A64, Yb); axpy6(kb4, hn * A65, Yb);
+        vjp_rec(rec_d, rec_n, n, i, m, 4, kappa, kb4, Yb, grid_bar, kappa_bar);
+        add6(yb, Yb);
+        axpy6(kb0, hn * A51, Yb); axpy6(kb1, hn * A52, Yb); axpy6(kb2, hn * A53, Yb); axpy6(kb3, hn * A54, Yb);
+        vjp_rec(rec_d, rec_n, n, i, m, 3, kappa, kb3, Yb, grid_bar, kappa_bar);
+        add6(yb, Yb);
+        axpy6(kb0, hn * A41, Yb); axpy6(kb1, hn * A42, Yb); axpy6(kb2, hn * A43, Yb);
+        vjp_rec(rec_d, rec_n, n, i, m, 2, kappa, kb2, Yb, grid_bar, kappa_bar);
+        add6(yb, Yb);
+        axpy6(kb0, hn * A31, Yb); axpy6(kb1, hn * A32, Yb);
+        vjp_rec(rec_d, rec_n, n, i, m, 1, kappa, kb1, Yb, grid_bar, kappa_bar);
+        add6(yb, Yb);
+        axpy6(kb0, hn * A21, Yb);
+        vjp_rec(rec_d, rec_n, n, i, m, 0, kappa, kb0, Yb, grid_bar, kappa_bar);
+        add6(yb, Yb);
+        lam = yb;
     }
     store6(y0_bar, n, i, lam);
     kappa_bar_out[i] = kappa_bar;
@@ -381,14 +533,16 @@ int adj_replay(const FieldDev& F, const double* y0, const double* kappa, const d
 int adj_backward(const FieldDev& F, const double* kappa, const double* h, const double* ck,
                  double* seg, double* stages, int n_steps, int K, const double* uT_bar, double* grid_bar,
                  double* y0_bar, double* kappa_bar, long long n, void* stream) {
-    if (stages) {       // all segments recomputed at once, then the reverse sweep reads them
+    if (stages) {       // all segments' stage records at once, then the reverse sweep applies them
         const long long threads = n * ((n_steps + K - 1) / K);
-        k_adj_stages<LAYOUT_F64X4><<<blocks(threads), 128, 0, (cudaStream_t)stream>>>(
-            F, kappa, h, ck, stages, n_steps, K, n);
+        double* rec_d = stages;
+        int32_t* rec_n = reinterpret_cast<int32_t*>(stages + (size_t)n_steps * 6 * kRecD * (size_t)n);
+        k_adj_records<LAYOUT_F64X4><<<blocks(threads), 128, 0, (cudaStream_t)stream>>>(
+            F, kappa, h, ck, rec_d, rec_n, n_steps, K, n);
         const int e = (int)cudaGetLastError();
         if (e) return e;
-        k_adj_reverse<LAYOUT_F64X4><<<chain_blocks(n), kChainBlock, 0, (cudaStream_t)stream>>>(
-            F, kappa, h, stages, n_steps, uT_bar, grid_bar, y0_bar, kappa_bar, n);
+        k_adj_reverse<<<chain_blocks(n), kChainBlock, 0, (cudaStream_t)stream>>>(
+            kappa, h, rec_d, rec_n, n_steps, uT_bar, grid_bar, y0_bar, kappa_bar, n);
         return (int)cudaGetLastError();
     }
     k_adj_backward<LAYOUT_F64X4><<<chain_blocks(n), kChainBlock, 0, (cudaStream_t)stream>>>(

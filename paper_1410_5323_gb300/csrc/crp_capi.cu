@@ -1687,7 +1687,7 @@ struct crp_adjoint {
     double *y0 = nullptr, *kappa = nullptr, *E = nullptr, *h = nullptr, *ck = nullptr;
     double *seg = nullptr, *y0_bar = nullptr, *kappa_bar = nullptr, *y0_tmp = nullptr;
     double *kappa_tmp = nullptr, *E_tmp = nullptr;
-    double* stages = nullptr;            // [n_steps][6 stages][6][n] stage states, if room
+    double* stages = nullptr;            // stage records of every step (kAdjRecordBytes each), if room
     int32_t* Z = nullptr;
     bool recorded = false;
 };
@@ -1732,11 +1732,13 @@ int crp_adjoint_create(const crp_field* field, int64_t n, int32_t n_steps, int32
     FieldDev F;
     int rc = field_fp64_desc(a->field, F);
     if (rc) { adj_free(a); delete a; return rc; }
-    // stage states of all steps (36 doubles per step and particle) when they fit in half of
-    // the free memory: the reverse pass then recomputes every segment in parallel
+    // stage records of all steps (kAdjRecordBytes per step and particle) when they fit in half
+    // of the free memory and the grid's node indices fit in int32: every segment's records are
+    // then formed in parallel and the serial reverse sweep only applies them
     size_t free_b = 0, total_b = 0;
-    const size_t st_bytes = (size_t)36 * sizeof(double) * (size_t)n_steps * (size_t)n;
-    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && st_bytes <= free_b / 2) {
+    const size_t st_bytes = kAdjRecordBytes * (size_t)n_steps * (size_t)n;
+    const long long nodes = (long long)F.nx * F.ny * F.nz;
+    if (nodes < (1ll << 31) && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && st_bytes <= free_b / 2) {
         if (dev_malloc(&a->stages, st_bytes) != cudaSuccess) {
             a->stages = nullptr;
             cudaGetLastError();

@@ -129,7 +129,10 @@ int launch_propagate_mixed(const PropArgs& a, int layout, int mod, int grid, int
 int propagate_mixed_occupancy(int layout, int mod, int block, int* blocks_per_sm);
 
 // Adjoint launchers (adjoint.cu). Arrays are component-major [component][n] for y,
-// [step][n] for h, [checkpoint][6][n] for checkpoints.
+// [step][n] for h, [checkpoint][6][n] for checkpoints. `stages`, when not NULL, holds the
+// stage records of every step: per step and particle kAdjRecordBytes (6 stages x (23 FP64:
+// direction, field, Jacobian, corner weights + 8 int32 corner nodes)), doubles first.
+constexpr size_t kAdjRecordBytes = 6 * (23 * sizeof(double) + 8 * sizeof(int32_t));
 int adj_init(const double* x0, const double* p0, const int32_t* Z, double* y0, double* kappa,
              double* E, long long n, void* stream);
 int adj_record(const FieldDev& F, const double* y0, const double* kappa, double tol, double hmin,
