@@ -706,6 +706,7 @@ def run_own(args):
         clocks = ClockSampler(local) if with_clocks else None
         barrier()
         torch.cuda.synchronize()
+        runs0 = crp.kernel_runs()
         if clocks:
             clocks.start()
         r = dict(step_ms=[], prop_ms=[], accepted=0, attempted=0, rcs=[], secondaries=0, launches=0)
@@ -720,6 +721,7 @@ def run_own(args):
             r["launches"] += c["launches"]
             r["rcs"].append(rc)
         torch.cuda.synchronize()
+        r["kernel_runs"] = crp.kernel_runs() - runs0
         barrier()
         r["clocks"] = clocks.stop() if clocks else None
         r["total_ms_max"], r["accepted_all"], r["attempted_all"] = aggregate(
@@ -823,13 +825,8 @@ def run_own(args):
                  "mixed_error_vs_fp64_oracle": forms_err,
                  "mixed_error_vs_fp64_by_distance": by_distance}
 
-    # our kernels in the timed region: per step inject init + slot count; per propagate slice
-    # prepare + work-list build (1 kernel, or 3 for the ordered builds) + 2 x (propagate + swap);
-    # the graph loop adds an init kernel per step and a condition kernel per slice.
-    slices = main["launches"] / 2
-    per_slice = 1 + (1 if order == 1 else 3) + 4 + (1 if slice_steps > 0 else 0)
-    per_step = 2 + (1 if spec is not None else 0) + (1 if amap is not None else 0)
-    gpu_launches = int(per_step * args.steps + slices * per_slice + (args.steps if slice_steps > 0 else 0))
+    # the library's kernels that ran in the timed region, counted on the device
+    gpu_launches = int(main["kernel_runs"])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
@@ -928,11 +925,13 @@ def run_adjoint(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     clocks = ClockSampler(local)
     fwd_ms, bwd_ms = [], []
+    runs0 = 0
     for it in range(args.warmup + args.steps):
         if it == args.warmup:
             if dist is not None:
                 dist.barrier()
             torch.cuda.synchronize()
+            runs0 = crp.kernel_runs()
             clocks.start()
         flush.zero_()
         e0, e1, e1b, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
@@ -950,6 +949,7 @@ def run_adjoint(args):
         if it >= args.warmup:
             fwd_ms.append(e0.elapsed_time(e1))
             bwd_ms.append(e1b.elapsed_time(e2))
+    runs = crp.kernel_runs() - runs0
     if dist is not None:
         dist.barrier()
     clk = clocks.stop()
@@ -1063,7 +1063,7 @@ def run_adjoint(args):
                    "parallelism": f"dp{ws} (chains split in blocks; dL/dB summed by one all-reduce per step)"},
         "forward_ms": sum(fwd_ms) / args.steps, "backward_ms": sum(bwd_ms) / args.steps,
         "roofline": roof, "e2e": e2e, "error_vs_fp64_oracle": err, "cpu_baseline": cpu,
-        "gpu_launches": 5 * args.steps,     # init + record; stage recompute + reverse + p0 gradient
+        "gpu_launches": int(runs),          # the library's kernels in the timed region, counted on the device
         "clocks": clk,
     }
 
@@ -1145,6 +1145,7 @@ def run_lens(args):
         lens.apply(x, out=y, stream=stream)
     clocks = ClockSampler(0 if ws == 1 else int(os.environ.get("LOCAL_RANK", "0")))
     torch.cuda.synchronize()
+    runs0 = crp.kernel_runs()
     clocks.start()
     ms = []
     for _ in range(args.steps):
@@ -1155,6 +1156,7 @@ def run_lens(args):
         e1.record(stream)
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
+    runs = crp.kernel_runs() - runs0
     clk = clocks.stop()
     t = sum(ms) * 1e-3
     value = nnz * n_maps * args.steps / t
@@ -1211,7 +1213,7 @@ def run_lens(args):
         "cpu_baseline": cpu,
         "e2e": {"value": nnz * n_maps * args.steps / te, "unit": "entries/s",
                 "h2d_bytes_per_step": int(xp.numel() * 8), "d2h_bytes_per_step": int(yp.numel() * 8)},
-        "gpu_launches": args.steps,
+        "gpu_launches": int(runs),
         "clocks": clk,
     }
     if rank == 0:

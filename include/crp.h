@@ -404,6 +404,12 @@ int crp_lens_bin(const crp_lens* lens, crp_sim* sim, int32_t nside, double e_min
 int crp_debug_fail_allocations(int32_t n);
 int crp_selftest_wait(int32_t limit, int32_t preset, void* stream);
 
+/* crp_kernel_runs(count): how many of this library's kernels have run on the current device
+ * since the library was loaded, including those launched from inside the propagate loop's
+ * CUDA graph (every kernel counts its own launches on the device). Synchronises the device;
+ * *count is written on CRP_OK. For benchmarks and tests (no counterpart in the paper). */
+int crp_kernel_runs(uint64_t* count);
+
 /* ---- propagation that allocates nothing -------------------------------------------------
  * This entry point has no counterpart in the paper; it exists for callers that must not
  * have this library allocate device memory. Some host programs own every byte of GPU

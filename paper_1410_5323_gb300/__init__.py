@@ -30,6 +30,7 @@ from .api import (  # noqa: F401
     Tables,
     debug_fail_allocations,
     healpix_ring,
+    kernel_runs,
     lib,
     selftest_wait,
 )

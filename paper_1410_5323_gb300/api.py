@@ -87,6 +87,14 @@ def debug_fail_allocations(n: int) -> None:
     _check(lib().crp_debug_fail_allocations(int(n)), "crp_debug_fail_allocations")
 
 
+def kernel_runs() -> int:
+    """How many of the library's kernels have run on the current device since it was loaded
+    (synchronises the device)."""
+    n = C.c_uint64()
+    _check(lib().crp_kernel_runs(C.byref(n)), "crp_kernel_runs")
+    return int(n.value)
+
+
 def selftest_wait(limit: int, preset: int = -1, stream=None) -> int:
     """Runs the kernels' bounded wait on a flag preset to `preset`; returns the status code
     (ERR_TIMEOUT when the flag is never set, OK otherwise) without raising."""
@@ -195,6 +203,7 @@ def lib() -> C.CDLL:
             "crp_lens_create": ([i32, i32, p, p, p, p, p], C.c_int),
             "crp_debug_fail_allocations": ([i32], C.c_int),
             "crp_selftest_wait": ([i32, i32, p], C.c_int),
+            "crp_kernel_runs": ([p], C.c_int),
             "crp_lens_destroy": ([p], C.c_int),
             "crp_lens_apply": ([p, p, p, i32, p], C.c_int),
             "crp_lens_bin": ([p, p, i32, d, p, p], C.c_int),

@@ -15,6 +15,11 @@
 #include "crp_internal.h"
 #include "crp_math.cuh"
 
+// Runs of this file's kernels (diagnostics: each launch adds one, from its first thread).
+namespace {
+__device__ unsigned long long g_kernel_runs = 0;
+}
+
 namespace crp {
 namespace {
 
@@ -34,6 +39,7 @@ __device__ __forceinline__ void store6(double* a, long long n, long long i, cons
 __global__ void k_adj_init(const double* __restrict__ x0, const double* __restrict__ p0,
                            const int32_t* __restrict__ Z, double* __restrict__ y0,
                            double* __restrict__ kappa, double* __restrict__ E, long long n) {
+    CRP_COUNT_RUN();
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double px = p0[3 * i], py = p0[3 * i + 1], pz = p0[3 * i + 2];
@@ -52,6 +58,7 @@ __global__ void k_adj_record(FieldDev F, const double* __restrict__ y0, const do
                              double tol, double hmin, double hmax, int n_steps, int K,
                              double* __restrict__ h_out, double* __restrict__ ck,
                              double* __restrict__ xT, double* __restrict__ uT, long long n) {
+    CRP_COUNT_RUN();
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
     Y6 y;
@@ -104,6 +111,7 @@ __global__ void k_adj_replay(FieldDev F, const double* __restrict__ y0, const do
                              const double* __restrict__ h, int n_steps, double* __restrict__ xT,
                              double* __restrict__ uT, unsigned long long* __restrict__ cell_hash,
                              long long n) {
+    CRP_COUNT_RUN();
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
     Y6 y;
@@ -309,6 +317,7 @@ template <int L>
 __global__ void k_adj_records(FieldDev F, const double* __restrict__ kap, const double* __restrict__ h,
                               const double* __restrict__ ck, double* __restrict__ rec_d,
                               int32_t* __restrict__ rec_n, int n_steps, int K, long long n) {
+    CRP_COUNT_RUN();
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const int n_seg = (n_steps + K - 1) / K;
     if (t >= n * n_seg) return;
@@ -407,6 +416,7 @@ __global__ void k_adj_reverse(const double* __restrict__ kap, const double* __re
                               const double* __restrict__ rec_d, const int32_t* __restrict__ rec_n,
                               int n_steps, const double* __restrict__ uT_bar, double* __restrict__ grid_bar,
                               double* __restrict__ y0_bar, double* __restrict__ kappa_bar_out, long long n) {
+    CRP_COUNT_RUN();
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double kappa = kap[i];
@@ -448,6 +458,7 @@ __global__ void k_adj_backward(FieldDev F, const double* __restrict__ kap, const
                                int K, const double* __restrict__ uT_bar, double* __restrict__ grid_bar,
                                double* __restrict__ y0_bar, double* __restrict__ kappa_bar_out,
                                long long n) {
+    CRP_COUNT_RUN();
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double kappa = kap[i];
@@ -479,6 +490,7 @@ __global__ void k_adj_p0bar(const double* __restrict__ y0, const double* __restr
                             const double* __restrict__ E, const double* __restrict__ y0_bar,
                             const double* __restrict__ kappa_bar, double* __restrict__ p0_bar,
                             double* __restrict__ x0_bar, long long n) {
+    CRP_COUNT_RUN();
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
     Y6 y, yb;
@@ -557,4 +569,15 @@ int adj_p0bar(const double* y0, const double* kappa, const double* E, const doub
     return (int)cudaGetLastError();
 }
 
+}  // namespace crp
+
+namespace crp {
+unsigned long long kernel_runs_adjoint() {
+    unsigned long long v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_kernel_runs, sizeof v) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return v;
+}
 }  // namespace crp

@@ -22,6 +22,11 @@
 #include "crp_math.cuh"
 #include "crp_sched.cuh"
 
+// Runs of this file's kernels (diagnostics: each launch adds one, from its first thread).
+namespace {
+__device__ unsigned long long g_kernel_runs = 0;
+}
+
 static_assert(CRP_STATUS_ACTIVE == crp::CRP_STATUS_ACTIVE_, "status numbering");
 static_assert(CRP_STATUS_DONE == crp::CRP_STATUS_DONE_, "status numbering");
 static_assert(CRP_STATUS_NAN == crp::CRP_STATUS_NAN_, "status numbering");
@@ -80,13 +85,15 @@ __global__ void k_layout(const In* __restrict__ in, Out* __restrict__ out, long 
 template <>
 __global__ void k_layout<float, float4>(const float* __restrict__ in, float4* __restrict__ out,
                                          long long n) {
+    CRP_COUNT_RUN();
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
         out[i] = make_float4(in[3 * i], in[3 * i + 1], in[3 * i + 2], 0.0f);
 }
 template <>
 __global__ void k_layout<double, double2>(const double* __restrict__ in, double2* __restrict__ out,
-                                           long long n) {   // two double2 per node
+                                           long long n) {
+    CRP_COUNT_RUN();   // two double2 per node
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         out[2 * i] = make_double2(in[3 * i], in[3 * i + 1]);
@@ -96,6 +103,7 @@ __global__ void k_layout<double, double2>(const double* __restrict__ in, double2
 template <>
 __global__ void k_layout<unsigned short, ushort4>(const unsigned short* __restrict__ in,
                                                   ushort4* __restrict__ out, long long n) {
+    CRP_COUNT_RUN();
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
         out[i] = make_ushort4(in[3 * i], in[3 * i + 1], in[3 * i + 2], 0);
@@ -105,6 +113,7 @@ __global__ void k_layout<unsigned short, ushort4>(const unsigned short* __restri
 // (i, j, k) holds its corners (i+a, j+b, k+c) mod n in the order 4a + 2b + c; FP32 keeps 3
 // floats per corner (96 B per cell), BF16 the 4 halves of the node (64 B per cell).
 __global__ void k_cells(const void* __restrict__ in, int bf16, int nx, int ny, int nz, void* __restrict__ out) {
+    CRP_COUNT_RUN();
     const long long n = (long long)nx * ny * nz;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
          c += (long long)gridDim.x * blockDim.x) {
@@ -128,6 +137,7 @@ __global__ void k_cells(const void* __restrict__ in, int bf16, int nx, int ny, i
 // per-corner expression the FP64 kernel would otherwise evaluate on every lookup.
 __global__ void k_widen(const void* __restrict__ in, int layout, double scale,
                         double2* __restrict__ out, long long n) {
+    CRP_COUNT_RUN();
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         double x, y, z;
@@ -155,6 +165,7 @@ __global__ void k_inject_init(SimState S, long long first, long long n, int uid_
                               int gid_given, unsigned long long uid_base, int n_fields,
                               int has_tables, int z_max, int n_max, unsigned long long seed,
                               int32_t* done_list, Counters* C) {
+    CRP_COUNT_RUN();
     const double INF = __longlong_as_double(0x7ff0000000000000LL);
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x) {
@@ -185,6 +196,7 @@ __global__ void k_inject_init(SimState S, long long first, long long n, int uid_
 }
 
 __global__ void k_set_used(Counters* C, unsigned long long n_used, unsigned long long n_prim) {
+    CRP_COUNT_RUN();
     C->n_used = n_used;
     C->reserve = n_used;
     C->n_primaries = n_prim;
@@ -192,6 +204,7 @@ __global__ void k_set_used(Counters* C, unsigned long long n_used, unsigned long
 
 // ---- propagate bookkeeping ----------------------------------------------------------------
 __global__ void k_prepare(Counters* C) {
+    CRP_COUNT_RUN();
     C->count[0] = 0;
     C->count[1] = 0;
     C->head[0] = 0;
@@ -219,6 +232,7 @@ __global__ void k_cost_hist(const int32_t* __restrict__ status, const double* __
                             const int32_t* __restrict__ Zc, const int32_t* __restrict__ gid,
                             int grid_major, int n_buckets, int use_shared,
                             unsigned* __restrict__ hist, const Counters* C) {
+    CRP_COUNT_RUN();
     extern __shared__ unsigned sh[];
     if (use_shared) {
         for (int b = threadIdx.x; b < n_buckets; b += blockDim.x) sh[b] = 0;
@@ -241,6 +255,7 @@ __global__ void k_cost_hist(const int32_t* __restrict__ status, const double* __
 
 // Exclusive scan of the histogram (one block of 1024 threads), clearing it for next time.
 __global__ void k_cost_scan(unsigned* hist, unsigned* offs, int n_buckets, Counters* C) {
+    CRP_COUNT_RUN();
     __shared__ unsigned part[1024];
     const int t = threadIdx.x;
     const int chunk = (n_buckets + blockDim.x - 1) / blockDim.x;
@@ -271,6 +286,7 @@ __global__ void k_cost_scatter(const int32_t* __restrict__ status, const double*
                                const int32_t* __restrict__ Zc, const int32_t* __restrict__ gid,
                                int grid_major, unsigned* __restrict__ offs,
                                int32_t* __restrict__ list, const Counters* C) {
+    CRP_COUNT_RUN();
     const long long n = (long long)*(volatile const unsigned long long*)&C->n_used;
     const int lane = threadIdx.x & 31;
     for (long long base = blockIdx.x * (long long)blockDim.x; base < n;
@@ -293,6 +309,7 @@ __global__ void k_cost_scatter(const int32_t* __restrict__ status, const double*
 // (warp-aggregated append).
 __global__ void k_build_worklist(const int32_t* __restrict__ status, int32_t* __restrict__ list,
                                  Counters* C) {
+    CRP_COUNT_RUN();
     const unsigned long long n = *(volatile unsigned long long*)&C->n_used;
     const int lane = threadIdx.x & 31;
     for (long long base = blockIdx.x * (long long)blockDim.x; base < (long long)n;
@@ -311,6 +328,7 @@ __global__ void k_build_worklist(const int32_t* __restrict__ status, int32_t* __
 // After a propagate launch over list `from`: fix the slot count, reset the pop head and
 // the list that the next launch pushes into.
 __global__ void k_swap(Counters* C, long long capacity, int from) {
+    CRP_COUNT_RUN();
     const unsigned long long r = C->reserve;
     C->n_used = r < (unsigned long long)capacity ? r : (unsigned long long)capacity;
     C->reserve = C->n_used;
@@ -329,6 +347,7 @@ struct ObsCols {
 
 __global__ void k_observe(SimState S, const int32_t* __restrict__ done, long long first,
                           long long n, ObsCols o) {
+    CRP_COUNT_RUN();
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x) {
         const int32_t i = done[first + k];
@@ -946,6 +965,14 @@ int crp_arrival_map(crp_sim* s, int32_t nside, double e_min_ev, uint64_t* map, v
 
 extern "C" {
 
+int crp_kernel_runs(uint64_t* count) {
+    if (!count) return fail(CRP_ERR_INVALID_ARG, "count is NULL");
+    CRP_CUDA(cudaDeviceSynchronize());
+    *count = kernel_runs_capi() + kernel_runs_fp64() + kernel_runs_mixed() + kernel_runs_adjoint() +
+             kernel_runs_sources() + kernel_runs_lens();
+    return CRP_OK;
+}
+
 int crp_debug_fail_allocations(int32_t n) {
     if (n < 0) return fail(CRP_ERR_INVALID_ARG, "n < 0");
     g_fail_allocs.store(n);
@@ -958,6 +985,7 @@ namespace {
 
 // Waits on a device flag with the scheduler's bounded wait; *status = 1 if the wait ran out.
 __global__ void k_selftest_wait(int32_t* flag, int limit, int* status) {
+    CRP_COUNT_RUN();
     int32_t v = -1;
     *status = bounded_acquire_wait(flag, limit, v) ? 0 : 1;
 }
@@ -1346,11 +1374,13 @@ int enqueue(crp_sim* s, const Plan& P, cudaStream_t st) {
 
 // Device-side loop control for crp_propagate_loop.
 __global__ void k_loop_init(Counters* C) {
+    CRP_COUNT_RUN();
     C->slices = 0;
     C->prev_accepted = C->accepted;
 }
 
 __global__ void k_loop_cond(Counters* C, cudaGraphConditionalHandle h, long long max_slices) {
+    CRP_COUNT_RUN();
     C->slices += 1;
     const bool active = C->n_used > C->n_done;
     const bool progressed = C->accepted != C->prev_accepted;
@@ -1563,6 +1593,7 @@ std::mutex g_noalloc_mu;
 void* g_noalloc_addr[64] = {};   // device address of the array, per device ordinal
 
 __global__ void k_noalloc_setup(Counters* C, FieldDev* F, FieldDev f, unsigned long long n) {
+    CRP_COUNT_RUN();
     Counters z{};
     z.n_used = n;
     z.reserve = n;
@@ -1828,3 +1859,14 @@ int crp_adjoint_read_steps(crp_adjoint* a, double* h, int32_t is_device) {
 }
 
 }  // extern "C"
+
+namespace crp {
+unsigned long long kernel_runs_capi() {
+    unsigned long long v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_kernel_runs, sizeof v) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return v;
+}
+}  // namespace crp

@@ -128,6 +128,20 @@ int propagate_fp64_occupancy(int layout, int mod, int block, int* blocks_per_sm)
 int launch_propagate_mixed(const PropArgs& a, int layout, int mod, int grid, int block, void* stream);
 int propagate_mixed_occupancy(int layout, int mod, int block, int* blocks_per_sm);
 
+// Diagnostics: every kernel counts its runs in a device counter of its own translation unit
+// (one atomic per launch, by the first thread of the first block); kernel_runs_*() read them.
+#define CRP_COUNT_RUN()                                                                         \
+    do {                                                                                        \
+        if ((threadIdx.x | threadIdx.y | threadIdx.z | blockIdx.x | blockIdx.y | blockIdx.z) == 0) \
+            atomicAdd(&g_kernel_runs, 1ull);                                                    \
+    } while (0)
+unsigned long long kernel_runs_capi();
+unsigned long long kernel_runs_fp64();
+unsigned long long kernel_runs_mixed();
+unsigned long long kernel_runs_adjoint();
+unsigned long long kernel_runs_sources();
+unsigned long long kernel_runs_lens();
+
 // Adjoint launchers (adjoint.cu). Arrays are component-major [component][n] for y,
 // [step][n] for h, [checkpoint][6][n] for checkpoints. `stages`, when not NULL, holds the
 // stage records of every step: per step and particle kAdjRecordBytes (6 stages x (23 FP64:

@@ -22,6 +22,11 @@
 #include "crp_internal.h"
 #include "crp_sky.cuh"
 
+// Runs of this file's kernels (diagnostics: each launch adds one, from its first thread).
+namespace {
+__device__ unsigned long long g_kernel_runs = 0;
+}
+
 namespace crp {
 namespace {
 
@@ -60,6 +65,7 @@ __global__ void __launch_bounds__(256) k_lens_apply_vec(int n_pix, const long lo
                                                         const int* __restrict__ rl, const int* __restrict__ col,
                                                         const float* __restrict__ val,
                                                         const double* __restrict__ x, double* __restrict__ y) {
+    CRP_COUNT_RUN();
     const int lane = threadIdx.x & (G - 1);
     constexpr int kGroups = 32 / G;                              // rows per warp
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
@@ -95,6 +101,7 @@ __global__ void __launch_bounds__(256) k_lens_apply_maps(int n_pix, int n_maps, 
                                                          const int* __restrict__ rl, const int* __restrict__ col,
                                                          const float* __restrict__ val,
                                                          const double* __restrict__ x, double* __restrict__ y) {
+    CRP_COUNT_RUN();
     const int lane = threadIdx.x & 31;
     const int chunks = (n_maps + 31) / 32;
     const long long warps = (long long)gridDim.x * blockDim.x / 32;
@@ -119,6 +126,7 @@ __global__ void __launch_bounds__(256) k_lens_apply_maps(int n_pix, int n_maps, 
 // the lens edges (binary search; the bin m with edges[m] <= R < edges[m+1]), pixel of -u.
 __global__ void k_lens_bin(SimState S, const Counters* C, int nside, int n_mat, const double* __restrict__ edges,
                            double e_min, double* __restrict__ x) {
+    CRP_COUNT_RUN();
     const long long n_pix = 12ll * nside * nside;
     const long long n = (long long)C->n_used;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -170,4 +178,15 @@ int launch_lens_bin(const SimState& S, const Counters* C, int nside, int n_mat, 
     return (int)cudaGetLastError();
 }
 
+}  // namespace crp
+
+namespace crp {
+unsigned long long kernel_runs_lens() {
+    unsigned long long v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_kernel_runs, sizeof v) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return v;
+}
 }  // namespace crp

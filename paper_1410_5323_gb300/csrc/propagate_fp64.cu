@@ -21,6 +21,11 @@
 #include "crp_sched.cuh"
 #include "crp_fp64.cuh"
 
+// Runs of this file's kernels (diagnostics: each launch adds one, from its first thread).
+namespace {
+__device__ unsigned long long g_kernel_runs = 0;
+}
+
 namespace crp {
 namespace {
 
@@ -37,6 +42,7 @@ using namespace fp64;
 
 template <int L, bool M>
 __global__ void CRP_FP64_BOUNDS k_propagate_fp64(const PropArgs a) {
+    CRP_COUNT_RUN();
     const int lane = threadIdx.x & 31;
     Counters* C = a.ctr;
     const unsigned long long n_work = *(volatile unsigned long long*)&C->count[a.list];
@@ -269,4 +275,15 @@ int propagate_fp64_occupancy(int layout, int mod, int block, int* blocks_per_sm)
     });
 }
 
+}  // namespace crp
+
+namespace crp {
+unsigned long long kernel_runs_fp64() {
+    unsigned long long v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_kernel_runs, sizeof v) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return v;
+}
 }  // namespace crp

@@ -25,6 +25,11 @@
 #include "crp_math.cuh"
 #include "crp_sched.cuh"
 
+// Runs of this file's kernels (diagnostics: each launch adds one, from its first thread).
+namespace {
+__device__ unsigned long long g_kernel_runs = 0;
+}
+
 namespace crp {
 namespace {
 
@@ -654,12 +659,14 @@ __device__ __forceinline__ void propagate_mixed_body(const PropArgs& a, float* s
 
 template <int L>
 __global__ void CRP_MIXED_BOUNDS k_propagate_mixed(const PropArgs a) {
+    CRP_COUNT_RUN();
     propagate_mixed_body<L, false>(a, nullptr);
 }
 
 // Modulated fields; dynamic shared memory: kModSlots floats per thread.
 template <int L>
 __global__ void CRP_MIXED_MOD_BOUNDS k_propagate_mixed_mod(const PropArgs a) {
+    CRP_COUNT_RUN();
     extern __shared__ float mod_sm[];
     propagate_mixed_body<L, true>(a, mod_sm);
 }
@@ -700,4 +707,15 @@ int propagate_mixed_occupancy(int layout, int mod, int block, int* blocks_per_sm
     });
 }
 
+}  // namespace crp
+
+namespace crp {
+unsigned long long kernel_runs_mixed() {
+    unsigned long long v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_kernel_runs, sizeof v) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return v;
+}
 }  // namespace crp

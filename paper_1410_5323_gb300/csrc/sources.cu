@@ -9,6 +9,11 @@
 #include "crp_math.cuh"
 #include "crp_sky.cuh"
 
+// Runs of this file's kernels (diagnostics: each launch adds one, from its first thread).
+namespace {
+__device__ unsigned long long g_kernel_runs = 0;
+}
+
 namespace crp {
 namespace {
 
@@ -26,6 +31,7 @@ __device__ __forceinline__ U4 words(unsigned long long seed, unsigned long long 
 // from the cutoff-free joint law, then an isotropic direction (Marsaglia 1972).
 __global__ void k_source_sample(SimState S, long long first, long long n, unsigned long long uid_base,
                                 crp_spectrum sp, unsigned long long seed) {
+    CRP_COUNT_RUN();
     // cumulative species weights w_i = x_i A_i^(alpha-1); inverse-CDF constants of E^-alpha
     double cum[CRP_MAX_SPECIES];
     double acc = 0.0;
@@ -95,6 +101,7 @@ __global__ void k_source_sample(SimState S, long long first, long long n, unsign
 }
 
 __global__ void k_healpix(int nside, const double* __restrict__ u, long long n, long long* __restrict__ pix) {
+    CRP_COUNT_RUN();
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x)
         pix[k] = sky::healpix_ring(nside, u[3 * k], u[3 * k + 1], u[3 * k + 2]);
@@ -104,6 +111,7 @@ __global__ void k_healpix(int nside, const double* __restrict__ u, long long n, 
 // the map (12 nside^2 32-bit counters) and adds its non-zero pixels to the global map once.
 __global__ void k_arrival_map(SimState S, const Counters* C, int nside, double e_min, int shared,
                               unsigned long long* __restrict__ map) {
+    CRP_COUNT_RUN();
     extern __shared__ unsigned int smap[];
     const long long npix = 12ll * nside * nside;
     if (shared) {
@@ -148,4 +156,15 @@ int launch_arrival_map(const SimState& S, const Counters* C, int nside, double e
     return (int)cudaGetLastError();
 }
 
+}  // namespace crp
+
+namespace crp {
+unsigned long long kernel_runs_sources() {
+    unsigned long long v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_kernel_runs, sizeof v) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return v;
+}
 }  // namespace crp

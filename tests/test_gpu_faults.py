@@ -65,3 +65,31 @@ def test_injected_allocation_failures_report_oom_and_leak_nothing():
     sim = _small_sim(crp)                    # the library still works
     sim.propagate(1e-4, I.KPC, I.MPC, 5 * I.MPC)
     assert sim.sync(timeout_s=60.0) == 0
+
+
+def test_kernel_run_counter_counts_every_launch():
+    """crp_kernel_runs counts the library's kernels on the device: injection is two kernels
+    (bookkeeping init, slot count); a slot-order propagate call is the prepare kernel, the
+    work-list build and two generations of (propagate, swap); the graph loop's kernels are
+    counted although the host never launches them one by one."""
+    import paper_1410_5323_gb300 as crp
+    from paper_1410_5323_gb300 import api
+
+    grid = I.kolmogorov_grid(16, 0.25 * I.MPC, 2, 8, 1e-13, 3).astype(np.float32)
+    p = I.make_particles(64, 5)
+    sim = crp.Simulation([crp.Field(grid, 0.25 * I.MPC)], None, capacity=len(p))
+    n0 = crp.kernel_runs()
+    sim.inject(p)
+    assert crp.kernel_runs() - n0 == 2
+    n1 = crp.kernel_runs()
+    sim.propagate(1e-4, I.KPC, I.MPC, 5 * I.MPC, order=api.ORDER_SLOT)
+    sim.sync(60.0)
+    assert crp.kernel_runs() - n1 == 6
+    sim.reset()
+    sim.inject(p)
+    n2 = crp.kernel_runs()
+    sim.propagate_loop(1e-4, I.KPC, I.MPC, 5 * I.MPC, max_steps=2, order=api.ORDER_SLOT)
+    sim.sync(60.0)
+    slices = sim.counts()["launches"] // 2
+    assert slices > 1
+    assert crp.kernel_runs() - n2 >= 6 * slices
