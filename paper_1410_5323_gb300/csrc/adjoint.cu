@@ -52,49 +52,6 @@ __global__ void k_adj_init(const double* __restrict__ x0, const double* __restri
     kappa[i] = (double)Z[i] * kC / e;
 }
 
-// Forward with the propagation module's controller only; records h_n and checkpoints.
-template <int L>
-__global__ void k_adj_record(FieldDev F, const double* __restrict__ y0, const double* __restrict__ kap,
-                             double tol, double hmin, double hmax, int n_steps, int K,
-                             double* __restrict__ h_out, double* __restrict__ ck,
-                             double* __restrict__ xT, double* __restrict__ uT, long long n) {
-    CRP_COUNT_RUN();
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    Y6 y;
-    load6(y0, n, i, y);
-    const double kappa = kap[i];
-    const double tol2 = tol * tol;
-    const float lg_tol = ctrl_log2(tol);
-    double hprop = __longlong_as_double(0x7ff0000000000000LL);
-    for (int m = 0; m < n_steps; ++m) {
-        if (m % K == 0) store6(ck + (long long)(m / K) * 6 * n, n, i, y);
-        const double h_prop = clampd(hprop, hmin, hmax);
-        double h = h_prop;
-        const Y6 k1 = deriv<L>(F, kappa, y);
-        Y6 y5, err;
-        double sx, su;
-        int rejected = 0;
-        for (;;) {
-            ck_attempt<L>(F, kappa, y, k1, h, y5, err);
-            error_sums(err, sx, su);
-            if (error_accept(sx, su, h, tol, tol2) || h <= hmin) break;
-            const float shrink = ctrl_factor(ctrl_log2r(sx, su, h, lg_tol), -0.25f, 0.1f, 1.0f);
-            h = fmax(h * widen_normal(shrink), hmin);
-            rejected = 1;
-        }
-        y = y5;
-        h_out[(long long)m * n + i] = h;
-        const float grow = (h == 0.0 || (sx == 0.0 && su == 0.0))
-                               ? 5.0f : ctrl_factor(ctrl_log2r(sx, su, h, lg_tol), -0.2f, 0.2f, 5.0f);
-        double hnext = h * widen_normal(grow);
-        if (!rejected && h < h_prop) hnext = fmax(hnext, h_prop);
-        hprop = clampd(hnext, hmin, hmax);
-    }
-    xT[3 * i] = y.x; xT[3 * i + 1] = y.y; xT[3 * i + 2] = y.z;
-    uT[3 * i] = y.ux; uT[3 * i + 1] = y.uy; uT[3 * i + 2] = y.uz;
-}
-
 template <int L, bool H = false>
 __device__ __forceinline__ void frozen_step(const FieldDev& F, double kappa, Y6& y, double h,
                                             unsigned long long* hh = nullptr) {
@@ -379,79 +336,6 @@ __global__ void k_adj_records(FieldDev F, const double* __restrict__ kap, const 
     }
 }
 
-// One stage of the reverse sweep from its record.
-__device__ __forceinline__ void vjp_rec(const double* __restrict__ rec_d, const int32_t* __restrict__ rec_n,
-                                        long long n, long long i, int m, int st, double kappa,
-                                        const Y6& kb, Y6& Yb, double* __restrict__ grid_bar,
-                                        double& kappa_bar) {
-    const double* d = rec_d + ((long long)(m * 6 + st) * kRecD) * n + i;
-    const int32_t* q = rec_n + ((long long)(m * 6 + st) * kRecN) * n + i;
-    const double B[3] = {__ldcs(d + 3 * n), __ldcs(d + 4 * n), __ldcs(d + 5 * n)};
-    double J[3][3], w[8];
-    long long node[8];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) J[a][b] = __ldcs(d + (6 + 3 * a + b) * n);
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        w[c] = __ldcs(d + (15 + c) * n);
-        node[c] = __ldcs(q + c * n);
-    }
-    vjp_apply(kappa, __ldcs(d), __ldcs(d + n), __ldcs(d + 2 * n), B, J, w, node, kb, Yb, grid_bar, kappa_bar);
-}
-
-// L2 prefetch of one step's records (read by the next iteration of the reverse sweep).
-__device__ __forceinline__ void prefetch_step(const double* rec_d, const int32_t* rec_n, long long n,
-                                              long long i, int m) {
-    const double* d = rec_d + ((long long)m * 6 * kRecD) * n + i;
-    for (int k = 0; k < 6 * kRecD; ++k) asm volatile("prefetch.global.L2 [%0];" ::"l"(d + k * n));
-    const int32_t* q = rec_n + ((long long)m * 6 * kRecN) * n + i;
-    for (int k = 0; k < 6 * kRecN; ++k) asm volatile("prefetch.global.L2 [%0];" ::"l"(q + k * n));
-}
-
-// Reverse sweep over the stage records, one thread per particle: the adjoint of
-// y' = y + h sum_i b_i k_i and of the stage sums, stages in reverse (the oracle's order).
-__global__ void k_adj_reverse(const double* __restrict__ kap, const double* __restrict__ h,
-                              const double* __restrict__ rec_d, const int32_t* __restrict__ rec_n,
-                              int n_steps, const double* __restrict__ uT_bar, double* __restrict__ grid_bar,
-                              double* __restrict__ y0_bar, double* __restrict__ kappa_bar_out, long long n) {
-    CRP_COUNT_RUN();
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const double kappa = kap[i];
-    Y6 lam{0.0, 0.0, 0.0, uT_bar[3 * i], uT_bar[3 * i + 1], uT_bar[3 * i + 2]};
-    double kappa_bar = 0.0;
-    for (int m = n_steps - 1; m >= 0; --m) {
-        if (m > 0) prefetch_step(rec_d, rec_n, n, i, m - 1);
-        const double hn = h[(long long)m * n + i];
-        Y6 kb0 = scale6(hn * cB5h[0], lam), kb1 = scale6(hn * cB5h[1], lam), kb2 = scale6(hn * cB5h[2], lam),
-           kb3 = scale6(hn * cB5h[3], lam), kb4 = scale6(hn * cB5h[4], lam), kb5 = scale6(hn * cB5h[5], lam);
-        Y6 yb = lam, Yb;
-        vjp_rec(rec_d, rec_n, n, i, m, 5, kappa, kb5, Yb, grid_bar, kappa_bar);
-        add6(yb, Yb);
-        axpy6(kb0, hn * A61, Yb); axpy6(kb1, hn * A62, Yb); axpy6(kb2, hn * A63, Yb);
-        axpy6(kb3, hn * A64, Yb); axpy6(kb4, hn * A65, Yb);
-        vjp_rec(rec_d, rec_n, n, i, m, 4, kappa, kb4, Yb, grid_bar, kappa_bar);
-        add6(yb, Yb);
-        axpy6(kb0, hn * A51, Yb); axpy6(kb1, hn * A52, Yb); axpy6(kb2, hn * A53, Yb); axpy6(kb3, hn * A54, Yb);
-        vjp_rec(rec_d, rec_n, n, i, m, 3, kappa, kb3, Yb, grid_bar, kappa_bar);
-        add6(yb, Yb);
-        axpy6(kb0, hn * A41, Yb); axpy6(kb1, hn * A42, Yb); axpy6(kb2, hn * A43, Yb);
-        vjp_rec(rec_d, rec_n, n, i, m, 2, kappa, kb2, Yb, grid_bar, kappa_bar);
-        add6(yb, Yb);
-        axpy6(kb0, hn * A31, Yb); axpy6(kb1, hn * A32, Yb);
-        vjp_rec(rec_d, rec_n, n, i, m, 1, kappa, kb1, Yb, grid_bar, kappa_bar);
-        add6(yb, Yb);
-        axpy6(kb0, hn * A21, Yb);
-        vjp_rec(rec_d, rec_n, n, i, m, 0, kappa, kb0, Yb, grid_bar, kappa_bar);
-        add6(yb, Yb);
-        lam = yb;
-    }
-    store6(y0_bar, n, i, lam);
-    kappa_bar_out[i] = kappa_bar;
-}
-
 template <int L>
 __global__ void k_adj_backward(FieldDev F, const double* __restrict__ kap, const double* __restrict__ h,
                                const double* __restrict__ ck, double* __restrict__ seg, int n_steps,
@@ -507,6 +391,247 @@ __global__ void k_adj_p0bar(const double* __restrict__ y0, const double* __restr
     }
 }
 
+// ---- team form: three lanes per particle ----------------------------------------------------
+// GB300 issues one FP64 warp instruction per 64 cycles per SM sub-partition, whatever the
+// number of active lanes, and the forward and reverse sweeps have one chain per particle: their
+// time is each lane's FP64 instruction count. A team of three lanes (lanes 3t, 3t+1, 3t+2; ten
+// teams per warp) shares one particle: lane c owns component c of the position and direction,
+// of every stage state, stage derivative and cotangent, forms axis c of each lookup, a share of
+// the corner weights, B_c and the c-th Lorentz component. Values of the whole particle (error
+// sums, accept decision, step size, kappa_bar) are formed by the same operations in all three
+// lanes. Every value is the one the one-lane form computes, so the results are the same bits.
+constexpr int kTeams = 10;
+
+struct Team {
+    unsigned mask;   // the team's lanes
+    int l0, c;       // its first lane, this lane's component
+    __device__ __forceinline__ double get(double v, int k) const { return __shfl_sync(mask, v, l0 + k); }
+    __device__ __forceinline__ long long get(long long v, int k) const { return __shfl_sync(mask, v, l0 + k); }
+    __device__ __forceinline__ int nx1() const { return c == 2 ? 0 : c + 1; }
+    __device__ __forceinline__ int nx2() const { return c == 0 ? 2 : c - 1; }
+};
+
+// B_c at the team's stage position (lane c holds its coordinate xc): the periodic trilinear
+// lookup of field_b, with the axes, the corner weights and the corner loads split over the
+// team. FP64 node copy: component c of node k at ((const double*)data)[4k + c].
+__device__ __forceinline__ double field_team(const FieldDev& F, const Team& T, double xc) {
+    const double oi = T.c == 0 ? F.oix : (T.c == 1 ? F.oiy : F.oiz);
+    const int nn = T.c == 0 ? F.nx : (T.c == 1 ? F.ny : F.nz);
+    long long i0, i1;
+    double w0, w1;
+    axis(xc, oi, F.inv_spacing, nn, F.pow2, i0, i1, w0, w1);
+    const long long ix0 = T.get(i0, 0), ix1 = T.get(i1, 0), iy0 = T.get(i0, 1), iy1 = T.get(i1, 1);
+    const long long iz0 = T.get(i0, 2), iz1 = T.get(i1, 2);
+    const double wx0 = T.get(w0, 0), wx1 = T.get(w1, 0), wy0 = T.get(w0, 1), wy1 = T.get(w1, 1);
+    const double wz0 = T.get(w0, 2), wz1 = T.get(w1, 2);
+    // lane 0 forms w00, w01 and t0..t3, lane 1 w10, w11 and t4..t7 (lane 2 repeats lane 1)
+    const double wxa = T.c == 0 ? wx0 : wx1;
+    const double wA = wxa * wy0, wB = wxa * wy1;
+    const double tA0 = wA * wz0, tA1 = wA * wz1, tB0 = wB * wz0, tB1 = wB * wz1;
+    const double t0 = T.get(tA0, 0), t1 = T.get(tA1, 0), t2 = T.get(tB0, 0), t3 = T.get(tB1, 0);
+    const double t4 = T.get(tA0, 1), t5 = T.get(tA1, 1), t6 = T.get(tB0, 1), t7 = T.get(tB1, 1);
+    const long long ny = F.ny, nz = F.nz;
+    const long long r00 = (ix0 * ny + iy0) * nz, r01 = (ix0 * ny + iy1) * nz;
+    const long long r10 = (ix1 * ny + iy0) * nz, r11 = (ix1 * ny + iy1) * nz;
+    const double* G = reinterpret_cast<const double*>(F.data) + T.c;
+    const double g0 = __ldg(G + 4 * (r00 + iz0)), g1 = __ldg(G + 4 * (r00 + iz1));
+    const double g2 = __ldg(G + 4 * (r01 + iz0)), g3 = __ldg(G + 4 * (r01 + iz1));
+    const double g4 = __ldg(G + 4 * (r10 + iz0)), g5 = __ldg(G + 4 * (r10 + iz1));
+    const double g6 = __ldg(G + 4 * (r11 + iz0)), g7 = __ldg(G + 4 * (r11 + iz1));
+    double B = __fma_rn(t0, g0, 0.0);
+    B = __fma_rn(t1, g1, B);
+    B = __fma_rn(t2, g2, B);
+    B = __fma_rn(t3, g3, B);
+    B = __fma_rn(t4, g4, B);
+    B = __fma_rn(t5, g5, B);
+    B = __fma_rn(t6, g6, B);
+    B = __fma_rn(t7, g7, B);
+    return B;
+}
+
+// Component c of f(Y) = (u, kappa u x B(x)): (ku_c = kappa fma(u_{c+1}, B_{c+2}, -(u_{c+2} B_{c+1}))).
+__device__ __forceinline__ void deriv_team(const FieldDev& F, const Team& T, double kappa, double yx,
+                                           double yu, double& kx, double& ku) {
+    const double B = field_team(F, T, yx);
+    const double u1 = T.get(yu, T.nx1()), u2 = T.get(yu, T.nx2());
+    const double B1 = T.get(B, T.nx1()), B2 = T.get(B, T.nx2());
+    kx = yu;
+    ku = kappa * __fma_rn(u1, B2, -(u2 * B1));
+}
+
+__device__ __forceinline__ Team make_team(long long n, long long& i, bool& active) {
+    const int lane = threadIdx.x & 31;
+    const int team = lane / 3;
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    i = warp * kTeams + team;
+    active = lane < 3 * kTeams && i < n;
+    Team T;
+    T.l0 = 3 * team;
+    T.c = lane - T.l0;
+    T.mask = 7u << T.l0;
+    return T;
+}
+
+// Forward with the propagation module's controller only, in team form; records h_n and
+// checkpoints (the same values as k_adj_record).
+__global__ void k_adj_record_team(FieldDev F, const double* __restrict__ y0, const double* __restrict__ kap,
+                                  double tol, double hmin, double hmax, int n_steps, int K,
+                                  double* __restrict__ h_out, double* __restrict__ ck,
+                                  double* __restrict__ xT, double* __restrict__ uT, long long n) {
+    CRP_COUNT_RUN();
+    long long i;
+    bool active;
+    const Team T = make_team(n, i, active);
+    if (!active) return;
+    const int c = T.c;
+    double yx = y0[(long long)c * n + i], yu = y0[(long long)(3 + c) * n + i];
+    const double kappa = kap[i];
+    const double tol2 = tol * tol;
+    const float lg_tol = ctrl_log2(tol);
+    double hprop = __longlong_as_double(0x7ff0000000000000LL);
+    for (int m = 0; m < n_steps; ++m) {
+        if (m % K == 0) {
+            double* q = ck + (long long)(m / K) * 6 * n;
+            q[(long long)c * n + i] = yx;
+            q[(long long)(3 + c) * n + i] = yu;
+        }
+        const double h_prop = clampd(hprop, hmin, hmax);
+        double h = h_prop;
+        double k1x, k1u;
+        deriv_team(F, T, kappa, yx, yu, k1x, k1u);
+        double y5x, y5u, sx, su;
+        int rejected = 0;
+        for (;;) {
+            double tx, tu, k2x, k2u, k3x, k3u, k4x, k4u, k5x, k5u, k6x, k6u;
+            tx = __fma_rn(h, A21 * k1x, yx); tu = __fma_rn(h, A21 * k1u, yu);
+            deriv_team(F, T, kappa, tx, tu, k2x, k2u);
+#define T3(k) __fma_rn(A32, k2##k, A31 * k1##k)
+            tx = __fma_rn(h, T3(x), yx); tu = __fma_rn(h, T3(u), yu);
+            deriv_team(F, T, kappa, tx, tu, k3x, k3u);
+#define T4(k) __fma_rn(A43, k3##k, __fma_rn(A42, k2##k, A41 * k1##k))
+            tx = __fma_rn(h, T4(x), yx); tu = __fma_rn(h, T4(u), yu);
+            deriv_team(F, T, kappa, tx, tu, k4x, k4u);
+#define T5(k) __fma_rn(A54, k4##k, __fma_rn(A53, k3##k, __fma_rn(A52, k2##k, A51 * k1##k)))
+            tx = __fma_rn(h, T5(x), yx); tu = __fma_rn(h, T5(u), yu);
+            deriv_team(F, T, kappa, tx, tu, k5x, k5u);
+#define T6(k) __fma_rn(A65, k5##k, __fma_rn(A64, k4##k, __fma_rn(A63, k3##k, __fma_rn(A62, k2##k, A61 * k1##k))))
+            tx = __fma_rn(h, T6(x), yx); tu = __fma_rn(h, T6(u), yu);
+            deriv_team(F, T, kappa, tx, tu, k6x, k6u);
+#define TB(k) __fma_rn(B6, k6##k, __fma_rn(B4, k4##k, __fma_rn(B3, k3##k, B1 * k1##k)))
+#define TE(k) (h * __fma_rn(E6, k6##k, __fma_rn(E5, k5##k, __fma_rn(E4, k4##k, __fma_rn(E3, k3##k, E1 * k1##k)))))
+            y5x = __fma_rn(h, TB(x), yx); y5u = __fma_rn(h, TB(u), yu);
+            const double ex = TE(x), eu = TE(u);
+#undef T3
+#undef T4
+#undef T5
+#undef T6
+#undef TB
+#undef TE
+            // squared norms ((e0^2 + e1^2) + e2^2) with fused products, as error_sums
+            const double ex0 = T.get(ex, 0), ex1 = T.get(ex, 1), ex2 = T.get(ex, 2);
+            const double eu0 = T.get(eu, 0), eu1 = T.get(eu, 1), eu2 = T.get(eu, 2);
+            sx = __fma_rn(ex2, ex2, __fma_rn(ex1, ex1, ex0 * ex0));
+            su = __fma_rn(eu2, eu2, __fma_rn(eu1, eu1, eu0 * eu0));
+            if (error_accept(sx, su, h, tol, tol2) || h <= hmin) break;
+            const float shrink = ctrl_factor(ctrl_log2r(sx, su, h, lg_tol), -0.25f, 0.1f, 1.0f);
+            h = fmax(h * widen_normal(shrink), hmin);
+            rejected = 1;
+        }
+        yx = y5x;
+        yu = y5u;
+        if (c == 0) h_out[(long long)m * n + i] = h;
+        const float grow = (h == 0.0 || (sx == 0.0 && su == 0.0))
+                               ? 5.0f : ctrl_factor(ctrl_log2r(sx, su, h, lg_tol), -0.2f, 0.2f, 5.0f);
+        double hnext = h * widen_normal(grow);
+        if (!rejected && h < h_prop) hnext = fmax(hnext, h_prop);
+        hprop = clampd(hnext, hmin, hmax);
+    }
+    xT[3 * i + c] = yx;
+    uT[3 * i + c] = yu;
+}
+
+// Reverse sweep over the stage records in team form: lane c owns component c of the cotangents.
+// Per stage: Bbar_c = kappa (bbar_{c+1} u_{c+2} - bbar_{c+2} u_{c+1}); kappa_bar += ((p0 + p1) + p2)
+// with p_k = bbar_k (u x B)_k; Ybar_u_c = abar_c + kappa (B_{c+1} bbar_{c+2} - B_{c+2} bbar_{c+1});
+// Ybar_x_c = (J[0][c] Bbar_0 + J[1][c] Bbar_1) + J[2][c] Bbar_2; lane c scatters w_k Bbar_c.
+__device__ __forceinline__ void vjp_rec_team(const double* __restrict__ rec_d, const int32_t* __restrict__ rec_n,
+                                             long long n, long long i, int m, int st, double kappa,
+                                             const Team& T, double kbx, double kbu, double& Ybx, double& Ybu,
+                                             double* __restrict__ grid_bar, double& kappa_bar) {
+    const int c = T.c, c1 = T.nx1(), c2 = T.nx2();
+    const double* d = rec_d + ((long long)(m * 6 + st) * kRecD) * n + i;
+    const int32_t* q = rec_n + ((long long)(m * 6 + st) * kRecN) * n + i;
+    const double u1 = __ldcs(d + c1 * n), u2 = __ldcs(d + c2 * n);
+    const double B1 = __ldcs(d + (3 + c1) * n), B2 = __ldcs(d + (3 + c2) * n);
+    const double J0 = __ldcs(d + (6 + c) * n), J1 = __ldcs(d + (9 + c) * n), J2 = __ldcs(d + (12 + c) * n);
+    const double bb1 = T.get(kbu, c1), bb2 = T.get(kbu, c2);
+    const double Bb = kappa * (bb1 * u2 - bb2 * u1);
+    const double uxB = u1 * B2 - u2 * B1;
+    const double p = kbu * uxB;
+    const double p0 = T.get(p, 0), p1 = T.get(p, 1), p2 = T.get(p, 2);
+    kappa_bar = kappa_bar + ((p0 + p1) + p2);
+    Ybu = kbx + kappa * (B1 * bb2 - B2 * bb1);
+    const double Bb0 = T.get(Bb, 0), Bb1 = T.get(Bb, 1), Bb2 = T.get(Bb, 2);
+    Ybx = (J0 * Bb0 + J1 * Bb1) + J2 * Bb2;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const double w = __ldcs(d + (15 + k) * n);
+        const long long node = __ldcs(q + k * n);
+        atomicAdd(grid_bar + node * 3 + c, w * Bb);
+    }
+}
+
+__global__ void k_adj_reverse_team(const double* __restrict__ kap, const double* __restrict__ h,
+                                   const double* __restrict__ rec_d, const int32_t* __restrict__ rec_n,
+                                   int n_steps, const double* __restrict__ uT_bar, double* __restrict__ grid_bar,
+                                   double* __restrict__ y0_bar, double* __restrict__ kappa_bar_out, long long n) {
+    CRP_COUNT_RUN();
+    long long i;
+    bool active;
+    const Team T = make_team(n, i, active);
+    if (!active) return;
+    const int c = T.c;
+    const double kappa = kap[i];
+    double lx = 0.0, lu = uT_bar[3 * i + c];
+    double kappa_bar = 0.0;
+    for (int m = n_steps - 1; m >= 0; --m) {
+        const double hn = h[(long long)m * n + i];
+        // stage cotangents kb_s = (h b_s) lam, per component
+        const double s0 = hn * cB5h[0], s1 = hn * cB5h[1], s2 = hn * cB5h[2], s3 = hn * cB5h[3],
+                     s4 = hn * cB5h[4], s5 = hn * cB5h[5];
+        double k0x = s0 * lx, k0u = s0 * lu, k1x = s1 * lx, k1u = s1 * lu, k2x = s2 * lx, k2u = s2 * lu;
+        double k3x = s3 * lx, k3u = s3 * lu, k4x = s4 * lx, k4u = s4 * lu;
+        const double k5x = s5 * lx, k5u = s5 * lu;
+        double ybx = lx, ybu = lu, Yx, Yu;
+#define AX(kx, ku, a) do { const double ha = hn * (a); kx = kx + ha * Yx; ku = ku + ha * Yu; } while (0)
+        vjp_rec_team(rec_d, rec_n, n, i, m, 5, kappa, T, k5x, k5u, Yx, Yu, grid_bar, kappa_bar);
+        ybx = ybx + Yx; ybu = ybu + Yu;
+        AX(k0x, k0u, A61); AX(k1x, k1u, A62); AX(k2x, k2u, A63); AX(k3x, k3u, A64); AX(k4x, k4u, A65);
+        vjp_rec_team(rec_d, rec_n, n, i, m, 4, kappa, T, k4x, k4u, Yx, Yu, grid_bar, kappa_bar);
+        ybx = ybx + Yx; ybu = ybu + Yu;
+        AX(k0x, k0u, A51); AX(k1x, k1u, A52); AX(k2x, k2u, A53); AX(k3x, k3u, A54);
+        vjp_rec_team(rec_d, rec_n, n, i, m, 3, kappa, T, k3x, k3u, Yx, Yu, grid_bar, kappa_bar);
+        ybx = ybx + Yx; ybu = ybu + Yu;
+        AX(k0x, k0u, A41); AX(k1x, k1u, A42); AX(k2x, k2u, A43);
+        vjp_rec_team(rec_d, rec_n, n, i, m, 2, kappa, T, k2x, k2u, Yx, Yu, grid_bar, kappa_bar);
+        ybx = ybx + Yx; ybu = ybu + Yu;
+        AX(k0x, k0u, A31); AX(k1x, k1u, A32);
+        vjp_rec_team(rec_d, rec_n, n, i, m, 1, kappa, T, k1x, k1u, Yx, Yu, grid_bar, kappa_bar);
+        ybx = ybx + Yx; ybu = ybu + Yu;
+        AX(k0x, k0u, A21);
+        vjp_rec_team(rec_d, rec_n, n, i, m, 0, kappa, T, k0x, k0u, Yx, Yu, grid_bar, kappa_bar);
+        ybx = ybx + Yx; ybu = ybu + Yu;
+#undef AX
+        lx = ybx;
+        lu = ybu;
+    }
+    y0_bar[(long long)c * n + i] = lx;
+    y0_bar[(long long)(3 + c) * n + i] = lu;
+    if (c == 0) kappa_bar_out[i] = kappa_bar;
+}
+
+int team_blocks(long long n) { return (int)((n + kTeams - 1) / kTeams); }   // one warp per block
+
 int blocks(long long n) { return (int)((n + 127) / 128); }
 
 // Kernels with one thread per chain run one warp per block: 4096 chains are then 128 blocks
@@ -526,7 +651,7 @@ int adj_init(const double* x0, const double* p0, const int32_t* Z, double* y0, d
 int adj_record(const FieldDev& F, const double* y0, const double* kappa, double tol, double hmin,
                double hmax, int n_steps, int K, double* h, double* ck, double* xT, double* uT,
                long long n, void* stream) {
-    k_adj_record<LAYOUT_F64X4><<<chain_blocks(n), kChainBlock, 0, (cudaStream_t)stream>>>(
+    k_adj_record_team<<<team_blocks(n), 32, 0, (cudaStream_t)stream>>>(
         F, y0, kappa, tol, hmin, hmax, n_steps, K, h, ck, xT, uT, n);
     return (int)cudaGetLastError();
 }
@@ -553,7 +678,7 @@ int adj_backward(const FieldDev& F, const double* kappa, const double* h, const 
             F, kappa, h, ck, rec_d, rec_n, n_steps, K, n);
         const int e = (int)cudaGetLastError();
         if (e) return e;
-        k_adj_reverse<<<chain_blocks(n), kChainBlock, 0, (cudaStream_t)stream>>>(
+        k_adj_reverse_team<<<team_blocks(n), 32, 0, (cudaStream_t)stream>>>(
             kappa, h, rec_d, rec_n, n_steps, uT_bar, grid_bar, y0_bar, kappa_bar, n);
         return (int)cudaGetLastError();
     }

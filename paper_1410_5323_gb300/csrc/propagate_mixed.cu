@@ -307,6 +307,18 @@ __device__ __forceinline__ Y deriv_f(const FieldF& F, int bx, int by, int bz, F3
 
 __device__ __forceinline__ float clampf_(float v, float lo, float hi) { return fminf(fmaxf(v, lo), hi); }
 
+// Exact widening of a float to double. Normal values with integer instructions (GB300's FP64
+// unit takes one warp instruction per 64 cycles per sub-partition, and the conversion would
+// be one of them, on the attempt's critical path); zeros, subnormals, infinities and NaN by
+// the conversion.
+__device__ __forceinline__ double widen(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xFFu;
+    if (e == 0u || e == 0xFFu) return (double)f;
+    const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
+    return __hiloint2double((int)hi, (int)(u << 29));
+}
+
 // r2^p for r2 > 0 (controller exponents on the squared ratio).
 __device__ __forceinline__ float powf_pos(float r2, float p) { return exp2f(p * __log2f(r2)); }
 
@@ -514,10 +526,10 @@ __device__ __forceinline__ void propagate_mixed_body(const PropArgs& a, float* s
 #undef SE
             att_step += 1;
             // ---- FP64 error norm and accept/reject ----
-            const double qx = fma((double)ex.z, (double)ex.z,
-                                  fma((double)ex.y, (double)ex.y, (double)ex.x * (double)ex.x));
-            const double qu = fma((double)eu.z, (double)eu.z,
-                                  fma((double)eu.y, (double)eu.y, (double)eu.x * (double)eu.x));
+            const double exx = widen(ex.x), exy = widen(ex.y), exz = widen(ex.z);
+            const double eux = widen(eu.x), euy = widen(eu.y), euz = widen(eu.z);
+            const double qx = fma(exz, exz, fma(exy, exy, exx * exx));
+            const double qu = fma(euz, euz, fma(euy, euy, eux * eux));
             const bool accept = (fmax(qx, qu) <= tol2) || (h <= hmin_c);
             const float r2 = fmaxf(ex.x * ex.x + ex.y * ex.y + ex.z * ex.z,
                                    eu.x * eu.x + eu.y * eu.y + eu.z * eu.z) * inv_tol2;
@@ -574,7 +586,7 @@ __device__ __forceinline__ void propagate_mixed_body(const PropArgs& a, float* s
                 fold(Rz, oz, 2, u.z, ul.z, S.u0z);
             }
             bool done = (h == h_dist);
-            s_c = s_c + (double)h;
+            s_c = s_c + widen(h);
             if (s_c >= dmax_c) done = true;
             if (done) s_c = dmax_c;
             n_steps += 1;
