@@ -78,6 +78,12 @@ def test_kernel_run_counter_counts_every_launch():
     grid = I.kolmogorov_grid(16, 0.25 * I.MPC, 2, 8, 1e-13, 3).astype(np.float32)
     p = I.make_particles(64, 5)
     sim = crp.Simulation([crp.Field(grid, 0.25 * I.MPC)], None, capacity=len(p))
+    nw = crp.kernel_runs()
+    sim.inject(p)
+    sim.propagate(1e-4, I.KPC, I.MPC, 5 * I.MPC, order=api.ORDER_SLOT)
+    sim.sync(60.0)
+    assert crp.kernel_runs() - nw == 2 + 6 + 1      # the first FP64-form call also widens the grid
+    sim.reset()
     n0 = crp.kernel_runs()
     sim.inject(p)
     assert crp.kernel_runs() - n0 == 2
