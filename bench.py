@@ -50,12 +50,14 @@ FLOP_PER_ACCEPTED_TABLES = 10
 FP64_PEAK_TFLOPS = 152 * 2 * 2.070e9 * 2 / 1e12
 FP64_OPS_PEAK_T = 152 * 2 * 2.070e9 / 1e12          # FP64 pipe instructions (T ops/s)
 FP32_PEAK_TFLOPS = 152 * 128 * 2.070e9 * 2 / 1e12   # FFMA lanes x 2
-# Mixed form: FP64 ops that remain per attempt (6 widenings, 2 x (mul + 2 fma), max, compare)
-# and per accepted step (path length add, distance bid, widen h, compare), the FP32 flops
-# per attempt (6 x (lookup 60 + Lorentz 9) + stages 120 + update/error 66 + ratio 12).
-MIXED_FP64_OPS_PER_ATTEMPT = 14
+# Mixed form: FP64 ops that remain per attempt: none outside the accept decision's guard band
+# (the FP32 norms certify the FP64 decision there; inside it, a fraction of order 1e-5 of the
+# attempts, 2 x (mul + 2 fma), max, compare); per accepted step (path length add, distance
+# bid and its conversion, compare, loss factor) 5; the FP32 flops per attempt (6 x (lookup 60
+# + Lorentz 9) + stages 120 + update/error 66 + squared norms and ratio 12, band tests 3).
+MIXED_FP64_OPS_PER_ATTEMPT = 0
 MIXED_FP64_OPS_PER_ACCEPTED = 5
-MIXED_FP32_FLOP_PER_ATTEMPT = 612
+MIXED_FP32_FLOP_PER_ATTEMPT = 615
 # DRAM bytes (read + write) of one lens launch measured by ncu on the current kernels, keyed by
 # the number of maps (the lens summary under profiles/ names the command).
 LENS_DRAM_BYTES = {1: 2.406e8, 32: 5.531e8}

@@ -405,6 +405,8 @@ constexpr int kTeams = 10;
 struct Team {
     unsigned mask;   // the team's lanes
     int l0, c;       // its first lane, this lane's component
+    double oi;       // origin / spacing along axis c (rounded once), grid size along it
+    int nn;
     __device__ __forceinline__ double get(double v, int k) const { return __shfl_sync(mask, v, l0 + k); }
     __device__ __forceinline__ long long get(long long v, int k) const { return __shfl_sync(mask, v, l0 + k); }
     __device__ __forceinline__ int nx1() const { return c == 2 ? 0 : c + 1; }
@@ -415,9 +417,9 @@ struct Team {
 // lookup of field_b, with the axes, the corner weights and the corner loads split over the
 // team. FP64 node copy: component c of node k at ((const double*)data)[4k + c].
 __device__ __forceinline__ double field_team(const FieldDev& F, const Team& T, double xc) {
-    const double oi = T.c == 0 ? F.oix : (T.c == 1 ? F.oiy : F.oiz);
-    const int nn = T.c == 0 ? F.nx : (T.c == 1 ? F.ny : F.nz);
     long long i0, i1;
+    const double oi = T.oi;
+    const int nn = T.nn;
     double w0, w1;
     axis(xc, oi, F.inv_spacing, nn, F.pow2, i0, i1, w0, w1);
     const long long ix0 = T.get(i0, 0), ix1 = T.get(i1, 0), iy0 = T.get(i0, 1), iy1 = T.get(i1, 1);
@@ -459,7 +461,7 @@ __device__ __forceinline__ void deriv_team(const FieldDev& F, const Team& T, dou
     ku = kappa * __fma_rn(u1, B2, -(u2 * B1));
 }
 
-__device__ __forceinline__ Team make_team(long long n, long long& i, bool& active) {
+__device__ __forceinline__ Team make_team(long long n, long long& i, bool& active, const FieldDev* F = nullptr) {
     const int lane = threadIdx.x & 31;
     const int team = lane / 3;
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
@@ -469,6 +471,12 @@ __device__ __forceinline__ Team make_team(long long n, long long& i, bool& activ
     T.l0 = 3 * team;
     T.c = lane - T.l0;
     T.mask = 7u << T.l0;
+    T.oi = 0.0;
+    T.nn = 1;
+    if (F) {
+        T.oi = T.c == 0 ? F->oix : (T.c == 1 ? F->oiy : F->oiz);
+        T.nn = T.c == 0 ? F->nx : (T.c == 1 ? F->ny : F->nz);
+    }
     return T;
 }
 
@@ -481,7 +489,7 @@ __global__ void k_adj_record_team(FieldDev F, const double* __restrict__ y0, con
     CRP_COUNT_RUN();
     long long i;
     bool active;
-    const Team T = make_team(n, i, active);
+    const Team T = make_team(n, i, active, &F);
     if (!active) return;
     const int c = T.c;
     double yx = y0[(long long)c * n + i], yu = y0[(long long)(3 + c) * n + i];
@@ -595,6 +603,12 @@ __global__ void k_adj_reverse_team(const double* __restrict__ kap, const double*
     double lx = 0.0, lu = uT_bar[3 * i + c];
     double kappa_bar = 0.0;
     for (int m = n_steps - 1; m >= 0; --m) {
+        if (m > 0) {   // the previous step's records into L2, a third of the lines per lane
+            const double* d = rec_d + ((long long)(m - 1) * 6 * kRecD) * n + i;
+            for (int k = c; k < 6 * kRecD; k += 3) asm volatile("prefetch.global.L2 [%0];" ::"l"(d + k * n));
+            const int32_t* q = rec_n + ((long long)(m - 1) * 6 * kRecN) * n + i;
+            for (int k = c; k < 6 * kRecN; k += 3) asm volatile("prefetch.global.L2 [%0];" ::"l"(q + k * n));
+        }
         const double hn = h[(long long)m * n + i];
         // stage cotangents kb_s = (h b_s) lam, per component
         const double s0 = hn * cB5h[0], s1 = hn * cB5h[1], s2 = hn * cB5h[2], s3 = hn * cB5h[3],

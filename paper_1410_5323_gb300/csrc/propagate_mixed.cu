@@ -9,9 +9,10 @@
 //     which resolves 1 kpc steps at 500 Mpc without any FP64 instruction; the direction
 //     is a double-float as well (its per-step increment is added with TwoSum), so rounding
 //     does not accumulate in it over thousands of steps;
-//   * the step-error norm and the accept/reject decision stay FP64: the six FP32 error
-//     components are widened and their squared norms compared against tol^2 in FP64
-//     (|dx|/h is computed as |sum_i e_i u_i|, so no division by h is needed);
+//   * the accept/reject decision is the FP64 one: the squared norms of the six FP32 error
+//     components, widened, compared against tol^2 in FP64 (|dx|/h is computed as
+//     |sum_i e_i u_i|, so no division by h is needed); the FP32 norms certify that decision
+//     outside a 2^-18 guard band around tol^2, and only norms inside it are formed in FP64;
 //   * path length s stays FP64 so the observer lands exactly on the distance limit;
 //   * continuous loss and interaction rates in FP32 from FP32 copies of the tables; the
 //     Philox streams and the nucleon rule are the same integers as in the FP64 form;
@@ -333,6 +334,16 @@ __device__ __forceinline__ void propagate_mixed_body(const PropArgs& a, float* s
     const SimState& S = a.st;
     const double tol2 = a.tol * a.tol;
     const float inv_tol2 = (float)(1.0 / tol2);
+    // Guard band of the accept decision: an FP32 squared norm at most tol2_lo (at least
+    // tol2_hi) certifies that the FP64 squared norm is at most (above) tol^2. The FP32 sum of
+    // three non-negative squares is within 2^-22 of the exact sum, the FP64 one within 2^-52,
+    // and the band is 2^-18 wide, so the certified decision is the FP64 decision; only norms
+    // inside the band are formed in FP64.
+    // (For tol^2 outside [2^-100, 2^100] FP32 subnormals or overflow would void the bound:
+    // there every norm is formed in FP64.)
+    const bool band = tol2 >= 0x1p-100 && tol2 <= 0x1p+100;
+    const float tol2_lo = band ? __double2float_rd(tol2 * (1.0 - 0x1p-18)) : -1.0f;
+    const float tol2_hi = band ? __double2float_ru(tol2 * (1.0 + 0x1p-18)) : __int_as_float(0x7fc00000);
 
     int slot = -1;
     // particle state (cell units)
@@ -525,14 +536,23 @@ __device__ __forceinline__ void propagate_mixed_body(const PropArgs& a, float* s
 #undef SB
 #undef SE
             att_step += 1;
-            // ---- FP64 error norm and accept/reject ----
-            const double exx = widen(ex.x), exy = widen(ex.y), exz = widen(ex.z);
-            const double eux = widen(eu.x), euy = widen(eu.y), euz = widen(eu.z);
-            const double qx = fma(exz, exz, fma(exy, exy, exx * exx));
-            const double qu = fma(euz, euz, fma(euy, euy, eux * eux));
-            const bool accept = (fmax(qx, qu) <= tol2) || (h <= hmin_c);
-            const float r2 = fmaxf(ex.x * ex.x + ex.y * ex.y + ex.z * ex.z,
-                                   eu.x * eu.x + eu.y * eu.y + eu.z * eu.z) * inv_tol2;
+            // ---- FP64 error norm and accept/reject (certified from FP32 outside the band) ----
+            const float qx32 = ex.x * ex.x + ex.y * ex.y + ex.z * ex.z;
+            const float qu32 = eu.x * eu.x + eu.y * eu.y + eu.z * eu.z;
+            bool accept;
+            if (qx32 <= tol2_lo && qu32 <= tol2_lo) {
+                accept = true;
+            } else if (qx32 >= tol2_hi || qu32 >= tol2_hi) {
+                accept = false;
+            } else {
+                const double exx = widen(ex.x), exy = widen(ex.y), exz = widen(ex.z);
+                const double eux = widen(eu.x), euy = widen(eu.y), euz = widen(eu.z);
+                const double qx = fma(exz, exz, fma(exy, exy, exx * exx));
+                const double qu = fma(euz, euz, fma(euy, euy, eux * eux));
+                accept = fmax(qx, qu) <= tol2;
+            }
+            accept = accept || (h <= hmin_c);
+            const float r2 = fmaxf(qx32, qu32) * inv_tol2;
             if (!accept) {
                 const float shrink = clampf_(0.95f * powf_pos(r2, -0.125f), 0.1f, 1.0f);
                 h = fmaxf(h * shrink, hmin_c);
