@@ -245,3 +245,39 @@ def test_adjoint_vs_central_differences_in_the_linear_horizon(c5):
             scale = float(torch.linalg.norm(pb[k // 3]))
             errs.append(abs(fd - float(pbf[k])) / scale)
     assert checked >= 28 and max(errs) < 1e-4, ("momentum", checked, errs)
+
+
+@pytest.mark.parametrize("n", [1, 7, 13, 31])
+def test_team_sweeps_with_partial_teams_match_the_oracle(n, oracle_lib):
+    """The forward record and the reverse sweep run three lanes per particle, ten particles
+    per warp: batch sizes that leave a warp partly filled give the oracle's steps, arrival
+    states and per-particle gradients bit for bit, and its grid gradient to rel 1e-10."""
+    import torch
+
+    import paper_1410_5323_gb300 as crp
+    from paper_1410_5323_gb300.adjoint import Adjoint
+
+    g, x0, p0, Z = _case(n, 16, 10 ** 19.2, seed=20 + n)
+    n_steps = 90
+    field = crp.Field(torch.from_numpy(g).cuda(), 0.25 * I.MPC)
+    adj = Adjoint(field, n, n_steps, 16)
+    xT, uT = adj.forward(torch.from_numpy(x0), torch.from_numpy(p0), torch.from_numpy(Z), 1e-4, I.KPC, I.MPC)
+    rng = np.random.default_rng(n)
+    lam = rng.standard_normal((n, 3))
+    gb, pb, xb = adj.backward(torch.from_numpy(lam), g.shape)
+    gb, pb, xb = gb.cpu().numpy(), pb.cpu().numpy(), xb.cpu().numpy()
+    h = adj.steps().cpu().numpy()
+    E, u, kap = _init(p0, Z)
+    of = O.OracleField(g, 0.25 * I.MPC)
+    go = np.zeros(g.shape)
+    for i in range(n):
+        y0 = np.concatenate([x0[i], u[i]])
+        ho, yT = O.record_steps(of, kap[i], y0, 1e-4, I.KPC, I.MPC, n_steps)
+        assert np.array_equal(h[:, i], ho), i
+        assert np.array_equal(xT[i].cpu().numpy(), yT[:3]) and np.array_equal(uT[i].cpu().numpy(), yT[3:])
+        yb, kb = O.adjoint(of, kap[i], y0, ho, np.concatenate([np.zeros(3), lam[i]]), go)
+        assert np.array_equal(xb[i], yb[:3]), i
+        dot = (u[i, 0] * yb[3] + u[i, 1] * yb[4]) + u[i, 2] * yb[5]
+        assert np.array_equal(pb[i], (yb[3:] - dot * u[i]) / E[i] + (-(kb * kap[i]) / E[i]) * u[i]), i
+    assert np.allclose(gb, go, rtol=1e-10, atol=1e-12 * np.abs(go).max())
+    assert np.array_equal(gb == 0, go == 0)
