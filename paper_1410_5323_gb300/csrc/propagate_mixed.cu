@@ -90,6 +90,10 @@ struct MF { F3 f0; float q; int lo; };
 
 constexpr int kModNodes = 27;            // cached node values per lane
 constexpr int kModSlots = kModNodes + 3; // + the step-start cell (wrapped) per axis
+// Per-thread shared-memory slots of the current particle's field constants in cell units
+// (kept out of registers: they are read once per step, not per attempt): 6 doubles (spacing,
+// 1/spacing, origin x/y/z, distance limit) then 3 floats (step limit, spacing, c x spacing).
+constexpr int kFieldWords = 6 * 2 + 4;
 
 
 template <int L>
@@ -163,8 +167,13 @@ __device__ __forceinline__ int wrap_near(int i, int n, int pow2) {
     return ((unsigned)i < (unsigned)n) ? i : wrap(i, n, pow2);
 }
 
-// Shared-memory slot k of this lane (column-major by lane: a warp's accesses hit 32 banks).
-__device__ __forceinline__ float& mslot(float* sm, int k) { return sm[k * blockDim.x + threadIdx.x]; }
+// Shared-memory slot k of this lane (column-major by lane: a warp's accesses hit 32 banks);
+// the modulation slots follow the field constants.
+__device__ __forceinline__ float& mslot(float* sm, int k) { return sm[(kFieldWords + k) * blockDim.x + threadIdx.x]; }
+__device__ __forceinline__ double& dslot(float* sm, int k) {
+    return reinterpret_cast<double*>(sm)[k * blockDim.x + threadIdx.x];
+}
+__device__ __forceinline__ float& fslot(float* sm, int k) { return sm[(12 + k) * blockDim.x + threadIdx.x]; }
 
 // Trilinear weights and the corner sum, in the same order for the cached and gathered paths.
 __device__ __forceinline__ float trilerp(float fx, float fy, float fz, float m0, float m1, float m2,
@@ -353,12 +362,10 @@ __device__ __forceinline__ void propagate_mixed_body(const PropArgs& a, float* s
     double E = 0, s_c = 0;
     float hprop = 0, tau = 0;
     int A = 0, Z = 0, n_int = 0, gid = 0;
-    unsigned long long uid = 0;
-    long long n_steps = 0, n_att = 0, taken = 0;
-    // field of the current particle
+    int taken = 0, att_call = 0;       // accepted steps and attempts of this call
+    // field of the current particle (its other constants in shared slots)
     FieldF F{};
-    double sp = 1.0, inv_sp = 1.0, ox = 0, oy = 0, oz = 0, dmax_c = 0;
-    float hmin_c = 0, hmax_c = 0, sp_f = 1.0f, csp_f = 1.0f;
+    float hmin_c = 0;
     // step state
     bool new_step = true;
     int bx = 0, by = 0, bz = 0;
@@ -366,26 +373,27 @@ __device__ __forceinline__ void propagate_mixed_body(const PropArgs& a, float* s
     MF mf{{0, 0, 0}, 1.0f, 0};
     float h = 0, h_first = 0, h_propc = 0, h_int = 0, h_dist = 0, rl = 0, rpd = 0, kappa = 0;
     int rejected = 0;
-    long long att_step = 0;
-    unsigned long long acc_tot = 0, att_tot = 0, sec_tot = 0;
+    int att_step = 0;
+    unsigned acc_tot = 0, att_tot = 0, sec_tot = 0;
     unsigned bits = 0;
 
-    auto to_x = [&](DF r, double o) { return o + ((double)r.hi + (double)r.lo) * sp; };
+    auto to_x = [&](DF r, double o) { return o + ((double)r.hi + (double)r.lo) * dslot(sm, 0); };
     auto from_x = [&](double x, double o) {
-        const double rr = (x - o) * inv_sp;
+        const double rr = (x - o) * dslot(sm, 1);
         const float hi = (float)rr;
         return DF{hi, (float)(rr - (double)hi)};
     };
     auto store = [&](int status, bool exact_end) {
-        S.x[slot] = to_x(Rx, ox); S.y[slot] = to_x(Ry, oy); S.z[slot] = to_x(Rz, oz);
+        S.x[slot] = to_x(Rx, dslot(sm, 2)); S.y[slot] = to_x(Ry, dslot(sm, 3)); S.z[slot] = to_x(Rz, dslot(sm, 4));
         S.ux[slot] = (double)u.x + (double)ul.x; S.uy[slot] = (double)u.y + (double)ul.y;
         S.uz[slot] = (double)u.z + (double)ul.z;
         S.E[slot] = E;
-        S.s[slot] = exact_end ? a.dmax : s_c * sp;
-        S.hprop[slot] = (double)hprop * sp;
+        S.s[slot] = exact_end ? a.dmax : s_c * dslot(sm, 0);
+        S.hprop[slot] = (double)hprop * dslot(sm, 0);
         S.tau[slot] = tau;
         S.A[slot] = A; S.Z[slot] = Z; S.n_int[slot] = n_int; S.status[slot] = status;
-        S.n_steps[slot] = n_steps; S.n_att[slot] = n_att;
+        S.n_steps[slot] = __ldcg(&S.n_steps[slot]) + taken;
+        S.n_att[slot] = __ldcg(&S.n_att[slot]) + att_call;
         if (status != CRP_STATUS_ACTIVE_) {
             const unsigned long long d = atomicAdd(&C->n_done, 1ull);
             a.done_list[d] = slot;
@@ -406,12 +414,15 @@ __device__ __forceinline__ void propagate_mixed_body(const PropArgs& a, float* s
             F.data = G.data; F.nx = G.nx; F.ny = G.ny; F.nz = G.nz; F.pow2 = G.pow2;
             F.scale = (float)G.scale;
             if constexpr (M) mf.q = (float)(G.spacing * G.m_inv_spacing);
-            sp = G.spacing; inv_sp = G.inv_spacing; sp_f = (float)sp; csp_f = (float)(kC * sp);
-            ox = G.ox; oy = G.oy; oz = G.oz;
+            const double sp = G.spacing, inv_sp = G.inv_spacing;
+            dslot(sm, 0) = sp; dslot(sm, 1) = inv_sp;
+            dslot(sm, 2) = G.ox; dslot(sm, 3) = G.oy; dslot(sm, 4) = G.oz;
+            dslot(sm, 5) = a.dmax * inv_sp;
+            fslot(sm, 0) = (float)(a.hmax * inv_sp);
+            fslot(sm, 1) = (float)sp;
+            fslot(sm, 2) = (float)(kC * sp);
             hmin_c = (float)(a.hmin * inv_sp);
-            hmax_c = (float)(a.hmax * inv_sp);
-            dmax_c = a.dmax * inv_sp;
-            Rx = from_x(__ldcg(&S.x[slot]), ox); Ry = from_x(__ldcg(&S.y[slot]), oy); Rz = from_x(__ldcg(&S.z[slot]), oz);
+            Rx = from_x(__ldcg(&S.x[slot]), G.ox); Ry = from_x(__ldcg(&S.y[slot]), G.oy); Rz = from_x(__ldcg(&S.z[slot]), G.oz);
             {
                 const double dx = __ldcg(&S.ux[slot]), dy = __ldcg(&S.uy[slot]), dz = __ldcg(&S.uz[slot]);
                 u = {(float)dx, (float)dy, (float)dz};
@@ -422,9 +433,8 @@ __device__ __forceinline__ void propagate_mixed_body(const PropArgs& a, float* s
             hprop = (float)(__ldcg(&S.hprop[slot]) * inv_sp);
             tau = (float)__ldcg(&S.tau[slot]);
             A = __ldcg(&S.A[slot]); Z = __ldcg(&S.Z[slot]); n_int = __ldcg(&S.n_int[slot]);
-            uid = (unsigned long long)__ldcg(&S.uid[slot]);
-            n_steps = __ldcg(&S.n_steps[slot]); n_att = __ldcg(&S.n_att[slot]);
             taken = 0;
+            att_call = 0;
             new_step = true;
         }
         if (__ballot_sync(kFull, slot >= 0) == 0) break;
@@ -453,18 +463,18 @@ __device__ __forceinline__ void propagate_mixed_body(const PropArgs& a, float* s
                     if (T.has_loss[sp_i]) {
                         const float* R = T.loss_f + (long long)sp_i * T.n_nodes;
                         const float v0 = __ldg(R + j), v1 = __ldg(R + j + 1);
-                        rl = exp10f(fmaf(fr, v1 - v0, v0)) * sp_f;
+                        rl = exp10f(fmaf(fr, v1 - v0, v0)) * fslot(sm, 1);
                     }
                     if (T.has_pd[sp_i]) {
                         const float* R = T.pd_f + (long long)sp_i * T.n_nodes;
                         const float v0 = __ldg(R + j), v1 = __ldg(R + j + 1);
-                        rpd = exp10f(fmaf(fr, v1 - v0, v0)) * sp_f;
+                        rpd = exp10f(fmaf(fr, v1 - v0, v0)) * fslot(sm, 1);
                     }
                 }
-                h_propc = clampf_(hprop, hmin_c, hmax_c);
+                h_propc = clampf_(hprop, hmin_c, fslot(sm, 0));
                 const float h_loss = rl > 0.0f ? 0.1f / rl : INF;
                 h_int = rpd > 0.0f ? fmaxf(tau, 0.0f) / rpd : INF;
-                h_dist = (float)(dmax_c - s_c);
+                h_dist = (float)(dslot(sm, 5) - s_c);
                 h = h_propc;
                 if (h_loss < h) h = h_loss;
                 if (h_int < h) h = h_int;
@@ -472,7 +482,7 @@ __device__ __forceinline__ void propagate_mixed_body(const PropArgs& a, float* s
                 h_first = h;
                 rejected = 0;
                 att_step = 0;
-                kappa = (float)Z * csp_f / (float)E;
+                kappa = (float)Z * fslot(sm, 2) / (float)E;
                 df_floor(Rx, bx, f0.x);
                 df_floor(Ry, by, f0.y);
                 df_floor(Rz, bz, f0.z);
@@ -490,9 +500,9 @@ __device__ __forceinline__ void propagate_mixed_body(const PropArgs& a, float* s
                         f = (float)(rm - fl);
                     };
                     int mbx, mby, mbz;
-                    mcell(Rx, ox, G.mox, G.mnx, mbx, mf.f0.x);
-                    mcell(Ry, oy, G.moy, G.mny, mby, mf.f0.y);
-                    mcell(Rz, oz, G.moz, G.mnz, mbz, mf.f0.z);
+                    mcell(Rx, dslot(sm, 2), G.mox, G.mnx, mbx, mf.f0.x);
+                    mcell(Ry, dslot(sm, 3), G.moy, G.mny, mby, mf.f0.y);
+                    mcell(Rz, dslot(sm, 4), G.moz, G.mnz, mbz, mf.f0.z);
                     mf.lo = (u.x < 0.0f ? 1 : 0) | (u.y < 0.0f ? 2 : 0) | (u.z < 0.0f ? 4 : 0);
                     mod_fill(sm, G, mbx, mby, mbz, mf.lo);
                 }
@@ -560,7 +570,7 @@ __device__ __forceinline__ void propagate_mixed_body(const PropArgs& a, float* s
                 continue;
             }
             if (!(fin3(dp) && fin3(du))) {
-                n_att += att_step;
+                att_call += att_step;
                 att_tot += att_step;
                 bits |= BIT_NAN;
                 store(CRP_STATUS_NAN_, false);
@@ -577,7 +587,7 @@ __device__ __forceinline__ void propagate_mixed_body(const PropArgs& a, float* s
                 }
             }
             // ---- accept ----
-            n_att += att_step;
+            att_call += att_step;
             att_tot += att_step;
             Rx = df_add(Rx, dp.x);
             Ry = df_add(Ry, dp.y);
@@ -601,35 +611,35 @@ __device__ __forceinline__ void propagate_mixed_body(const PropArgs& a, float* s
                     R = from_x(xd, o);
                     if (odd) { uc = -uc; ucl = -ucl; u0col[slot] = -u0col[slot]; }
                 };
-                fold(Rx, ox, 0, u.x, ul.x, S.u0x);
-                fold(Ry, oy, 1, u.y, ul.y, S.u0y);
-                fold(Rz, oz, 2, u.z, ul.z, S.u0z);
+                fold(Rx, dslot(sm, 2), 0, u.x, ul.x, S.u0x);
+                fold(Ry, dslot(sm, 3), 1, u.y, ul.y, S.u0y);
+                fold(Rz, dslot(sm, 4), 2, u.z, ul.z, S.u0z);
             }
             bool done = (h == h_dist);
             s_c = s_c + widen(h);
-            if (s_c >= dmax_c) done = true;
-            if (done) s_c = dmax_c;
-            n_steps += 1;
+            if (s_c >= dslot(sm, 5)) done = true;
+            if (done) s_c = dslot(sm, 5);
             acc_tot += 1;
             taken += 1;
             const float grow = (r2 == 0.0f) ? 5.0f : clampf_(0.95f * powf_pos(r2, -0.1f), 0.2f, 5.0f);
             float hnext = h * grow;
             if (!rejected && h_first < h_propc) hnext = fmaxf(hnext, h_propc);
-            hprop = clampf_(hnext, hmin_c, hmax_c);
+            hprop = clampf_(hnext, hmin_c, fslot(sm, 0));
             if (rl > 0.0f) E = E * (double)__expf(-h * rl);
             if (rpd > 0.0f) {
                 if (fires) {
                     const unsigned kk = (unsigned)(n_int + 1);
+                    const unsigned long long uid = (unsigned long long)__ldcg(&S.uid[slot]);
                     const int dz = nucleon_proton(a.seed, uid, kk, A, Z) ? 1 : 0;
                     const double E_sec = E / (double)A;
                     const double E_par = E * (double)(A - 1) / (double)A;
                     const long long qs = (long long)q;
                     const unsigned long long uid2 = (1ull << 32) + uid * 64ull + kk;
-                    S.x[qs] = to_x(Rx, ox); S.y[qs] = to_x(Ry, oy); S.z[qs] = to_x(Rz, oz);
+                    S.x[qs] = to_x(Rx, dslot(sm, 2)); S.y[qs] = to_x(Ry, dslot(sm, 3)); S.z[qs] = to_x(Rz, dslot(sm, 4));
                     S.ux[qs] = (double)u.x + (double)ul.x; S.uy[qs] = (double)u.y + (double)ul.y;
                     S.uz[qs] = (double)u.z + (double)ul.z;
                     S.E[qs] = E_sec;
-                    S.s[qs] = done ? a.dmax : s_c * sp;
+                    S.s[qs] = done ? a.dmax : s_c * dslot(sm, 0);
                     S.hprop[qs] = __longlong_as_double(0x7ff0000000000000LL);
                     S.tau[qs] = -crp_log(uniform01(a.seed, uid2, 0u, 0u));
                     S.u0x[qs] = S.u0x[slot]; S.u0y[qs] = S.u0y[slot]; S.u0z[qs] = S.u0z[slot];
@@ -677,11 +687,14 @@ __device__ __forceinline__ void propagate_mixed_body(const PropArgs& a, float* s
     }
 }
 
-// Register caps (more resident warps to hide gather latency); build-time tuning knobs.
+// Register caps (more resident warps to hide gather latency); build-time tuning knobs. By
+// default the unmodulated kernel is bounded to 128 registers (16 warps per SM with 128-thread
+// blocks): with the field constants in shared slots and 32-bit per-call counters its state fits
+// (the BF16 cell layout without spills), and the latency-bound lookups gain from the extra warps.
 #ifdef CRP_MIXED_MAXNREG
 #define CRP_MIXED_BOUNDS __maxnreg__(CRP_MIXED_MAXNREG)
 #else
-#define CRP_MIXED_BOUNDS __launch_bounds__(256)
+#define CRP_MIXED_BOUNDS __launch_bounds__(256, 2)
 #endif
 #ifdef CRP_MIXED_MOD_MAXNREG
 #define CRP_MIXED_MOD_BOUNDS __maxnreg__(CRP_MIXED_MOD_MAXNREG)
@@ -689,18 +702,20 @@ __device__ __forceinline__ void propagate_mixed_body(const PropArgs& a, float* s
 #define CRP_MIXED_MOD_BOUNDS __launch_bounds__(256)
 #endif
 
+// Dynamic shared memory: kFieldWords words per thread (field constants), + kModSlots floats per
+// thread for modulated fields.
 template <int L>
 __global__ void CRP_MIXED_BOUNDS k_propagate_mixed(const PropArgs a) {
     CRP_COUNT_RUN();
-    propagate_mixed_body<L, false>(a, nullptr);
+    extern __shared__ double field_sm[];
+    propagate_mixed_body<L, false>(a, reinterpret_cast<float*>(field_sm));
 }
 
-// Modulated fields; dynamic shared memory: kModSlots floats per thread.
 template <int L>
 __global__ void CRP_MIXED_MOD_BOUNDS k_propagate_mixed_mod(const PropArgs a) {
     CRP_COUNT_RUN();
-    extern __shared__ float mod_sm[];
-    propagate_mixed_body<L, true>(a, mod_sm);
+    extern __shared__ double mod_sm[];
+    propagate_mixed_body<L, true>(a, reinterpret_cast<float*>(mod_sm));
 }
 
 }  // namespace
@@ -721,7 +736,7 @@ int with_mixed_kernel(int layout, int mod, Fn&& fn) {
     }
 }
 
-size_t mixed_smem(int mod, int block) { return mod ? (size_t)kModSlots * sizeof(float) * block : 0; }
+size_t mixed_smem(int mod, int block) { return (size_t)(kFieldWords + (mod ? kModSlots : 0)) * sizeof(float) * block; }
 
 int launch_propagate_mixed(const PropArgs& a, int layout, int mod, int grid, int block, void* stream) {
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
