@@ -562,31 +562,46 @@ __global__ void k_adj_record_team(FieldDev F, const double* __restrict__ y0, con
 // Per stage: Bbar_c = kappa (bbar_{c+1} u_{c+2} - bbar_{c+2} u_{c+1}); kappa_bar += ((p0 + p1) + p2)
 // with p_k = bbar_k (u x B)_k; Ybar_u_c = abar_c + kappa (B_{c+1} bbar_{c+2} - B_{c+2} bbar_{c+1});
 // Ybar_x_c = (J[0][c] Bbar_0 + J[1][c] Bbar_1) + J[2][c] Bbar_2; lane c scatters w_k Bbar_c.
-__device__ __forceinline__ void vjp_rec_team(const double* __restrict__ rec_d, const int32_t* __restrict__ rec_n,
-                                             long long n, long long i, int m, int st, double kappa,
-                                             const Team& T, double kbx, double kbu, double& Ybx, double& Ybu,
-                                             double* __restrict__ grid_bar, double& kappa_bar) {
+// One stage's record, the part lane c applies: u_{c+1}, u_{c+2}, B_{c+1}, B_{c+2}, column c of J,
+// the corner weights and nodes. Loaded one stage ahead of its use (the sweep runs one warp per
+// sub-partition, so registers do not limit occupancy here).
+struct RecT {
+    double u1, u2, B1, B2, J0, J1, J2, w[8];
+    int32_t node[8];
+};
+
+__device__ __forceinline__ RecT load_rec_team(const double* __restrict__ rec_d, const int32_t* __restrict__ rec_n,
+                                              long long n, long long i, int m, int st, const Team& T) {
     const int c = T.c, c1 = T.nx1(), c2 = T.nx2();
     const double* d = rec_d + ((long long)(m * 6 + st) * kRecD) * n + i;
     const int32_t* q = rec_n + ((long long)(m * 6 + st) * kRecN) * n + i;
-    const double u1 = __ldcs(d + c1 * n), u2 = __ldcs(d + c2 * n);
-    const double B1 = __ldcs(d + (3 + c1) * n), B2 = __ldcs(d + (3 + c2) * n);
-    const double J0 = __ldcs(d + (6 + c) * n), J1 = __ldcs(d + (9 + c) * n), J2 = __ldcs(d + (12 + c) * n);
-    const double bb1 = T.get(kbu, c1), bb2 = T.get(kbu, c2);
-    const double Bb = kappa * (bb1 * u2 - bb2 * u1);
-    const double uxB = u1 * B2 - u2 * B1;
+    RecT r;
+    r.u1 = __ldcs(d + c1 * n); r.u2 = __ldcs(d + c2 * n);
+    r.B1 = __ldcs(d + (3 + c1) * n); r.B2 = __ldcs(d + (3 + c2) * n);
+    r.J0 = __ldcs(d + (6 + c) * n); r.J1 = __ldcs(d + (9 + c) * n); r.J2 = __ldcs(d + (12 + c) * n);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        r.w[k] = __ldcs(d + (15 + k) * n);
+        r.node[k] = __ldcs(q + k * n);
+    }
+    return r;
+}
+
+__device__ __forceinline__ void vjp_rec_team(const RecT& r, double kappa, const Team& T, double kbx, double kbu,
+                                             double& Ybx, double& Ybu, double* __restrict__ grid_bar,
+                                             double& kappa_bar) {
+    const int c = T.c;
+    const double bb1 = T.get(kbu, T.nx1()), bb2 = T.get(kbu, T.nx2());
+    const double Bb = kappa * (bb1 * r.u2 - bb2 * r.u1);
+    const double uxB = r.u1 * r.B2 - r.u2 * r.B1;
     const double p = kbu * uxB;
     const double p0 = T.get(p, 0), p1 = T.get(p, 1), p2 = T.get(p, 2);
     kappa_bar = kappa_bar + ((p0 + p1) + p2);
-    Ybu = kbx + kappa * (B1 * bb2 - B2 * bb1);
+    Ybu = kbx + kappa * (r.B1 * bb2 - r.B2 * bb1);
     const double Bb0 = T.get(Bb, 0), Bb1 = T.get(Bb, 1), Bb2 = T.get(Bb, 2);
-    Ybx = (J0 * Bb0 + J1 * Bb1) + J2 * Bb2;
+    Ybx = (r.J0 * Bb0 + r.J1 * Bb1) + r.J2 * Bb2;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        const double w = __ldcs(d + (15 + k) * n);
-        const long long node = __ldcs(q + k * n);
-        atomicAdd(grid_bar + node * 3 + c, w * Bb);
-    }
+    for (int k = 0; k < 8; ++k) atomicAdd(grid_bar + (long long)r.node[k] * 3 + c, r.w[k] * Bb);
 }
 
 __global__ void k_adj_reverse_team(const double* __restrict__ kap, const double* __restrict__ h,
@@ -617,23 +632,30 @@ __global__ void k_adj_reverse_team(const double* __restrict__ kap, const double*
         double k3x = s3 * lx, k3u = s3 * lu, k4x = s4 * lx, k4u = s4 * lu;
         const double k5x = s5 * lx, k5u = s5 * lu;
         double ybx = lx, ybu = lu, Yx, Yu;
+        // each stage's record is loaded before the previous stage is applied
+        RecT cur = load_rec_team(rec_d, rec_n, n, i, m, 5, T), nxt;
 #define AX(kx, ku, a) do { const double ha = hn * (a); kx = kx + ha * Yx; ku = ku + ha * Yu; } while (0)
-        vjp_rec_team(rec_d, rec_n, n, i, m, 5, kappa, T, k5x, k5u, Yx, Yu, grid_bar, kappa_bar);
+        nxt = load_rec_team(rec_d, rec_n, n, i, m, 4, T);
+        vjp_rec_team(cur, kappa, T, k5x, k5u, Yx, Yu, grid_bar, kappa_bar);
         ybx = ybx + Yx; ybu = ybu + Yu;
         AX(k0x, k0u, A61); AX(k1x, k1u, A62); AX(k2x, k2u, A63); AX(k3x, k3u, A64); AX(k4x, k4u, A65);
-        vjp_rec_team(rec_d, rec_n, n, i, m, 4, kappa, T, k4x, k4u, Yx, Yu, grid_bar, kappa_bar);
+        cur = load_rec_team(rec_d, rec_n, n, i, m, 3, T);
+        vjp_rec_team(nxt, kappa, T, k4x, k4u, Yx, Yu, grid_bar, kappa_bar);
         ybx = ybx + Yx; ybu = ybu + Yu;
         AX(k0x, k0u, A51); AX(k1x, k1u, A52); AX(k2x, k2u, A53); AX(k3x, k3u, A54);
-        vjp_rec_team(rec_d, rec_n, n, i, m, 3, kappa, T, k3x, k3u, Yx, Yu, grid_bar, kappa_bar);
+        nxt = load_rec_team(rec_d, rec_n, n, i, m, 2, T);
+        vjp_rec_team(cur, kappa, T, k3x, k3u, Yx, Yu, grid_bar, kappa_bar);
         ybx = ybx + Yx; ybu = ybu + Yu;
         AX(k0x, k0u, A41); AX(k1x, k1u, A42); AX(k2x, k2u, A43);
-        vjp_rec_team(rec_d, rec_n, n, i, m, 2, kappa, T, k2x, k2u, Yx, Yu, grid_bar, kappa_bar);
+        cur = load_rec_team(rec_d, rec_n, n, i, m, 1, T);
+        vjp_rec_team(nxt, kappa, T, k2x, k2u, Yx, Yu, grid_bar, kappa_bar);
         ybx = ybx + Yx; ybu = ybu + Yu;
         AX(k0x, k0u, A31); AX(k1x, k1u, A32);
-        vjp_rec_team(rec_d, rec_n, n, i, m, 1, kappa, T, k1x, k1u, Yx, Yu, grid_bar, kappa_bar);
+        nxt = load_rec_team(rec_d, rec_n, n, i, m, 0, T);
+        vjp_rec_team(cur, kappa, T, k1x, k1u, Yx, Yu, grid_bar, kappa_bar);
         ybx = ybx + Yx; ybu = ybu + Yu;
         AX(k0x, k0u, A21);
-        vjp_rec_team(rec_d, rec_n, n, i, m, 0, kappa, T, k0x, k0u, Yx, Yu, grid_bar, kappa_bar);
+        vjp_rec_team(nxt, kappa, T, k0x, k0u, Yx, Yu, grid_bar, kappa_bar);
         ybx = ybx + Yx; ybu = ybu + Yu;
 #undef AX
         lx = ybx;
