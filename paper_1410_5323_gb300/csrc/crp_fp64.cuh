@@ -56,11 +56,7 @@ __device__ __forceinline__ V3 corner(const FieldDev& F, long long node) {
 // (GB300 rounds and converts FP64 values on its FP64 pipe, which the lookups' arithmetic
 // already saturates). Exact for |r| < 2^63, where it equals floor() and its conversion;
 // beyond that, and for infinities and NaN, i = 0 and fl = r (any index is wrapped into the
-// grid afterwards). Every range's result is formed and the right one selected, without
-// branches, so the lanes of a warp (or the axes of a team) never diverge here:
-//   |r| < 1:            floor is 0, -0 or -1;
-//   1 <= |r| < 2^52:    fb fraction bits; n = |trunc r|; floor = n, -n or -(n + 1);
-//   2^52 <= |r| < 2^63: r is integral.
+// grid afterwards).
 __device__ __forceinline__ void floor_split(double r, long long& i, double& fl) {
     constexpr long long kSign = (long long)0x8000000000000000ull;
     constexpr long long kMant = 0xFFFFFFFFFFFFFll;
@@ -68,24 +64,34 @@ __device__ __forceinline__ void floor_split(double r, long long& i, double& fl) 
     const int ef = (int)((b >> 52) & 0x7FF);
     const bool neg = b < 0;
     const long long mag = b & ~kSign;
-    const unsigned long long m = (unsigned long long)((mag & kMant) | (kMant + 1));
-    const int fb = min(max(1075 - ef, 1), 63);
-    const unsigned long long fm = (1ull << fb) - 1ull;
-    const long long n = (long long)(m >> fb);
-    const bool has_frac = ((unsigned long long)mag & fm) != 0ull;
-    const long long k = n + 1;                                   // 1 <= k <= 2^52
-    const int p = 63 - __clzll(k);
-    const long long negk = kSign | ((long long)(1023 + p) << 52) |
-                           ((long long)((unsigned long long)k << max(52 - p, 0)) & kMant);
-    const long long big = (long long)(m << min(max(ef - 1075, 0), 63));
-    const long long nbig = (long long)(0ull - (unsigned long long)big);
-    const long long i_gen = neg ? (has_frac ? -k : -n) : n;
-    const long long fl_gen = neg ? (has_frac ? negk : b) : (long long)((unsigned long long)b & ~fm);
-    const bool m1 = neg && mag != 0;
-    const long long i_small = m1 ? -1 : 0;
-    const long long fl_small = m1 ? (long long)0xBFF0000000000000ull : (b & kSign);
-    i = ef < 1023 ? i_small : (ef < 1075 ? i_gen : (ef < 1086 ? (neg ? nbig : big) : 0));
-    fl = __longlong_as_double(ef < 1023 ? fl_small : (ef < 1075 ? fl_gen : b));
+    if (ef < 1023) {                                   // |r| < 1: floor is 0, -0 or -1
+        const bool m1 = neg && mag != 0;
+        i = m1 ? -1 : 0;
+        fl = __longlong_as_double(m1 ? (long long)0xBFF0000000000000ull : (b & kSign));
+    } else if (ef < 1075) {                            // 1 <= |r| < 2^52: fb fraction bits
+        const int fb = 1075 - ef;
+        const long long fm = (1ll << fb) - 1;
+        const long long n = ((mag & kMant) | (kMant + 1)) >> fb;       // |trunc r|
+        if (!neg) {
+            i = n;
+            fl = __longlong_as_double(b & ~fm);
+        } else if ((mag & fm) == 0) {
+            i = -n;
+            fl = r;
+        } else {                                       // floor = -(n + 1), n + 1 <= 2^52
+            const long long k = n + 1;
+            const int p = 63 - __clzll(k);
+            i = -k;
+            fl = __longlong_as_double(kSign | ((long long)(1023 + p) << 52) | ((k << (52 - p)) & kMant));
+        }
+    } else if (ef < 1086) {                            // 2^52 <= |r| < 2^63: integral
+        const long long n = ((mag & kMant) | (kMant + 1)) << (ef - 1075);
+        i = neg ? -n : n;
+        fl = r;
+    } else {
+        i = 0;
+        fl = r;
+    }
 }
 
 // One axis of the periodic lookup: r = x (1/spacing) - o (1/spacing) with one rounding (oi is
