@@ -217,7 +217,7 @@ typedef struct {
     int32_t form;            /* CRP_FORM_FP64 or CRP_FORM_MIXED */
     int32_t block_size;      /* threads per block, multiple of 32; 0: default */
     int32_t blocks_per_sm;   /* 0: the occupancy limit */
-    int32_t cadence;         /* attempts between refill checks; 0: default (1) */
+    int32_t cadence;         /* attempts between refill checks; 0: default (2 in the precision form, 1 in FP64) */
     int64_t max_steps;       /* accepted steps per particle per call; <= 0: no limit */
     int32_t order;           /* work-list order: CRP_ORDER_* (0: default = CRP_ORDER_COST) */
     int32_t pickup;          /* secondaries created in a launch: CRP_PICKUP_* (0: default = OFF) */
