@@ -496,9 +496,13 @@ def precision_error_by_distance(crp, w, fields, tabs, parts, idx,
     out = {"sample_primaries": len(sub), "reference": "FP64 form on the GPU (bit-identical to the FP64 oracle)",
            "distances_mpc": [d for d in distances_mpc if d * I.MPC <= w.dmax_m],
            "median_deg": [], "p95_deg": [], "max_deg": [], "chaos_floor_median_deg": [],
-           "chaos_floor_p95_deg": []}
+           "chaos_floor_p95_deg": [],
+           # both forms against a finer FP64 reference (tolerance / 10): how far each is from the
+           # trajectory the method converges to, at the workload's tolerance
+           "fine_reference": "FP64 form at tolerance / 10", "fp64_vs_fine_p95_deg": [],
+           "precision_vs_fine_p95_deg": [], "fp64_vs_fine_median_deg": [], "precision_vs_fine_median_deg": []}
 
-    def final_u(p, form, dmax):
+    def final_u(p, form, dmax, tol=None):
         sim = crp.Simulation(fields, tabs, seed=w.rng_seed, capacity=capacity_for(p))
         if box is not None:
             sim.set_boundary(box)
@@ -506,7 +510,7 @@ def precision_error_by_distance(crp, w, fields, tabs, parts, idx,
             sim.sample_sources(crp.Spectrum.of(*w.spectrum), p.x)
         else:
             sim.inject(p)
-        sim.propagate(w.tol, w.hmin_m, w.hmax_m, dmax, form=form)
+        sim.propagate(w.tol if tol is None else tol, w.hmin_m, w.hmax_m, dmax, form=form)
         sim.sync(timeout_s=600.0, raise_on_error=False)
         d = sim.state()
         prim = d["uid"] < 2 ** 32
@@ -519,6 +523,12 @@ def precision_error_by_distance(crp, w, fields, tabs, parts, idx,
         floor_ = final_u(bumped, crp.FORM_FP64, dist * I.MPC) if w.spectrum is None else ref
         e = angle_deg(ref, mix)
         f = angle_deg(ref, floor_)
+        fine = final_u(sub, crp.FORM_FP64, dist * I.MPC, tol=w.tol / 10.0)
+        ef, em = angle_deg(fine, ref), angle_deg(fine, mix)
+        out["fp64_vs_fine_p95_deg"].append(float(np.quantile(ef, 0.95)))
+        out["precision_vs_fine_p95_deg"].append(float(np.quantile(em, 0.95)))
+        out["fp64_vs_fine_median_deg"].append(float(np.median(ef)))
+        out["precision_vs_fine_median_deg"].append(float(np.median(em)))
         out["median_deg"].append(float(np.median(e)))
         out["p95_deg"].append(float(np.quantile(e, 0.95)))
         out["max_deg"].append(float(e.max()))
