@@ -990,9 +990,11 @@ def run_adjoint(args):
     }
     for tt in terms.values():
         tt["frac"] = tt["achieved"] / tt["peak"]
-    roof = roofline_from_terms(terms, None, "k_adj_record + k_adj_stages + k_adj_reverse (+ init, p0-bar)",
-                               note=f"{n} independent chains: one lane per chain in the record and "
-                                    "reverse sweeps")
+    roof = roofline_from_terms(terms, None,
+                               "k_adj_record_team + k_adj_records + k_adj_reverse_team (+ init, p0-bar)",
+                               note=f"{n} independent chains: three lanes per chain (one per axis) in the "
+                                    "serial record and reverse sweeps, one thread per (chain, segment) "
+                                    "in the stage records")
 
     # ---- end to end: inputs from pinned host memory, gradients back ----
     hx0 = torch.from_numpy(p.x).pin_memory()

@@ -480,8 +480,8 @@ __device__ __forceinline__ Team make_team(long long n, long long& i, bool& activ
     return T;
 }
 
-// Forward with the propagation module's controller only, in team form; records h_n and
-// checkpoints (the same values as k_adj_record).
+// Forward with the propagation module's controller only, in team form; records h_n and the
+// checkpoints of every K-th step (the oracle's frozen forward, value for value).
 __global__ void k_adj_record_team(FieldDev F, const double* __restrict__ y0, const double* __restrict__ kap,
                                   double tol, double hmin, double hmax, int n_steps, int K,
                                   double* __restrict__ h_out, double* __restrict__ ck,
@@ -496,54 +496,60 @@ __global__ void k_adj_record_team(FieldDev F, const double* __restrict__ y0, con
     const double kappa = kap[i];
     const double tol2 = tol * tol;
     const float lg_tol = ctrl_log2(tol);
+    // one attempt per iteration: teams that retry a step and teams that start one run the
+    // attempt together (a rejection in one team does not make the warp repeat it for the rest)
     double hprop = __longlong_as_double(0x7ff0000000000000LL);
-    for (int m = 0; m < n_steps; ++m) {
-        if (m % K == 0) {
-            double* q = ck + (long long)(m / K) * 6 * n;
-            q[(long long)c * n + i] = yx;
-            q[(long long)(3 + c) * n + i] = yu;
+    double h = 0.0, h_prop = 0.0, k1x = 0.0, k1u = 0.0;
+    int m = 0, rejected = 0;
+    bool new_step = true;
+    while (m < n_steps) {
+        if (new_step) {
+            if (m % K == 0) {
+                double* q = ck + (long long)(m / K) * 6 * n;
+                q[(long long)c * n + i] = yx;
+                q[(long long)(3 + c) * n + i] = yu;
+            }
+            h_prop = clampd(hprop, hmin, hmax);
+            h = h_prop;
+            deriv_team(F, T, kappa, yx, yu, k1x, k1u);
+            rejected = 0;
+            new_step = false;
         }
-        const double h_prop = clampd(hprop, hmin, hmax);
-        double h = h_prop;
-        double k1x, k1u;
-        deriv_team(F, T, kappa, yx, yu, k1x, k1u);
-        double y5x, y5u, sx, su;
-        int rejected = 0;
-        for (;;) {
-            double tx, tu, k2x, k2u, k3x, k3u, k4x, k4u, k5x, k5u, k6x, k6u;
-            tx = __fma_rn(h, A21 * k1x, yx); tu = __fma_rn(h, A21 * k1u, yu);
-            deriv_team(F, T, kappa, tx, tu, k2x, k2u);
+        double tx, tu, k2x, k2u, k3x, k3u, k4x, k4u, k5x, k5u, k6x, k6u;
+        tx = __fma_rn(h, A21 * k1x, yx); tu = __fma_rn(h, A21 * k1u, yu);
+        deriv_team(F, T, kappa, tx, tu, k2x, k2u);
 #define T3(k) __fma_rn(A32, k2##k, A31 * k1##k)
-            tx = __fma_rn(h, T3(x), yx); tu = __fma_rn(h, T3(u), yu);
-            deriv_team(F, T, kappa, tx, tu, k3x, k3u);
+        tx = __fma_rn(h, T3(x), yx); tu = __fma_rn(h, T3(u), yu);
+        deriv_team(F, T, kappa, tx, tu, k3x, k3u);
 #define T4(k) __fma_rn(A43, k3##k, __fma_rn(A42, k2##k, A41 * k1##k))
-            tx = __fma_rn(h, T4(x), yx); tu = __fma_rn(h, T4(u), yu);
-            deriv_team(F, T, kappa, tx, tu, k4x, k4u);
+        tx = __fma_rn(h, T4(x), yx); tu = __fma_rn(h, T4(u), yu);
+        deriv_team(F, T, kappa, tx, tu, k4x, k4u);
 #define T5(k) __fma_rn(A54, k4##k, __fma_rn(A53, k3##k, __fma_rn(A52, k2##k, A51 * k1##k)))
-            tx = __fma_rn(h, T5(x), yx); tu = __fma_rn(h, T5(u), yu);
-            deriv_team(F, T, kappa, tx, tu, k5x, k5u);
+        tx = __fma_rn(h, T5(x), yx); tu = __fma_rn(h, T5(u), yu);
+        deriv_team(F, T, kappa, tx, tu, k5x, k5u);
 #define T6(k) __fma_rn(A65, k5##k, __fma_rn(A64, k4##k, __fma_rn(A63, k3##k, __fma_rn(A62, k2##k, A61 * k1##k))))
-            tx = __fma_rn(h, T6(x), yx); tu = __fma_rn(h, T6(u), yu);
-            deriv_team(F, T, kappa, tx, tu, k6x, k6u);
+        tx = __fma_rn(h, T6(x), yx); tu = __fma_rn(h, T6(u), yu);
+        deriv_team(F, T, kappa, tx, tu, k6x, k6u);
 #define TB(k) __fma_rn(B6, k6##k, __fma_rn(B4, k4##k, __fma_rn(B3, k3##k, B1 * k1##k)))
 #define TE(k) (h * __fma_rn(E6, k6##k, __fma_rn(E5, k5##k, __fma_rn(E4, k4##k, __fma_rn(E3, k3##k, E1 * k1##k)))))
-            y5x = __fma_rn(h, TB(x), yx); y5u = __fma_rn(h, TB(u), yu);
-            const double ex = TE(x), eu = TE(u);
+        const double y5x = __fma_rn(h, TB(x), yx), y5u = __fma_rn(h, TB(u), yu);
+        const double ex = TE(x), eu = TE(u);
 #undef T3
 #undef T4
 #undef T5
 #undef T6
 #undef TB
 #undef TE
-            // squared norms ((e0^2 + e1^2) + e2^2) with fused products, as error_sums
-            const double ex0 = T.get(ex, 0), ex1 = T.get(ex, 1), ex2 = T.get(ex, 2);
-            const double eu0 = T.get(eu, 0), eu1 = T.get(eu, 1), eu2 = T.get(eu, 2);
-            sx = __fma_rn(ex2, ex2, __fma_rn(ex1, ex1, ex0 * ex0));
-            su = __fma_rn(eu2, eu2, __fma_rn(eu1, eu1, eu0 * eu0));
-            if (error_accept(sx, su, h, tol, tol2) || h <= hmin) break;
+        // squared norms ((e0^2 + e1^2) + e2^2) with fused products, as error_sums
+        const double ex0 = T.get(ex, 0), ex1 = T.get(ex, 1), ex2 = T.get(ex, 2);
+        const double eu0 = T.get(eu, 0), eu1 = T.get(eu, 1), eu2 = T.get(eu, 2);
+        const double sx = __fma_rn(ex2, ex2, __fma_rn(ex1, ex1, ex0 * ex0));
+        const double su = __fma_rn(eu2, eu2, __fma_rn(eu1, eu1, eu0 * eu0));
+        if (!(error_accept(sx, su, h, tol, tol2) || h <= hmin)) {
             const float shrink = ctrl_factor(ctrl_log2r(sx, su, h, lg_tol), -0.25f, 0.1f, 1.0f);
             h = fmax(h * widen_normal(shrink), hmin);
             rejected = 1;
+            continue;
         }
         yx = y5x;
         yu = y5u;
@@ -553,6 +559,8 @@ __global__ void k_adj_record_team(FieldDev F, const double* __restrict__ y0, con
         double hnext = h * widen_normal(grow);
         if (!rejected && h < h_prop) hnext = fmax(hnext, h_prop);
         hprop = clampd(hnext, hmin, hmax);
+        ++m;
+        new_step = true;
     }
     xT[3 * i + c] = yx;
     uT[3 * i + c] = yu;
