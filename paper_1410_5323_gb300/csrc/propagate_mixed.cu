@@ -91,9 +91,12 @@ struct MF { F3 f0; float q; int lo; };
 constexpr int kModNodes = 27;            // cached node values per lane
 constexpr int kModSlots = kModNodes + 3; // + the step-start cell (wrapped) per axis
 // Per-thread shared-memory slots of the current particle's field constants in cell units
-// (kept out of registers: they are read once per step, not per attempt): 6 doubles (spacing,
-// 1/spacing, origin x/y/z, distance limit) then 3 floats (step limit, spacing, c x spacing).
-constexpr int kFieldWords = 6 * 2 + 4;
+// (kept out of registers: they are read once per step, not per attempt): 3 doubles (spacing,
+// 1/spacing, distance limit) then 3 floats (step limit, spacing, c x spacing). The grid origin,
+// needed only when a particle is loaded, stored or split, is read from the field record.
+// Few slots keep the block's shared memory small, so that L1 keeps most of the SM's
+// shared/L1 storage (see launch_propagate_mixed).
+constexpr int kFieldWords = 3 * 2 + 3;
 
 
 template <int L>
@@ -173,7 +176,12 @@ __device__ __forceinline__ float& mslot(float* sm, int k) { return sm[(kFieldWor
 __device__ __forceinline__ double& dslot(float* sm, int k) {
     return reinterpret_cast<double*>(sm)[k * blockDim.x + threadIdx.x];
 }
-__device__ __forceinline__ float& fslot(float* sm, int k) { return sm[(12 + k) * blockDim.x + threadIdx.x]; }
+__device__ __forceinline__ float& fslot(float* sm, int k) { return sm[(6 + k) * blockDim.x + threadIdx.x]; }
+// Grid origin along axis c (metres), from the field record.
+__device__ __forceinline__ double origin(const PropArgs& a, int gid, int c) {
+    const FieldDev& G = a.fields[gid];
+    return __ldg(c == 0 ? &G.ox : (c == 1 ? &G.oy : &G.oz));
+}
 
 // Trilinear weights and the corner sum, in the same order for the cached and gathered paths.
 __device__ __forceinline__ float trilerp(float fx, float fy, float fz, float m0, float m1, float m2,
@@ -384,7 +392,7 @@ __device__ __forceinline__ void propagate_mixed_body(const PropArgs& a, float* s
         return DF{hi, (float)(rr - (double)hi)};
     };
     auto store = [&](int status, bool exact_end) {
-        S.x[slot] = to_x(Rx, dslot(sm, 2)); S.y[slot] = to_x(Ry, dslot(sm, 3)); S.z[slot] = to_x(Rz, dslot(sm, 4));
+        S.x[slot] = to_x(Rx, origin(a, gid, 0)); S.y[slot] = to_x(Ry, origin(a, gid, 1)); S.z[slot] = to_x(Rz, origin(a, gid, 2));
         S.ux[slot] = (double)u.x + (double)ul.x; S.uy[slot] = (double)u.y + (double)ul.y;
         S.uz[slot] = (double)u.z + (double)ul.z;
         S.E[slot] = E;
@@ -416,8 +424,7 @@ __device__ __forceinline__ void propagate_mixed_body(const PropArgs& a, float* s
             if constexpr (M) mf.q = (float)(G.spacing * G.m_inv_spacing);
             const double sp = G.spacing, inv_sp = G.inv_spacing;
             dslot(sm, 0) = sp; dslot(sm, 1) = inv_sp;
-            dslot(sm, 2) = G.ox; dslot(sm, 3) = G.oy; dslot(sm, 4) = G.oz;
-            dslot(sm, 5) = a.dmax * inv_sp;
+            dslot(sm, 2) = a.dmax * inv_sp;
             fslot(sm, 0) = (float)(a.hmax * inv_sp);
             fslot(sm, 1) = (float)sp;
             fslot(sm, 2) = (float)(kC * sp);
@@ -474,7 +481,7 @@ __device__ __forceinline__ void propagate_mixed_body(const PropArgs& a, float* s
                 h_propc = clampf_(hprop, hmin_c, fslot(sm, 0));
                 const float h_loss = rl > 0.0f ? 0.1f / rl : INF;
                 h_int = rpd > 0.0f ? fmaxf(tau, 0.0f) / rpd : INF;
-                h_dist = (float)(dslot(sm, 5) - s_c);
+                h_dist = (float)(dslot(sm, 2) - s_c);
                 h = h_propc;
                 if (h_loss < h) h = h_loss;
                 if (h_int < h) h = h_int;
@@ -500,9 +507,9 @@ __device__ __forceinline__ void propagate_mixed_body(const PropArgs& a, float* s
                         f = (float)(rm - fl);
                     };
                     int mbx, mby, mbz;
-                    mcell(Rx, dslot(sm, 2), G.mox, G.mnx, mbx, mf.f0.x);
-                    mcell(Ry, dslot(sm, 3), G.moy, G.mny, mby, mf.f0.y);
-                    mcell(Rz, dslot(sm, 4), G.moz, G.mnz, mbz, mf.f0.z);
+                    mcell(Rx, origin(a, gid, 0), G.mox, G.mnx, mbx, mf.f0.x);
+                    mcell(Ry, origin(a, gid, 1), G.moy, G.mny, mby, mf.f0.y);
+                    mcell(Rz, origin(a, gid, 2), G.moz, G.mnz, mbz, mf.f0.z);
                     mf.lo = (u.x < 0.0f ? 1 : 0) | (u.y < 0.0f ? 2 : 0) | (u.z < 0.0f ? 4 : 0);
                     mod_fill(sm, G, mbx, mby, mbz, mf.lo);
                 }
@@ -611,14 +618,14 @@ __device__ __forceinline__ void propagate_mixed_body(const PropArgs& a, float* s
                     R = from_x(xd, o);
                     if (odd) { uc = -uc; ucl = -ucl; u0col[slot] = -u0col[slot]; }
                 };
-                fold(Rx, dslot(sm, 2), 0, u.x, ul.x, S.u0x);
-                fold(Ry, dslot(sm, 3), 1, u.y, ul.y, S.u0y);
-                fold(Rz, dslot(sm, 4), 2, u.z, ul.z, S.u0z);
+                fold(Rx, origin(a, gid, 0), 0, u.x, ul.x, S.u0x);
+                fold(Ry, origin(a, gid, 1), 1, u.y, ul.y, S.u0y);
+                fold(Rz, origin(a, gid, 2), 2, u.z, ul.z, S.u0z);
             }
             bool done = (h == h_dist);
             s_c = s_c + widen(h);
-            if (s_c >= dslot(sm, 5)) done = true;
-            if (done) s_c = dslot(sm, 5);
+            if (s_c >= dslot(sm, 2)) done = true;
+            if (done) s_c = dslot(sm, 2);
             acc_tot += 1;
             taken += 1;
             const float grow = (r2 == 0.0f) ? 5.0f : clampf_(0.95f * powf_pos(r2, -0.1f), 0.2f, 5.0f);
@@ -635,7 +642,7 @@ __device__ __forceinline__ void propagate_mixed_body(const PropArgs& a, float* s
                     const double E_par = E * (double)(A - 1) / (double)A;
                     const long long qs = (long long)q;
                     const unsigned long long uid2 = (1ull << 32) + uid * 64ull + kk;
-                    S.x[qs] = to_x(Rx, dslot(sm, 2)); S.y[qs] = to_x(Ry, dslot(sm, 3)); S.z[qs] = to_x(Rz, dslot(sm, 4));
+                    S.x[qs] = to_x(Rx, origin(a, gid, 0)); S.y[qs] = to_x(Ry, origin(a, gid, 1)); S.z[qs] = to_x(Rz, origin(a, gid, 2));
                     S.ux[qs] = (double)u.x + (double)ul.x; S.uy[qs] = (double)u.y + (double)ul.y;
                     S.uz[qs] = (double)u.z + (double)ul.z;
                     S.E[qs] = E_sec;
@@ -738,10 +745,33 @@ int with_mixed_kernel(int layout, int mod, Fn&& fn) {
 
 size_t mixed_smem(int mod, int block) { return (size_t)(kFieldWords + (mod ? kModSlots : 0)) * sizeof(float) * block; }
 
+// Shared-memory carveout that holds the launch's blocks per SM and leaves the rest of the SM's
+// unified L1/shared storage to L1: the gathers are served from L1 (the driver's own choice for
+// this kernel was a 100 KB carveout, 37 KB used). Percent of the SM's shared-memory maximum,
+// with the driver's per-block reservation; the driver rounds up to a configuration it supports.
+static int mixed_carveout_pct(int grid, size_t shm_per_block) {
+    int dev = 0, smem = 0, sms = 0, reserved = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+        smem <= 0 || sms <= 0) {
+        cudaGetLastError();
+        return -1;   // the driver's default
+    }
+    const long long bps = (grid + sms - 1) / sms;
+    const long long need = bps * ((long long)shm_per_block + reserved);
+    const long long pct = (100 * need + smem - 1) / smem + 1;
+    return pct > 100 ? 100 : (int)pct;
+}
+
 int launch_propagate_mixed(const PropArgs& a, int layout, int mod, int grid, int block, void* stream) {
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const size_t shm = mixed_smem(mod, block);
+    const int pct = mixed_carveout_pct(grid, shm);
     return with_mixed_kernel(layout, mod, [&](void (*k)(const PropArgs)) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+        if (e != cudaSuccess) return (int)e;
         k<<<grid, block, shm, st>>>(a);
         return (int)cudaGetLastError();
     });
@@ -750,6 +780,9 @@ int launch_propagate_mixed(const PropArgs& a, int layout, int mod, int grid, int
 int propagate_mixed_occupancy(int layout, int mod, int block, int* blocks_per_sm) {
     const size_t shm = mixed_smem(mod, block);
     return with_mixed_kernel(layout, mod, [&](void (*k)(const PropArgs)) {
+        // the query sees the driver's default carveout, not the one a previous launch chose
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, -1);
+        if (e != cudaSuccess) return (int)e;
         return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, block, shm);
     });
 }
