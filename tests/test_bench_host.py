@@ -74,7 +74,7 @@ def test_roofline_bound_is_the_max_term_not_the_sum():
 
 def test_traffic_per_call():
     assert bench.traffic_for("fp64_256cube_1M_nuclei", "fp64", 2.0e9, 2) == pytest.approx(140.6 * 1.0e9)
-    assert bench.traffic_for("fp64_256cube_1M_nuclei", "mixed", 1.0e9, 1) == pytest.approx(99.5e9)
+    assert bench.traffic_for("fp64_256cube_1M_nuclei", "mixed", 1.0e9, 1) == pytest.approx(99.4e9)
     assert bench.traffic_for("no_such_workload", "fp64", 1.0e9, 1) is None
     assert bench.traffic_for("fp64_256cube_1M_nuclei", "fp64", 1.0e9, 0) is None
 
