@@ -438,9 +438,9 @@ int crp_kernel_runs(uint64_t* count);
  *
  * Limits and sharing: n <= CRP_NOALLOC_MAX_PARTICLES, else CRP_ERR_INVALID_ARG and nothing
  * runs. The first call on a device looks up the static array's device address (once per
- * device, with that device current), so make that first call before any stream capture
- * begins. Every call reuses the same array and clears what must start at zero, so calls
- * that overlap on the GPU (from several host threads or streams) race: serialise them.
+ * device, with that device current). Every call reuses the same array and clears what
+ * must start at zero, so calls that overlap on the GPU (from several host threads or
+ * streams) race: serialise them.
  * It never calls cudaMalloc, cudaFree or any allocating routine. */
 #define CRP_NOALLOC_MAX_PARTICLES 262144
 #define CRP_NOALLOC_SCRATCH_BYTES (512 + 3 * 4 * CRP_NOALLOC_MAX_PARTICLES)
