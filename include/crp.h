@@ -269,7 +269,11 @@ int crp_read_state(crp_sim* sim, int32_t column, void* dst, int32_t dst_is_devic
 /* ---- observer records (Sec. 3.1 observers) ---------------------------------------------
  * Copies the records of particles that have finished (status != ACTIVE), in the order
  * they finished, starting at the `first`-th finished particle, at most `capacity`
- * records; *n_out receives the number written. Caller-allocated columns, host or device. */
+ * records; *n_out receives the number written. Caller-allocated columns, host or device;
+ * NULL columns are skipped. Host columns that are all page-locked (cudaHostAlloc,
+ * cudaHostRegister, torch pin_memory) are written by the gather kernel directly; other host
+ * columns go through a device staging block (allocated and freed by the call). The call
+ * waits for the device; columns must hold `capacity` entries. */
 typedef struct {
     int64_t* uid;
     int32_t *A, *Z, *n_int, *status;

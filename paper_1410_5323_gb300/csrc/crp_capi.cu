@@ -4,6 +4,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cstdint>
 #include <mutex>
@@ -845,7 +846,57 @@ int crp_source_inject(crp_sim* s, const crp_particles* p, int64_t n, void* strea
         return fail(CRP_ERR_INVALID_ARG, "injection exceeds the simulation capacity");
     const int n_fields = (int)s->host_fields.size();
     const TablesDev* tab = s->tables ? &s->tables->dev : nullptr;
-    if (!p->is_device) {   // host columns: validate before touching the device
+    // host columns: validate before touching the device (a branch-free pass over all
+    // particles, then, only if it found an invalid one, the pass that names the error)
+    bool bad = false;
+    if (!p->is_device) {
+        const int zmax = tab ? tab->z_max : 0, nmax = tab ? tab->n_max : 0;
+        const bool t = tab != nullptr;
+        auto scan = [&](long long lo, long long hi) {
+            unsigned acc = 0;
+            for (long long i = lo; i < hi; ++i) {
+                const int A = p->A[i], Z = p->Z[i];
+                acc |= (unsigned)(A < 1) | (unsigned)(Z < -A) | (unsigned)(Z > A) |
+                       (unsigned)(t & ((Z < 0) | (Z > zmax) | (A - Z > nmax)));
+            }
+            if (p->uid)
+                for (long long i = lo; i < hi; ++i)
+                    acc |= (unsigned)((unsigned long long)p->uid[i] >= (1ull << 32));
+            if (p->grid_id)
+                for (long long i = lo; i < hi; ++i)
+                    acc |= (unsigned)((unsigned)p->grid_id[i] >= (unsigned)n_fields);
+            return acc;
+        };
+        // one host core reads these columns at a fraction of the memory bandwidth: large
+        // batches are scanned by several threads (chunks of at least 2^20 particles)
+        const long long kChunk = 1ll << 20;
+        long long nt = std::min<long long>(n / kChunk, std::max(1u, std::thread::hardware_concurrency()));
+        nt = std::max(1ll, std::min(nt, 32ll));
+        unsigned acc = 0;
+        if (nt == 1) {
+            acc = scan(0, n);
+        } else {
+            std::vector<unsigned> part((size_t)nt, 0u);
+            std::vector<std::thread> th;
+            bool spawned = true;
+            try {
+                th.reserve((size_t)nt);
+                for (long long k = 0; k < nt; ++k)
+                    th.emplace_back([&, k] { part[(size_t)k] = scan(n * k / nt, n * (k + 1) / nt); });
+            } catch (...) {   // no threads to be had: the whole scan on this one
+                spawned = false;
+            }
+            for (auto& x : th) x.join();
+            if (spawned) {
+                for (unsigned v : part) acc |= v;
+            } else {
+                acc = scan(0, n);
+            }
+        }
+        if (!p->uid) acc |= (unsigned)(h.n_primaries + (unsigned long long)n > (1ull << 32));
+        bad = acc != 0;
+    }
+    if (bad) {
         for (long long i = 0; i < n; ++i) {
             const int A = p->A[i], Z = p->Z[i];
             if (A < 1 || Z < -A || Z > A) return fail(CRP_ERR_INVALID_ARG, "particle with invalid A/Z");
@@ -1546,7 +1597,29 @@ int crp_observe(crp_sim* s, const crp_observer* o, int64_t first, int64_t capaci
               o->uz, o->u0x, o->u0y, o->u0z, o->s, o->n_steps, o->n_att};
     void* tmp = nullptr;
     ObsCols t = d;
-    if (!o->is_device) {   // gather on the device into one staging block, then copy out
+    // Host columns in pinned (page-locked) memory are written by the gather kernel directly,
+    // through their device addresses; other host memory goes through a staging block.
+    bool direct = !o->is_device;
+    if (direct) {
+        void** cols[] = {(void**)&t.uid, (void**)&t.A, (void**)&t.Z, (void**)&t.n_int,
+                         (void**)&t.status, (void**)&t.E, (void**)&t.x, (void**)&t.y,
+                         (void**)&t.z, (void**)&t.ux, (void**)&t.uy, (void**)&t.uz,
+                         (void**)&t.u0x, (void**)&t.u0y, (void**)&t.u0z, (void**)&t.s,
+                         (void**)&t.n_steps, (void**)&t.n_att};
+        for (void** c : cols) {
+            if (!*c) continue;
+            cudaPointerAttributes pa{};
+            if (cudaPointerGetAttributes(&pa, *c) != cudaSuccess || pa.type != cudaMemoryTypeHost ||
+                !pa.devicePointer) {
+                cudaGetLastError();
+                direct = false;
+                break;
+            }
+            *c = pa.devicePointer;
+        }
+        if (!direct) t = d;
+    }
+    if (!o->is_device && !direct) {   // gather on the device into one staging block, then copy out
         size_t off = 0;
         const size_t sz8 = (size_t)n * 8, sz4 = (size_t)n * 4;
         CRP_CUDA(dev_malloc(&tmp, 13 * sz8 + 4 * sz4 + 2 * sz8));
@@ -1565,7 +1638,7 @@ int crp_observe(crp_sim* s, const crp_observer* o, int64_t first, int64_t capaci
     k_observe<<<grid_for(n, 256, 4096), 256>>>(s->st, s->done_list, first, n, t);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    if (e == cudaSuccess && !o->is_device) {
+    if (e == cudaSuccess && !o->is_device && !direct) {
         struct { void* dst; void* src; size_t sz; } cps[] = {
             {d.uid, t.uid, 8}, {d.E, t.E, 8}, {d.x, t.x, 8}, {d.y, t.y, 8}, {d.z, t.z, 8},
             {d.ux, t.ux, 8}, {d.uy, t.uy, 8}, {d.uz, t.uz, 8}, {d.u0x, t.u0x, 8},

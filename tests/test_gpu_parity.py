@@ -210,6 +210,22 @@ def test_observer_records_match_state(oracle_lib):
     assert len(obs["uid"]) == sim.counts()["n_done"] == len(st["uid"])
     for k in obs:
         assert np.array_equal(obs[k], st[k]), k
+    # pinned host columns (written by the gather kernel directly), device columns and pageable
+    # host columns (staged) give the same records; a window of the finished list too
+    n = sim.counts()["n_done"]
+    ref = sim.observe()
+    for kind in ("pinned", "device"):
+        out = (sim.observe_buffers(n + 7, pinned=True) if kind == "pinned"
+               else sim.observe_buffers(n + 7, device="cuda"))
+        got = sim.observe(out=out)
+        for k in ref:
+            v = got[k].cpu().numpy() if hasattr(got[k], "cpu") else got[k]
+            assert np.array_equal(v, ref[k]), (kind, k)
+    first, cnt = 3, max(n - 10, 1)
+    out = sim.observe_buffers(cnt, pinned=True)
+    got = sim.observe(first=first, capacity=cnt, out=out)
+    for k in ref:
+        assert np.array_equal(got[k].numpy(), ref[k][first:first + cnt]), ("window", k)
 
 
 def test_device_columns_inject_like_host(oracle_lib):
@@ -243,10 +259,43 @@ def test_invalid_arguments_rejected():
     assert e.value.code == crp.api.ERR_INVALID_ARG
     with pytest.raises(crp.CrpError):
         sim.inject(I.make_particles(5, 1))         # above capacity
+    # every kind of invalid host particle is refused before the device is touched, wherever
+    # it sits in the batch
+    for field, value, where in (("A", 0, 1), ("Z", 2, 0), ("Z", -1, 1), ("uid", -1, 1),
+                                ("uid", 1 << 32, 0), ("grid_id", 1, 1), ("grid_id", -1, 0)):
+        bad = I.make_particles(2, 1)
+        getattr(bad, field)[where] = value
+        with pytest.raises(crp.CrpError) as e:
+            sim.inject(bad)
+        assert e.value.code == crp.api.ERR_INVALID_ARG, (field, value)
+        assert sim.counts()["n_used"] == 0, (field, value)
+    sim.inject(I.make_particles(2, 1))             # a valid batch still goes in
+    assert sim.counts()["n_used"] == 2
     with pytest.raises(crp.CrpError):
         sim.propagate(-1.0, I.KPC, I.MPC, I.MPC)
     with pytest.raises(crp.CrpError):
         sim.propagate(1e-4, I.MPC, I.KPC, I.MPC)   # max step below min step
+
+
+def test_invalid_particle_in_large_host_batch_rejected():
+    """Batches of 2^21 and more are validated by several host threads; an invalid particle in
+    any chunk (first, inner boundary, last) is still refused before the device is touched."""
+    import paper_1410_5323_gb300 as crp
+
+    n = (1 << 21) + 5
+    g = np.zeros((4, 4, 4, 3), dtype=np.float32)
+    sim = crp.Simulation([crp.Field(g, I.MPC)], None, capacity=n)
+    p = I.make_particles(n, 3)
+    for where in (0, n // 2, n - 1):
+        A = p.A.copy()
+        A[where] = 0
+        q = I.Particles(p.x, p.u, p.E, A, p.Z, p.uid, p.grid_id)
+        with pytest.raises(crp.CrpError) as e:
+            sim.inject(q)
+        assert e.value.code == crp.api.ERR_INVALID_ARG, where
+        assert sim.counts()["n_used"] == 0, where
+    sim.inject(p)
+    assert sim.counts()["n_used"] == n
 
 
 def test_full_size_workload_sampled_bit_identical(oracle_lib):
