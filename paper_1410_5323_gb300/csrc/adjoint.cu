@@ -545,19 +545,19 @@ __global__ void k_adj_record_team(FieldDev F, const double* __restrict__ y0, con
         const double eu0 = T.get(eu, 0), eu1 = T.get(eu, 1), eu2 = T.get(eu, 2);
         const double sx = __fma_rn(ex2, ex2, __fma_rn(ex1, ex1, ex0 * ex0));
         const double su = __fma_rn(eu2, eu2, __fma_rn(eu1, eu1, eu0 * eu0));
-        if (!(error_accept(sx, su, h, tol, tol2) || h <= hmin)) {
+        if (!(error_accept(sx, su, h, tol, tol2) || le_pos(h, hmin))) {
             const float shrink = ctrl_factor(ctrl_log2r(sx, su, h, lg_tol), -0.25f, 0.1f, 1.0f);
-            h = fmax(h * widen_normal(shrink), hmin);
+            h = max_pos(h * widen_normal(shrink), hmin);
             rejected = 1;
             continue;
         }
         yx = y5x;
         yu = y5u;
         if (c == 0) h_out[(long long)m * n + i] = h;
-        const float grow = (h == 0.0 || (sx == 0.0 && su == 0.0))
+        const float grow = (is_zero(h) || (is_zero(sx) && is_zero(su)))
                                ? 5.0f : ctrl_factor(ctrl_log2r(sx, su, h, lg_tol), -0.2f, 0.2f, 5.0f);
         double hnext = h * widen_normal(grow);
-        if (!rejected && h < h_prop) hnext = fmax(hnext, h_prop);
+        if (!rejected && lt_pos(h, h_prop)) hnext = max_pos(hnext, h_prop);
         hprop = clampd(hnext, hmin, hmax);
         ++m;
         new_step = true;

@@ -243,6 +243,34 @@ __device__ __forceinline__ void ck_attempt(const FieldDev& F, double kappa, cons
 #undef SE
 }
 
+// Compares, minima and maxima of step sizes and error sums on their bit patterns, with
+// integer instructions (GB300 runs FP64 compares and min/max on its FP64 pipe). Each helper
+// equals the IEEE operation on the operand domain it states.
+__device__ __forceinline__ long long dbits(double v) { return __double_as_longlong(v); }
+// v == 0.0 (either sign), any v
+__device__ __forceinline__ bool is_zero(double v) { return (dbits(v) << 1) == 0; }
+// a <= b for a in [+0, +inf] or a NaN of either sign, b in [+0, +inf]
+__device__ __forceinline__ bool le_sum(double a, double b) {
+    return (unsigned long long)dbits(a) <= (unsigned long long)dbits(b);
+}
+// a <= b for a not NaN, b in [+0, +inf]; a < b for a not NaN, b in (+0, +inf]
+__device__ __forceinline__ bool le_pos(double a, double b) { return dbits(a) <= dbits(b); }
+__device__ __forceinline__ bool lt_pos(double a, double b) { return dbits(a) < dbits(b); }
+// a == b for a, b not NaN
+__device__ __forceinline__ bool eq_num(double a, double b) {
+    const long long x = dbits(a), y = dbits(b);
+    return x == y || ((x | y) << 1) == 0;
+}
+// fmax(a, b) for a not NaN, b in (+0, +inf]
+__device__ __forceinline__ double max_pos(double a, double b) { return lt_pos(a, b) ? b : a; }
+// fmin(fmax(v, lo), hi) for 0 < lo <= hi < +inf and any v but a signaling NaN (a quiet NaN
+// gives lo, as fmax does)
+__device__ __forceinline__ double clampd(double v, double lo, double hi) {
+    const long long x = dbits(v);
+    if ((x & 0x7FFFFFFFFFFFFFFFll) > 0x7FF0000000000000ll || x < dbits(lo)) return lo;
+    return x > dbits(hi) ? hi : v;
+}
+
 // Error of an attempt, kept squared: sx = |dx|^2, su = |du|^2, each ((a0^2 + a1^2) + a2^2).
 // Accept iff the step has zero length or sx <= (h tol)^2 and su <= tol^2 (r <= 1 for
 // r = max(|dx|/h, |du|)/tol, compared as squares; a NaN sum rejects).
@@ -252,9 +280,9 @@ __device__ __forceinline__ void error_sums(const Y6& e, double& sx, double& su) 
 }
 
 __device__ __forceinline__ bool error_accept(double sx, double su, double h, double tol, double tol2) {
-    if (h == 0.0) return true;
+    if (is_zero(h)) return true;
     const double ht = h * tol;
-    return sx <= ht * ht && su <= tol2;
+    return le_sum(sx, ht * ht) && le_sum(su, tol2);
 }
 
 // Step-size controller. The factor is a heuristic, so only its inputs (the FP64 error sums)
@@ -365,9 +393,6 @@ __device__ __forceinline__ bool table_rates_f32(const TablesDev& t, int A, int Z
     return true;
 }
 
-__device__ __forceinline__ double clampd(double v, double lo, double hi) {
-    return fmin(fmax(v, lo), hi);
-}
 
 // Mirror fold of one coordinate into [lo, hi] (hi = lo + L, inv = 1/L): returns true when
 // the number of reflections is odd (the direction component reverses).
@@ -382,8 +407,8 @@ __device__ __forceinline__ bool reflect_axis(double& x, double lo, double hi, do
 }
 
 __device__ __forceinline__ bool finite6(const Y6& y) {
-    return isfinite(y.x) && isfinite(y.y) && isfinite(y.z) && isfinite(y.ux) &&
-           isfinite(y.uy) && isfinite(y.uz);
+    auto fin = [](double v) { return ((unsigned long long)dbits(v) >> 52 & 0x7FFu) != 0x7FFu; };
+    return fin(y.x) && fin(y.y) && fin(y.z) && fin(y.ux) && fin(y.uy) && fin(y.uz);
 }
 
 

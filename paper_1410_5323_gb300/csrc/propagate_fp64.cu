@@ -12,7 +12,9 @@
 // order as the stated reading, so results are bit-identical to the FP64 oracle. Work that
 // the reading leaves to the implementation stays off the FP64 pipe, which bounds this
 // kernel: the lookup's floors and indices are integer operations on the bits of the grid
-// coordinate, and the step-size factor is FP32 (from the bits of the FP64 error sums).
+// coordinate, the step-size factor is FP32 (from the bits of the FP64 error sums), and the
+// compares, minima and maxima of step sizes and error sums are integer operations on their
+// bits (exact on the operand domains the helpers state).
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 
@@ -115,9 +117,9 @@ __global__ void CRP_FP64_BOUNDS k_propagate_fp64(const PropArgs a) {
                 h_int = rpd_f > 0.0f ? widen_f32(__fdiv_rn(__double2float_rn(fmax(tau, 0.0)), rpd_f)) : INF;
                 h_dist = a.dmax - s;
                 h = h_propc;
-                if (h_loss < h) h = h_loss;
-                if (h_int < h) h = h_int;
-                if (h_dist < h) h = h_dist;
+                if (lt_pos(h_loss, h)) h = h_loss;
+                if (lt_pos(h_int, h)) h = h_int;
+                if (dbits(h_dist) < dbits(h)) h = h_dist;   // h_dist is never -0
                 h_first = h;
                 kappa = (double)Z * kC / E;   // E and Z are constant within a step
                 k1 = deriv<L, false, M>(F, kappa, y);   // rejected attempts reuse k1
@@ -131,9 +133,9 @@ __global__ void CRP_FP64_BOUNDS k_propagate_fp64(const PropArgs a) {
             att_step += 1;
             double sx, su;
             error_sums(err, sx, su);
-            if (!(error_accept(sx, su, h, a.tol, tol2) || h <= a.hmin)) {
+            if (!(error_accept(sx, su, h, a.tol, tol2) || le_pos(h, a.hmin))) {
                 const float shrink = ctrl_factor(ctrl_log2r(sx, su, h, lg_tol), -0.25f, 0.1f, 1.0f);
-                h = fmax(h * widen_normal(shrink), a.hmin);
+                h = max_pos(h * widen_normal(shrink), a.hmin);
                 rejected = 1;
                 continue;
             }
@@ -144,7 +146,7 @@ __global__ void CRP_FP64_BOUNDS k_propagate_fp64(const PropArgs a) {
                 store(CRP_STATUS_NAN_);
                 continue;
             }
-            const bool fires = (rpd > 0.0 && h == h_int);
+            const bool fires = (dbits(rpd) > 0 && eq_num(h, h_int));
             unsigned long long q = 0;
             if (fires) {
                 q = atomicAdd(&C->reserve, 1ull);
@@ -169,20 +171,20 @@ __global__ void CRP_FP64_BOUNDS k_propagate_fp64(const PropArgs a) {
                     y.uz = -y.uz; S.u0z[slot] = -S.u0z[slot];
                 }
             }
-            const bool done = (h == h_dist);
+            const bool done = eq_num(h, h_dist);
             s = done ? a.dmax : s + h;
             n_steps += 1;
             acc_tot += 1;
             taken += 1;
-            const float grow = (h == 0.0 || (sx == 0.0 && su == 0.0))
+            const float grow = (is_zero(h) || (is_zero(sx) && is_zero(su)))
                                    ? 5.0f : ctrl_factor(ctrl_log2r(sx, su, h, lg_tol), -0.2f, 0.2f, 5.0f);
             double hnext = h * widen_normal(grow);
-            if (!rejected && h_first < h_propc) hnext = fmax(hnext, h_propc);
+            if (!rejected && lt_pos(h_first, h_propc)) hnext = max_pos(hnext, h_propc);
             hprop = clampd(hnext, a.hmin, a.hmax);
             // ---- continuous loss at gamma0 ----
-            if (rl > 0.0) E = E * crp_exp(-h * rl);
+            if (dbits(rl) > 0) E = E * crp_exp(-h * rl);
             // ---- photo-disintegration ----
-            if (rpd > 0.0) {
+            if (dbits(rpd) > 0) {
                 if (fires) {
                     const unsigned kk = (unsigned)(n_int + 1);
                     const int dz = nucleon_proton(a.seed, uid, kk, A, Z) ? 1 : 0;
