@@ -787,6 +787,13 @@ def run_own(args):
                   for t in (v if isinstance(v, tuple) else (v,)))
         out = sim.observe_buffers(cap, pinned=True) if amap is None else None
         hmap = torch.empty_like(amap, device="cpu").pin_memory() if amap is not None else None
+        # the observer's buffers are set up once, like the pinned inputs: one untimed fill
+        # takes the first device write into the new page-locked pages (about 0.1 s for
+        # 1.6 GB here) out of the steady-state steps
+        if out is not None:
+            sim.observe(out=out)
+        elif hmap is not None:
+            hmap.copy_(amap)
         e2e_times, e2e_steps, d2h = [], 0, 0
         n_e2e = max(1, min(args.steps, args.e2e_steps))
         for _ in range(n_e2e):          # the device path is already warm
