@@ -11,6 +11,8 @@
 // Compiled with --fmad=false; per-particle arithmetic follows the oracle's order.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "crp_fp64.cuh"
 #include "crp_internal.h"
 #include "crp_math.cuh"
@@ -266,20 +268,20 @@ __device__ __forceinline__ Y6 deriv_from(double kappa, const Y6& y, const Look& 
     return k;
 }
 
-// Stage records of every step, all segments at once: thread (particle i, segment sg)
+// Stage records of the segments [sg0, sg0 + n_seg): thread (particle i, segment sg)
 // recomputes its segment from the checkpoint. Each step evaluates f at its six stage states
 // with the forward stage sums (as ck_attempt) and advances y by the 5th-order update, so the
 // states are the frozen forward's, bit for bit.
 template <int L>
 __global__ void k_adj_records(FieldDev F, const double* __restrict__ kap, const double* __restrict__ h,
                               const double* __restrict__ ck, double* __restrict__ rec_d,
-                              int32_t* __restrict__ rec_n, int n_steps, int K, long long n) {
+                              int32_t* __restrict__ rec_n, int n_steps, int K, int sg0, int n_seg,
+                              long long n) {
     CRP_COUNT_RUN();
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const int n_seg = (n_steps + K - 1) / K;
     if (t >= n * n_seg) return;
     const long long i = t % n;
-    const int sg = (int)(t / n);
+    const int sg = sg0 + (int)(t / n);
     const double kappa = kap[i];
     const int m0 = sg * K, m1 = min(m0 + K, n_steps);
     Y6 y;
@@ -614,8 +616,9 @@ __device__ __forceinline__ void vjp_rec_team(const RecT& r, double kappa, const 
 
 __global__ void k_adj_reverse_team(const double* __restrict__ kap, const double* __restrict__ h,
                                    const double* __restrict__ rec_d, const int32_t* __restrict__ rec_n,
-                                   int n_steps, const double* __restrict__ uT_bar, double* __restrict__ grid_bar,
-                                   double* __restrict__ y0_bar, double* __restrict__ kappa_bar_out, long long n) {
+                                   int m_hi, int m_lo, int first, const double* __restrict__ uT_bar,
+                                   double* __restrict__ grid_bar, double* __restrict__ y0_bar,
+                                   double* __restrict__ kappa_bar_out, long long n) {
     CRP_COUNT_RUN();
     long long i;
     bool active;
@@ -623,10 +626,17 @@ __global__ void k_adj_reverse_team(const double* __restrict__ kap, const double*
     if (!active) return;
     const int c = T.c;
     const double kappa = kap[i];
+    // steps m_hi - 1 down to m_lo; a later range continues from the cotangents the previous
+    // one left in y0_bar and kappa_bar_out (the same values in the same order as one sweep)
     double lx = 0.0, lu = uT_bar[3 * i + c];
     double kappa_bar = 0.0;
-    for (int m = n_steps - 1; m >= 0; --m) {
-        if (m > 0) {   // the previous step's records into L2, a third of the lines per lane
+    if (!first) {
+        lx = y0_bar[(long long)c * n + i];
+        lu = y0_bar[(long long)(3 + c) * n + i];
+        kappa_bar = kappa_bar_out[i];
+    }
+    for (int m = m_hi - 1; m >= m_lo; --m) {
+        if (m > m_lo) {   // the previous step's records into L2, a third of the lines per lane
             const double* d = rec_d + ((long long)(m - 1) * 6 * kRecD) * n + i;
             for (int k = c; k < 6 * kRecD; k += 3) asm volatile("prefetch.global.L2 [%0];" ::"l"(d + k * n));
             const int32_t* q = rec_n + ((long long)(m - 1) * 6 * kRecN) * n + i;
@@ -669,6 +679,8 @@ __global__ void k_adj_reverse_team(const double* __restrict__ kap, const double*
         lx = ybx;
         lu = ybu;
     }
+    // every lane has read its state above before any lane of the team writes it here
+    __syncwarp(T.mask);
     y0_bar[(long long)c * n + i] = lx;
     y0_bar[(long long)(3 + c) * n + i] = lu;
     if (c == 0) kappa_bar_out[i] = kappa_bar;
@@ -713,18 +725,48 @@ int adj_replay(const FieldDev& F, const double* y0, const double* kappa, const d
 
 int adj_backward(const FieldDev& F, const double* kappa, const double* h, const double* ck,
                  double* seg, double* stages, int n_steps, int K, const double* uT_bar, double* grid_bar,
-                 double* y0_bar, double* kappa_bar, long long n, void* stream) {
-    if (stages) {       // all segments' stage records at once, then the reverse sweep applies them
-        const long long threads = n * ((n_steps + K - 1) / K);
+                 double* y0_bar, double* kappa_bar, long long n, void* stream, void* aux_stream,
+                 void* const* events, int n_events) {
+    if (stages) {
+        // Stage records in chunks of checkpoint segments, last chunk first, on the auxiliary
+        // stream; the reverse sweep takes each chunk once its event has fired. The records
+        // kernel (FP64-throughput-bound, many threads) then runs beside the reverse sweep
+        // (one warp per ten chains, latency-bound). Without an auxiliary stream: one chunk.
+        const cudaStream_t st = (cudaStream_t)stream, aux = (cudaStream_t)aux_stream;
+        const int S = (n_steps + K - 1) / K;
+        int J = (aux && n_events >= 2) ? std::min(n_events - 1, S) : 1;
+        const int C = (S + J - 1) / J;
+        J = (S + C - 1) / C;
         double* rec_d = stages;
         int32_t* rec_n = reinterpret_cast<int32_t*>(stages + (size_t)n_steps * 6 * kRecD * (size_t)n);
-        k_adj_records<LAYOUT_F64X4><<<blocks(threads), 128, 0, (cudaStream_t)stream>>>(
-            F, kappa, h, ck, rec_d, rec_n, n_steps, K, n);
-        const int e = (int)cudaGetLastError();
-        if (e) return e;
-        k_adj_reverse_team<<<team_blocks(n), 32, 0, (cudaStream_t)stream>>>(
-            kappa, h, rec_d, rec_n, n_steps, uT_bar, grid_bar, y0_bar, kappa_bar, n);
-        return (int)cudaGetLastError();
+        const cudaStream_t rs = J > 1 ? aux : st;
+        cudaError_t e = cudaSuccess;
+        if (J > 1) {
+            e = cudaEventRecord((cudaEvent_t)events[0], st);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(aux, (cudaEvent_t)events[0], 0);
+            if (e != cudaSuccess) return (int)e;
+        }
+        for (int j = 0; j < J; ++j) {
+            const int hi = S - j * C, lo = std::max(0, hi - C);
+            k_adj_records<LAYOUT_F64X4><<<blocks(n * (hi - lo)), 128, 0, rs>>>(
+                F, kappa, h, ck, rec_d, rec_n, n_steps, K, lo, hi - lo, n);
+            e = cudaGetLastError();
+            if (e == cudaSuccess && J > 1) e = cudaEventRecord((cudaEvent_t)events[1 + j], aux);
+            if (e != cudaSuccess) return (int)e;
+        }
+        for (int j = 0; j < J; ++j) {
+            const int hi = S - j * C, lo = std::max(0, hi - C);
+            if (J > 1) {
+                e = cudaStreamWaitEvent(st, (cudaEvent_t)events[1 + j], 0);
+                if (e != cudaSuccess) return (int)e;
+            }
+            k_adj_reverse_team<<<team_blocks(n), 32, 0, st>>>(
+                kappa, h, rec_d, rec_n, std::min(hi * K, n_steps), lo * K, j == 0 ? 1 : 0, uT_bar,
+                grid_bar, y0_bar, kappa_bar, n);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return (int)e;
+        }
+        return 0;
     }
     k_adj_backward<LAYOUT_F64X4><<<chain_blocks(n), kChainBlock, 0, (cudaStream_t)stream>>>(
         F, kappa, h, ck, seg, n_steps, K, uT_bar, grid_bar, y0_bar, kappa_bar, n);

@@ -1796,6 +1796,11 @@ struct crp_adjoint {
     double* stages = nullptr;            // stage records of every step (kAdjRecordBytes each), if room
     int32_t* Z = nullptr;
     bool recorded = false;
+    // the backward pass forms the stage records in chunks on `aux` beside the reverse sweep
+    static constexpr int kEvents = 9;   // up to 8 chunks
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev[kEvents] = {};
+    int n_ev = 0;
 };
 
 namespace {
@@ -1806,6 +1811,8 @@ void adj_free(crp_adjoint* a) {
     for (double* p : ds)
         if (p) cudaFree(p);
     if (a->Z) cudaFree(a->Z);
+    for (int k = 0; k < a->n_ev; ++k) cudaEventDestroy(a->ev[k]);
+    if (a->aux) cudaStreamDestroy(a->aux);
 }
 
 }  // namespace
@@ -1849,6 +1856,16 @@ int crp_adjoint_create(const crp_field* field, int64_t n, int32_t n_steps, int32
             a->stages = nullptr;
             cudaGetLastError();
         }
+    }
+    if (a->stages) {   // without a stream and events the records form in one chunk
+        if (cudaStreamCreateWithFlags(&a->aux, cudaStreamNonBlocking) == cudaSuccess) {
+            while (a->n_ev < crp_adjoint::kEvents &&
+                   cudaEventCreateWithFlags(&a->ev[a->n_ev], cudaEventDisableTiming) == cudaSuccess)
+                ++a->n_ev;
+        } else {
+            a->aux = nullptr;
+        }
+        cudaGetLastError();
     }
     *out = a;
     return CRP_OK;
@@ -1918,7 +1935,8 @@ int crp_adjoint_backward(crp_adjoint* a, const double* uT_bar, double* grid_bar,
     if (rc) return rc;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     int e = adj_backward(F, a->kappa, a->h, a->ck, a->seg, a->stages, a->n_steps, a->K, uT_bar, grid_bar,
-                         a->y0_bar, a->kappa_bar, a->n, st);
+                         a->y0_bar, a->kappa_bar, a->n, st, a->aux, reinterpret_cast<void* const*>(a->ev),
+                         a->n_ev);
     if (e) return cuda_fail((cudaError_t)e, "adjoint backward");
     e = adj_p0bar(a->y0, a->kappa, a->E, a->y0_bar, a->kappa_bar, p0_bar, x0_bar, a->n, st);
     if (e) return cuda_fail((cudaError_t)e, "adjoint p0 gradient");

@@ -154,9 +154,13 @@ int adj_record(const FieldDev& F, const double* y0, const double* kappa, double 
                long long n, void* stream);
 int adj_replay(const FieldDev& F, const double* y0, const double* kappa, const double* h, int n_steps,
                double* xT, double* uT, unsigned long long* cell_hash, long long n, void* stream);
+// With `stages`, the records are formed in up to n_events - 1 chunks on `aux_stream` (events[0]
+// orders it after `stream`, events[1 + j] hands chunk j to the reverse sweep on `stream`);
+// aux_stream NULL: one chunk on `stream`.
 int adj_backward(const FieldDev& F, const double* kappa, const double* h, const double* ck,
                  double* seg, double* stages, int n_steps, int K, const double* uT_bar, double* grid_bar,
-                 double* y0_bar, double* kappa_bar, long long n, void* stream);
+                 double* y0_bar, double* kappa_bar, long long n, void* stream, void* aux_stream,
+                 void* const* events, int n_events);
 int adj_p0bar(const double* y0, const double* kappa, const double* E, const double* y0_bar,
               const double* kappa_bar, double* p0_bar, double* x0_bar, long long n, void* stream);
 
