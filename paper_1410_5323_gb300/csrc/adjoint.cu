@@ -92,13 +92,14 @@ struct Look {
     long long node[8];
 };
 
-template <int L>
+// P2: the grid's sizes are powers of two (indices wrap with a mask, as in field_b).
+template <int L, bool P2 = false>
 __device__ __forceinline__ void lookup_jac(const FieldDev& F, double x, double y, double z, Look& o) {
     long long ix[2], iy[2], iz[2];
     double wx[2], wy[2], wz[2];
-    axis(x, F.oix, F.inv_spacing, F.nx, F.pow2, ix[0], ix[1], wx[0], wx[1]);
-    axis(y, F.oiy, F.inv_spacing, F.ny, F.pow2, iy[0], iy[1], wy[0], wy[1]);
-    axis(z, F.oiz, F.inv_spacing, F.nz, F.pow2, iz[0], iz[1], wz[0], wz[1]);
+    axis<P2>(x, F.oix, F.inv_spacing, F.nx, F.pow2, ix[0], ix[1], wx[0], wx[1]);
+    axis<P2>(y, F.oiy, F.inv_spacing, F.ny, F.pow2, iy[0], iy[1], wy[0], wy[1]);
+    axis<P2>(z, F.oiz, F.inv_spacing, F.nz, F.pow2, iz[0], iz[1], wz[0], wz[1]);
     const double dd[2] = {-F.inv_spacing, F.inv_spacing};
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
@@ -272,7 +273,7 @@ __device__ __forceinline__ Y6 deriv_from(double kappa, const Y6& y, const Look& 
 // recomputes its segment from the checkpoint. Each step evaluates f at its six stage states
 // with the forward stage sums (as ck_attempt) and advances y by the 5th-order update, so the
 // states are the frozen forward's, bit for bit.
-template <int L>
+template <int L, bool P2>
 __global__ void k_adj_records(FieldDev F, const double* __restrict__ kap, const double* __restrict__ h,
                               const double* __restrict__ ck, double* __restrict__ rec_d,
                               int32_t* __restrict__ rec_n, int n_steps, int K, int sg0, int n_seg,
@@ -290,7 +291,7 @@ __global__ void k_adj_records(FieldDev F, const double* __restrict__ kap, const 
         const double h_ = h[(long long)m * n + i];
         Look o;
         Y6 t_;
-        lookup_jac<L>(F, y.x, y.y, y.z, o);
+        lookup_jac<L, P2>(F, y.x, y.y, y.z, o);
         put_rec(rec_d, rec_n, n, i, m, 0, y, o);
         const Y6 k1 = deriv_from(kappa, y, o);
 #define ADJ_STAGE(dst, expr)                                                                \
@@ -301,27 +302,27 @@ __global__ void k_adj_records(FieldDev F, const double* __restrict__ kap, const 
         } while (0)
 #define R2(c) (A21 * k1.c)
         ADJ_STAGE(t_, R2);
-        lookup_jac<L>(F, t_.x, t_.y, t_.z, o);
+        lookup_jac<L, P2>(F, t_.x, t_.y, t_.z, o);
         put_rec(rec_d, rec_n, n, i, m, 1, t_, o);
         const Y6 k2 = deriv_from(kappa, t_, o);
 #define R3(c) __fma_rn(A32, k2.c, A31 * k1.c)
         ADJ_STAGE(t_, R3);
-        lookup_jac<L>(F, t_.x, t_.y, t_.z, o);
+        lookup_jac<L, P2>(F, t_.x, t_.y, t_.z, o);
         put_rec(rec_d, rec_n, n, i, m, 2, t_, o);
         const Y6 k3 = deriv_from(kappa, t_, o);
 #define R4(c) __fma_rn(A43, k3.c, __fma_rn(A42, k2.c, A41 * k1.c))
         ADJ_STAGE(t_, R4);
-        lookup_jac<L>(F, t_.x, t_.y, t_.z, o);
+        lookup_jac<L, P2>(F, t_.x, t_.y, t_.z, o);
         put_rec(rec_d, rec_n, n, i, m, 3, t_, o);
         const Y6 k4 = deriv_from(kappa, t_, o);
 #define R5(c) __fma_rn(A54, k4.c, __fma_rn(A53, k3.c, __fma_rn(A52, k2.c, A51 * k1.c)))
         ADJ_STAGE(t_, R5);
-        lookup_jac<L>(F, t_.x, t_.y, t_.z, o);
+        lookup_jac<L, P2>(F, t_.x, t_.y, t_.z, o);
         put_rec(rec_d, rec_n, n, i, m, 4, t_, o);
         const Y6 k5 = deriv_from(kappa, t_, o);
 #define R6(c) __fma_rn(A65, k5.c, __fma_rn(A64, k4.c, __fma_rn(A63, k3.c, __fma_rn(A62, k2.c, A61 * k1.c))))
         ADJ_STAGE(t_, R6);
-        lookup_jac<L>(F, t_.x, t_.y, t_.z, o);
+        lookup_jac<L, P2>(F, t_.x, t_.y, t_.z, o);
         put_rec(rec_d, rec_n, n, i, m, 5, t_, o);
         const Y6 k6 = deriv_from(kappa, t_, o);
 #define RB(c) __fma_rn(B6, k6.c, __fma_rn(B4, k4.c, __fma_rn(B3, k3.c, B1 * k1.c)))
@@ -418,12 +419,13 @@ struct Team {
 // B_c at the team's stage position (lane c holds its coordinate xc): the periodic trilinear
 // lookup of field_b, with the axes, the corner weights and the corner loads split over the
 // team. FP64 node copy: component c of node k at ((const double*)data)[4k + c].
+template <bool P2>
 __device__ __forceinline__ double field_team(const FieldDev& F, const Team& T, double xc) {
     long long i0, i1;
     const double oi = T.oi;
     const int nn = T.nn;
     double w0, w1;
-    axis(xc, oi, F.inv_spacing, nn, F.pow2, i0, i1, w0, w1);
+    axis<P2>(xc, oi, F.inv_spacing, nn, F.pow2, i0, i1, w0, w1);
     const long long ix0 = T.get(i0, 0), ix1 = T.get(i1, 0), iy0 = T.get(i0, 1), iy1 = T.get(i1, 1);
     const long long iz0 = T.get(i0, 2), iz1 = T.get(i1, 2);
     const double wx0 = T.get(w0, 0), wx1 = T.get(w1, 0), wy0 = T.get(w0, 1), wy1 = T.get(w1, 1);
@@ -454,9 +456,10 @@ __device__ __forceinline__ double field_team(const FieldDev& F, const Team& T, d
 }
 
 // Component c of f(Y) = (u, kappa u x B(x)): (ku_c = kappa fma(u_{c+1}, B_{c+2}, -(u_{c+2} B_{c+1}))).
+template <bool P2>
 __device__ __forceinline__ void deriv_team(const FieldDev& F, const Team& T, double kappa, double yx,
                                            double yu, double& kx, double& ku) {
-    const double B = field_team(F, T, yx);
+    const double B = field_team<P2>(F, T, yx);
     const double u1 = T.get(yu, T.nx1()), u2 = T.get(yu, T.nx2());
     const double B1 = T.get(B, T.nx1()), B2 = T.get(B, T.nx2());
     kx = yu;
@@ -484,6 +487,7 @@ __device__ __forceinline__ Team make_team(long long n, long long& i, bool& activ
 
 // Forward with the propagation module's controller only, in team form; records h_n and the
 // checkpoints of every K-th step (the oracle's frozen forward, value for value).
+template <bool P2>
 __global__ void k_adj_record_team(FieldDev F, const double* __restrict__ y0, const double* __restrict__ kap,
                                   double tol, double hmin, double hmax, int n_steps, int K,
                                   double* __restrict__ h_out, double* __restrict__ ck,
@@ -513,25 +517,25 @@ __global__ void k_adj_record_team(FieldDev F, const double* __restrict__ y0, con
             }
             h_prop = clampd(hprop, hmin, hmax);
             h = h_prop;
-            deriv_team(F, T, kappa, yx, yu, k1x, k1u);
+            deriv_team<P2>(F, T, kappa, yx, yu, k1x, k1u);
             rejected = 0;
             new_step = false;
         }
         double tx, tu, k2x, k2u, k3x, k3u, k4x, k4u, k5x, k5u, k6x, k6u;
         tx = __fma_rn(h, A21 * k1x, yx); tu = __fma_rn(h, A21 * k1u, yu);
-        deriv_team(F, T, kappa, tx, tu, k2x, k2u);
+        deriv_team<P2>(F, T, kappa, tx, tu, k2x, k2u);
 #define T3(k) __fma_rn(A32, k2##k, A31 * k1##k)
         tx = __fma_rn(h, T3(x), yx); tu = __fma_rn(h, T3(u), yu);
-        deriv_team(F, T, kappa, tx, tu, k3x, k3u);
+        deriv_team<P2>(F, T, kappa, tx, tu, k3x, k3u);
 #define T4(k) __fma_rn(A43, k3##k, __fma_rn(A42, k2##k, A41 * k1##k))
         tx = __fma_rn(h, T4(x), yx); tu = __fma_rn(h, T4(u), yu);
-        deriv_team(F, T, kappa, tx, tu, k4x, k4u);
+        deriv_team<P2>(F, T, kappa, tx, tu, k4x, k4u);
 #define T5(k) __fma_rn(A54, k4##k, __fma_rn(A53, k3##k, __fma_rn(A52, k2##k, A51 * k1##k)))
         tx = __fma_rn(h, T5(x), yx); tu = __fma_rn(h, T5(u), yu);
-        deriv_team(F, T, kappa, tx, tu, k5x, k5u);
+        deriv_team<P2>(F, T, kappa, tx, tu, k5x, k5u);
 #define T6(k) __fma_rn(A65, k5##k, __fma_rn(A64, k4##k, __fma_rn(A63, k3##k, __fma_rn(A62, k2##k, A61 * k1##k))))
         tx = __fma_rn(h, T6(x), yx); tu = __fma_rn(h, T6(u), yu);
-        deriv_team(F, T, kappa, tx, tu, k6x, k6u);
+        deriv_team<P2>(F, T, kappa, tx, tu, k6x, k6u);
 #define TB(k) __fma_rn(B6, k6##k, __fma_rn(B4, k4##k, __fma_rn(B3, k3##k, B1 * k1##k)))
 #define TE(k) (h * __fma_rn(E6, k6##k, __fma_rn(E5, k5##k, __fma_rn(E4, k4##k, __fma_rn(E3, k3##k, E1 * k1##k)))))
         const double y5x = __fma_rn(h, TB(x), yx), y5u = __fma_rn(h, TB(u), yu);
@@ -707,8 +711,9 @@ int adj_init(const double* x0, const double* p0, const int32_t* Z, double* y0, d
 int adj_record(const FieldDev& F, const double* y0, const double* kappa, double tol, double hmin,
                double hmax, int n_steps, int K, double* h, double* ck, double* xT, double* uT,
                long long n, void* stream) {
-    k_adj_record_team<<<team_blocks(n), 32, 0, (cudaStream_t)stream>>>(
-        F, y0, kappa, tol, hmin, hmax, n_steps, K, h, ck, xT, uT, n);
+    auto k = F.pow2 ? k_adj_record_team<true> : k_adj_record_team<false>;
+    k<<<team_blocks(n), 32, 0, (cudaStream_t)stream>>>(F, y0, kappa, tol, hmin, hmax, n_steps, K, h, ck,
+                                                        xT, uT, n);
     return (int)cudaGetLastError();
 }
 
@@ -748,8 +753,8 @@ int adj_backward(const FieldDev& F, const double* kappa, const double* h, const 
         }
         for (int j = 0; j < J; ++j) {
             const int hi = S - j * C, lo = std::max(0, hi - C);
-            k_adj_records<LAYOUT_F64X4><<<blocks(n * (hi - lo)), 128, 0, rs>>>(
-                F, kappa, h, ck, rec_d, rec_n, n_steps, K, lo, hi - lo, n);
+            auto k = F.pow2 ? k_adj_records<LAYOUT_F64X4, true> : k_adj_records<LAYOUT_F64X4, false>;
+            k<<<blocks(n * (hi - lo)), 128, 0, rs>>>(F, kappa, h, ck, rec_d, rec_n, n_steps, K, lo, hi - lo, n);
             e = cudaGetLastError();
             if (e == cudaSuccess && J > 1) e = cudaEventRecord((cudaEvent_t)events[1 + j], aux);
             if (e != cudaSuccess) return (int)e;

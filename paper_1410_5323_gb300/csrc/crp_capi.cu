@@ -412,6 +412,7 @@ namespace {
 struct Plan {
     PropArgs a{};
     int grid = 0, block = 0, order = 0, mixed = 0, n_buckets = 0, layout = 0, mod = 0;
+    int p2 = 0;   // every field's vector grid has power-of-two sizes
 };
 
 }  // namespace
@@ -1343,11 +1344,13 @@ int make_plan(crp_sim* s, const crp_params* prm, double tol, double hmin, double
             layout = layout == LAYOUT_BF16X4 ? LAYOUT_BF16_CELLS : LAYOUT_F32_CELLS;
         }
     }
+    int p2 = 1;   // the mask-wrap kernels when every vector grid's sizes are powers of two
+    for (const FieldDev& hf : s->host_fields) p2 &= hf.pow2 ? 1 : 0;
     int bps = prm->blocks_per_sm;
     if (bps <= 0) {
         int occ = 0;
-        const int oe = mixed ? propagate_mixed_occupancy(layout, s->mod, block, &occ)
-                             : propagate_fp64_occupancy(layout, s->mod, block, &occ);
+        const int oe = mixed ? propagate_mixed_occupancy(layout, s->mod, p2, block, &occ)
+                             : propagate_fp64_occupancy(layout, s->mod, p2, block, &occ);
         if (oe != 0 || occ < 1) occ = 1;
         bps = occ;
     }
@@ -1357,6 +1360,7 @@ int make_plan(crp_sim* s, const crp_params* prm, double tol, double hmin, double
     P.mixed = mixed ? 1 : 0;
     P.layout = layout;
     P.mod = s->mod;
+    P.p2 = p2;
     P.n_buckets = order == CRP_ORDER_GRID ? kBuckets * (int)s->host_fields.size() : kBuckets;
     PropArgs& a = P.a;
     a.st = s->st;
@@ -1416,8 +1420,8 @@ int enqueue(crp_sim* s, const Plan& P, cudaStream_t st) {
     for (int gen = 0; gen < 2; ++gen) {
         if (a.pickup) CRP_CUDA(cudaMemsetAsync(s->lists[1 - gen], 0xff, sizeof(int32_t) * s->capacity, st));
         a.list = gen;
-        int e = P.mixed ? launch_propagate_mixed(a, P.layout, P.mod, P.grid, P.block, st)
-                        : launch_propagate_fp64(a, P.layout, P.mod, P.grid, P.block, st);
+        int e = P.mixed ? launch_propagate_mixed(a, P.layout, P.mod, P.p2, P.grid, P.block, st)
+                        : launch_propagate_fp64(a, P.layout, P.mod, P.p2, P.grid, P.block, st);
         if (e) return cuda_fail((cudaError_t)e, "propagate kernel launch");
         k_swap<<<1, 1, 0, st>>>(s->ctr, s->capacity, gen);
         CRP_CUDA(cudaGetLastError());
@@ -1445,6 +1449,7 @@ __global__ void k_loop_cond(Counters* C, cudaGraphConditionalHandle h, long long
 bool same_plan(const Plan& x, const Plan& y) {
     return std::memcmp(&x.a, &y.a, sizeof(PropArgs)) == 0 && x.grid == y.grid &&
            x.block == y.block && x.order == y.order && x.mixed == y.mixed && x.n_buckets == y.n_buckets &&
+           x.p2 == y.p2 &&
            x.layout == y.layout;
 }
 
@@ -1748,7 +1753,7 @@ extern "C" int crp_propagate_noalloc(const void* grid, int32_t nx, int32_t ny, i
     CRP_CUDA(cudaGetLastError());
     const int block = 128;
     int occ = 0;
-    if (propagate_fp64_occupancy(LAYOUT_F32X4, 0, block, &occ) != 0 || occ < 1) occ = 1;
+    if (propagate_fp64_occupancy(LAYOUT_F32X4, 0, f.pow2, block, &occ) != 0 || occ < 1) occ = 1;
     PropArgs a{};
     a.st = S;
     a.fields = fdev;
@@ -1765,7 +1770,7 @@ extern "C" int crp_propagate_noalloc(const void* grid, int32_t nx, int32_t ny, i
     a.ctr = ctr;
     for (int gen = 0; gen < 2; ++gen) {
         a.list = gen;
-        int e = launch_propagate_fp64(a, LAYOUT_F32X4, 0, sms * occ, block, st);
+        int e = launch_propagate_fp64(a, LAYOUT_F32X4, 0, f.pow2, sms * occ, block, st);
         if (e) return cuda_fail((cudaError_t)e, "propagate kernel launch");
         k_swap<<<1, 1, 0, st>>>(ctr, n, gen);
         CRP_CUDA(cudaGetLastError());

@@ -95,7 +95,10 @@ __device__ __forceinline__ void floor_split(double r, long long& i, double& fl) 
 }
 
 // One axis of the periodic lookup: r = x (1/spacing) - o (1/spacing) with one rounding (oi is
-// the product o (1/spacing), rounded once), i0 = floor(r) mod n, weights (1 - f, f).
+// the product o (1/spacing), rounded once), i0 = floor(r) mod n, weights (1 - f, f). P2: the
+// caller guarantees n is a power of two, and the 64-bit modulo's code (inlined at every
+// lookup, never run for such grids) is left out of the kernel.
+template <bool P2 = false>
 __device__ __forceinline__ void axis(double x, double oi, double inv, int n, int pow2,
                                      long long& i0, long long& i1, double& w0, double& w1) {
     const double r = __fma_rn(x, inv, -oi);
@@ -104,7 +107,7 @@ __device__ __forceinline__ void axis(double x, double oi, double inv, int n, int
     floor_split(r, i, fl);
     const double fr = r - fl;
     long long a;
-    if (pow2) a = i & (long long)(n - 1);
+    if (P2 || pow2) a = i & (long long)(n - 1);
     else { a = i % n; if (a < 0) a += n; }
     i0 = a;
     i1 = (a + 1 == n) ? 0 : a + 1;
@@ -145,15 +148,15 @@ __device__ __forceinline__ double modulation(const FieldDev& F, double x, double
 // weight ((w_x * w_y) * w_z), each corner added with one rounding (fused multiply-add from
 // 0). With M, the result is scaled by the modulation value.
 // With H, every lookup also folds its cell index into *hh (the visited-cell sequence of a
-// trajectory; no effect on the arithmetic).
-template <int L, bool H = false, bool M = false>
+// trajectory; no effect on the arithmetic). P2: the vector grid's sizes are powers of two.
+template <int L, bool H = false, bool M = false, bool P2 = false>
 __device__ __forceinline__ V3 field_b(const FieldDev& F, double x, double y, double z,
                                       unsigned long long* hh = nullptr) {
     long long ix0, ix1, iy0, iy1, iz0, iz1;
     double wx0, wx1, wy0, wy1, wz0, wz1;
-    axis(x, F.oix, F.inv_spacing, F.nx, F.pow2, ix0, ix1, wx0, wx1);
-    axis(y, F.oiy, F.inv_spacing, F.ny, F.pow2, iy0, iy1, wy0, wy1);
-    axis(z, F.oiz, F.inv_spacing, F.nz, F.pow2, iz0, iz1, wz0, wz1);
+    axis<P2>(x, F.oix, F.inv_spacing, F.nx, F.pow2, ix0, ix1, wx0, wx1);
+    axis<P2>(y, F.oiy, F.inv_spacing, F.ny, F.pow2, iy0, iy1, wy0, wy1);
+    axis<P2>(z, F.oiz, F.inv_spacing, F.nz, F.pow2, iz0, iz1, wz0, wz1);
     const long long ny = F.ny, nz = F.nz;
     if constexpr (H) *hh = *hh * 0x9E3779B97F4A7C15ull + (unsigned long long)((ix0 * ny + iy0) * nz + iz0) + 1ull;
     const long long r00 = (ix0 * ny + iy0) * nz, r01 = (ix0 * ny + iy1) * nz;
@@ -186,10 +189,10 @@ __device__ __forceinline__ V3 field_b(const FieldDev& F, double x, double y, dou
 struct Y6 { double x, y, z, ux, uy, uz; };
 
 // f(y) = (u, kappa u x B(x)); a cross-product component a b - c d as kappa fma(a, b, -(c d)).
-template <int L, bool H = false, bool M = false>
+template <int L, bool H = false, bool M = false, bool P2 = false>
 __device__ __forceinline__ Y6 deriv(const FieldDev& F, double kappa, const Y6& y,
                                     unsigned long long* hh = nullptr) {
-    const V3 B = field_b<L, H, M>(F, y.x, y.y, y.z, hh);
+    const V3 B = field_b<L, H, M, P2>(F, y.x, y.y, y.z, hh);
     Y6 k;
     k.x = y.ux; k.y = y.uy; k.z = y.uz;
     k.ux = kappa * __fma_rn(y.uy, B.z, -(y.uz * B.y));
@@ -209,26 +212,26 @@ __device__ __forceinline__ Y6 deriv(const FieldDev& F, double kappa, const Y6& y
     } while (0)
 
 // One Cash-Karp attempt of size h from y with k1 = f(y).
-template <int L, bool H = false, bool M = false>
+template <int L, bool H = false, bool M = false, bool P2 = false>
 __device__ __forceinline__ void ck_attempt(const FieldDev& F, double kappa, const Y6& y,
                                            const Y6& k1, double h, Y6& y5, Y6& err,
                                            unsigned long long* hh = nullptr) {
     Y6 t;
 #define S2(c) (A21 * k1.c)
     CRP_STAGE(t, S2);
-    const Y6 k2 = deriv<L, H, M>(F, kappa, t, hh);
+    const Y6 k2 = deriv<L, H, M, P2>(F, kappa, t, hh);
 #define S3(c) __fma_rn(A32, k2.c, A31 * k1.c)
     CRP_STAGE(t, S3);
-    const Y6 k3 = deriv<L, H, M>(F, kappa, t, hh);
+    const Y6 k3 = deriv<L, H, M, P2>(F, kappa, t, hh);
 #define S4(c) __fma_rn(A43, k3.c, __fma_rn(A42, k2.c, A41 * k1.c))
     CRP_STAGE(t, S4);
-    const Y6 k4 = deriv<L, H, M>(F, kappa, t, hh);
+    const Y6 k4 = deriv<L, H, M, P2>(F, kappa, t, hh);
 #define S5(c) __fma_rn(A54, k4.c, __fma_rn(A53, k3.c, __fma_rn(A52, k2.c, A51 * k1.c)))
     CRP_STAGE(t, S5);
-    const Y6 k5 = deriv<L, H, M>(F, kappa, t, hh);
+    const Y6 k5 = deriv<L, H, M, P2>(F, kappa, t, hh);
 #define S6(c) __fma_rn(A65, k5.c, __fma_rn(A64, k4.c, __fma_rn(A63, k3.c, __fma_rn(A62, k2.c, A61 * k1.c))))
     CRP_STAGE(t, S6);
-    const Y6 k6 = deriv<L, H, M>(F, kappa, t, hh);
+    const Y6 k6 = deriv<L, H, M, P2>(F, kappa, t, hh);
 #define SB(c) __fma_rn(B6, k6.c, __fma_rn(B4, k4.c, __fma_rn(B3, k3.c, B1 * k1.c)))
     CRP_STAGE(y5, SB);
 #define SE(c) (h * __fma_rn(E6, k6.c, __fma_rn(E5, k5.c, __fma_rn(E4, k4.c, __fma_rn(E3, k3.c, E1 * k1.c)))))

@@ -123,10 +123,12 @@ int launch_lens_bin(const SimState& S, const Counters* C, int nside, int n_mat, 
                     double* x, int grid, void* stream);
 
 // `mod`: 1 for simulations whose fields carry a modulation grid.
-int launch_propagate_fp64(const PropArgs& a, int layout, int mod, int grid, int block, void* stream);
-int propagate_fp64_occupancy(int layout, int mod, int block, int* blocks_per_sm);
-int launch_propagate_mixed(const PropArgs& a, int layout, int mod, int grid, int block, void* stream);
-int propagate_mixed_occupancy(int layout, int mod, int block, int* blocks_per_sm);
+// p2: every vector grid of the launch has power-of-two sizes (the kernels then wrap cell
+// indices with a mask; with p2 = 0 they take the general wrap, valid for any size).
+int launch_propagate_fp64(const PropArgs& a, int layout, int mod, int p2, int grid, int block, void* stream);
+int propagate_fp64_occupancy(int layout, int mod, int p2, int block, int* blocks_per_sm);
+int launch_propagate_mixed(const PropArgs& a, int layout, int mod, int p2, int grid, int block, void* stream);
+int propagate_mixed_occupancy(int layout, int mod, int p2, int block, int* blocks_per_sm);
 
 // Diagnostics: every kernel counts its runs in a device counter of its own translation unit
 // (one atomic per launch, by the first thread of the first block); kernel_runs_*() read them.

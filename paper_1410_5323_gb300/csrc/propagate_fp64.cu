@@ -42,7 +42,7 @@ using namespace fp64;
 #define CRP_FP64_BOUNDS __launch_bounds__(256)
 #endif
 
-template <int L, bool M>
+template <int L, bool M, bool P2>
 __global__ void CRP_FP64_BOUNDS k_propagate_fp64(const PropArgs a) {
     CRP_COUNT_RUN();
     const int lane = threadIdx.x & 31;
@@ -122,14 +122,14 @@ __global__ void CRP_FP64_BOUNDS k_propagate_fp64(const PropArgs a) {
                 if (dbits(h_dist) < dbits(h)) h = h_dist;   // h_dist is never -0
                 h_first = h;
                 kappa = (double)Z * kC / E;   // E and Z are constant within a step
-                k1 = deriv<L, false, M>(F, kappa, y);   // rejected attempts reuse k1
+                k1 = deriv<L, false, M, P2>(F, kappa, y);   // rejected attempts reuse k1
                 rejected = 0;
                 att_step = 0;
                 new_step = false;
             }
             // ---- propagation: one Cash-Karp attempt ----
             Y6 y5, err;
-            ck_attempt<L, false, M>(F, kappa, y, k1, h, y5, err);
+            ck_attempt<L, false, M, P2>(F, kappa, y, k1, h, y5, err);
             att_step += 1;
             double sx, su;
             error_sums(err, sx, su);
@@ -246,33 +246,38 @@ __global__ void CRP_FP64_BOUNDS k_propagate_fp64(const PropArgs a) {
 
 }  // namespace
 
-// Kernel for (layout, modulated): the FP64 form reads FP64 or FP32 vector grids; a
-// modulated field is read through its FP64 copy only.
-template <typename Fn>
-int with_fp64_kernel(int layout, int mod, Fn&& fn) {
+// Kernel for (layout, modulated, power-of-two vector grids): the FP64 form reads FP64 or
+// FP32 vector grids; a modulated field is read through its FP64 copy only.
+template <bool P2, typename Fn>
+int with_fp64_kernel_p2(int layout, int mod, Fn&& fn) {
     if (mod) {
         if (layout != LAYOUT_F64X4) return (int)cudaErrorInvalidValue;
-        return fn(k_propagate_fp64<LAYOUT_F64X4, true>);
+        return fn(k_propagate_fp64<LAYOUT_F64X4, true, P2>);
     }
     switch (layout) {
-    case LAYOUT_F32X4: return fn(k_propagate_fp64<LAYOUT_F32X4, false>);
-    case LAYOUT_F64X4: return fn(k_propagate_fp64<LAYOUT_F64X4, false>);
-    case LAYOUT_BF16X4: return fn(k_propagate_fp64<LAYOUT_BF16X4, false>);
-    case LAYOUT_F16X4: return fn(k_propagate_fp64<LAYOUT_F16X4, false>);
+    case LAYOUT_F32X4: return fn(k_propagate_fp64<LAYOUT_F32X4, false, P2>);
+    case LAYOUT_F64X4: return fn(k_propagate_fp64<LAYOUT_F64X4, false, P2>);
+    case LAYOUT_BF16X4: return fn(k_propagate_fp64<LAYOUT_BF16X4, false, P2>);
+    case LAYOUT_F16X4: return fn(k_propagate_fp64<LAYOUT_F16X4, false, P2>);
     default: return (int)cudaErrorInvalidValue;
     }
 }
 
-int launch_propagate_fp64(const PropArgs& a, int layout, int mod, int grid, int block, void* stream) {
+template <typename Fn>
+int with_fp64_kernel(int layout, int mod, int p2, Fn&& fn) {
+    return p2 ? with_fp64_kernel_p2<true>(layout, mod, fn) : with_fp64_kernel_p2<false>(layout, mod, fn);
+}
+
+int launch_propagate_fp64(const PropArgs& a, int layout, int mod, int p2, int grid, int block, void* stream) {
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    return with_fp64_kernel(layout, mod, [&](void (*k)(const PropArgs)) {
+    return with_fp64_kernel(layout, mod, p2, [&](void (*k)(const PropArgs)) {
         k<<<grid, block, 0, st>>>(a);
         return (int)cudaGetLastError();
     });
 }
 
-int propagate_fp64_occupancy(int layout, int mod, int block, int* blocks_per_sm) {
-    return with_fp64_kernel(layout, mod, [&](void (*k)(const PropArgs)) {
+int propagate_fp64_occupancy(int layout, int mod, int p2, int block, int* blocks_per_sm) {
+    return with_fp64_kernel(layout, mod, p2, [&](void (*k)(const PropArgs)) {
         return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, block, 0);
     });
 }

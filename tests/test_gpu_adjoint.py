@@ -87,6 +87,37 @@ def test_reverse_pass_matches_oracle_reverse_pass(oracle_lib):
     assert np.array_equal(gb == 0, go == 0)
 
 
+def test_reverse_pass_on_a_grid_of_other_sizes(oracle_lib):
+    """A non-cubic grid whose sizes are not powers of two (the general index wrap in the
+    forward record and the stage records): the same bit-for-bit agreement per particle."""
+    import torch
+
+    import paper_1410_5323_gb300 as crp
+    from paper_1410_5323_gb300.adjoint import Adjoint, perturbed_targets
+
+    g = (np.random.default_rng(21).standard_normal((12, 10, 14, 3)) * 1e-13).astype(np.float32)
+    _, x0, p0, Z = _case(40, 16, 10 ** 19.5, seed=6)
+    n_steps = 120
+    field = crp.Field(torch.from_numpy(g).cuda(), 0.25 * I.MPC)
+    adj = Adjoint(field, len(Z), n_steps, 16)
+    _, uT = adj.forward(torch.from_numpy(x0), torch.from_numpy(p0), torch.from_numpy(Z), 1e-4, I.KPC, I.MPC)
+    t = perturbed_targets(uT).cpu().numpy()
+    lam = _lam(uT.cpu().numpy(), t)
+    gb, pb, xb = adj.backward(torch.from_numpy(lam), g.shape)
+    gb, xb = gb.cpu().numpy(), xb.cpu().numpy()
+    h = adj.steps().cpu().numpy()
+    E, u, kap = _init(p0, Z)
+    of = O.OracleField(g, 0.25 * I.MPC)
+    go = np.zeros(g.shape)
+    for i in range(len(Z)):
+        y0 = np.concatenate([x0[i], u[i]])
+        ho, _ = O.record_steps(of, kap[i], y0, 1e-4, I.KPC, I.MPC, n_steps)
+        assert np.array_equal(h[:, i], ho), i
+        yb, _ = O.adjoint(of, kap[i], y0, h[:, i], np.concatenate([np.zeros(3), lam[i]]), go)
+        assert np.array_equal(xb[i], yb[:3]), i
+    assert np.allclose(gb, go, rtol=1e-10, atol=1e-12 * np.abs(go).max())
+
+
 def test_autograd_function_gives_the_adjoint_gradients(oracle_lib):
     import torch
 

@@ -141,9 +141,14 @@ def test_grid_storage_types(oracle_lib, dt):
     assert_bit_identical(sim.state(), st.snapshot())
 
 
-def test_several_grids_by_grid_id(oracle_lib):
+@pytest.mark.parametrize("mixed_sizes", [False, True])
+def test_several_grids_by_grid_id(oracle_lib, mixed_sizes):
+    """All power-of-two grids take the kernels that wrap indices with a mask; one grid of
+    other sizes among them switches the launch to the general wrap for all."""
     grids = [I.kolmogorov_grid(16, 0.25 * I.MPC, 2, 8, b, s).astype(np.float32)
              for s, b in ((1, 1e-13), (2, 5e-13), (3, 2e-14))]
+    if mixed_sizes:
+        grids[1] = (np.random.default_rng(11).standard_normal((12, 16, 10, 3)) * 3e-13).astype(np.float32)
     p = I.make_particles(300, 10, energy=("loguniform", 1e17, 1e20))
     p.grid_id[:] = np.arange(300) % 3
     args = (grids, p, None, 1e-4, I.KPC, I.MPC, 20 * I.MPC)
