@@ -73,8 +73,8 @@ MIXED_MOD_FP32_FLOP_PER_ATTEMPT = 228
 # DRAM bytes (read + write) per attempted step of the propagate kernels, measured by ncu at
 # reduced batch (both launches of one call; the summaries under profiles/ name the command);
 # traffic of a call = this x its attempts. Keyed by (workload, form).
-DRAM_BYTES_PER_ATTEMPT = {("fp64_256cube_1M_nuclei", "fp64"): 138.7,
-                          ("fp64_256cube_1M_nuclei", "mixed"): 99.4,      # cell-major grid copy
+DRAM_BYTES_PER_ATTEMPT = {("fp64_256cube_1M_nuclei", "fp64"): 139.1,
+                          ("fp64_256cube_1M_nuclei", "mixed"): 99.3,      # cell-major grid copy
                           ("modulated_440cube_300kpc_x_256cube_50kpc_1M_nuclei", "fp64"): 373.2}
 
 
