@@ -75,7 +75,7 @@ MIXED_MOD_FP32_FLOP_PER_ATTEMPT = 228
 # traffic of a call = this x its attempts. Keyed by (workload, form).
 DRAM_BYTES_PER_ATTEMPT = {("fp64_256cube_1M_nuclei", "fp64"): 139.1,
                           ("fp64_256cube_1M_nuclei", "mixed"): 99.3,      # cell-major grid copy
-                          ("modulated_440cube_300kpc_x_256cube_50kpc_1M_nuclei", "fp64"): 373.2}
+                          ("modulated_440cube_300kpc_x_256cube_50kpc_1M_nuclei", "fp64"): 372.8}
 
 
 def parse():
