@@ -737,9 +737,19 @@ int adj_backward(const FieldDev& F, const double* kappa, const double* h, const 
         // stream; the reverse sweep takes each chunk once its event has fired. The records
         // kernel (FP64-throughput-bound, many threads) then runs beside the reverse sweep
         // (one warp per ten chains, latency-bound). Without an auxiliary stream: one chunk.
+        // A chunk of C segments is n * C threads; C is the smallest that still gives every SM
+        // about one 128-thread block (fewer blocks leave SMs idle for the chunk's whole run).
         const cudaStream_t st = (cudaStream_t)stream, aux = (cudaStream_t)aux_stream;
         const int S = (n_steps + K - 1) / K;
-        int J = (aux && n_events >= 2) ? std::min(n_events - 1, S) : 1;
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+            cudaGetLastError();
+            sms = 1;
+        }
+        const long long c_min = std::max(1ll, (long long)((0.8 * sms * 128.0 + (double)n - 1.0) / (double)n));
+        int J = (aux && n_events >= 2) ? (int)std::min<long long>(n_events - 1, S / c_min) : 1;
+        J = std::max(1, J);
         const int C = (S + J - 1) / J;
         J = (S + C - 1) / C;
         double* rec_d = stages;
