@@ -294,10 +294,14 @@ int crp_observe(crp_sim* sim, const crp_observer* out, int64_t first, int64_t ca
  * checkpoint. Initial momenta p0 are in eV/c: E = |p0|, u0 = p0/E, kappa = Z c / E.
  * All array arguments are device pointers; [n][3] arrays are row-major.
  * Memory owned by the handle: 8 B x n x (n_steps + 6 (n_steps / checkpoint_every + 1) +
- * 6 (checkpoint_every + 1) + 20), plus 8 B x 36 x n x n_steps for the stage states of every
- * step when that fits in half of the device's free memory at creation (then the backward pass
- * recomputes all checkpoint segments in parallel; otherwise one segment at a time; the
- * results are the same). */
+ * 6 (checkpoint_every + 1) + 20), plus 1296 B x n x n_steps for the stage records of every
+ * step (direction, field, Jacobian, corner weights and corner nodes of its six stages) when
+ * that fits in half of the device's free memory at creation and the grid has fewer than 2^31
+ * nodes. With the records, the backward pass forms them for all checkpoint segments in
+ * parallel, in chunks on a CUDA stream the handle owns (ordered after the caller's stream,
+ * and the caller's stream after it, with events the handle owns), while the reverse sweep
+ * consumes the chunks already formed; without them it recomputes one segment at a time
+ * inside the reverse sweep. The results are the same either way. */
 typedef struct crp_adjoint crp_adjoint;
 int crp_adjoint_create(const crp_field* field, int64_t n, int32_t n_steps,
                        int32_t checkpoint_every, crp_adjoint** out);
